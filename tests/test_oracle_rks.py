@@ -1,0 +1,346 @@
+"""Pins of the FP64 rKS oracle against the paper's invariants and closed forms.
+
+Every pin checks the oracle against something other than itself: the
+definitions and theorems of the paper (sketch-orthonormality Def. 2.3, the
+Krylov relation Eq. 2.4 / 2.16, the Rayleigh quotient Thm 2.4, the residual
+bounds of Sec. 4.1, the locking bound Eq. 4.21), brute force (MGS Arnoldi,
+dense eigenvalues), and closed-form spectra.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import rks as R
+from oracle.sketch import omega_matrix
+from paper_2508_05400_gb300 import inputs as I
+
+
+def _decomposition_errors(st):
+    """Errors of the full decomposition A U = U T + u b^T and of its sketch."""
+    T, b, U = R.full_T(st)
+    u = st.Ua[:, st.ja]
+    Sall = np.hstack([st.Sq, st.Sa])
+    Uall = np.hstack([st.Uq, st.Ua])
+    orth = np.linalg.norm(Sall.T @ Sall - np.eye(Sall.shape[1]))
+    sketch = np.linalg.norm(st.Omega @ Uall - Sall) / np.linalg.norm(Sall)
+    AU = st.A @ U
+    rel = np.linalg.norm(AU - U @ T - np.outer(u, b)) / np.linalg.norm(AU)
+    return orth, sketch, rel
+
+
+def _expand_from_scratch(A, m, d, zeta=8, seed=0, Omega=None):
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    Om = omega_matrix(n, d, zeta, seed) if Omega is None else Omega
+    st = R.start(A, Om, I.start_vector(n, 1))
+    R.extend(st, m)
+    return st
+
+
+def test_expansion_invariants():
+    # Alg. 2 from k = 0 yields a randomized Arnoldi factorization (Def. 2.1):
+    # (Omega U)^T (Omega U) = I, A U = U B + u b^T, B upper Hessenberg with a
+    # positive subdiagonal, and B = (Omega U)^T Omega A U (Thm 2.4, Eq. 2.9).
+    A = I.convdiff_2d(20, 20, 1.0, 20.0, 10.0).to_scipy()
+    st = _expand_from_scratch(A, 30, 64)
+    orth, sketch, rel = _decomposition_errors(st)
+    assert orth < 1e-12 and sketch < 1e-14 and rel < 1e-13
+    B = st.Ba[:30, :]
+    assert np.all(np.tril(B, -2) == 0)
+    assert np.all(np.diag(B, -1) > 0)
+    S = st.Sa[:, :30]
+    rq = S.T @ (st.Omega @ (A @ st.Ua[:, :30]))
+    assert np.linalg.norm(rq - B) < 1e-12 * np.linalg.norm(B)
+
+
+def test_identity_sketch_reduces_to_arnoldi():
+    # With Omega = I, sketch-orthonormal means orthonormal and Alg. 2 is the
+    # Arnoldi process: B equals the Hessenberg matrix of a brute-force
+    # modified Gram-Schmidt Arnoldi (unique for a positive subdiagonal).
+    n, m = 60, 12
+    A = I.paper_tridiag(n, "logarithmic", 4).to_scipy().toarray() + \
+        0.05 * I.normal(9, n * n).reshape(n, n)
+    st = _expand_from_scratch(A, m, n, Omega=sp.identity(n, format="csr"))
+    V = np.zeros((n, m + 1)); H = np.zeros((m + 1, m))
+    v = I.start_vector(n, 1)
+    V[:, 0] = v / np.linalg.norm(v)
+    for j in range(m):
+        w = A @ V[:, j]
+        for i in range(j + 1):
+            H[i, j] = V[:, i] @ w
+            w = w - H[i, j] * V[:, i]
+        H[j + 1, j] = np.linalg.norm(w)
+        V[:, j + 1] = w / H[j + 1, j]
+    assert np.allclose(st.Ba, H, atol=1e-12)
+    assert np.allclose(st.Ua, V, atol=1e-12)
+
+
+@pytest.mark.parametrize("which", R.WHICH)
+def test_ordered_schur_against_numpy(which):
+    rng = np.random.default_rng(5)
+    for m in (10, 33, 80):
+        B = rng.standard_normal((m, m))
+        T, Q = R.ordered_schur(B, which, nsort=8)
+        assert np.linalg.norm(Q.T @ Q - np.eye(m)) < 1e-13 * m
+        assert np.linalg.norm(Q @ T @ Q.T - B) < 1e-13 * m * np.linalg.norm(B)
+        assert np.all(np.tril(T, -2) == 0)
+        blocks = R.schur_blocks(T)
+        for s, z in blocks:
+            if z == 2:   # standardised 2x2 block: equal diagonal, complex pair
+                assert abs(T[s, s] - T[s + 1, s + 1]) < 1e-12 * np.linalg.norm(B)
+                assert T[s, s + 1] * T[s + 1, s] < 0
+        lam = np.array([R.block_eigenvalue(T, s, z) for s, z in blocks])
+        ref = np.linalg.eigvals(B)
+        ref = ref[ref.imag >= 0]
+        ref_keys = np.sort(R.key(ref, which))
+        keys = R.key(lam, which)
+        assert np.allclose(keys[:8], ref_keys[:8], atol=1e-10 * np.abs(ref).max())
+        assert np.all(np.diff(keys[:8]) >= -1e-10 * np.abs(ref).max())
+
+
+def test_contraction_keeps_decomposition():
+    # Truncation (Alg. 1; Eqs. 3.5-3.6): U Q(:,1:k), S Q(:,1:k), b^T Q(:,1:k),
+    # u and s unchanged is again an rKS decomposition with S = Omega U.
+    A = I.convdiff_2d(20, 20, 1.0, 20.0, 10.0).to_scipy()
+    st = _expand_from_scratch(A, 30, 64)
+    Ta, b, Q = R.contract(st, 8, "LR")
+    assert st.ja in (8, 9)
+    orth, sketch, rel = _decomposition_errors(st)
+    assert orth < 1e-12 and sketch < 1e-13 and rel < 1e-12
+    R.extend(st, 30)
+    orth, sketch, rel = _decomposition_errors(st)
+    assert orth < 1e-12 and sketch < 1e-13 and rel < 1e-12
+
+
+def test_toeplitz_closed_form_small():
+    # Non-symmetric Toeplitz (2, -1.3, -0.7) at n = 30, where the eigenvalue
+    # condition numbers stay small enough for 1e-10 (LM, k = 4).
+    n = 30
+    A = I.toeplitz_tridiag(n).to_scipy()
+    res = R.rks(A, 4, 12, 40, I.start_vector(n, 1), zeta=4, seed=0, which="LM", tol=1e-14)
+    ex = I.toeplitz_eigenvalues(n, -1.3, 2.0, -0.7)
+    ex = ex[np.argsort(-np.abs(ex))][:4]
+    assert res.converged
+    assert np.max(np.abs(res.eigvals - ex) / np.abs(ex)) < 1e-10
+    assert res.resid.max() < 1e-11
+
+
+def test_symmetric_toeplitz_closed_form():
+    n = 100
+    s = np.sqrt(0.91)
+    A = I.toeplitz_tridiag(n, -s, 2.0, -s).to_scipy()
+    res = R.rks(A, 4, 12, 40, I.start_vector(n, 1), zeta=4, seed=0, which="LM", tol=1e-12)
+    ex = I.toeplitz_eigenvalues(n, -s, 2.0, -s)
+    ex = ex[np.argsort(-np.abs(ex))][:4]
+    assert res.converged
+    assert np.max(np.abs(res.eigvals - ex) / np.abs(ex)) < 1e-10
+
+
+@pytest.mark.parametrize("lock", [False, True])
+def test_convdiff_kronecker_closed_form(lock):
+    # The 2D upwind operator with constant nu is a Kronecker sum of 1D Toeplitz
+    # operators; LR eigenvalues from rKS with deflation match it.
+    N = 30
+    A = I.convdiff_2d(N, N, 1.0, 20.0, 10.0).to_scipy()
+    ex = np.sort(I.convdiff_2d_eigenvalues(N, N, 1.0, 20.0, 10.0))[::-1][:6]
+    res = R.rks(A, 6, 18, 64, I.start_vector(N * N, 1), zeta=8, seed=0, which="LR",
+                tol=1e-13, lock_vectors=lock)
+    assert res.converged
+    if lock:
+        assert res.nlocked > 0
+    assert np.max(np.abs(res.eigvals - ex) / np.abs(ex)) < 1e-10
+    assert res.resid.max() < 1e-13
+
+
+def _planted_spectrum_matrix(n, seed):
+    """A = X D X^{-1} with known eigenvalues (including complex pairs), X well conditioned."""
+    rng = np.random.default_rng(seed)
+    lam = np.concatenate([np.linspace(1.0, 3.0, n - 6), [5.0, -4.5, 0.02]])
+    D = np.diag(lam)
+    Blk = np.zeros((n, n)); Blk[: n - 3, : n - 3] = D[: n - 3, : n - 3]
+    # three complex pairs a +- ib as 2x2 blocks replace the last three singles
+    pairs = [(4.0, 1.0), (-0.5, 3.5), (0.01, 0.05)]
+    lam_all = list(np.linspace(1.0, 3.0, n - 6))
+    Blk = np.zeros((n, n))
+    Blk[: n - 6, : n - 6] = np.diag(lam_all)
+    for t, (a, b) in enumerate(pairs):
+        i = n - 6 + 2 * t
+        Blk[i:i + 2, i:i + 2] = [[a, b], [-b, a]]
+        lam_all += [a + 1j * b, a - 1j * b]
+    Qx, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    X = Qx @ (np.eye(n) + 0.1 * np.triu(rng.standard_normal((n, n)), 1) / np.sqrt(n))
+    A = X @ Blk @ np.linalg.inv(X)
+    return A, np.array(lam_all), np.linalg.cond(X)
+
+
+@pytest.mark.parametrize("which,k", [("LM", 4), ("SM", 3), ("LR", 4), ("SR", 2)])
+def test_bruteforce_planted_spectrum(which, k):
+    n = 150
+    A, lam, condX = _planted_spectrum_matrix(n, 11)
+    want = lam[np.argsort(R.key(lam, which), kind="stable")][:k]
+    res = R.rks(A, k, 16, 64, I.start_vector(n, 1), zeta=8, seed=0, which=which, tol=1e-13)
+    assert res.converged
+    # each computed value matches a wanted one within cond(X) * 1e-12
+    for lam_c in res.eigvals:
+        assert np.min(np.abs(want - lam_c)) < condX * 1e-12 * max(1.0, abs(lam_c))
+    # and the dense brute force agrees with the planted spectrum
+    dense = np.linalg.eigvals(A)
+    assert all(np.min(np.abs(dense - w)) < 1e-10 for w in want)
+
+
+def test_residual_estimate_band():
+    # Sec. 4.1 remark (exact bound): with eps the distortion of Omega on
+    # span[U u], sqrt((1-eps)/(1+eps)) |b^T y| <= ||A x - l x|| / ||x||
+    # <= sqrt((1+eps)/(1-eps)) |b^T y| for x = U y, ||y|| = 1.
+    N = 20
+    A = I.convdiff_2d(N, N, 1.0, 20.0, 10.0).to_scipy()
+    n = N * N
+    Om = omega_matrix(n, 256, 8, 0)      # eps < 1 needs d well above m
+    st = R.start(sp.csr_matrix(A), Om, I.start_vector(n, 1))
+    R.extend(st, 24)
+    for _ in range(3):
+        R.contract(st, 6, "LR")
+        T, b, U = R.full_T(st)
+        u = st.Ua[:, st.ja]
+        Qb, _ = np.linalg.qr(np.hstack([U, u[:, None]]))
+        sv = np.linalg.svd(Om @ Qb, compute_uv=False)
+        eps = max(sv.max() ** 2 - 1, 1 - sv.min() ** 2)
+        assert eps < 1
+        lam, Y, est = R.ritz(T, b, "LR")
+        X = U @ Y
+        true = np.linalg.norm(A @ X - X * lam, axis=0) / np.linalg.norm(X, axis=0)
+        bty = np.abs(b @ Y)
+        lo = np.sqrt((1 - eps) / (1 + eps)) * bty
+        hi = np.sqrt((1 + eps) / (1 - eps)) * bty
+        assert np.all(true >= lo * (1 - 1e-9)) and np.all(true <= hi * (1 + 1e-9))
+        R.extend(st, 24)
+
+
+def test_locking_bound_and_deflated_operator():
+    # Eq. 4.21: a locked Ritz pair (l, x = U_q y), ||y|| = 1, satisfies
+    # ||A x - l x|| <= sqrt(q)/sqrt(1-eps) * max|b_locked|, and Thm 4.3:
+    # (I - U_q (Omega U_q)^T Omega) A U_q = U_q T_qq - U_q T_qq + O(b) ~ 0.
+    N = 30
+    A = sp.csr_matrix(I.convdiff_2d(N, N, 1.0, 20.0, 10.0).to_scipy())
+    n = N * N
+    Om = omega_matrix(n, 64, 8, 0)
+    st = R.start(A, Om, I.start_vector(n, 1))
+    R.extend(st, 24)
+    locked_total = 0
+    for _ in range(60):
+        R.contract(st, 6, "LR")
+        ja = st.ja
+        b_before = st.Ba[ja, :].copy()
+        u = st.Ua[:, ja].copy()
+        q0 = st.q
+        r = R.lock(st, 6, 1e-11)
+        if r:
+            locked_total += r
+            q = st.q
+            bq = np.concatenate([np.zeros(q0), b_before[:r]])   # lock-time b of U_q
+            Qb, _ = np.linalg.qr(np.hstack([st.Uq, u[:, None]]))
+            sv = np.linalg.svd(Om @ Qb, compute_uv=False)
+            eps = max(sv.max() ** 2 - 1, 1 - sv.min() ** 2)
+            lam, W = np.linalg.eig(st.Tqq)
+            W = W / np.linalg.norm(W, axis=0)
+            X = st.Uq @ W
+            res = np.linalg.norm(A @ X - X * lam, axis=0)
+            bound = np.sqrt(q) / np.sqrt(1 - eps) * max(np.abs(bq).max(), 1e-300)
+            # earlier locked vectors carry their own (smaller or equal) b
+            assert np.all(res[-r:] <= bound * 1.0001 + 1e-10 * np.abs(lam[-r:]))
+            P = st.Uq @ (st.Sq.T @ (Om @ (A @ st.Uq)))
+            Aq_Uq = A @ st.Uq - P
+            assert np.linalg.norm(Aq_Uq) < 1e-8 * np.linalg.norm(A @ st.Uq)
+        T, b, U = R.full_T(st)
+        lam, Y, est = R.ritz(T, b, "LR")
+        if st.q >= 6 or np.all(est <= 1e-11):
+            break
+        R.extend(st, 24 - st.q)
+    assert locked_total > 0
+    orth, sketch, rel = _decomposition_errors(st)
+    assert orth < 1e-11 and rel < 1e-11
+
+
+def test_whitening_restores_orthonormal_sketch():
+    # Sec. 3.3: S = QR, U <- U R^{-1}, T <- R T R^{-1}, b^T <- b^T R^{-1} keeps
+    # the Krylov relation and the spectrum, and makes Omega U orthonormal.
+    A = I.convdiff_2d(20, 20, 1.0, 20.0, 10.0).to_scipy()
+    st = _expand_from_scratch(A, 30, 64)
+    R.contract(st, 8, "LR")
+    ja = st.ja
+    G = np.eye(ja) + 0.05 * np.triu(np.ones((ja, ja)), 1)   # spoil orthonormality
+    st.Ua[:, :ja] = st.Ua[:, :ja] @ G
+    st.Sa[:, :ja] = st.Sa[:, :ja] @ G
+    Ta = st.Ba[:ja, :]
+    st.Ba = np.vstack([np.linalg.solve(G, Ta @ G), st.Ba[ja, :] @ G])
+    ev0 = np.sort_complex(np.linalg.eigvals(st.Ba[:ja, :]))
+    R.whiten(st)
+    S = st.Sa[:, :ja]
+    assert np.linalg.norm(S.T @ S - np.eye(ja)) < 1e-13
+    _, sketch, rel = _decomposition_errors(st)
+    assert sketch < 1e-13 and rel < 1e-12
+    assert np.allclose(np.sort_complex(np.linalg.eigvals(st.Ba[:ja, :])), ev0, rtol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Planted mistakes: each pin above must catch a plausible bug in the oracle.
+# ---------------------------------------------------------------------------
+
+def _extend_with(monkeypatch, mutation):
+    """Run a mutated Alg. 2 (mistake planted in the oracle, on the CPU)."""
+    orig_lstsq = np.linalg.lstsq
+
+    def run():
+        A = sp.csr_matrix(I.convdiff_2d(20, 20, 1.0, 20.0, 10.0).to_scipy())
+        st = _expand_from_scratch(A, 20, 64)
+        return st
+    if mutation == "sign":
+        def bad(a, b, rcond=None):
+            x = orig_lstsq(a, b, rcond=rcond)
+            return (-x[0],) + tuple(x[1:])
+        monkeypatch.setattr(np.linalg, "lstsq", bad)
+    elif mutation == "dropped_term":
+        def bad(a, b, rcond=None):
+            x = orig_lstsq(a, b, rcond=rcond)
+            y = x[0].copy()
+            if y.size > 1:
+                y[0] = 0.0
+            return (y,) + tuple(x[1:])
+        monkeypatch.setattr(np.linalg, "lstsq", bad)
+    elif mutation == "transposed":
+        def bad(a, b, rcond=None):
+            return orig_lstsq(a[::-1, :], b, rcond=rcond)
+        monkeypatch.setattr(np.linalg, "lstsq", bad)
+    st = run()
+    monkeypatch.undo()
+    return st
+
+
+@pytest.mark.parametrize("mutation", ["sign", "dropped_term", "transposed"])
+def test_planted_mistakes_are_caught(monkeypatch, mutation):
+    st = _extend_with(monkeypatch, mutation)
+    orth, sketch, rel = _decomposition_errors(st)
+    B = st.Ba[:20, :]
+    S = st.Sa[:, :20]
+    rq = S.T @ (st.Omega @ (st.A @ st.Ua[:, :20]))
+    rq_err = np.linalg.norm(rq - B) / np.linalg.norm(B)
+    # the expansion invariant test would fail on at least one of its checks
+    assert orth > 1e-6 or rq_err > 1e-6 or rel > 1e-6
+
+
+def test_planted_missing_coupling_breaks_eigenvalues(monkeypatch):
+    # Dropping T_qa (the coefficients of A u_j on the locked vectors, which the
+    # lock step folds into T_qq) must break the true residuals once vectors
+    # are locked.
+    orig = R.lock
+
+    def lock_without_coupling(st, k, eta_lock):
+        st.Tqa[:] = 0.0
+        return orig(st, k, eta_lock)
+    monkeypatch.setattr(R, "lock", lock_without_coupling)
+    N = 30
+    A = I.convdiff_2d(N, N, 1.0, 20.0, 10.0).to_scipy()
+    res = R.rks(A, 6, 18, 64, I.start_vector(N * N, 1), zeta=8, seed=0, which="LR",
+                tol=1e-13, maxit=80)
+    assert res.nlocked > 1
+    assert res.resid.max() > 1e-8
