@@ -1,0 +1,214 @@
+/*
+ * rks.h - C ABI of librks: randomized Krylov-Schur (rKS) with deflation on a
+ * GB300 GPU (sm_103a).
+ *
+ * The solver computes k eigenpairs (lambda, x) of a sparse non-symmetric
+ * A in R^{n x n} (CSR), A x = lambda x (Eq. 2.1), following Algorithm 1 (rKS)
+ * and Algorithm 2 (extension by randomized Arnoldi) of de Damas & Grigori,
+ * "Randomized Krylov-Schur eigensolver with deflation", with the locking of
+ * converged Schur vectors of Sec. 4.2-4.4 and the residual estimates of
+ * Sec. 4.1.  The Krylov dimension is m = k + p; Omega in R^{d x n} is a
+ * sparse-sign embedding (zeta nonzeros +-1/sqrt(zeta) per column, rows and
+ * signs from a SplitMix64 hash of (seed, column), see rks_sketch_pairs).
+ *
+ * Conventions for every entry point:
+ *  - return value: RKS_OK (0) or a negative rks_status; no exceptions cross
+ *    the ABI; rks_strerror() gives a static message;
+ *  - dense arrays are column-major; "n x k" means n rows;
+ *  - array arguments are host pointers unless opts.mem_device = 1 was given
+ *    to rks_create, in which case the arrays passed to rks_create,
+ *    rks_get_schur and rks_get_eigpairs (not rks_info) are device pointers
+ *    of the current CUDA device;
+ *  - the caller owns every array it passes; rks_create copies A (and u1)
+ *    into memory owned by the context; rks_destroy frees it all;
+ *  - a context is used by one host thread at a time; its kernels run on
+ *    opts.stream (a cudaStream_t), or on a stream the context creates.
+ */
+#ifndef RKS_H
+#define RKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rks_ctx rks_ctx;
+
+typedef enum {
+  RKS_OK = 0,
+  RKS_EINVAL = -1,      /* invalid argument (sizes, CSR structure, d < 2*zeta, ...) */
+  RKS_ENOMEM = -2,      /* device or host allocation failed */
+  RKS_ECUDA = -3,       /* a CUDA call failed */
+  RKS_ENOCONV = -4,     /* maxit restarts without convergence: results are the
+                           current (partial) decomposition and are valid */
+  RKS_EBREAKDOWN = -5,  /* beta_{j+1} = 0: an invariant subspace was reached
+                           before k pairs converged (Sec. 2.1) */
+  RKS_ENAN = -6,        /* a non-finite value appeared (e.g. NaN in A) */
+  RKS_ESTATE = -7,      /* call out of order (e.g. rks_get_* before rks_solve) */
+  RKS_EDENSE = -8       /* the small dense Schur iteration failed */
+} rks_status;
+
+/* Wanted part of the spectrum (Sec. 5: largest / smallest modulus; real part). */
+typedef enum { RKS_LM = 0, RKS_SM = 1, RKS_LR = 2, RKS_SR = 3 } rks_which;
+
+/* Element type of the CSR values passed to rks_create. */
+typedef enum { RKS_F64 = 0, RKS_F32 = 1 } rks_dtype;
+
+typedef struct {
+  int zeta;            /* nonzeros per column of Omega; default 8 */
+  int maxit;           /* maximum number of restarts; default 1000 */
+  int lock;            /* 1: lock converged Schur vectors (Sec. 4.4); default 1 */
+  int mem_device;      /* 1: array arguments are device pointers; default 0 */
+  void* stream;        /* cudaStream_t for all work; NULL: the context's own */
+  const double* u1;    /* start vector (n), host or device per mem_device;
+                          NULL: N(0,1) entries from SplitMix64(seed + 1) and
+                          Box-Muller, generated on the device */
+  double eta_lock;     /* locking threshold, relative to |lambda|; 0: tol */
+  int max_restarts;    /* stop after this many contractions whatever the
+                          estimates say (fixed-iteration runs, Sec. 5); 0: none;
+                          -1: only the initial expansion of Algorithm 1 */
+  int profile;         /* 1: time every kernel launch with CUDA events on the
+                          context's stream (see rks_get_stats); default 0 */
+} rks_opts;
+
+typedef struct {
+  int nconv;           /* number of pairs whose estimate is <= tol */
+  int nlocked;         /* locked Schur vectors q */
+  int restarts;        /* contractions performed */
+  int64_t nmatvec;     /* products with A */
+  int converged;       /* 1 if all k estimates are <= tol */
+  double max_est;      /* max_i |b^T y_i| / |lambda_i| (Eq. 4.8) */
+  double max_resid;    /* max_i ||A x_i - lambda_i x_i|| / (||A||_1 ||x_i||), FP64 */
+  double t_solve_ms;   /* wall time of rks_solve (CUDA events on the stream) */
+} rks_info;
+
+/* Kernel classes of rks_stats: the steps of one Arnoldi step of Algorithm 2
+ * and of the restart of Algorithm 1. */
+enum {
+  RKS_K_SPMV = 0,      /* w = A u_j fused with z = Omega w */
+  RKS_K_LS = 1,        /* b = S^+ z (CGS2 in the sketch), three small kernels */
+  RKS_K_UPDATE = 2,    /* u~ = w - U b fused with s~ = Omega u~ */
+  RKS_K_FINISH = 3,    /* beta = ||s~||, append to S and B */
+  RKS_K_RESTART = 4,   /* U_k = U Q (Eq. 3.5) */
+  RKS_K_OTHER = 5,     /* start vector, Ritz vectors, residuals */
+  RKS_NK = 6
+};
+
+/* Counters of the last rks_solve.  launches counts every kernel the library
+ * launched.  ms (event time) is filled when opts.profile = 1, else 0.  bytes
+ * and flops are the algorithmic traffic / work of the launches: SpMV
+ * nnz*(P_A + 4) + 4(n+1) + 2 P_V n; update (c + 2) P_V n for c basis
+ * columns; restart (m_a + k_a + 2) P_V n; P = bytes per value. */
+typedef struct {
+  int64_t launches[RKS_NK];
+  double ms[RKS_NK];
+  double bytes[RKS_NK];
+  double flops[RKS_NK];
+  double host_ms;      /* host time in the small dense step (Schur ... locking) */
+} rks_stats;
+
+/* Counters of the last rks_solve (see rks_stats). */
+int rks_get_stats(const rks_ctx* c, rks_stats* out);
+
+/* Fill *o with the defaults above. */
+void rks_opts_default(rks_opts* o);
+
+/* Create a solver for A (n x n, CSR: rowptr[n+1], colind[nnz] (0-based, each
+ * row's columns in [0, n)), vals[nnz] of type vals_dtype).  k wanted pairs,
+ * p extra Krylov directions (m = k + p, 1 <= k, 2 <= p, m + 1 <= n), sketch
+ * size d (d >= m + 1 and d >= 2*zeta), which part of the spectrum, tolerance
+ * tol > 0 on the estimates |b^T y|/|lambda| (Sec. 5.1), and the seed of
+ * Omega.  opts may be NULL (defaults).  Copies A to the device and validates
+ * its structure (rowptr non-decreasing, rowptr[0] = 0, column indices in
+ * range); on error *out is NULL. */
+int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* colind,
+               const void* vals, int vals_dtype, int k, int p, int d, int which,
+               double tol, uint64_t seed, const rks_opts* opts);
+
+/* Run Algorithm 1 to convergence (or maxit / max_restarts).  info may be
+ * NULL.  Returns RKS_OK, RKS_ENOCONV (results valid but not converged),
+ * RKS_EBREAKDOWN, RKS_ENAN or a CUDA error.  May be called again: it
+ * restarts from the start vector. */
+int rks_solve(rks_ctx* c, rks_info* info);
+
+/* The rKS decomposition A U = U T + u b^T of the last solve (Def. 2.9), with
+ * kk = rks_nkept(c) columns (k, or k + 1 when a complex pair straddles the
+ * cut).  T: kk x kk (host, FP64); U: n x kk FP64 (host or device per
+ * mem_device), unit sketch norm columns ||Omega U e_i|| = 1; b: kk (host).
+ * Any pointer may be NULL. */
+int rks_get_schur(rks_ctx* c, double* T, double* U, double* b);
+
+/* Number of columns kk of the decomposition returned by rks_get_schur. */
+int rks_nkept(const rks_ctx* c);
+
+/* Ritz pairs of the last solve, best first (Sec. 4.1): lam_re, lam_im (kk,
+ * host); X (n x kk FP64, host or device per mem_device) in LAPACK dgeev real
+ * packing: a conjugate pair occupies columns (j, j+1) = (Re x, Im x) of the
+ * eigenvector of the member with Im > 0; resid (kk, host) =
+ * ||A x - lambda x|| / (||A||_1 ||x||) computed in FP64 on the device.  Any
+ * pointer may be NULL. */
+int rks_get_eigpairs(rks_ctx* c, double* lam_re, double* lam_im, double* X, double* resid);
+
+/* Residual estimates |b^T y_i| / |lambda_i| (Eq. 4.8) of the last solve, in
+ * the order of rks_get_eigpairs (kk values, host). */
+int rks_get_estimates(rks_ctx* c, double* est);
+
+/* The sketch-orthonormal Krylov decomposition as it stands (for tests of
+ * Algorithm 2): ncols_out = number of basis columns j + 1 (locked + active
+ * + the last vector u).  U: n x (j+1) FP64 with unit sketch norm columns,
+ * S = Omega U: d x (j+1), H: (j+1) x j with column i holding the projection
+ * coefficients of A u_i on u_0..u_i (rows 0..i) and beta_{i+1} (row i+1),
+ * for the columns produced by the last expansion (other entries 0).
+ * Array pointers may be NULL; sizes must allow m + 1 columns.  Host
+ * pointers only. */
+int rks_get_krylov(rks_ctx* c, int* ncols_out, double* U, double* S, double* H);
+
+/* ||A||_1 (max column sum of |a_ij|), computed at rks_create. */
+double rks_norm1(const rks_ctx* c);
+
+/* Free everything owned by the context (device memory, stream, events).
+ * Safe on NULL. */
+void rks_destroy(rks_ctx* c);
+
+/* Static message for a status code. */
+const char* rks_strerror(int status);
+
+/* ---- Sketch primitives (Sec. 5 setup; Def. 1.1) ---------------------- */
+
+/* The (row, sign) pairs of Omega: for column i and slot t < zeta,
+ * rows[i*zeta + t] in [0, d) and signs[i*zeta + t] in {-1, +1}.  Device
+ * pointers (int32 and int8), written on `stream` (NULL: default stream).
+ * Hash: base_i = mix(seed * 0x9E3779B97F4A7C15 + i); draw r =
+ * mix(base_i + (r+1) * 0x9E3779B97F4A7C15), mix = SplitMix64's output
+ * function; row = ((draw >> 32) * d) >> 32, sign = -1 if draw & 1; a draw
+ * repeating an earlier row of the column is skipped; at most 32*zeta draws.
+ * Requires d >= 2*zeta, 1 <= zeta <= 16. */
+int rks_sketch_pairs(int64_t n, int d, int zeta, uint64_t seed, int32_t* rows, int8_t* signs,
+                     void* stream);
+
+/* z = Omega x for a device vector x (n doubles) into device z (d doubles),
+ * entries sign/sqrt(zeta), FP64 accumulation.  Same requirements. */
+int rks_sketch_apply(int64_t n, int d, int zeta, uint64_t seed, const double* x, double* z,
+                     void* stream);
+
+/* ---- Host-side small dense FP64 steps (Algorithm 1 contraction) ------ */
+
+/* Ordered real Schur form (Prop. 2.8) of the m x m matrix B (column-major,
+ * host): B = Q T Q^T with T quasi-triangular (standardised 2x2 blocks) and
+ * the nsort best diagonal blocks for `which` leading, best first.  T and Q
+ * are m x m host arrays.  Returns RKS_OK, RKS_EINVAL or RKS_EDENSE.  Runs on
+ * the host only (no GPU needed). */
+int rks_host_ordered_schur(int m, const double* B, int which, int nsort, double* T, double* Q);
+
+/* Eigenvalues and unit 2-norm eigenvectors of a quasi-triangular T (n x n,
+ * host): a 2x2 block gives the pair (Im > 0 first).  Y_re, Y_im: n x n host
+ * arrays (column j = eigenvector j).  Host only. */
+int rks_host_quasi_eig(int n, const double* T, double* lam_re, double* lam_im, double* Y_re, double* Y_im);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RKS_H */

@@ -1,0 +1,879 @@
+// C ABI of librks: context management and the rKS driver (Algorithm 1).
+//
+// Device: all n-dimensional work (SpMV, sketches, the RGS update, the restart
+// product U Q, eigenvectors and residuals) runs in the kernels of kernels.cu
+// on the context's stream.  Host: the m x m FP64 contraction (Schur form,
+// reordering, truncation, whitening, locking, Ritz pairs and estimates) runs
+// in dense.cpp between expansions, on the Rayleigh quotient copied back from
+// the device.
+//
+// Column layout of the basis U (n x (m+1), column-major, ld = n rounded up
+// to 32): columns 0..q-1 are the locked Schur vectors U_q (Sec. 4.3), columns
+// q..q+ja-1 the active basis, column q+ja the last vector u.  S = Omega U is
+// kept both on the device (d x (m+1)) and on the host.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/rks.h"
+#include "dense.h"
+#include "rks_impl.h"
+
+using rks::Csr;
+typedef std::complex<double> cd;
+
+struct rks_ctx {
+  // problem
+  int64_t n = 0, nnz = 0;
+  int k = 0, p = 0, m = 0, d = 0, zeta = 8, which = 0;
+  double tol = 0, eta_lock = 0, zscale = 1;
+  uint64_t seed = 0;
+  rks_opts opts;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // device
+  int32_t* rowptr = nullptr;
+  int32_t* colind = nullptr;
+  double* vals = nullptr;
+  Csr A;
+  double* U = nullptr;
+  int64_t ldu = 0;
+  double* S = nullptr;
+  double* colscale = nullptr;
+  double *z_raw = nullptr, *s_raw = nullptr, *z1 = nullptr, *r1 = nullptr, *r = nullptr, *rs = nullptr;
+  double* coef = nullptr;
+  int* flag = nullptr;
+  double* Qd = nullptr;
+  double* u1 = nullptr;
+  double* X = nullptr;
+  double* AX = nullptr;
+  double* rsum = nullptr;
+  int* pcol = nullptr;
+  double* plam = nullptr;
+  // host state
+  double norm1 = 0;
+  std::vector<double> S_h, cs_h, coef_h, Ba, Tqq, Tqa;
+  int q = 0, ja = 0;
+  int64_t nmatvec = 0;
+  int restarts = 0;
+  int last_expand_from = 0;
+  // instrumentation (rks_get_stats)
+  rks_stats stats;
+  std::vector<cudaEvent_t> evpool;   // pairs: [2i] start, [2i+1] stop
+  std::vector<int> evclass;
+  int evused = 0;
+  // results
+  bool solved = false;
+  int kk = 0;
+  std::vector<double> Tfull, bfull, lre, lim, est, resid;
+  std::vector<cd> Y;
+};
+
+namespace {
+
+#define CK(x)                                                              \
+  do {                                                                     \
+    cudaError_t e_ = (x);                                                  \
+    if (e_ != cudaSuccess) {                                               \
+      std::fprintf(stderr, "librks: %s failed: %s\n", #x, cudaGetErrorString(e_)); \
+      return e_ == cudaErrorMemoryAllocation ? RKS_ENOMEM : RKS_ECUDA;    \
+    }                                                                      \
+  } while (0)
+
+template <class T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) { *p = nullptr; return e == cudaErrorMemoryAllocation ? RKS_ENOMEM : RKS_ECUDA; }
+  return RKS_OK;
+}
+
+int launch_err() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "librks: kernel launch failed: %s\n", cudaGetErrorString(e));
+    return RKS_ECUDA;
+  }
+  return RKS_OK;
+}
+
+inline double& M(std::vector<double>& a, int ld, int i, int j) { return a[i + (size_t)j * ld]; }
+
+// Launch accounting: every kernel launch is counted; with opts.profile the
+// launches of a class are bracketed by CUDA events on the context's stream.
+int prof_begin(rks_ctx* c, int cls) {
+  if (!c->opts.profile) return -1;
+  if ((size_t)(2 * c->evused + 2) > c->evpool.size()) {
+    for (int t = 0; t < 64; ++t) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      c->evpool.push_back(e);
+    }
+    c->evclass.resize(c->evpool.size() / 2);
+  }
+  int slot = c->evused++;
+  c->evclass[slot] = cls;
+  cudaEventRecord(c->evpool[2 * slot], c->stream);
+  return slot;
+}
+
+void prof_end(rks_ctx* c, int slot, int cls, int nlaunch, double bytes, double flops) {
+  c->stats.launches[cls] += nlaunch;
+  c->stats.bytes[cls] += bytes;
+  c->stats.flops[cls] += flops;
+  if (slot >= 0) cudaEventRecord(c->evpool[2 * slot + 1], c->stream);
+}
+
+// Called after a stream synchronisation: fold the recorded event pairs.
+void prof_flush(rks_ctx* c) {
+  for (int s = 0; s < c->evused; ++s) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->evpool[2 * s], c->evpool[2 * s + 1]) == cudaSuccess)
+      c->stats.ms[c->evclass[s]] += ms;
+  }
+  c->evused = 0;
+}
+
+// Append column j (global index) of the expansion to the host Rayleigh quotient.
+void absorb_columns(rks_ctx* c, int from, int to) {
+  const int ldc = c->m + 1;
+  const int ldb = c->m + 1;
+  const int ldt = c->k + 2;
+  for (int j = from; j < to; ++j) {
+    int a = j - c->q;
+    for (int i = 0; i < c->q; ++i) M(c->Tqa, ldt, i, a) = c->coef_h[i + (size_t)j * ldc];
+    for (int i = 0; i <= a; ++i) M(c->Ba, ldb, i, a) = c->coef_h[c->q + i + (size_t)j * ldc];
+    M(c->Ba, ldb, a + 1, a) = c->coef_h[j + 1 + (size_t)j * ldc];
+    for (int i = a + 2; i <= c->m; ++i) M(c->Ba, ldb, i, a) = 0.0;
+  }
+}
+
+int read_flag(rks_ctx* c, int* f) {
+  CK(cudaMemcpyAsync(f, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return RKS_OK;
+}
+
+int flag_status(int f) {
+  if (f & rks::RKS_FLAG_NAN) return RKS_ENAN;
+  if (f & rks::RKS_FLAG_HASH) return RKS_EINVAL;
+  if (f & rks::RKS_FLAG_BREAKDOWN) return RKS_EBREAKDOWN;
+  return RKS_OK;
+}
+
+// Algorithm 2: extend from the last vector at column q+ja to column m.
+int expand(rks_ctx* c) {
+  const int c0 = c->q + c->ja;
+  const double n = (double)c->n, P = sizeof(double);
+  const double spmv_bytes = (double)c->nnz * (P + 4) + 4.0 * (n + 1) + 2 * P * n;
+  for (int j = c0; j < c->m; ++j) {
+    const int col = j + 1;
+    int s = prof_begin(c, RKS_K_SPMV);
+    rks::launch_spmv_sketch(c->A, c->U + (int64_t)j * c->ldu, c->colscale + j, c->U + (int64_t)col * c->ldu,
+                            c->d, c->zeta, c->seed, c->z_raw, c->flag, c->stream);
+    prof_end(c, s, RKS_K_SPMV, 1, spmv_bytes, 2.0 * c->nnz);
+    s = prof_begin(c, RKS_K_LS);
+    rks::launch_ls(col, c->d, c->S, c->z_raw, c->zscale, c->colscale, c->r1, c->z1, c->r, c->rs, c->stream);
+    prof_end(c, s, RKS_K_LS, 3, 3.0 * P * c->d * col, 6.0 * c->d * col);
+    s = prof_begin(c, RKS_K_UPDATE);
+    rks::launch_update_sketch(c->n, c->U, c->ldu, col, c->rs, c->d, c->zeta, c->seed, c->s_raw, c->flag,
+                              c->stream);
+    prof_end(c, s, RKS_K_UPDATE, 1, (col + 2) * P * n, 2.0 * n * col);
+    s = prof_begin(c, RKS_K_FINISH);
+    rks::launch_finish(col, c->d, c->zscale, c->s_raw, c->z_raw, c->S, c->colscale, c->r, c->coef, c->m + 1,
+                       c->flag, c->stream);
+    prof_end(c, s, RKS_K_FINISH, 1, 3.0 * P * c->d, 2.0 * c->d);
+    ++c->nmatvec;
+  }
+  int rc = launch_err();
+  if (rc) return rc;
+  c->last_expand_from = c0;
+  // bring back coefficients, scales and sketches
+  CK(cudaMemcpyAsync(c->coef_h.data(), c->coef, c->coef_h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaMemcpyAsync(c->cs_h.data(), c->colscale, c->cs_h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaMemcpyAsync(c->S_h.data(), c->S, c->S_h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  int f = 0;
+  rc = read_flag(c, &f);
+  if (rc) return rc;
+  prof_flush(c);
+  rc = flag_status(f);
+  if (rc) return rc;
+  absorb_columns(c, c0, c->m);
+  c->ja = c->m - c->q;
+  return RKS_OK;
+}
+
+// Householder QR of the d x ka matrix S (column-major, ld d), R upper
+// triangular with positive diagonal (ka x ka, ld ka); S is overwritten by Q.
+void house_qr(int d, int ka, double* S, double* R) {
+  std::vector<double> V((size_t)d * ka, 0.0), beta(ka, 0.0);
+  std::vector<double> A(S, S + (size_t)d * ka);
+  for (int j = 0; j < ka; ++j) {
+    double s = 0.0;
+    for (int i = j; i < d; ++i) s += A[i + (size_t)j * d] * A[i + (size_t)j * d];
+    double nrm = std::sqrt(s);
+    double x0 = A[j + (size_t)j * d];
+    double v0 = x0 >= 0 ? x0 + nrm : x0 - nrm;
+    double* v = &V[(size_t)j * d];
+    v[j] = 1.0;
+    double vtv = 1.0;
+    for (int i = j + 1; i < d; ++i) { v[i] = (v0 != 0.0) ? A[i + (size_t)j * d] / v0 : 0.0; vtv += v[i] * v[i]; }
+    beta[j] = (nrm == 0.0) ? 0.0 : 2.0 / vtv;
+    for (int cc = j; cc < ka; ++cc) {
+      double acc = 0.0;
+      for (int i = j; i < d; ++i) acc += v[i] * A[i + (size_t)cc * d];
+      acc *= beta[j];
+      for (int i = j; i < d; ++i) A[i + (size_t)cc * d] -= acc * v[i];
+    }
+  }
+  // R and explicit Q (first ka columns)
+  for (int j = 0; j < ka; ++j)
+    for (int i = 0; i < ka; ++i) R[i + (size_t)j * ka] = (i <= j) ? A[i + (size_t)j * d] : 0.0;
+  std::vector<double> Q((size_t)d * ka, 0.0);
+  for (int j = 0; j < ka; ++j) Q[j + (size_t)j * d] = 1.0;
+  for (int h = ka - 1; h >= 0; --h) {
+    const double* v = &V[(size_t)h * d];
+    for (int cc = 0; cc < ka; ++cc) {
+      double acc = 0.0;
+      for (int i = h; i < d; ++i) acc += v[i] * Q[i + (size_t)cc * d];
+      acc *= beta[h];
+      for (int i = h; i < d; ++i) Q[i + (size_t)cc * d] -= acc * v[i];
+    }
+  }
+  for (int j = 0; j < ka; ++j) {      // positive diagonal of R
+    if (R[j + (size_t)j * ka] < 0) {
+      for (int cc = j; cc < ka; ++cc) R[j + (size_t)cc * ka] = -R[j + (size_t)cc * ka];
+      for (int i = 0; i < d; ++i) Q[i + (size_t)j * d] = -Q[i + (size_t)j * d];
+    }
+  }
+  std::memcpy(S, Q.data(), Q.size() * sizeof(double));
+}
+
+// Algorithm 1 contraction + whitening (Sec. 3.3) + locking (Sec. 4.4) +
+// restart product on the device.  Sets c->kk results of the Ritz step.
+int contract(rks_ctx* c) {
+  const int m = c->m, q = c->q, ma = c->ja, d = c->d;
+  const int ldb = m + 1, ldt = c->k + 2;
+  std::vector<double> H((size_t)ma * ma), Q((size_t)ma * ma), b(ma);
+  for (int j = 0; j < ma; ++j) {
+    for (int i = 0; i < ma; ++i) H[i + (size_t)j * ma] = M(c->Ba, ldb, i, j);
+    b[j] = M(c->Ba, ldb, ma, j);
+  }
+  rks_dense::hessenberg(ma, H.data(), ma, Q.data(), ma);
+  if (rks_dense::schur(ma, H.data(), ma, Q.data(), ma) != 0) return RKS_EDENSE;
+  const int want = c->k - q;
+  rks_dense::reorder(ma, H.data(), ma, Q.data(), ma, ma, c->which, std::min(want + 1, ma));
+  // truncation size: blocks covering `want` columns, pairs kept whole
+  int ka = 0;
+  for (const auto& B : rks_dense::blocks(ma, H.data(), ma)) {
+    if (ka >= want) break;
+    ka = B.start + B.size;
+  }
+  ka = std::min(ka, ma - 1);
+  // truncated pieces
+  std::vector<double> Ta((size_t)ka * ka), bk(ka, 0.0), Qk((size_t)ma * ka);
+  for (int j = 0; j < ka; ++j) {
+    for (int i = 0; i < ka; ++i) Ta[i + (size_t)j * ka] = H[i + (size_t)j * ma];
+    for (int i = 0; i < ma; ++i) Qk[i + (size_t)j * ma] = Q[i + (size_t)j * ma];
+    double acc = 0.0;
+    for (int i = 0; i < ma; ++i) acc += b[i] * Q[i + (size_t)j * ma];
+    bk[j] = acc;
+  }
+  std::vector<double> Tqa_new((size_t)ldt * ka, 0.0);
+  for (int j = 0; j < ka; ++j)
+    for (int i = 0; i < q; ++i) {
+      double acc = 0.0;
+      for (int l = 0; l < ma; ++l) acc += M(c->Tqa, ldt, i, l) * Qk[l + (size_t)j * ma];
+      Tqa_new[i + (size_t)j * ldt] = acc;
+    }
+  // sketches of the kept columns: S_a <- S_a Qk ; last column moves to q+ka
+  std::vector<double> Sa((size_t)d * ka, 0.0);
+  for (int j = 0; j < ka; ++j)
+    for (int l = 0; l < ma; ++l) {
+      double w = Qk[l + (size_t)j * ma];
+      const double* src = &c->S_h[(size_t)(q + l) * d];
+      double* dst = &Sa[(size_t)j * d];
+      for (int i = 0; i < d; ++i) dst[i] += w * src[i];
+    }
+  // whitening when the sketch lost orthonormality (Sec. 3.3, Eqs. 3.7-3.8)
+  double gerr = 0.0;
+  for (int a = 0; a < ka; ++a)
+    for (int bb = 0; bb < ka; ++bb) {
+      double acc = 0.0;
+      for (int i = 0; i < d; ++i) acc += Sa[i + (size_t)a * d] * Sa[i + (size_t)bb * d];
+      acc -= (a == bb) ? 1.0 : 0.0;
+      gerr += acc * acc;
+    }
+  if (ka > 0 && std::sqrt(gerr) > 1e-10) {
+    std::vector<double> R((size_t)ka * ka), Rinv((size_t)ka * ka, 0.0);
+    house_qr(d, ka, Sa.data(), R.data());
+    for (int j = 0; j < ka; ++j) {          // Rinv by back substitution
+      Rinv[j + (size_t)j * ka] = 1.0 / R[j + (size_t)j * ka];
+      for (int i = j - 1; i >= 0; --i) {
+        double acc = 0.0;
+        for (int l = i + 1; l <= j; ++l) acc += R[i + (size_t)l * ka] * Rinv[l + (size_t)j * ka];
+        Rinv[i + (size_t)j * ka] = -acc / R[i + (size_t)i * ka];
+      }
+    }
+    auto matmul = [](int r, int inner, int cc, const double* X, int ldx, const double* Yv, int ldy,
+                     double* Z, int ldz) {
+      for (int j = 0; j < cc; ++j)
+        for (int i = 0; i < r; ++i) {
+          double acc = 0.0;
+          for (int l = 0; l < inner; ++l) acc += X[i + (size_t)l * ldx] * Yv[l + (size_t)j * ldy];
+          Z[i + (size_t)j * ldz] = acc;
+        }
+    };
+    std::vector<double> tmp((size_t)std::max(ma, ka) * ka);
+    matmul(ma, ka, ka, Qk.data(), ma, Rinv.data(), ka, tmp.data(), ma);
+    std::copy(tmp.begin(), tmp.begin() + (size_t)ma * ka, Qk.begin());
+    std::vector<double> t2((size_t)ka * ka);
+    matmul(ka, ka, ka, Ta.data(), ka, Rinv.data(), ka, t2.data(), ka);
+    matmul(ka, ka, ka, R.data(), ka, t2.data(), ka, Ta.data(), ka);
+    std::vector<double> b2(ka);
+    for (int j = 0; j < ka; ++j) {
+      double acc = 0.0;
+      for (int l = 0; l < ka; ++l) acc += bk[l] * Rinv[l + (size_t)j * ka];
+      b2[j] = acc;
+    }
+    bk = b2;
+    if (q) {
+      std::vector<double> t3((size_t)ldt * ka, 0.0);
+      matmul(q, ka, ka, Tqa_new.data(), ldt, Rinv.data(), ka, t3.data(), ldt);
+      Tqa_new = t3;
+    }
+  }
+  // device restart: U[:, q..q+ka-1] = U[:, q..m-1] diag(colscale) Qk ; u -> column q+ka
+  std::vector<double> Qp((size_t)ma * ka);
+  for (int j = 0; j < ka; ++j)
+    for (int l = 0; l < ma; ++l) Qp[l + (size_t)j * ma] = c->cs_h[q + l] * Qk[l + (size_t)j * ma];
+  CK(cudaMemcpyAsync(c->Qd, Qp.data(), Qp.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  int ps = prof_begin(c, RKS_K_RESTART);
+  rks::launch_rows_gemm(c->n, c->U, c->ldu, q, ma, c->Qd, ka, c->U, c->ldu, q, m, c->stream);
+  prof_end(c, ps, RKS_K_RESTART, 1, (double)(ma + ka + 2) * sizeof(double) * c->n, 2.0 * c->n * ma * ka);
+  int rc = launch_err();
+  if (rc) return rc;
+  const double s_last_scale = c->cs_h[m];
+  for (int j = 0; j < ka; ++j) c->cs_h[q + j] = 1.0;
+  c->cs_h[q + ka] = s_last_scale;
+  for (int j = q + ka + 1; j <= m; ++j) c->cs_h[j] = 0.0;
+  for (int j = 0; j < ka; ++j) std::memcpy(&c->S_h[(size_t)(q + j) * d], &Sa[(size_t)j * d], d * sizeof(double));
+  std::memmove(&c->S_h[(size_t)(q + ka) * d], &c->S_h[(size_t)m * d], d * sizeof(double));
+  CK(cudaMemcpyAsync(c->colscale, c->cs_h.data(), c->cs_h.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     c->stream));
+  CK(cudaMemcpyAsync(c->S, c->S_h.data(), c->S_h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  // locking: leading active blocks with small |b| (relative to |lambda|)
+  int r = 0;
+  if (c->opts.lock) {
+    double tn = 0.0;
+    for (double v : Ta) tn += v * v;
+    tn = std::sqrt(tn);
+    for (const auto& B : rks_dense::blocks(ka, Ta.data(), ka)) {
+      if (q + r + B.size > c->k) break;
+      double lam = std::hypot(B.re, B.im);
+      double thr = c->eta_lock * std::max(lam, 2.220446049250313e-16 * tn);
+      bool ok = true;
+      for (int t = 0; t < B.size; ++t) ok = ok && std::fabs(bk[B.start + t]) <= thr;
+      if (!ok) break;
+      r = B.start + B.size;
+    }
+  }
+  if (r > 0) {
+    const int qn = q + r;
+    std::vector<double> Tqq2((size_t)ldt * ldt, 0.0), Tqa2((size_t)ldt * ka, 0.0);
+    for (int j = 0; j < q; ++j)
+      for (int i = 0; i <= j + 1 && i < q; ++i) Tqq2[i + (size_t)j * ldt] = M(c->Tqq, ldt, i, j);
+    for (int j = 0; j < r; ++j) {
+      for (int i = 0; i < q; ++i) Tqq2[i + (size_t)(q + j) * ldt] = Tqa_new[i + (size_t)j * ldt];
+      for (int i = 0; i < r; ++i) Tqq2[q + i + (size_t)(q + j) * ldt] = Ta[i + (size_t)j * ka];
+    }
+    for (int j = r; j < ka; ++j) {
+      for (int i = 0; i < q; ++i) Tqa2[i + (size_t)(j - r) * ldt] = Tqa_new[i + (size_t)j * ldt];
+      for (int i = 0; i < r; ++i) Tqa2[q + i + (size_t)(j - r) * ldt] = Ta[i + (size_t)j * ka];
+    }
+    std::vector<double> Ta2((size_t)(ka - r) * (ka - r));
+    for (int j = r; j < ka; ++j)
+      for (int i = r; i < ka; ++i) Ta2[(i - r) + (size_t)(j - r) * (ka - r)] = Ta[i + (size_t)j * ka];
+    std::vector<double> b2(bk.begin() + r, bk.end());
+    c->Tqq = Tqq2;
+    c->Tqa.assign((size_t)ldt * (m + 1), 0.0);
+    std::copy(Tqa2.begin(), Tqa2.end(), c->Tqa.begin());
+    Ta = Ta2;
+    bk = b2;
+    c->q = qn;
+    ka -= r;
+  } else {
+    c->Tqa.assign((size_t)ldt * (m + 1), 0.0);
+    std::copy(Tqa_new.begin(), Tqa_new.end(), c->Tqa.begin());
+  }
+  c->ja = ka;
+  std::fill(c->Ba.begin(), c->Ba.end(), 0.0);
+  for (int j = 0; j < ka; ++j) {
+    for (int i = 0; i < ka; ++i) M(c->Ba, ldb, i, j) = Ta[i + (size_t)j * ka];
+    M(c->Ba, ldb, ka, j) = bk[j];
+  }
+  return RKS_OK;
+}
+
+// Ritz pairs of the full T = [[Tqq, Tqa], [0, T_a]] and estimates (Eq. 4.8).
+void ritz(rks_ctx* c) {
+  const int q = c->q, ja = c->ja, kk = q + ja, ldt = c->k + 2, ldb = c->m + 1;
+  c->kk = kk;
+  c->Tfull.assign((size_t)kk * kk, 0.0);
+  c->bfull.assign(kk, 0.0);
+  for (int j = 0; j < q; ++j)
+    for (int i = 0; i < q; ++i) c->Tfull[i + (size_t)j * kk] = M(c->Tqq, ldt, i, j);
+  for (int j = 0; j < ja; ++j) {
+    for (int i = 0; i < q; ++i) c->Tfull[i + (size_t)(q + j) * kk] = M(c->Tqa, ldt, i, j);
+    for (int i = 0; i < ja; ++i) c->Tfull[q + i + (size_t)(q + j) * kk] = M(c->Ba, ldb, i, j);
+    c->bfull[q + j] = M(c->Ba, ldb, ja, j);
+  }
+  std::vector<double> lre(kk), lim(kk);
+  std::vector<cd> Y((size_t)kk * kk);
+  rks_dense::quasi_eig(kk, c->Tfull.data(), kk, lre.data(), lim.data(), Y.data(), kk);
+  std::vector<int> order(kk);
+  for (int i = 0; i < kk; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return rks_dense::key(lre[a], lim[a], c->which) < rks_dense::key(lre[b], lim[b], c->which);
+  });
+  c->lre.resize(kk); c->lim.resize(kk); c->est.resize(kk); c->Y.resize((size_t)kk * kk);
+  for (int t = 0; t < kk; ++t) {
+    int o = order[t];
+    c->lre[t] = lre[o];
+    c->lim[t] = lim[o];
+    cd bty = 0.0;
+    for (int i = 0; i < kk; ++i) {
+      c->Y[i + (size_t)t * kk] = Y[i + (size_t)o * kk];
+      bty += c->bfull[i] * Y[i + (size_t)o * kk];
+    }
+    double al = std::hypot(lre[o], lim[o]);
+    c->est[t] = std::abs(bty) / std::max(al, 1e-300);
+  }
+}
+
+// Ritz vectors X = U Y (real packing), A X and FP64 residuals.
+int finalize(rks_ctx* c) {
+  const int kk = c->kk;
+  if (!c->X) {
+    int rc = dalloc(&c->X, (size_t)c->ldu * (c->k + 1));
+    if (rc) return rc;
+    rc = dalloc(&c->AX, (size_t)c->ldu * (c->k + 1));
+    if (rc) return rc;
+    rc = dalloc(&c->rsum, (size_t)4 * (c->k + 1));
+    if (rc) return rc;
+    rc = dalloc(&c->pcol, (size_t)2 * (c->k + 1));
+    if (rc) return rc;
+    rc = dalloc(&c->plam, (size_t)2 * (c->k + 1));
+    if (rc) return rc;
+  }
+  std::vector<double> Yr((size_t)kk * kk);
+  std::vector<int> col, colim;
+  std::vector<double> pl_re, pl_im;
+  for (int t = 0; t < kk;) {
+    bool pair = c->lim[t] > 0 && t + 1 < kk;
+    for (int i = 0; i < kk; ++i) {
+      Yr[i + (size_t)t * kk] = c->Y[i + (size_t)t * kk].real();
+      if (pair) Yr[i + (size_t)(t + 1) * kk] = c->Y[i + (size_t)t * kk].imag();
+    }
+    col.push_back(t);
+    colim.push_back(pair ? t + 1 : -1);
+    pl_re.push_back(c->lre[t]);
+    pl_im.push_back(pair ? c->lim[t] : 0.0);
+    t += pair ? 2 : 1;
+  }
+  const int np = (int)col.size();
+  CK(cudaMemcpyAsync(c->Qd, Yr.data(), Yr.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  int ps = prof_begin(c, RKS_K_OTHER);
+  rks::launch_rows_gemm(c->n, c->U, c->ldu, 0, kk, c->Qd, kk, c->X, c->ldu, 0, -1, c->stream);
+  rks::launch_spmm(c->A, c->X, c->ldu, c->AX, c->ldu, kk, c->stream);
+  std::vector<int> pc(2 * np);
+  std::vector<double> pv(2 * np);
+  for (int t = 0; t < np; ++t) { pc[t] = col[t]; pc[np + t] = colim[t]; pv[t] = pl_re[t]; pv[np + t] = pl_im[t]; }
+  CK(cudaMemcpyAsync(c->pcol, pc.data(), pc.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->plam, pv.data(), pv.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->rsum, 0, sizeof(double) * 4 * np, c->stream));
+  rks::launch_resid_sums(c->n, c->X, c->AX, c->ldu, np, c->pcol, c->pcol + np, c->plam, c->plam + np, c->rsum,
+                         c->stream);
+  prof_end(c, ps, RKS_K_OTHER, 3, 0.0, 0.0);
+  int rc = launch_err();
+  if (rc) return rc;
+  std::vector<double> sums(4 * np);
+  CK(cudaMemcpyAsync(sums.data(), c->rsum, sums.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  prof_flush(c);
+  c->resid.assign(kk, 0.0);
+  for (int t = 0; t < np; ++t) {
+    double res = std::sqrt(sums[4 * t]) / (c->norm1 * std::sqrt(std::max(sums[4 * t + 1], 1e-300)));
+    c->resid[col[t]] = res;
+    if (colim[t] >= 0) c->resid[colim[t]] = res;
+  }
+  return RKS_OK;
+}
+
+void free_ctx(rks_ctx* c) {
+  if (!c) return;
+  cudaFree(c->rowptr); cudaFree(c->colind); cudaFree(c->vals);
+  cudaFree(c->U); cudaFree(c->S); cudaFree(c->colscale);
+  cudaFree(c->z_raw); cudaFree(c->s_raw); cudaFree(c->z1); cudaFree(c->r1); cudaFree(c->r); cudaFree(c->rs);
+  cudaFree(c->coef); cudaFree(c->flag); cudaFree(c->Qd); cudaFree(c->u1);
+  cudaFree(c->X); cudaFree(c->AX); cudaFree(c->rsum); cudaFree(c->pcol); cudaFree(c->plam);
+  for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rks_opts_default(rks_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->zeta = 8;
+  o->maxit = 1000;
+  o->lock = 1;
+}
+
+const char* rks_strerror(int s) {
+  switch (s) {
+    case RKS_OK: return "ok";
+    case RKS_EINVAL: return "invalid argument";
+    case RKS_ENOMEM: return "out of memory";
+    case RKS_ECUDA: return "CUDA error";
+    case RKS_ENOCONV: return "not converged within maxit restarts (results are partial)";
+    case RKS_EBREAKDOWN: return "breakdown: invariant subspace reached";
+    case RKS_ENAN: return "non-finite value encountered";
+    case RKS_ESTATE: return "call out of order";
+    case RKS_EDENSE: return "small dense Schur iteration failed";
+    default: return "unknown status";
+  }
+}
+
+int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* colind, const void* vals,
+               int vals_dtype, int k, int p, int d, int which, double tol, uint64_t seed, const rks_opts* opts) {
+  if (!out) return RKS_EINVAL;
+  *out = nullptr;
+  rks_opts o;
+  rks_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.zeta == 0) o.zeta = 8;
+  if (o.maxit <= 0) o.maxit = 1000;
+  const int m = k + p;
+  if (n <= 0 || !rowptr || !colind || !vals || k < 1 || p < 2 || (int64_t)m + 1 > n || d < m + 1 ||
+      o.zeta < 1 || o.zeta > 16 || d < 2 * o.zeta || d > 8192 || which < 0 || which > 3 || !(tol > 0) ||
+      (vals_dtype != RKS_F64 && vals_dtype != RKS_F32) || n > (int64_t)INT32_MAX)
+    return RKS_EINVAL;
+  // the restart product keeps an (m x (k+2)) tile of Q' and 128 x (k+2) outputs in shared memory
+  if (rks::rows_gemm_smem(m, k + 2, 128) > 200 * 1024) return RKS_EINVAL;
+  rks_ctx* c = new (std::nothrow) rks_ctx();
+  if (!c) return RKS_ENOMEM;
+  c->n = n; c->k = k; c->p = p; c->m = m; c->d = d; c->zeta = o.zeta; c->which = which;
+  c->tol = tol; c->seed = seed; c->opts = o;
+  c->eta_lock = o.eta_lock > 0 ? o.eta_lock : tol;
+  c->zscale = 1.0 / std::sqrt((double)o.zeta);
+  const cudaMemcpyKind kind = o.mem_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  int rc = RKS_OK;
+  auto fail = [&](int code) { free_ctx(c); return code; };
+  if (o.stream) {
+    c->stream = (cudaStream_t)o.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(RKS_ECUDA);
+    c->own_stream = true;
+  }
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) return fail(RKS_ECUDA);
+  // CSR: read nnz from rowptr[n]
+  int32_t nnz32 = 0;
+  if (cudaMemcpy(&nnz32, rowptr + n, sizeof(int32_t), o.mem_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) !=
+      cudaSuccess)
+    return fail(RKS_ECUDA);
+  if (nnz32 < 0) return fail(RKS_EINVAL);
+  c->nnz = nnz32;
+  if ((rc = dalloc(&c->rowptr, n + 1)) || (rc = dalloc(&c->colind, c->nnz)) || (rc = dalloc(&c->vals, c->nnz)))
+    return fail(rc);
+  if (cudaMemcpyAsync(c->rowptr, rowptr, (n + 1) * sizeof(int32_t), kind, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->colind, colind, c->nnz * sizeof(int32_t), kind, c->stream) != cudaSuccess)
+    return fail(RKS_ECUDA);
+  if (vals_dtype == RKS_F64) {
+    if (cudaMemcpyAsync(c->vals, vals, c->nnz * sizeof(double), kind, c->stream) != cudaSuccess) return fail(RKS_ECUDA);
+  } else {
+    float* tmp = nullptr;
+    if ((rc = dalloc(&tmp, c->nnz))) return fail(rc);
+    if (cudaMemcpyAsync(tmp, vals, c->nnz * sizeof(float), kind, c->stream) != cudaSuccess) { cudaFree(tmp); return fail(RKS_ECUDA); }
+    rks::launch_f32_to_f64(c->nnz, tmp, c->vals, c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+  }
+  if ((rc = dalloc(&c->flag, 4))) return fail(rc);
+  if (cudaMemsetAsync(c->flag, 0, 4 * sizeof(int), c->stream) != cudaSuccess) return fail(RKS_ECUDA);
+  rks::launch_check_csr(n, c->nnz, c->rowptr, c->colind, c->flag, c->stream);
+  int bad = 0;
+  if (cudaMemcpyAsync(&bad, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(RKS_ECUDA);
+  if (bad) return fail(RKS_EINVAL);
+  c->A.n = n; c->A.nnz = c->nnz; c->A.rowptr = c->rowptr; c->A.colind = c->colind; c->A.vals = c->vals;
+  // ||A||_1
+  {
+    double* colsum = nullptr;
+    if ((rc = dalloc(&colsum, n))) return fail(rc);
+    cudaMemsetAsync(colsum, 0, n * sizeof(double), c->stream);
+    rks::launch_col_abs_sums(c->nnz, c->colind, c->vals, colsum, c->stream);
+    std::vector<double> h(n);
+    cudaError_t e = cudaMemcpyAsync(h.data(), colsum, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(colsum);
+    if (e != cudaSuccess) return fail(RKS_ECUDA);
+    c->norm1 = *std::max_element(h.begin(), h.end());
+    if (!std::isfinite(c->norm1)) return fail(RKS_ENAN);
+    if (c->norm1 == 0.0) c->norm1 = 1.0;
+  }
+  c->ldu = (n + 31) / 32 * 32;
+  if ((rc = dalloc(&c->U, (size_t)c->ldu * (m + 1))) || (rc = dalloc(&c->S, (size_t)d * (m + 1))) ||
+      (rc = dalloc(&c->colscale, m + 1)) || (rc = dalloc(&c->z_raw, d)) || (rc = dalloc(&c->s_raw, d)) ||
+      (rc = dalloc(&c->z1, d)) || (rc = dalloc(&c->r1, m + 1)) || (rc = dalloc(&c->r, m + 1)) ||
+      (rc = dalloc(&c->rs, m + 1)) || (rc = dalloc(&c->coef, (size_t)(m + 1) * m)) ||
+      (rc = dalloc(&c->Qd, (size_t)(m + 1) * (m + 1))))
+    return fail(rc);
+  if (o.u1) {
+    if ((rc = dalloc(&c->u1, n))) return fail(rc);
+    if (cudaMemcpyAsync(c->u1, o.u1, n * sizeof(double), kind, c->stream) != cudaSuccess) return fail(RKS_ECUDA);
+  }
+  c->opts.u1 = nullptr;  // the caller's pointer is not kept
+  c->S_h.assign((size_t)d * (m + 1), 0.0);
+  c->cs_h.assign(m + 1, 0.0);
+  c->coef_h.assign((size_t)(m + 1) * m, 0.0);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(RKS_ECUDA);
+  if (rks::configure_kernels() != cudaSuccess) return fail(RKS_ECUDA);
+  *out = c;
+  return RKS_OK;
+}
+
+static int solve_impl(rks_ctx* c) {
+  const int m = c->m, d = c->d;
+  c->solved = false;
+  c->q = 0; c->ja = 0; c->nmatvec = 0; c->restarts = 0; c->kk = 0;
+  std::memset(&c->stats, 0, sizeof(c->stats));
+  c->evused = 0;
+  c->Ba.assign((size_t)(m + 1) * m, 0.0);
+  c->Tqq.assign((size_t)(c->k + 2) * (c->k + 2), 0.0);
+  c->Tqa.assign((size_t)(c->k + 2) * (m + 1), 0.0);
+  CK(cudaMemsetAsync(c->flag, 0, 4 * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(c->z_raw, 0, d * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(c->s_raw, 0, d * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(c->coef, 0, (size_t)(m + 1) * m * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(c->S, 0, (size_t)d * (m + 1) * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(c->colscale, 0, (m + 1) * sizeof(double), c->stream));
+  // start vector (Sec. 3.1, k = 0): u_1 = u~_1 / ||Omega u~_1||
+  int ps = prof_begin(c, RKS_K_OTHER);
+  if (c->u1) CK(cudaMemcpyAsync(c->U, c->u1, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  else rks::launch_start_vector(c->n, c->seed + 1, c->U, c->stream);
+  rks::launch_sketch_vec(c->n, c->U, 1.0, d, c->zeta, c->seed, c->s_raw, c->flag, c->stream);
+  rks::launch_start_finish(d, c->zscale, c->s_raw, c->S, c->colscale, c->flag, c->stream);
+  prof_end(c, ps, RKS_K_OTHER, c->u1 ? 2 : 3, 0.0, 0.0);
+  int rc = launch_err();
+  if (rc) return rc;
+  rc = expand(c);                      // Algorithm 1, initial expansion to m
+  if (rc) return rc;
+  if (c->opts.max_restarts < 0) { c->solved = true; return RKS_OK; }
+  const int limit = c->opts.max_restarts > 0 ? std::min(c->opts.maxit, c->opts.max_restarts) : c->opts.maxit;
+  bool converged = false;
+  while (true) {
+    auto h0 = std::chrono::steady_clock::now();
+    rc = contract(c);                  // Schur, reorder, truncate, whiten, lock, restart
+    if (rc) return rc;
+    ++c->restarts;
+    ritz(c);
+    c->stats.host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
+    double mx = 0.0;
+    for (double e : c->est) mx = std::max(mx, e);
+    if (c->q >= c->k || mx <= c->tol) { converged = true; break; }
+    if (c->restarts >= limit) break;
+    rc = expand(c);                    // Algorithm 2 from k to m
+    if (rc) return rc;
+  }
+  rc = finalize(c);
+  if (rc) return rc;
+  c->solved = true;
+  return converged ? RKS_OK : RKS_ENOCONV;
+}
+
+int rks_solve(rks_ctx* c, rks_info* info) {
+  if (!c) return RKS_EINVAL;
+  cudaEventRecord(c->ev0, c->stream);
+  int rc = solve_impl(c);
+  cudaEventRecord(c->ev1, c->stream);
+  cudaEventSynchronize(c->ev1);
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->nlocked = c->q;
+    info->restarts = c->restarts;
+    info->nmatvec = c->nmatvec;
+    double me = 0.0, mr = 0.0;
+    int nc = 0;
+    for (size_t i = 0; i < c->est.size() && c->restarts > 0; ++i) {
+      me = std::max(me, c->est[i]);
+      if (c->est[i] <= c->tol) ++nc;
+    }
+    for (double v : c->resid) mr = std::max(mr, v);
+    info->nconv = nc;
+    info->max_est = me;
+    info->max_resid = mr;
+    info->converged = (rc == RKS_OK && c->restarts > 0) ? 1 : 0;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    info->t_solve_ms = ms;
+  }
+  return rc;
+}
+
+int rks_nkept(const rks_ctx* c) { return c ? c->kk : 0; }
+
+int rks_get_stats(const rks_ctx* c, rks_stats* out) {
+  if (!c || !out) return RKS_EINVAL;
+  *out = c->stats;
+  return RKS_OK;
+}
+double rks_norm1(const rks_ctx* c) { return c ? c->norm1 : 0.0; }
+
+int rks_get_schur(rks_ctx* c, double* T, double* U, double* b) {
+  if (!c) return RKS_EINVAL;
+  if (!c->solved || c->kk == 0) return RKS_ESTATE;
+  const int kk = c->kk;
+  if (T) std::memcpy(T, c->Tfull.data(), sizeof(double) * kk * kk);
+  if (b) std::memcpy(b, c->bfull.data(), sizeof(double) * kk);
+  if (U) {
+    CK(cudaMemcpy2DAsync(U, c->n * sizeof(double), c->U, c->ldu * sizeof(double), c->n * sizeof(double), kk,
+                         c->opts.mem_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return RKS_OK;
+}
+
+int rks_get_eigpairs(rks_ctx* c, double* lam_re, double* lam_im, double* X, double* resid) {
+  if (!c) return RKS_EINVAL;
+  if (!c->solved || c->kk == 0) return RKS_ESTATE;
+  const int kk = c->kk;
+  if (lam_re) std::memcpy(lam_re, c->lre.data(), sizeof(double) * kk);
+  if (lam_im) std::memcpy(lam_im, c->lim.data(), sizeof(double) * kk);
+  if (resid) std::memcpy(resid, c->resid.data(), sizeof(double) * kk);
+  if (X) {
+    CK(cudaMemcpy2DAsync(X, c->n * sizeof(double), c->X, c->ldu * sizeof(double), c->n * sizeof(double), kk,
+                         c->opts.mem_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return RKS_OK;
+}
+
+int rks_get_estimates(rks_ctx* c, double* est) {
+  if (!c || !est) return RKS_EINVAL;
+  if (!c->solved || c->kk == 0) return RKS_ESTATE;
+  std::memcpy(est, c->est.data(), sizeof(double) * c->kk);
+  return RKS_OK;
+}
+
+int rks_get_krylov(rks_ctx* c, int* ncols_out, double* U, double* S, double* H) {
+  if (!c) return RKS_EINVAL;
+  if (!c->solved) return RKS_ESTATE;
+  const int nc = c->q + c->ja + 1;
+  if (ncols_out) *ncols_out = nc;
+  if (U) {
+    CK(cudaMemcpy2DAsync(U, c->n * sizeof(double), c->U, c->ldu * sizeof(double), c->n * sizeof(double), nc,
+                         cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int j = 0; j < nc; ++j) {
+      double s = c->cs_h[j];
+      double* col = U + (size_t)j * c->n;
+      for (int64_t i = 0; i < c->n; ++i) col[i] *= s;
+    }
+  }
+  if (S) std::memcpy(S, c->S_h.data(), sizeof(double) * (size_t)c->d * nc);
+  if (H) {
+    std::memset(H, 0, sizeof(double) * (size_t)nc * (nc - 1));
+    for (int j = c->last_expand_from; j < nc - 1; ++j)
+      for (int i = 0; i <= j + 1; ++i) H[i + (size_t)j * nc] = c->coef_h[i + (size_t)j * (c->m + 1)];
+  }
+  return RKS_OK;
+}
+
+void rks_destroy(rks_ctx* c) { free_ctx(c); }
+
+int rks_host_ordered_schur(int m, const double* B, int which, int nsort, double* T, double* Q) {
+  if (m <= 0 || !B || !T || !Q || which < 0 || which > 3) return RKS_EINVAL;
+  std::memcpy(T, B, sizeof(double) * (size_t)m * m);
+  rks_dense::hessenberg(m, T, m, Q, m);
+  if (rks_dense::schur(m, T, m, Q, m) != 0) return RKS_EDENSE;
+  rks_dense::reorder(m, T, m, Q, m, m, which, std::min(std::max(nsort, 0), m));
+  return RKS_OK;
+}
+
+int rks_host_quasi_eig(int n, const double* T, double* lam_re, double* lam_im, double* Y_re, double* Y_im) {
+  if (n <= 0 || !T || !lam_re || !lam_im) return RKS_EINVAL;
+  std::vector<cd> Y((size_t)n * n);
+  rks_dense::quasi_eig(n, T, n, lam_re, lam_im, Y.data(), n);
+  for (size_t i = 0; i < Y.size(); ++i) {
+    if (Y_re) Y_re[i] = Y[i].real();
+    if (Y_im) Y_im[i] = Y[i].imag();
+  }
+  return RKS_OK;
+}
+
+int rks_sketch_pairs(int64_t n, int d, int zeta, uint64_t seed, int32_t* rows, int8_t* signs, void* stream) {
+  if (n <= 0 || zeta < 1 || zeta > 16 || d < 2 * zeta || !rows || !signs) return RKS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* flag = nullptr;
+  int rc = dalloc(&flag, 1);
+  if (rc) return rc;
+  cudaMemsetAsync(flag, 0, sizeof(int), st);
+  rks::launch_sketch_pairs(n, d, zeta, seed, rows, signs, flag, st);
+  int f = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&f, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(flag);
+  if (e != cudaSuccess) return RKS_ECUDA;
+  return f ? RKS_EINVAL : RKS_OK;
+}
+
+int rks_sketch_apply(int64_t n, int d, int zeta, uint64_t seed, const double* x, double* z, void* stream) {
+  if (n <= 0 || zeta < 1 || zeta > 16 || d < 2 * zeta || d > 8192 || !x || !z) return RKS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (rks::configure_kernels() != cudaSuccess) return RKS_ECUDA;
+  int* flag = nullptr;
+  int rc = dalloc(&flag, 1);
+  if (rc) return rc;
+  cudaMemsetAsync(flag, 0, sizeof(int), st);
+  cudaMemsetAsync(z, 0, d * sizeof(double), st);
+  rks::launch_sketch_vec(n, x, 1.0, d, zeta, seed, z, flag, st);
+  // the kernel sums sign * x_i; the 1/sqrt(zeta) scale is applied here
+  std::vector<double> h(d);
+  int f = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), z, d * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&f, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    const double sc = 1.0 / std::sqrt((double)zeta);
+    for (double& v : h) v *= sc;
+    e = cudaMemcpyAsync(z, h.data(), d * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFree(flag);
+  if (e != cudaSuccess) return RKS_ECUDA;
+  return f ? RKS_EINVAL : RKS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// Internal declarations of librks (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rks {
+
+enum : int { RKS_FLAG_NAN = 1, RKS_FLAG_BREAKDOWN = 2, RKS_FLAG_HASH = 4 };
+
+// CTAs of the kernels that carry a sketch (one shared-memory bin set each,
+// folded into the global d-vector with one atomic per bin).
+constexpr int kSketchCtas = 152 * 2;
+
+struct Csr {
+  int64_t n = 0, nnz = 0;
+  const int32_t* rowptr = nullptr;
+  const int32_t* colind = nullptr;
+  const double* vals = nullptr;
+};
+
+void launch_sketch_pairs(int64_t n, int d, int zeta, uint64_t seed, int32_t* rows, int8_t* signs, int* flag,
+                         cudaStream_t st);
+void launch_sketch_vec(int64_t n, const double* x, double xscale, int d, int zeta, uint64_t seed, double* out_raw,
+                       int* flag, cudaStream_t st);
+void launch_spmv_sketch(const Csr& A, const double* x, const double* xscale, double* w, int d, int zeta,
+                        uint64_t seed, double* out_raw, int* flag, cudaStream_t st);
+void launch_ls(int c, int d, const double* S, const double* z_raw, double zscale, const double* colscale,
+               double* r1, double* z1, double* r, double* rs, cudaStream_t st);
+void launch_update_sketch(int64_t n, double* U, int64_t ldu, int c, const double* rs, int d, int zeta,
+                          uint64_t seed, double* out_raw, int* flag, cudaStream_t st);
+void launch_finish(int c, int d, double zscale, double* s_raw, double* z_raw, double* S, double* colscale,
+                   const double* r, double* coef, int ldcoef, int* flag, cudaStream_t st);
+void launch_start_finish(int d, double zscale, double* s_raw, double* S, double* colscale, int* flag,
+                         cudaStream_t st);
+void launch_start_vector(int64_t n, uint64_t seed, double* x, cudaStream_t st);
+cudaError_t configure_kernels();
+int rows_gemm_smem(int nin, int nout, int threads);
+void launch_rows_gemm(int64_t n, const double* A, int64_t lda, int a0, int nin, const double* B, int nout,
+                      double* C, int64_t ldc, int c0, int move_src, cudaStream_t st);
+void launch_spmm(const Csr& A, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncols, cudaStream_t st);
+void launch_resid_sums(int64_t n, const double* X, const double* AX, int64_t ld, int npairs, const int* col,
+                       const int* colim, const double* lre, const double* lim, double* out, cudaStream_t st);
+void launch_col_abs_sums(int64_t nnz, const int32_t* colind, const double* vals, double* colsum, cudaStream_t st);
+void launch_f32_to_f64(int64_t n, const float* a, double* b, cudaStream_t st);
+void launch_fill(int64_t n, double v, double* a, cudaStream_t st);
+void launch_check_csr(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind, int* bad,
+                      cudaStream_t st);
+
+}  // namespace rks

@@ -1,0 +1,315 @@
+"""Python binding of librks (ctypes): argument marshalling only.
+
+Every computation happens in the C ABI declared in ``include/rks.h`` (CUDA
+kernels for sm_103a plus the host-side small dense step).  PyTorch is used
+only to hold device buffers and to provide streams.  If ``librks.so`` has not
+been built, loading fails with an error: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librks.so")
+
+WHICH = {"LM": 0, "SM": 1, "LR": 2, "SR": 3}
+STATUS = {0: "RKS_OK", -1: "RKS_EINVAL", -2: "RKS_ENOMEM", -3: "RKS_ECUDA", -4: "RKS_ENOCONV",
+          -5: "RKS_EBREAKDOWN", -6: "RKS_ENAN", -7: "RKS_ESTATE", -8: "RKS_EDENSE"}
+RKS_OK, RKS_EINVAL, RKS_ENOCONV = 0, -1, -4
+
+
+class RKSError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({strerror(code)})")
+
+
+class Opts(C.Structure):
+    _fields_ = [("zeta", C.c_int), ("maxit", C.c_int), ("lock", C.c_int), ("mem_device", C.c_int),
+                ("stream", C.c_void_p), ("u1", C.c_void_p), ("eta_lock", C.c_double),
+                ("max_restarts", C.c_int), ("profile", C.c_int)]
+
+
+KCLASSES = ("spmv_sketch", "ls", "update_sketch", "finish", "restart", "other")
+
+
+class Stats(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 6), ("ms", C.c_double * 6), ("bytes", C.c_double * 6),
+                ("flops", C.c_double * 6), ("host_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        out = {name: {"launches": self.launches[i], "ms": self.ms[i], "bytes": self.bytes[i],
+                      "flops": self.flops[i]} for i, name in enumerate(KCLASSES)}
+        out["host_ms"] = self.host_ms
+        out["launches_total"] = int(sum(self.launches))
+        return out
+
+
+class Info(C.Structure):
+    _fields_ = [("nconv", C.c_int), ("nlocked", C.c_int), ("restarts", C.c_int),
+                ("nmatvec", C.c_int64), ("converged", C.c_int), ("max_est", C.c_double),
+                ("max_resid", C.c_double), ("t_solve_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+
+
+def lib() -> C.CDLL:
+    """Load librks.so (built by ``paper_2508_05400_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"librks.so is not built ({LIB_PATH}); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        L.rks_opts_default.argtypes = [C.POINTER(Opts)]
+        L.rks_opts_default.restype = None
+        L.rks_strerror.argtypes = [C.c_int]
+        L.rks_strerror.restype = C.c_char_p
+        L.rks_create.argtypes = [C.POINTER(_P), C.c_int64, _P, _P, _P, C.c_int, C.c_int, C.c_int,
+                                 C.c_int, C.c_int, C.c_double, C.c_uint64, C.POINTER(Opts)]
+        L.rks_create.restype = C.c_int
+        L.rks_solve.argtypes = [_P, C.POINTER(Info)]
+        L.rks_solve.restype = C.c_int
+        L.rks_get_schur.argtypes = [_P, _P, _P, _P]
+        L.rks_get_schur.restype = C.c_int
+        L.rks_get_eigpairs.argtypes = [_P, _P, _P, _P, _P]
+        L.rks_get_eigpairs.restype = C.c_int
+        L.rks_get_estimates.argtypes = [_P, _P]
+        L.rks_get_estimates.restype = C.c_int
+        L.rks_get_krylov.argtypes = [_P, C.POINTER(C.c_int), _P, _P, _P]
+        L.rks_get_krylov.restype = C.c_int
+        L.rks_get_stats.argtypes = [_P, C.POINTER(Stats)]
+        L.rks_get_stats.restype = C.c_int
+        L.rks_nkept.argtypes = [_P]
+        L.rks_nkept.restype = C.c_int
+        L.rks_norm1.argtypes = [_P]
+        L.rks_norm1.restype = C.c_double
+        L.rks_destroy.argtypes = [_P]
+        L.rks_destroy.restype = None
+        L.rks_sketch_pairs.argtypes = [C.c_int64, C.c_int, C.c_int, C.c_uint64, _P, _P, _P]
+        L.rks_sketch_pairs.restype = C.c_int
+        L.rks_sketch_apply.argtypes = [C.c_int64, C.c_int, C.c_int, C.c_uint64, _P, _P, _P]
+        L.rks_sketch_apply.restype = C.c_int
+        L.rks_host_ordered_schur.argtypes = [C.c_int, _P, C.c_int, C.c_int, _P, _P]
+        L.rks_host_ordered_schur.restype = C.c_int
+        L.rks_host_quasi_eig.argtypes = [C.c_int, _P, _P, _P, _P, _P]
+        L.rks_host_quasi_eig.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().rks_strerror(code).decode()
+
+
+def _check(code: int, where: str, ok=(RKS_OK,)):
+    if code not in ok:
+        raise RKSError(code, where)
+    return code
+
+
+def _ptr(a) -> int | None:
+    """Address of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _host(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+def _fortran(shape) -> np.ndarray:
+    return np.zeros(shape, dtype=np.float64, order="F")
+
+
+class Solver:
+    """One rKS problem: ``rks_create`` on construction, ``rks_destroy`` on close.
+
+    Host mode (default): rowptr/colind/vals/u1 are numpy arrays.  Device mode
+    (``device=True``): they are CUDA tensors (torch) and results that are
+    n-dimensional are written into CUDA tensors the caller passes.
+    """
+
+    def __init__(self, n, rowptr, colind, vals, k, p, d, which="LM", tol=1e-10, seed=0, *,
+                 zeta=8, maxit=1000, lock=True, u1=None, eta_lock=0.0, max_restarts=0,
+                 device=False, stream=None, profile=False):
+        L = lib()
+        self.n, self.k, self.p, self.d = int(n), int(k), int(p), int(d)
+        self.device = bool(device)
+        if device:
+            self._keep = (rowptr, colind, vals, u1)
+            vdt = 0 if str(vals.dtype).endswith("float64") else 1
+        else:
+            rowptr = _host(rowptr, np.int32)
+            colind = _host(colind, np.int32)
+            vals = np.ascontiguousarray(vals)
+            if vals.dtype not in (np.float64, np.float32):
+                vals = vals.astype(np.float64)
+            vdt = 0 if vals.dtype == np.float64 else 1
+            if u1 is not None:
+                u1 = _host(u1, np.float64)
+            self._keep = (rowptr, colind, vals, u1)
+        o = Opts()
+        L.rks_opts_default(C.byref(o))
+        o.zeta, o.maxit, o.lock, o.mem_device = int(zeta), int(maxit), int(bool(lock)), int(device)
+        o.stream = stream
+        o.u1 = _ptr(u1)
+        o.eta_lock = float(eta_lock)
+        o.max_restarts = int(max_restarts)
+        o.profile = int(bool(profile))
+        h = _P()
+        _check(L.rks_create(C.byref(h), self.n, _ptr(rowptr), _ptr(colind), _ptr(vals), vdt,
+                            self.k, self.p, self.d, WHICH[which] if isinstance(which, str) else int(which),
+                            float(tol), int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(o)), "rks_create")
+        self._h = h
+
+    @classmethod
+    def from_csr(cls, A, k, p, d, **kw):
+        """From an ``inputs.CSR`` (host arrays)."""
+        return cls(A.n, A.rowptr, A.colind, A.vals, k, p, d, **kw)
+
+    def solve(self, allow_noconv=True) -> dict:
+        info = Info()
+        rc = lib().rks_solve(self._h, C.byref(info))
+        _check(rc, "rks_solve", ok=(RKS_OK, RKS_ENOCONV) if allow_noconv else (RKS_OK,))
+        out = info.as_dict()
+        out["status"] = STATUS.get(rc, rc)
+        return out
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(lib().rks_get_stats(self._h, C.byref(st)), "rks_get_stats")
+        return st.as_dict()
+
+    @property
+    def nkept(self) -> int:
+        return lib().rks_nkept(self._h)
+
+    @property
+    def norm1(self) -> float:
+        return lib().rks_norm1(self._h)
+
+    def schur(self, U_out=None):
+        """(T, U, b) of the decomposition A U = U T + u b^T (U on host unless U_out given)."""
+        kk = self.nkept
+        T = _fortran((kk, kk))
+        b = np.zeros(kk)
+        U = U_out if U_out is not None else _fortran((self.n, kk))
+        _check(lib().rks_get_schur(self._h, T.ctypes.data, _ptr(U), b.ctypes.data), "rks_get_schur")
+        return T, U, b
+
+    def eigpairs(self, X_out=None, want_vectors=True):
+        """(lam complex[kk], X real-packed n x kk or None, resid[kk])."""
+        kk = self.nkept
+        lre, lim, res = np.zeros(kk), np.zeros(kk), np.zeros(kk)
+        X = None
+        if want_vectors:
+            X = X_out if X_out is not None else _fortran((self.n, kk))
+        _check(lib().rks_get_eigpairs(self._h, lre.ctypes.data, lim.ctypes.data, _ptr(X),
+                                      res.ctypes.data), "rks_get_eigpairs")
+        return lre + 1j * lim, X, res
+
+    def estimates(self) -> np.ndarray:
+        e = np.zeros(self.nkept)
+        _check(lib().rks_get_estimates(self._h, e.ctypes.data), "rks_get_estimates")
+        return e
+
+    def krylov(self):
+        """(U, S, H) of the current sketch-orthonormal Krylov decomposition."""
+        m = self.k + self.p
+        U = _fortran((self.n, m + 1))
+        S = _fortran((self.d, m + 1))
+        H = _fortran((m + 1, m))
+        nc = C.c_int()
+        Hbuf = np.zeros((m + 1) * m)
+        _check(lib().rks_get_krylov(self._h, C.byref(nc), U.ctypes.data, S.ctypes.data,
+                                    Hbuf.ctypes.data), "rks_get_krylov")
+        j = nc.value
+        H = Hbuf[: j * (j - 1)].reshape((j, j - 1), order="F")
+        return U[:, :j], S[:, :j], H
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rks_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def unpack_eigvecs(lam: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """Complex eigenvectors from the LAPACK dgeev real packing."""
+    kk = lam.size
+    Z = np.zeros((X.shape[0], kk), dtype=complex)
+    j = 0
+    while j < kk:
+        if lam[j].imag > 0 and j + 1 < kk:
+            Z[:, j] = X[:, j] + 1j * X[:, j + 1]
+            Z[:, j + 1] = X[:, j] - 1j * X[:, j + 1]
+            j += 2
+        else:
+            Z[:, j] = X[:, j]
+            j += 1
+    return Z
+
+
+def sketch_pairs(n: int, d: int, zeta: int, seed: int):
+    """All (row, sign) pairs of Omega from the device hash, as numpy arrays (n, zeta)."""
+    import torch
+    rows = torch.empty(n * zeta, dtype=torch.int32, device="cuda")
+    signs = torch.empty(n * zeta, dtype=torch.int8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().rks_sketch_pairs(n, d, zeta, seed, rows.data_ptr(), signs.data_ptr(), stream),
+           "rks_sketch_pairs")
+    torch.cuda.synchronize()
+    return rows.cpu().numpy().reshape(n, zeta), signs.cpu().numpy().reshape(n, zeta)
+
+
+def sketch_apply(x, d: int, zeta: int, seed: int):
+    """z = Omega x on the device for a CUDA float64 tensor x."""
+    import torch
+    z = torch.empty(d, dtype=torch.float64, device=x.device)
+    stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().rks_sketch_apply(x.numel(), d, zeta, seed, x.data_ptr(), z.data_ptr(), stream),
+           "rks_sketch_apply")
+    return z
+
+
+def host_ordered_schur(B: np.ndarray, which: str, nsort: int):
+    m = B.shape[0]
+    Bf = np.asfortranarray(B, dtype=np.float64)
+    T, Q = _fortran((m, m)), _fortran((m, m))
+    _check(lib().rks_host_ordered_schur(m, Bf.ctypes.data, WHICH[which], nsort, T.ctypes.data,
+                                        Q.ctypes.data), "rks_host_ordered_schur")
+    return T, Q
+
+
+def host_quasi_eig(T: np.ndarray):
+    n = T.shape[0]
+    Tf = np.asfortranarray(T, dtype=np.float64)
+    lre, lim = np.zeros(n), np.zeros(n)
+    Yr, Yi = _fortran((n, n)), _fortran((n, n))
+    _check(lib().rks_host_quasi_eig(n, Tf.ctypes.data, lre.ctypes.data, lim.ctypes.data,
+                                    Yr.ctypes.data, Yi.ctypes.data), "rks_host_quasi_eig")
+    return lre + 1j * lim, Yr + 1j * Yi

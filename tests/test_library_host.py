@@ -1,0 +1,95 @@
+"""CPU-side tests of librks: it builds, loads, exports the ABI, validates
+arguments, and its host-side dense step (Algorithm 1 contraction) agrees with
+the oracle's LAPACK-based ordered Schur form.  No GPU is touched."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import rks as R
+from paper_2508_05400_gb300 import build as B
+from paper_2508_05400_gb300 import rks as K
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return K.lib()
+
+
+def _declared_symbols():
+    hdr = open(os.path.join(ROOT, "include", "rks.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(rks_[a-z0-9_]+)\s*\(", hdr)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared_symbols()
+    assert "rks_create" in names and "rks_solve" in names and len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_strerror_and_defaults(lib):
+    for code in K.STATUS:
+        assert K.strerror(code)
+    o = K.Opts()
+    lib.rks_opts_default(o)
+    assert (o.zeta, o.maxit, o.lock, o.mem_device, o.max_restarts) == (8, 1000, 1, 0, 0)
+
+
+@pytest.mark.parametrize("kw", [dict(k=0), dict(p=1), dict(d=5), dict(tol=0.0), dict(which=7),
+                                dict(n_override=3), dict(zeta=40)])
+def test_create_rejects_bad_arguments_before_any_device_call(lib, kw):
+    from paper_2508_05400_gb300 import inputs as I
+    A = I.toeplitz_tridiag(50)
+    args = dict(k=4, p=8, d=40, tol=1e-8, which=0, zeta=4)
+    n_override = kw.pop("n_override", None)
+    args.update(kw)
+    o = K.Opts()
+    lib.rks_opts_default(o)
+    o.zeta = args["zeta"]
+    h = K._P()
+    rc = lib.rks_create(h, n_override or A.n, A.rowptr.ctypes.data, A.colind.ctypes.data,
+                        A.vals.ctypes.data, 0, args["k"], args["p"], args["d"], args["which"],
+                        args["tol"], 0, o)
+    assert rc == K.RKS_EINVAL
+    assert not h.value
+
+
+@pytest.mark.parametrize("which", ["LM", "SM", "LR", "SR"])
+def test_host_ordered_schur_matches_oracle(lib, which):
+    rng = np.random.default_rng(7)
+    for m in (4, 17, 40, 120):
+        Bm = rng.standard_normal((m, m))
+        T, Q = K.host_ordered_schur(Bm, which, 12)
+        To, Qo = R.ordered_schur(Bm, which, 12)
+        assert np.linalg.norm(Q @ T @ Q.T - Bm) < 1e-13 * m * np.linalg.norm(Bm)
+        assert np.linalg.norm(Q.T @ Q - np.eye(m)) < 1e-13 * m
+        assert np.all(np.tril(T, -2) == 0)
+        lam = np.array([R.block_eigenvalue(T, s, z) for s, z in R.schur_blocks(T)])
+        lamo = np.array([R.block_eigenvalue(To, s, z) for s, z in R.schur_blocks(To)])
+        nb = min(12, lam.size, lamo.size)
+        assert np.allclose(lam[:nb], lamo[:nb], atol=1e-10 * np.abs(lamo).max())
+        # same leading invariant subspace as the oracle's (up to rotation)
+        kcols = sum(z for _, z in R.schur_blocks(T)[:nb])
+        if kcols == sum(z for _, z in R.schur_blocks(To)[:nb]):
+            sv = np.linalg.svd(Q[:, :kcols].T @ Qo[:, :kcols], compute_uv=False)
+            assert sv.min() > 1 - 1e-8
+
+
+def test_host_quasi_eig_matches_scipy(lib):
+    import scipy.linalg as sla
+    rng = np.random.default_rng(3)
+    T, _ = K.host_ordered_schur(rng.standard_normal((25, 25)), "LR", 25)
+    lam, Y = K.host_quasi_eig(T)
+    assert np.linalg.norm(T @ Y - Y * lam) < 1e-12 * np.linalg.norm(T)
+    assert np.allclose(np.linalg.norm(Y, axis=0), 1.0)
+    assert np.allclose(np.sort_complex(lam), np.sort_complex(sla.eigvals(T)), atol=1e-12)
+    # pairs come Im > 0 first
+    for j in range(24):
+        if lam[j].imag > 0:
+            assert np.isclose(lam[j + 1], lam[j].conj())
