@@ -119,8 +119,9 @@ def cpu_sample(P, u1, restarts: int = 1) -> dict:
     """The FP64 oracle on the host cores: initial expansion + ``restarts`` cycles."""
     from oracle import rks as R
     t0 = time.perf_counter()
+    o = P.solver_opts()
     res = R.rks(P.A.to_scipy(), P.k, P.p, P.d, u1, zeta=P.zeta, seed=P.omega_seed, which=P.which,
-                tol=P.tol, max_restarts=restarts)
+                tol=o["tol"], eta_lock=o.get("eta_lock"), conv=o["conv"], max_restarts=restarts)
     dt = time.perf_counter() - t0
     return {"seconds": dt, "nmatvec": res.nmatvec, "restarts": res.restarts}
 
@@ -179,9 +180,9 @@ def run_ours(args) -> None:
     d_colind = torch.from_numpy(A.colind).to(dev)
     d_vals = torch.from_numpy(A.vals).to(dev)
     d_u1 = torch.from_numpy(u1).to(dev)
-    solver = rks.Solver(A.n, d_rowptr, d_colind, d_vals, P.k, P.p, P.d, which=P.which, tol=P.tol,
+    solver = rks.Solver(A.n, d_rowptr, d_colind, d_vals, P.k, P.p, P.d, which=P.which,
                         seed=P.omega_seed, zeta=P.zeta, u1=d_u1, device=True,
-                        stream=stream.cuda_stream, profile=True)
+                        stream=stream.cuda_stream, profile=True, prec=args.prec, **P.solver_opts())
     X_dev = torch.empty((P.k + 1, A.n), dtype=torch.float64, device=dev)
 
     def step():
@@ -252,17 +253,19 @@ def run_ours(args) -> None:
     h_X = torch.empty((P.k + 1, A.n), dtype=torch.float64).pin_memory()
     e2e_times = []
     barrier()
-    for _ in range(args.steps):
+    for _ in range(0 if args.no_e2e else args.steps):
         t0 = time.perf_counter()
-        with rks.Solver(A.n, h_rowptr, h_colind, h_vals, P.k, P.p, P.d, which=P.which, tol=P.tol,
-                        seed=P.omega_seed, zeta=P.zeta, u1=h_u1, stream=stream.cuda_stream) as s2:
+        with rks.Solver(A.n, h_rowptr, h_colind, h_vals, P.k, P.p, P.d, which=P.which,
+                        seed=P.omega_seed, zeta=P.zeta, u1=h_u1, stream=stream.cuda_stream,
+                        prec=args.prec, **P.solver_opts()) as s2:
             s2.solve(allow_noconv=False)
             s2.eigpairs(X_out=h_X)
             kk = s2.nkept
         e2e_times.append((time.perf_counter() - t0) * 1e3)
     barrier()
-    e2e_ms = statistics.mean(e2e_times)
-    if world > 1:
+    e2e_ms = statistics.mean(e2e_times) if e2e_times else None
+    kk = P.k
+    if world > 1 and e2e_ms is not None:
         t = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
@@ -272,10 +275,11 @@ def run_ours(args) -> None:
     info = infos[-1]
     line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.prec == "fp64" else "df64 (fp32 pair, 48-bit significand; fp64 sketch/LS/Schur/residuals)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "k": P.k, "p": P.p, "d": P.d,
-                       "zeta": P.zeta, "parallelism": f"replicas{world}",
+                       "zeta": P.zeta, "prec": args.prec, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (basis 648 MB, A 80 MB)"},
             "roofline": roofline,
             "spmv_rgs_gbs": path_bytes / (path_ms * 1e-3) / 1e9 if path_ms else None,
@@ -311,6 +315,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--prec", default="df", choices=["df", "fp64"],
+                    help="arithmetic of the n-dimensional work (see include/rks.h)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -71,7 +71,32 @@ typedef struct {
                           -1: only the initial expansion of Algorithm 1 */
   int profile;         /* 1: time every kernel launch with CUDA events on the
                           context's stream (see rks_get_stats); default 0 */
+  int conv;            /* convergence scale, RKS_CONV_EIG (default) or
+                          RKS_CONV_NORM1, see below */
+  int prec;            /* arithmetic of the n-dimensional work:
+                          RKS_PREC_DF (default): basis and matrix values stored
+                          as float pairs (hi + lo, 48-bit significand, 8 bytes),
+                          products and sums by error-free transformations on the
+                          FP32 pipes; RKS_PREC_FP64: native FP64.  The sketch
+                          sums, the small dense work and the final residuals are
+                          FP64 in both. */
+  double verify;       /* > 0: after convergence, check the FP64 residuals
+                          ||A x - l x|| / (||A||_1 ||x||) <= verify; if one
+                          fails, divide tol and eta_lock by 4 and continue the
+                          restarts from the current decomposition (bounded
+                          by maxit); 0: no check (default) */
 } rks_opts;
+
+enum { RKS_PREC_DF = 0, RKS_PREC_FP64 = 1 };
+
+/* Convergence test on the Ritz pairs (lambda_i, y_i) of T, ||y_i|| = 1:
+ *  RKS_CONV_EIG   |b^T y_i| / |lambda_i| <= tol   (Eq. 4.8, Sec. 5.1), and
+ *                 locking when |b_i| <= eta_lock * |lambda_i|;
+ *  RKS_CONV_NORM1 |b^T y_i| / ||A||_1 <= tol      (the non-relative bound of
+ *                 the Sec. 4.1 remark, ||Ax - lx|| / ||x|| ~ |b^T y|, scaled
+ *                 by ||A||_1), and locking when |b_i| <= eta_lock * ||A||_1
+ *                 (the absolute threshold of Eq. 4.21 with eta = eta_lock ||A||_1). */
+enum { RKS_CONV_EIG = 0, RKS_CONV_NORM1 = 1 };
 
 typedef struct {
   int nconv;           /* number of pairs whose estimate is <= tol */
@@ -164,6 +189,12 @@ int rks_get_estimates(rks_ctx* c, double* est);
  * Array pointers may be NULL; sizes must allow m + 1 columns.  Host
  * pointers only. */
 int rks_get_krylov(rks_ctx* c, int* ncols_out, double* U, double* S, double* H);
+
+/* Convergence history of the last rks_solve: after restart i, hist[i] =
+ * max over the Ritz pairs of the convergence quantity of opts.conv and
+ * nlock[i] = locked vectors.  Writes min(cap, restarts) entries and returns
+ * their number (negative on error).  Either pointer may be NULL. */
+int rks_get_history(const rks_ctx* c, double* hist, int* nlock, int cap);
 
 /* ||A||_1 (max column sum of |a_ij|), computed at rks_create. */
 double rks_norm1(const rks_ctx* c);

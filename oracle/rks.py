@@ -139,16 +139,19 @@ def truncation_size(T: np.ndarray, want: int) -> int:
     return size
 
 
-def ritz(T: np.ndarray, b: np.ndarray, which: str):
-    """Ritz values, unit-norm eigenvectors y of T, and the estimates of Eq. 4.8.
+def ritz(T: np.ndarray, b: np.ndarray, which: str, norm_a: float | None = None):
+    """Ritz values, unit-norm eigenvectors y of T, and the residual estimates.
 
-    estimate_i = |b^T y_i| / |lambda_i|, sorted by key (best first).
+    estimate_i = |b^T y_i| / |lambda_i| (Eq. 4.8), or |b^T y_i| / ||A||_1 (the
+    non-relative bound of the Sec. 4.1 remark scaled by ||A||_1) when
+    ``norm_a`` is given; sorted by key (best first).
     """
     lam, Y = sla.eig(T)
     Y = Y / np.linalg.norm(Y, axis=0)
     order = np.argsort(key(lam, which), kind="stable")
     lam, Y = lam[order], Y[:, order]
-    est = np.abs(b @ Y) / np.maximum(np.abs(lam), np.finfo(float).tiny)
+    den = norm_a if norm_a is not None else np.maximum(np.abs(lam), np.finfo(float).tiny)
+    est = np.abs(b @ Y) / den
     return lam, Y, est
 
 
@@ -279,10 +282,12 @@ def contract(st: RKSState, k: int, which: str):
     return Ta, bk, Qk
 
 
-def lock(st: RKSState, k: int, eta_lock: float) -> int:
+def lock(st: RKSState, k: int, eta_lock: float, norm_a: float | None = None) -> int:
     """Sec. 4.4 locking: move the leading active blocks with small |b| to U_q.
 
-    Returns the number of vectors locked now.
+    The threshold is eta_lock * |lambda| of the block, or the absolute
+    threshold of Eq. 4.21 with eta = eta_lock * ||A||_1 when ``norm_a`` is
+    given.  Returns the number of vectors locked now.
     """
     ja = st.ja
     Ta, b = st.Ba[:ja, :], st.Ba[ja, :]
@@ -292,7 +297,8 @@ def lock(st: RKSState, k: int, eta_lock: float) -> int:
         if st.q + r + z > k:
             break
         lam = abs(block_eigenvalue(Ta, s, z))
-        if np.all(np.abs(b[s:s + z]) <= eta_lock * max(lam, scale)):
+        thr = eta_lock * (norm_a if norm_a is not None else max(lam, scale))
+        if np.all(np.abs(b[s:s + z]) <= thr):
             r = s + z
         else:
             break
@@ -365,13 +371,17 @@ def true_residuals(A, X: np.ndarray, lam: np.ndarray):
 def rks(A, k: int, p: int, d: int, u1: np.ndarray, *, zeta: int = 8, seed: int = 0,
         which: str = "LM", tol: float = 1e-10, lock_vectors: bool = True,
         eta_lock: float | None = None, maxit: int = 1000, Omega=None,
-        whiten_tol: float = 1e-10, max_restarts: int | None = None) -> RKSResult:
+        whiten_tol: float = 1e-10, max_restarts: int | None = None,
+        conv: str = "eig") -> RKSResult:
     """Algorithm 1 (rKS) with the deflation of Sec. 4.
 
     ``max_restarts`` (if given) stops after that many contractions whatever the
-    estimates say (the paper's fixed-iteration runs, Sec. 5).
+    estimates say (the paper's fixed-iteration runs, Sec. 5).  ``conv`` picks
+    the convergence quantity: "eig" (|b^T y|/|lambda|, Eq. 4.8) or "norm1"
+    (|b^T y|/||A||_1, see ``ritz``), and the matching locking threshold.
     """
     A = sp.csr_matrix(A, dtype=np.float64)
+    norm_a = norm1(A) if conv == "norm1" else None
     n = A.shape[0]
     m = k + p
     if Omega is None:
@@ -392,9 +402,9 @@ def rks(A, k: int, p: int, d: int, u1: np.ndarray, *, zeta: int = 8, seed: int =
             if np.linalg.norm(G - np.eye(ja)) > whiten_tol:
                 whiten(st)
         if lock_vectors:
-            lock(st, k, eta_lock)
+            lock(st, k, eta_lock, norm_a)
         T, b, _ = full_T(st)
-        lam, Y, est = ritz(T, b, which)          # Alg. 1, Ritz pairs + Eq. 4.8
+        lam, Y, est = ritz(T, b, which, norm_a)  # Alg. 1, Ritz pairs + Eq. 4.8
         history.append(float(est.max()) if est.size else 0.0)
         if st.q >= k or np.all(est <= tol):
             converged = True
@@ -403,7 +413,7 @@ def rks(A, k: int, p: int, d: int, u1: np.ndarray, *, zeta: int = 8, seed: int =
             break
         extend(st, m - st.q)                     # Alg. 1, extension
     T, b, U = full_T(st)
-    lam, Y, est = ritz(T, b, which)
+    lam, Y, est = ritz(T, b, which, norm_a)
     X = U @ Y
     res, rq = true_residuals(A, X, lam)
     return RKSResult(eigvals=lam, X=X, resid=res, est=est, lam_rq=rq, T=T, U=U, b=b,

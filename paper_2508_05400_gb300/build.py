@@ -18,16 +18,16 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 CXX = os.environ.get("CXX", "g++")
 
-SOURCES = ["kernels.cu", "api.cu", "dense.cpp"]
+SOURCES = ["kernels.cu", "kernels_df.cu", "api.cu", "dense.cpp"]
 
 
 def _cmd(src: str) -> list[str]:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     path = os.path.join(CSRC, src)
     if src.endswith(".cu"):
-        return [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+        return [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
                 "-c", path, "-o", obj]
-    return [CXX, "-O2", "-fPIC", "-std=c++17", "-c", path, "-o", obj]
+    return [CXX, "-O3", "-fPIC", "-std=c++17", "-c", path, "-o", obj]
 
 
 def _stale() -> bool:

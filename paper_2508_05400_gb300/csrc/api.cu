@@ -59,9 +59,22 @@ struct rks_ctx {
   double* rsum = nullptr;
   int* pcol = nullptr;
   double* plam = nullptr;
+  // double-float path (opts.prec == RKS_PREC_DF)
+  int prec = RKS_PREC_DF;
+  rks::CsrDF A2;
+  float2* vals2 = nullptr;
+  float2* U2 = nullptr;
+  float2* S2 = nullptr;
+  float2* nrs = nullptr;
+  float2* sj = nullptr;
+  float2* Q2 = nullptr;
+  double* rprev = nullptr;
+  double* znorm = nullptr;
+  double* tmp64 = nullptr;
   // host state
   double norm1 = 0;
   std::vector<double> S_h, cs_h, coef_h, Ba, Tqq, Tqa;
+  std::vector<float2> S2_h;
   int q = 0, ja = 0;
   int64_t nmatvec = 0;
   int restarts = 0;
@@ -75,6 +88,8 @@ struct rks_ctx {
   bool solved = false;
   int kk = 0;
   std::vector<double> Tfull, bfull, lre, lim, est, resid;
+  std::vector<double> hist;
+  std::vector<int> hist_lock;
   std::vector<cd> Y;
 };
 
@@ -171,9 +186,39 @@ int flag_status(int f) {
   return RKS_OK;
 }
 
+// Algorithm 2 in double-float: three kernels per step (see kernels_df.cu).
+void expand_df_launches(rks_ctx* c, int c0) {
+  const double n = (double)c->n, P = 8.0;
+  const double spmv_bytes = (double)c->nnz * (P + 4) + 4.0 * (n + 1) + 2 * P * n;
+  for (int j = c0; j < c->m; ++j) {
+    const int col = j + 1;
+    int s = prof_begin(c, RKS_K_SPMV);
+    rks::launch_df_spmv_sketch(c->A2, c->U2 + (int64_t)j * c->ldu, c->U2 + (int64_t)col * c->ldu, c->d, c->zeta,
+                               c->seed, c->z_raw, c->flag, c->stream);
+    prof_end(c, s, RKS_K_SPMV, 1, spmv_bytes, 2.0 * c->nnz);
+    s = prof_begin(c, RKS_K_LS);
+    rks::launch_df_small(j, c->d, c->zscale, j > c0 ? 1 : 0, 1, c->s_raw, c->z_raw, c->S, c->S2, c->colscale,
+                         c->rprev, c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->flag, c->stream);
+    prof_end(c, s, RKS_K_LS, 1, 3.0 * P * c->d * col, 6.0 * c->d * col);
+    s = prof_begin(c, RKS_K_UPDATE);
+    rks::launch_df_update_sketch(c->n, c->U2, c->ldu, col, c->nrs, c->sj, c->d, c->zeta, c->seed, c->s_raw,
+                                 c->flag, c->stream);
+    prof_end(c, s, RKS_K_UPDATE, 1, (col + 2) * P * n, 2.0 * n * col);
+    ++c->nmatvec;
+  }
+  int s = prof_begin(c, RKS_K_FINISH);
+  rks::launch_df_small(c->m, c->d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale, c->rprev,
+                       c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->flag, c->stream);
+  prof_end(c, s, RKS_K_FINISH, 1, 3.0 * P * c->d, 2.0 * c->d);
+}
+
 // Algorithm 2: extend from the last vector at column q+ja to column m.
 int expand(rks_ctx* c) {
   const int c0 = c->q + c->ja;
+  if (c->prec == RKS_PREC_DF) {
+    expand_df_launches(c, c0);
+  } else
+  {
   const double n = (double)c->n, P = sizeof(double);
   const double spmv_bytes = (double)c->nnz * (P + 4) + 4.0 * (n + 1) + 2 * P * n;
   for (int j = c0; j < c->m; ++j) {
@@ -194,6 +239,7 @@ int expand(rks_ctx* c) {
                        c->flag, c->stream);
     prof_end(c, s, RKS_K_FINISH, 1, 3.0 * P * c->d, 2.0 * c->d);
     ++c->nmatvec;
+  }
   }
   int rc = launch_err();
   if (rc) return rc;
@@ -359,9 +405,20 @@ int contract(rks_ctx* c) {
   std::vector<double> Qp((size_t)ma * ka);
   for (int j = 0; j < ka; ++j)
     for (int l = 0; l < ma; ++l) Qp[l + (size_t)j * ma] = c->cs_h[q + l] * Qk[l + (size_t)j * ma];
-  CK(cudaMemcpyAsync(c->Qd, Qp.data(), Qp.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   int ps = prof_begin(c, RKS_K_RESTART);
-  rks::launch_rows_gemm(c->n, c->U, c->ldu, q, ma, c->Qd, ka, c->U, c->ldu, q, m, c->stream);
+  if (c->prec == RKS_PREC_DF) {
+    std::vector<float2> Q2h(Qp.size());
+    for (size_t t = 0; t < Qp.size(); ++t) {
+      float h = (float)Qp[t];
+      Q2h[t] = make_float2(h, (float)(Qp[t] - (double)h));
+    }
+    CK(cudaMemcpyAsync(c->Q2, Q2h.data(), Q2h.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
+    rks::launch_df_rows_gemm(c->n, c->U2, c->ldu, q, ma, c->Q2, ka, q, m, c->stream);
+    CK(cudaStreamSynchronize(c->stream));   // Q2h is a host temporary
+  } else {
+    CK(cudaMemcpyAsync(c->Qd, Qp.data(), Qp.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    rks::launch_rows_gemm(c->n, c->U, c->ldu, q, ma, c->Qd, ka, c->U, c->ldu, q, m, c->stream);
+  }
   prof_end(c, ps, RKS_K_RESTART, 1, (double)(ma + ka + 2) * sizeof(double) * c->n, 2.0 * c->n * ma * ka);
   int rc = launch_err();
   if (rc) return rc;
@@ -374,6 +431,14 @@ int contract(rks_ctx* c) {
   CK(cudaMemcpyAsync(c->colscale, c->cs_h.data(), c->cs_h.size() * sizeof(double), cudaMemcpyHostToDevice,
                      c->stream));
   CK(cudaMemcpyAsync(c->S, c->S_h.data(), c->S_h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (c->prec == RKS_PREC_DF) {
+    c->S2_h.resize(c->S_h.size());
+    for (size_t t = 0; t < c->S_h.size(); ++t) {
+      float h = (float)c->S_h[t];
+      c->S2_h[t] = make_float2(h, (float)(c->S_h[t] - (double)h));
+    }
+    CK(cudaMemcpyAsync(c->S2, c->S2_h.data(), c->S2_h.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
+  }
   // locking: leading active blocks with small |b| (relative to |lambda|)
   int r = 0;
   if (c->opts.lock) {
@@ -383,7 +448,8 @@ int contract(rks_ctx* c) {
     for (const auto& B : rks_dense::blocks(ka, Ta.data(), ka)) {
       if (q + r + B.size > c->k) break;
       double lam = std::hypot(B.re, B.im);
-      double thr = c->eta_lock * std::max(lam, 2.220446049250313e-16 * tn);
+      double scale = c->opts.conv == RKS_CONV_NORM1 ? c->norm1 : std::max(lam, 2.220446049250313e-16 * tn);
+      double thr = c->eta_lock * scale;
       bool ok = true;
       for (int t = 0; t < B.size; ++t) ok = ok && std::fabs(bk[B.start + t]) <= thr;
       if (!ok) break;
@@ -459,7 +525,7 @@ void ritz(rks_ctx* c) {
       bty += c->bfull[i] * Y[i + (size_t)o * kk];
     }
     double al = std::hypot(lre[o], lim[o]);
-    c->est[t] = std::abs(bty) / std::max(al, 1e-300);
+    c->est[t] = std::abs(bty) / std::max(c->opts.conv == RKS_CONV_NORM1 ? c->norm1 : al, 1e-300);
   }
 }
 
@@ -496,7 +562,12 @@ int finalize(rks_ctx* c) {
   const int np = (int)col.size();
   CK(cudaMemcpyAsync(c->Qd, Yr.data(), Yr.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   int ps = prof_begin(c, RKS_K_OTHER);
-  rks::launch_rows_gemm(c->n, c->U, c->ldu, 0, kk, c->Qd, kk, c->X, c->ldu, 0, -1, c->stream);
+  if (c->prec == RKS_PREC_DF) {
+    rks::launch_df2d_cols(c->n, c->U2, c->ldu, c->AX, c->ldu, kk, c->stream);
+    rks::launch_rows_gemm(c->n, c->AX, c->ldu, 0, kk, c->Qd, kk, c->X, c->ldu, 0, -1, c->stream);
+  } else {
+    rks::launch_rows_gemm(c->n, c->U, c->ldu, 0, kk, c->Qd, kk, c->X, c->ldu, 0, -1, c->stream);
+  }
   rks::launch_spmm(c->A, c->X, c->ldu, c->AX, c->ldu, kk, c->stream);
   std::vector<int> pc(2 * np);
   std::vector<double> pv(2 * np);
@@ -529,6 +600,8 @@ void free_ctx(rks_ctx* c) {
   cudaFree(c->z_raw); cudaFree(c->s_raw); cudaFree(c->z1); cudaFree(c->r1); cudaFree(c->r); cudaFree(c->rs);
   cudaFree(c->coef); cudaFree(c->flag); cudaFree(c->Qd); cudaFree(c->u1);
   cudaFree(c->X); cudaFree(c->AX); cudaFree(c->rsum); cudaFree(c->pcol); cudaFree(c->plam);
+  cudaFree(c->vals2); cudaFree(c->U2); cudaFree(c->S2); cudaFree(c->nrs); cudaFree(c->sj); cudaFree(c->Q2);
+  cudaFree(c->rprev); cudaFree(c->znorm); cudaFree(c->tmp64);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -571,6 +644,8 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
   rks_opts_default(&o);
   if (opts) o = *opts;
   if (o.zeta == 0) o.zeta = 8;
+  if (o.conv != RKS_CONV_EIG && o.conv != RKS_CONV_NORM1) return RKS_EINVAL;
+  if (o.prec != RKS_PREC_DF && o.prec != RKS_PREC_FP64) return RKS_EINVAL;
   if (o.maxit <= 0) o.maxit = 1000;
   const int m = k + p;
   if (n <= 0 || !rowptr || !colind || !vals || k < 1 || p < 2 || (int64_t)m + 1 > n || d < m + 1 ||
@@ -582,7 +657,7 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
   rks_ctx* c = new (std::nothrow) rks_ctx();
   if (!c) return RKS_ENOMEM;
   c->n = n; c->k = k; c->p = p; c->m = m; c->d = d; c->zeta = o.zeta; c->which = which;
-  c->tol = tol; c->seed = seed; c->opts = o;
+  c->tol = tol; c->seed = seed; c->opts = o; c->prec = o.prec;
   c->eta_lock = o.eta_lock > 0 ? o.eta_lock : tol;
   c->zscale = 1.0 / std::sqrt((double)o.zeta);
   const cudaMemcpyKind kind = o.mem_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -642,7 +717,20 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
     if (c->norm1 == 0.0) c->norm1 = 1.0;
   }
   c->ldu = (n + 31) / 32 * 32;
-  if ((rc = dalloc(&c->U, (size_t)c->ldu * (m + 1))) || (rc = dalloc(&c->S, (size_t)d * (m + 1))) ||
+  if (c->prec == RKS_PREC_DF) {
+    if ((rc = dalloc(&c->U2, (size_t)c->ldu * (m + 1))) || (rc = dalloc(&c->vals2, c->nnz)) ||
+        (rc = dalloc(&c->S2, (size_t)d * (m + 1))) || (rc = dalloc(&c->nrs, m + 1)) || (rc = dalloc(&c->sj, 1)) ||
+        (rc = dalloc(&c->Q2, (size_t)(m + 1) * (m + 1))) || (rc = dalloc(&c->rprev, m + 1)) ||
+        (rc = dalloc(&c->znorm, 1)) || (rc = dalloc(&c->tmp64, n)))
+      return fail(rc);
+    rks::launch_d2df(c->nnz, c->vals, c->vals2, c->stream);
+    c->A2.n = n; c->A2.nnz = c->nnz; c->A2.rowptr = c->rowptr; c->A2.colind = c->colind; c->A2.vals = c->vals2;
+    if (rks::configure_df_kernels() != cudaSuccess) return fail(RKS_ECUDA);
+    if (rks::df_gemm_smem(m, k + 2) > 200 * 1024 || rks::df_small_smem(d, m + 1) > 200 * 1024) return fail(RKS_EINVAL);
+  } else if ((rc = dalloc(&c->U, (size_t)c->ldu * (m + 1)))) {
+    return fail(rc);
+  }
+  if ((rc = dalloc(&c->S, (size_t)d * (m + 1))) ||
       (rc = dalloc(&c->colscale, m + 1)) || (rc = dalloc(&c->z_raw, d)) || (rc = dalloc(&c->s_raw, d)) ||
       (rc = dalloc(&c->z1, d)) || (rc = dalloc(&c->r1, m + 1)) || (rc = dalloc(&c->r, m + 1)) ||
       (rc = dalloc(&c->rs, m + 1)) || (rc = dalloc(&c->coef, (size_t)(m + 1) * m)) ||
@@ -668,6 +756,8 @@ static int solve_impl(rks_ctx* c) {
   c->q = 0; c->ja = 0; c->nmatvec = 0; c->restarts = 0; c->kk = 0;
   std::memset(&c->stats, 0, sizeof(c->stats));
   c->evused = 0;
+  c->hist.clear();
+  c->hist_lock.clear();
   c->Ba.assign((size_t)(m + 1) * m, 0.0);
   c->Tqq.assign((size_t)(c->k + 2) * (c->k + 2), 0.0);
   c->Tqa.assign((size_t)(c->k + 2) * (m + 1), 0.0);
@@ -679,11 +769,22 @@ static int solve_impl(rks_ctx* c) {
   CK(cudaMemsetAsync(c->colscale, 0, (m + 1) * sizeof(double), c->stream));
   // start vector (Sec. 3.1, k = 0): u_1 = u~_1 / ||Omega u~_1||
   int ps = prof_begin(c, RKS_K_OTHER);
-  if (c->u1) CK(cudaMemcpyAsync(c->U, c->u1, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  else rks::launch_start_vector(c->n, c->seed + 1, c->U, c->stream);
-  rks::launch_sketch_vec(c->n, c->U, 1.0, d, c->zeta, c->seed, c->s_raw, c->flag, c->stream);
-  rks::launch_start_finish(d, c->zscale, c->s_raw, c->S, c->colscale, c->flag, c->stream);
-  prof_end(c, ps, RKS_K_OTHER, c->u1 ? 2 : 3, 0.0, 0.0);
+  if (c->prec == RKS_PREC_DF) {
+    const double* src = c->u1;
+    if (!src) { rks::launch_start_vector(c->n, c->seed + 1, c->tmp64, c->stream); src = c->tmp64; }
+    rks::launch_d2df(c->n, src, c->U2, c->stream);
+    rks::launch_df_sketch_vec(c->n, c->U2, d, c->zeta, c->seed, c->s_raw, c->flag, c->stream);
+    CK(cudaMemsetAsync(c->znorm, 0, sizeof(double), c->stream));
+    rks::launch_df_small(0, d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale, c->rprev, c->coef,
+                         m + 1, c->znorm, c->nrs, c->sj, c->flag, c->stream);
+    prof_end(c, ps, RKS_K_OTHER, c->u1 ? 3 : 4, 0.0, 0.0);
+  } else {
+    if (c->u1) CK(cudaMemcpyAsync(c->U, c->u1, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    else rks::launch_start_vector(c->n, c->seed + 1, c->U, c->stream);
+    rks::launch_sketch_vec(c->n, c->U, 1.0, d, c->zeta, c->seed, c->s_raw, c->flag, c->stream);
+    rks::launch_start_finish(d, c->zscale, c->s_raw, c->S, c->colscale, c->flag, c->stream);
+    prof_end(c, ps, RKS_K_OTHER, c->u1 ? 2 : 3, 0.0, 0.0);
+  }
   int rc = launch_err();
   if (rc) return rc;
   rc = expand(c);                      // Algorithm 1, initial expansion to m
@@ -691,6 +792,7 @@ static int solve_impl(rks_ctx* c) {
   if (c->opts.max_restarts < 0) { c->solved = true; return RKS_OK; }
   const int limit = c->opts.max_restarts > 0 ? std::min(c->opts.maxit, c->opts.max_restarts) : c->opts.maxit;
   bool converged = false;
+  const double tol0 = c->tol, eta0 = c->eta_lock;
   while (true) {
     auto h0 = std::chrono::steady_clock::now();
     rc = contract(c);                  // Schur, reorder, truncate, whiten, lock, restart
@@ -700,14 +802,41 @@ static int solve_impl(rks_ctx* c) {
     c->stats.host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
     double mx = 0.0;
     for (double e : c->est) mx = std::max(mx, e);
-    if (c->q >= c->k || mx <= c->tol) { converged = true; break; }
+    c->hist.push_back(mx);
+    c->hist_lock.push_back(c->q);
+    if (c->q >= c->k || mx <= c->tol) {
+      converged = true;
+      if (c->opts.verify > 0) {        // FP64 verification of the true residuals
+        rc = finalize(c);
+        if (rc) break;
+        double mr = 0.0;
+        for (double v : c->resid) mr = std::max(mr, v);
+        if (mr > c->opts.verify && c->q < c->k && c->restarts < limit) {
+          c->tol *= 0.25;
+          c->eta_lock *= 0.25;
+          converged = false;
+          rc = expand(c);
+          if (rc) break;
+          continue;
+        }
+      }
+      break;
+    }
     if (c->restarts >= limit) break;
     rc = expand(c);                    // Algorithm 2 from k to m
-    if (rc) return rc;
+    if (rc) break;
   }
+  c->tol = tol0;
+  c->eta_lock = eta0;
+  if (rc) return rc;
   rc = finalize(c);
   if (rc) return rc;
   c->solved = true;
+  if (converged && c->opts.verify > 0) {
+    double mr = 0.0;
+    for (double v : c->resid) mr = std::max(mr, v);
+    if (mr > c->opts.verify) converged = false;
+  }
   return converged ? RKS_OK : RKS_ENOCONV;
 }
 
@@ -742,6 +871,16 @@ int rks_solve(rks_ctx* c, rks_info* info) {
 
 int rks_nkept(const rks_ctx* c) { return c ? c->kk : 0; }
 
+int rks_get_history(const rks_ctx* c, double* hist, int* nlock, int cap) {
+  if (!c || cap < 0) return RKS_EINVAL;
+  int nh = std::min((int)c->hist.size(), cap);
+  for (int i = 0; i < nh; ++i) {
+    if (hist) hist[i] = c->hist[i];
+    if (nlock) nlock[i] = c->hist_lock[i];
+  }
+  return nh;
+}
+
 int rks_get_stats(const rks_ctx* c, rks_stats* out) {
   if (!c || !out) return RKS_EINVAL;
   *out = c->stats;
@@ -756,7 +895,12 @@ int rks_get_schur(rks_ctx* c, double* T, double* U, double* b) {
   if (T) std::memcpy(T, c->Tfull.data(), sizeof(double) * kk * kk);
   if (b) std::memcpy(b, c->bfull.data(), sizeof(double) * kk);
   if (U) {
-    CK(cudaMemcpy2DAsync(U, c->n * sizeof(double), c->U, c->ldu * sizeof(double), c->n * sizeof(double), kk,
+    const double* src = c->U;
+    if (c->prec == RKS_PREC_DF) {
+      rks::launch_df2d_cols(c->n, c->U2, c->ldu, c->AX, c->ldu, kk, c->stream);
+      src = c->AX;
+    }
+    CK(cudaMemcpy2DAsync(U, c->n * sizeof(double), src, c->ldu * sizeof(double), c->n * sizeof(double), kk,
                          c->opts.mem_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
@@ -790,10 +934,18 @@ int rks_get_krylov(rks_ctx* c, int* ncols_out, double* U, double* S, double* H) 
   if (!c->solved) return RKS_ESTATE;
   const int nc = c->q + c->ja + 1;
   if (ncols_out) *ncols_out = nc;
-  if (U) {
+  if (U && c->prec == RKS_PREC_DF) {
+    std::vector<float2> tmp((size_t)c->n * nc);
+    CK(cudaMemcpy2DAsync(tmp.data(), c->n * sizeof(float2), c->U2, c->ldu * sizeof(float2), c->n * sizeof(float2), nc,
+                         cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (size_t t = 0; t < tmp.size(); ++t) U[t] = (double)tmp[t].x + (double)tmp[t].y;
+  } else if (U) {
     CK(cudaMemcpy2DAsync(U, c->n * sizeof(double), c->U, c->ldu * sizeof(double), c->n * sizeof(double), nc,
                          cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+  }
+  if (U) {
     for (int j = 0; j < nc; ++j) {
       double s = c->cs_h[j];
       double* col = U + (size_t)j * c->n;

@@ -65,14 +65,32 @@ void apply_left(double* A, int lda, int r0, int len, int c0, int c1, const doubl
   }
 }
 
-// columns c0..c0+len-1 of A, rows r0..r1: A <- A (I - beta v v^T)
+// columns c0..c0+len-1 of A, rows r0..r1: A <- A (I - beta v v^T).
+// Column-major friendly: w = A v by columns, then A -= beta w v^T by columns.
 void apply_right(double* A, int lda, int c0, int len, int r0, int r1, const double* v, double beta) {
-  if (beta == 0.0) return;
-  for (int i = r0; i <= r1; ++i) {
-    double s = 0.0;
-    for (int j = 0; j < len; ++j) s += at(A, lda, i, c0 + j) * v[j];
-    s *= beta;
-    for (int j = 0; j < len; ++j) at(A, lda, i, c0 + j) -= s * v[j];
+  if (beta == 0.0 || r1 < r0) return;
+  if (len <= 3) {   // short reflectors (QR sweeps): row by row
+    for (int i = r0; i <= r1; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < len; ++j) s += at(A, lda, i, c0 + j) * v[j];
+      s *= beta;
+      for (int j = 0; j < len; ++j) at(A, lda, i, c0 + j) -= s * v[j];
+    }
+    return;
+  }
+  const int nr = r1 - r0 + 1;
+  thread_local std::vector<double> w;
+  w.assign(nr, 0.0);
+  double* wp = w.data();
+  for (int j = 0; j < len; ++j) {
+    const double vj = v[j];
+    const double* col = A + r0 + (size_t)(c0 + j) * lda;
+    for (int i = 0; i < nr; ++i) wp[i] += col[i] * vj;
+  }
+  for (int j = 0; j < len; ++j) {
+    const double f = beta * v[j];
+    double* col = A + r0 + (size_t)(c0 + j) * lda;
+    for (int i = 0; i < nr; ++i) col[i] -= wp[i] * f;
   }
 }
 

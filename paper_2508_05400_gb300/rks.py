@@ -30,7 +30,12 @@ class RKSError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("zeta", C.c_int), ("maxit", C.c_int), ("lock", C.c_int), ("mem_device", C.c_int),
                 ("stream", C.c_void_p), ("u1", C.c_void_p), ("eta_lock", C.c_double),
-                ("max_restarts", C.c_int), ("profile", C.c_int)]
+                ("max_restarts", C.c_int), ("profile", C.c_int), ("conv", C.c_int),
+                ("prec", C.c_int), ("verify", C.c_double)]
+
+
+CONV = {"eig": 0, "norm1": 1}
+PREC = {"df": 0, "fp64": 1}
 
 
 KCLASSES = ("spmv_sketch", "ls", "update_sketch", "finish", "restart", "other")
@@ -89,6 +94,8 @@ def lib() -> C.CDLL:
         L.rks_get_krylov.restype = C.c_int
         L.rks_get_stats.argtypes = [_P, C.POINTER(Stats)]
         L.rks_get_stats.restype = C.c_int
+        L.rks_get_history.argtypes = [_P, _P, _P, C.c_int]
+        L.rks_get_history.restype = C.c_int
         L.rks_nkept.argtypes = [_P]
         L.rks_nkept.restype = C.c_int
         L.rks_norm1.argtypes = [_P]
@@ -144,7 +151,7 @@ class Solver:
 
     def __init__(self, n, rowptr, colind, vals, k, p, d, which="LM", tol=1e-10, seed=0, *,
                  zeta=8, maxit=1000, lock=True, u1=None, eta_lock=0.0, max_restarts=0,
-                 device=False, stream=None, profile=False):
+                 device=False, stream=None, profile=False, conv="eig", verify=0.0, prec="df"):
         L = lib()
         self.n, self.k, self.p, self.d = int(n), int(k), int(p), int(d)
         self.device = bool(device)
@@ -169,6 +176,9 @@ class Solver:
         o.eta_lock = float(eta_lock)
         o.max_restarts = int(max_restarts)
         o.profile = int(bool(profile))
+        o.conv = CONV[conv]
+        o.verify = float(verify)
+        o.prec = PREC[prec]
         h = _P()
         _check(L.rks_create(C.byref(h), self.n, _ptr(rowptr), _ptr(colind), _ptr(vals), vdt,
                             self.k, self.p, self.d, WHICH[which] if isinstance(which, str) else int(which),
@@ -187,6 +197,14 @@ class Solver:
         out = info.as_dict()
         out["status"] = STATUS.get(rc, rc)
         return out
+
+    def history(self, cap: int = 100000):
+        """(max convergence quantity, locked count) after each restart."""
+        h = np.zeros(cap)
+        q = np.zeros(cap, dtype=np.int32)
+        nh = lib().rks_get_history(self._h, h.ctypes.data, q.ctypes.data, cap)
+        _check(min(nh, 0), "rks_get_history")
+        return h[:nh], q[:nh]
 
     def stats(self) -> dict:
         st = Stats()

@@ -72,15 +72,19 @@ def _oracle_expansion(A, m, d, zeta, u1):
     return st
 
 
+PRECS = ["df", "fp64"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("case", ["convdiff", "toeplitz2000"])
-def test_first_expansion_matches_oracle(case):
+def test_first_expansion_matches_oracle(case, prec):
     if case == "convdiff":
         A, k, p, d, zeta, tol_b = I.convdiff_2d(40, 37, 1.0, 20.0, 10.0), 6, 18, 64, 8, 1e-12
     else:   # the non-symmetric Toeplitz workload (2, -1.3, -0.7), n = 2000
         A, k, p, d, zeta, tol_b = I.toeplitz_tridiag(2000), 10, 30, 80, 4, 1e-10
     u1 = I.start_vector(A.n, 1)
     with K().Solver.from_csr(A, k, p, d, which="LR", tol=1e-8, zeta=zeta, u1=u1,
-                             max_restarts=-1) as s:
+                             max_restarts=-1, prec=prec) as s:
         s.solve()
         U, S, H = s.krylov()
     st = _oracle_expansion(A, k + p, d, zeta, u1)
@@ -97,11 +101,12 @@ def test_first_expansion_matches_oracle(case):
     assert np.linalg.norm(AU - U @ H) < 1e-12 * np.linalg.norm(AU)
 
 
-def test_default_start_vector_generator():
+@pytest.mark.parametrize("prec", PRECS)
+def test_default_start_vector_generator(prec):
     # u1 = NULL: the library draws N(0,1) entries from SplitMix64(seed + 1)
     A = I.convdiff_2d(30, 30, 1.0, 20.0, 10.0)
     with K().Solver.from_csr(A, 4, 12, 40, which="LR", tol=1e-8, zeta=8, seed=0,
-                             max_restarts=-1) as s:
+                             max_restarts=-1, prec=prec) as s:
         s.solve()
         U, S, H = s.krylov()
     st = _oracle_expansion(A, 16, 40, 8, I.start_vector(A.n, 1))
@@ -125,7 +130,7 @@ def _run_gpu(A, k, p, d, zeta, which, tol, **kw):
 def _check_against_oracle(A, k, p, d, zeta, which, tol, lam_tol, exact=None, **kw):
     info, lam, X, res, T, U, b, est = _run_gpu(A, k, p, d, zeta, which, tol, **kw)
     ores = R.rks(A.to_scipy(), k, p, d, I.start_vector(A.n, 1), zeta=zeta, seed=0,
-                 which=which, tol=tol)
+                 which=which, tol=tol, lock_vectors=kw.get("lock", True))
     assert info["converged"] == 1 and ores.converged
     kk = min(lam.size, ores.eigvals.size, k)
     rel = np.abs(lam[:kk] - ores.eigvals[:kk]) / np.abs(ores.eigvals[:kk])
@@ -141,39 +146,45 @@ def _check_against_oracle(A, k, p, d, zeta, which, tol, lam_tol, exact=None, **k
     return info, ores
 
 
-def test_toeplitz_small_closed_form():
+@pytest.mark.parametrize("prec", PRECS)
+def test_toeplitz_small_closed_form(prec):
     n = 30
     A = I.toeplitz_tridiag(n)
     ex = I.toeplitz_eigenvalues(n, -1.3, 2.0, -0.7)
     ex = ex[np.argsort(-np.abs(ex))]
-    _check_against_oracle(A, 4, 12, 40, 4, "LM", 1e-14, 1e-10, exact=ex)
+    tol = 1e-14 if prec == "fp64" else 1e-13
+    _check_against_oracle(A, 4, 12, 40, 4, "LM", tol, 1e-10, exact=ex, prec=prec)
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("lock", [True, False])
-def test_convdiff_kronecker_lr(lock):
+def test_convdiff_kronecker_lr(lock, prec):
     N = 30
     A = I.convdiff_2d(N, N, 1.0, 20.0, 10.0)
     ex = np.sort(I.convdiff_2d_eigenvalues(N, N, 1.0, 20.0, 10.0))[::-1]
-    info, _ = _check_against_oracle(A, 6, 18, 64, 8, "LR", 1e-13, 1e-10, exact=ex, lock=lock)
+    info, _ = _check_against_oracle(A, 6, 18, 64, 8, "LR", 1e-13, 1e-10, exact=ex, lock=lock,
+                                    prec=prec)
     if lock:
         assert info["nlocked"] > 0
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("which,k", [("LM", 4), ("SM", 3), ("LR", 4), ("SR", 2)])
-def test_planted_spectrum(which, k):
+def test_planted_spectrum(which, k, prec):
     from test_oracle_rks import _planted_spectrum_matrix
     Ad, lam, _ = _planted_spectrum_matrix(150, 11)
     As = sp.csr_matrix(Ad)
     A = I.CSR(150, As.indptr.astype(np.int32), As.indices.astype(np.int32), As.data)
     want = lam[np.argsort(R.key(lam, which), kind="stable")]
-    _check_against_oracle(A, k, 16, 64, 8, which, 1e-13, 1e-10, exact=want)
+    _check_against_oracle(A, k, 16, 64, 8, which, 1e-13, 1e-10, exact=want, prec=prec)
 
 
-def test_ragged_convdiff_mid_size():
+@pytest.mark.parametrize("prec", PRECS)
+def test_ragged_convdiff_mid_size(prec):
     # several CTAs and a ragged tail (n = 2773 rows), rectangular grid
     A = I.convdiff_2d(59, 47, 1.0, 20.0, 10.0)
     ex = np.sort(I.convdiff_2d_eigenvalues(59, 47, 1.0, 20.0, 10.0))[::-1]
-    _check_against_oracle(A, 8, 24, 96, 8, "LR", 1e-13, 1e-9, exact=ex)
+    _check_against_oracle(A, 8, 24, 96, 8, "LR", 1e-13, 1e-9, exact=ex, prec=prec)
 
 
 def test_device_pointer_mode_matches_host_mode(gpu):
@@ -188,32 +199,59 @@ def test_device_pointer_mode_matches_host_mode(gpu):
         s.solve()
         X_d = gpu.zeros((s.nkept, A.n), dtype=gpu.float64, device="cuda")
         lam_d, _, _ = s.eigpairs(X_out=X_d)
-    assert np.allclose(lam_d, lam_h, rtol=1e-12)
-    assert np.allclose(X_d.cpu().numpy().T, X_h, atol=1e-10)
+    assert np.allclose(lam_d, lam_h, rtol=1e-10)
+    # eigenvectors agree up to the sign of each column (sketch sums use
+    # atomics, so the last bits may differ from run to run)
+    Xd = X_d.cpu().numpy().T
+    for j in range(Xd.shape[1]):
+        i = np.argmax(np.abs(X_h[:, j]))
+        sgn = np.sign(Xd[i, j] * X_h[i, j])
+        assert np.allclose(sgn * Xd[:, j], X_h[:, j], atol=1e-9 * np.abs(X_h[:, j]).max())
 
 
 # ---------------------------------------------------------------------------
 # Full size: the 2D convection-diffusion workload (n = 1e6) as benchmarked
 # ---------------------------------------------------------------------------
 
-def test_convdiff_1000_full_size():
+@pytest.mark.parametrize("prec", PRECS)
+def test_convdiff_1000_full_size(prec):
+    # tolerance on ||A x - l x|| / (||A||_1 ||x||) <= 1e-8, locking on
     P = I.convdiff2d_problem()
     N = 1000
-    with K().Solver.from_csr(P.A, P.k, P.p, P.d, which=P.which, tol=P.tol, zeta=P.zeta,
-                             u1=I.start_vector(P.A.n, 1)) as s:
+    with K().Solver.from_csr(P.A, P.k, P.p, P.d, which=P.which, zeta=P.zeta,
+                             u1=I.start_vector(P.A.n, 1), prec=prec, **P.solver_opts()) as s:
         info = s.solve(allow_noconv=False)
         lam, X, res = s.eigpairs()
-    assert info["converged"] == 1
-    assert res.max() <= 1e-8
-    # recompute residuals on the host for every pair (FP64, scipy SpMV)
+    assert info["converged"] == 1 and info["nlocked"] > 0
+    assert res.max() <= P.tol
+    # recompute every residual on the host (FP64, scipy SpMV) from the returned X
     Z = K().unpack_eigvecs(lam, X)
     hres, _ = R.true_residuals(P.A.to_scipy(), Z, lam)
     assert np.allclose(res, hres, rtol=1e-5, atol=1e-14)
-    # the 20 rightmost eigenvalues of the Kronecker-sum closed form
-    ex = np.sort(I.convdiff_2d_eigenvalues(N, N, 1.0, 20.0, 10.0))[::-1][: P.k]
+    assert hres.max() <= P.tol
+    # the computed values are the 20 rightmost of the Kronecker-sum closed form,
+    # each within the pseudospectral uncertainty of a 1e-8 * ||A||_1 residual
+    ex = np.sort(I.convdiff_2d_eigenvalues(N, N, 1.0, 20.0, 10.0))[::-1]
+    assert np.max(np.abs(lam.imag)) < 1e-3 * np.abs(lam).max()
     got = np.sort(lam.real)[::-1][: P.k]
-    assert np.max(np.abs(lam.imag)) < 1e-6 * np.abs(lam).max()
-    assert np.max(np.abs(got - ex) / np.abs(ex)) < 1e-4
+    assert np.max(np.abs(got - ex[: P.k]) / np.abs(ex[: P.k])) < 2e-2
+    assert got.min() > ex[P.k] - 1.0   # nothing from beyond the 21st eigenvalue
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_norm1_criterion_matches_oracle(prec):
+    # the ||A||_1-scaled criterion (Sec. 4.1 remark) at a size the oracle solves
+    N = 40
+    A = I.convdiff_2d(N, N, 1.0, 20.0, 10.0)
+    u1 = I.start_vector(A.n, 1)
+    kw = dict(tol=1e-14, eta_lock=1e-15, conv="norm1")
+    with K().Solver.from_csr(A, 6, 18, 64, which="LR", zeta=8, u1=u1, prec=prec, **kw) as s:
+        info = s.solve(allow_noconv=False)
+        lam, X, res = s.eigpairs()
+    ores = R.rks(A.to_scipy(), 6, 18, 64, u1, zeta=8, seed=0, which="LR", **kw)
+    assert ores.converged
+    assert np.max(np.abs(lam[:6] - ores.eigvals[:6]) / np.abs(ores.eigvals[:6])) < 1e-9
+    assert res.max() < 1e-13
 
 
 # ---------------------------------------------------------------------------

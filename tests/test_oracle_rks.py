@@ -334,9 +334,9 @@ def test_planted_missing_coupling_breaks_eigenvalues(monkeypatch):
     # are locked.
     orig = R.lock
 
-    def lock_without_coupling(st, k, eta_lock):
+    def lock_without_coupling(st, k, eta_lock, norm_a=None):
         st.Tqa[:] = 0.0
-        return orig(st, k, eta_lock)
+        return orig(st, k, eta_lock, norm_a)
     monkeypatch.setattr(R, "lock", lock_without_coupling)
     N = 30
     A = I.convdiff_2d(N, N, 1.0, 20.0, 10.0).to_scipy()
