@@ -77,9 +77,17 @@ typedef struct {
                           RKS_PREC_DF (default): basis and matrix values stored
                           as float pairs (hi + lo, 48-bit significand, 8 bytes),
                           products and sums by error-free transformations on the
-                          FP32 pipes; RKS_PREC_FP64: native FP64.  The sketch
-                          sums, the small dense work and the final residuals are
-                          FP64 in both. */
+                          FP32 pipes; RKS_PREC_FP64: native FP64;
+                          RKS_PREC_MIXED: FP32 basis and FP32 matrix values with
+                          compensated (error-free) products and sums until the
+                          estimates reach mixed_tol or stagnate, then a
+                          double-float solve started from the sum of the FP32
+                          Schur vectors (all wanted directions to FP32
+                          accuracy) finishes to tol.  The sketch sums, the
+                          small dense work and the final residuals are FP64 in
+                          all three. */
+  double mixed_tol;    /* RKS_PREC_MIXED: tolerance of the FP32 phase on the
+                          opts.conv scale; 0: 64 * 2^-24 */
   double verify;       /* > 0: after convergence, check the FP64 residuals
                           ||A x - l x|| / (||A||_1 ||x||) <= verify; if one
                           fails, divide tol and eta_lock by 4 and continue the
@@ -87,7 +95,7 @@ typedef struct {
                           by maxit); 0: no check (default) */
 } rks_opts;
 
-enum { RKS_PREC_DF = 0, RKS_PREC_FP64 = 1 };
+enum { RKS_PREC_DF = 0, RKS_PREC_FP64 = 1, RKS_PREC_MIXED = 2 };
 
 /* Convergence test on the Ritz pairs (lambda_i, y_i) of T, ||y_i|| = 1:
  *  RKS_CONV_EIG   |b^T y_i| / |lambda_i| <= tol   (Eq. 4.8, Sec. 5.1), and
@@ -223,6 +231,28 @@ int rks_sketch_pairs(int64_t n, int d, int zeta, uint64_t seed, int32_t* rows, i
  * entries sign/sqrt(zeta), FP64 accumulation.  Same requirements. */
 int rks_sketch_apply(int64_t n, int d, int zeta, uint64_t seed, const double* x, double* z,
                      void* stream);
+
+/* Largest sketch size d accepted by rks_sketch_apply_noalloc. */
+#define RKS_NOALLOC_MAX_D 8192
+
+/* z = Omega x exactly as rks_sketch_apply, but without allocating anything:
+ * no cudaMalloc, cudaFree or allocating library call.  This has no
+ * counterpart in the paper; it is for callers that cannot allocate device
+ * memory, such as code running inside another framework's memory pool (which
+ * already owns the device memory, so a private cudaMalloc can fail or
+ * fragment it) or latency-critical loops that cannot pay the device-wide
+ * synchronisation cudaFree implies.  Its scratch (d FP64 sums and a status
+ * word) lives in one fixed device array of RKS_NOALLOC_MAX_D + 1 doubles that
+ * every GPU loading the library holds until the process exits; d larger than
+ * RKS_NOALLOC_MAX_D returns RKS_EINVAL.  The first call on a device (with that
+ * device current) looks up the array's device address; make that first call
+ * before any stream capture.  All calls share the array: the sums are cleared
+ * at the start of each call, and calls that overlap on the GPU (different
+ * streams or host threads) race on it.  x: n doubles, z: d doubles, device
+ * pointers; the call synchronises `stream` to read the status.  Returns
+ * RKS_OK, RKS_EINVAL (arguments, or the hash draw cap reached) or RKS_ECUDA. */
+int rks_sketch_apply_noalloc(int64_t n, int d, int zeta, uint64_t seed, const double* x, double* z,
+                             void* stream);
 
 /* ---- Host-side small dense FP64 steps (Algorithm 1 contraction) ------ */
 

@@ -31,11 +31,11 @@ class Opts(C.Structure):
     _fields_ = [("zeta", C.c_int), ("maxit", C.c_int), ("lock", C.c_int), ("mem_device", C.c_int),
                 ("stream", C.c_void_p), ("u1", C.c_void_p), ("eta_lock", C.c_double),
                 ("max_restarts", C.c_int), ("profile", C.c_int), ("conv", C.c_int),
-                ("prec", C.c_int), ("verify", C.c_double)]
+                ("prec", C.c_int), ("mixed_tol", C.c_double), ("verify", C.c_double)]
 
 
 CONV = {"eig": 0, "norm1": 1}
-PREC = {"df": 0, "fp64": 1}
+PREC = {"df": 0, "fp64": 1, "mixed": 2}
 
 
 KCLASSES = ("spmv_sketch", "ls", "update_sketch", "finish", "restart", "other")
@@ -106,6 +106,8 @@ def lib() -> C.CDLL:
         L.rks_sketch_pairs.restype = C.c_int
         L.rks_sketch_apply.argtypes = [C.c_int64, C.c_int, C.c_int, C.c_uint64, _P, _P, _P]
         L.rks_sketch_apply.restype = C.c_int
+        L.rks_sketch_apply_noalloc.argtypes = [C.c_int64, C.c_int, C.c_int, C.c_uint64, _P, _P, _P]
+        L.rks_sketch_apply_noalloc.restype = C.c_int
         L.rks_host_ordered_schur.argtypes = [C.c_int, _P, C.c_int, C.c_int, _P, _P]
         L.rks_host_ordered_schur.restype = C.c_int
         L.rks_host_quasi_eig.argtypes = [C.c_int, _P, _P, _P, _P, _P]
@@ -151,7 +153,8 @@ class Solver:
 
     def __init__(self, n, rowptr, colind, vals, k, p, d, which="LM", tol=1e-10, seed=0, *,
                  zeta=8, maxit=1000, lock=True, u1=None, eta_lock=0.0, max_restarts=0,
-                 device=False, stream=None, profile=False, conv="eig", verify=0.0, prec="df"):
+                 device=False, stream=None, profile=False, conv="eig", verify=0.0, prec="df",
+                 mixed_tol=0.0):
         L = lib()
         self.n, self.k, self.p, self.d = int(n), int(k), int(p), int(d)
         self.device = bool(device)
@@ -179,6 +182,7 @@ class Solver:
         o.conv = CONV[conv]
         o.verify = float(verify)
         o.prec = PREC[prec]
+        o.mixed_tol = float(mixed_tol)
         h = _P()
         _check(L.rks_create(C.byref(h), self.n, _ptr(rowptr), _ptr(colind), _ptr(vals), vdt,
                             self.k, self.p, self.d, WHICH[which] if isinstance(which, str) else int(which),
@@ -312,6 +316,16 @@ def sketch_apply(x, d: int, zeta: int, seed: int):
     _check(lib().rks_sketch_apply(x.numel(), d, zeta, seed, x.data_ptr(), z.data_ptr(), stream),
            "rks_sketch_apply")
     return z
+
+
+def sketch_apply_noalloc(x, z, d: int, zeta: int, seed: int) -> int:
+    """z = Omega x through the allocation-free entry point (x, z: CUDA float64 tensors).
+
+    For callers that cannot allocate device memory; returns the status code.
+    """
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    return lib().rks_sketch_apply_noalloc(x.numel(), d, zeta, seed, x.data_ptr(), z.data_ptr(), stream)
 
 
 def host_ordered_schur(B: np.ndarray, which: str, nsort: int):
