@@ -182,7 +182,8 @@ def run_ours(args) -> None:
     d_u1 = torch.from_numpy(u1).to(dev)
     solver = rks.Solver(A.n, d_rowptr, d_colind, d_vals, P.k, P.p, P.d, which=P.which,
                         seed=P.omega_seed, zeta=P.zeta, u1=d_u1, device=True,
-                        stream=stream.cuda_stream, profile=True, prec=args.prec, **P.solver_opts())
+                        stream=stream.cuda_stream, profile=True, prec=args.prec, maxit=args.maxit,
+                        **P.solver_opts())
     X_dev = torch.empty((P.k + 1, A.n), dtype=torch.float64, device=dev)
 
     def step():
@@ -257,7 +258,7 @@ def run_ours(args) -> None:
         t0 = time.perf_counter()
         with rks.Solver(A.n, h_rowptr, h_colind, h_vals, P.k, P.p, P.d, which=P.which,
                         seed=P.omega_seed, zeta=P.zeta, u1=h_u1, stream=stream.cuda_stream,
-                        prec=args.prec, **P.solver_opts()) as s2:
+                        prec=args.prec, maxit=args.maxit, **P.solver_opts()) as s2:
             s2.solve(allow_noconv=False)
             s2.eigpairs(X_out=h_X)
             kk = s2.nkept
@@ -316,6 +317,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--maxit", type=int, default=4000, help="restart limit of each solve")
     ap.add_argument("--prec", default="df", choices=["df", "fp64"],
                     help="arithmetic of the n-dimensional work (see include/rks.h)")
     args = ap.parse_args()

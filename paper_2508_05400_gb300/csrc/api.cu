@@ -61,21 +61,30 @@ struct rks_ctx {
   double* plam = nullptr;
   // double-float path (opts.prec == RKS_PREC_DF)
   int prec = RKS_PREC_DF;
-  rks::CsrDF A2;
+  rks::CsrDF A2;        // the value array and basis in use (DF pairs or FP32)
   float2* vals2 = nullptr;
   float2* U2 = nullptr;
+  float* valsf = nullptr;  // mixed precision: FP32 values and basis
+  float* Uf = nullptr;
+  void* Ub = nullptr;      // basis in use: U2 or Uf
+  bool f32 = false;        // basis in use is FP32
+  int phase_restarts = 0;
   float2* S2 = nullptr;
   float2* nrs = nullptr;
   float2* sj = nullptr;
   float2* Q2 = nullptr;
   double* rprev = nullptr;
   double* znorm = nullptr;
+  uint16_t* otab = nullptr;  // packed Omega (rows + signs), built once from the hash
+  float2* lsr1 = nullptr;    // least-squares scratch: first-pass coefficients (m+1)
+  float2* lsz1 = nullptr;    // and the projected sketch (d)
   double* tmp64 = nullptr;
   // host state
   double norm1 = 0;
   std::vector<double> S_h, cs_h, coef_h, Ba, Tqq, Tqa;
   std::vector<float2> S2_h;
   int q = 0, ja = 0;
+  int brow = 0;            // row of b in the active Rayleigh quotient (active columns kept at the last restart)
   int64_t nmatvec = 0;
   int restarts = 0;
   int last_expand_from = 0;
@@ -188,34 +197,37 @@ int flag_status(int f) {
 
 // Algorithm 2 in double-float: three kernels per step (see kernels_df.cu).
 void expand_df_launches(rks_ctx* c, int c0) {
-  const double n = (double)c->n, P = 8.0;
-  const double spmv_bytes = (double)c->nnz * (P + 4) + 4.0 * (n + 1) + 2 * P * n;
+  const double n = (double)c->n, P = 8.0, PV = c->f32 ? 4.0 : 8.0;
+  const double spmv_bytes = (double)c->nnz * (PV + 4) + 4.0 * (n + 1) + 2 * PV * n;
   for (int j = c0; j < c->m; ++j) {
     const int col = j + 1;
     int s = prof_begin(c, RKS_K_SPMV);
-    rks::launch_df_spmv_sketch(c->A2, c->U2 + (int64_t)j * c->ldu, c->U2 + (int64_t)col * c->ldu, c->d, c->zeta,
-                               c->seed, c->z_raw, c->flag, c->stream);
+    const size_t es = c->f32 ? sizeof(float) : sizeof(float2);
+    char* ub = static_cast<char*>(c->Ub);
+    rks::launch_df_spmv_sketch(c->A2, ub + (size_t)j * c->ldu * es, ub + (size_t)col * c->ldu * es, c->d, c->zeta,
+                               c->otab, c->z_raw, c->stream);
     prof_end(c, s, RKS_K_SPMV, 1, spmv_bytes, 2.0 * c->nnz);
     s = prof_begin(c, RKS_K_LS);
     rks::launch_df_small(j, c->d, c->zscale, j > c0 ? 1 : 0, 1, c->s_raw, c->z_raw, c->S, c->S2, c->colscale,
-                         c->rprev, c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->flag, c->stream);
-    prof_end(c, s, RKS_K_LS, 1, 3.0 * P * c->d * col, 6.0 * c->d * col);
+                         c->rprev, c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1, c->flag, c->stream);
+    prof_end(c, s, RKS_K_LS, 3, 3.0 * P * c->d * col, 6.0 * c->d * col);
     s = prof_begin(c, RKS_K_UPDATE);
-    rks::launch_df_update_sketch(c->n, c->U2, c->ldu, col, c->nrs, c->sj, c->d, c->zeta, c->seed, c->s_raw,
-                                 c->flag, c->stream);
-    prof_end(c, s, RKS_K_UPDATE, 1, (col + 2) * P * n, 2.0 * n * col);
+    rks::launch_df_update_sketch(c->n, c->Ub, c->ldu, col, c->nrs, c->sj, c->d, c->zeta, c->otab, c->s_raw,
+                                 c->f32, c->stream);
+    prof_end(c, s, RKS_K_UPDATE, 1, (col + 2) * (c->f32 ? 4.0 : P) * n, 2.0 * n * col);
     ++c->nmatvec;
   }
   int s = prof_begin(c, RKS_K_FINISH);
   rks::launch_df_small(c->m, c->d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale, c->rprev,
-                       c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->flag, c->stream);
+                       c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1, c->flag, c->stream);
   prof_end(c, s, RKS_K_FINISH, 1, 3.0 * P * c->d, 2.0 * c->d);
 }
 
 // Algorithm 2: extend from the last vector at column q+ja to column m.
 int expand(rks_ctx* c) {
   const int c0 = c->q + c->ja;
-  if (c->prec == RKS_PREC_DF) {
+  c->brow = c->ja;
+  if (c->prec != RKS_PREC_FP64) {
     expand_df_launches(c, c0);
   } else
   {
@@ -317,7 +329,7 @@ int contract(rks_ctx* c) {
     for (int i = 0; i < ma; ++i) H[i + (size_t)j * ma] = M(c->Ba, ldb, i, j);
     b[j] = M(c->Ba, ldb, ma, j);
   }
-  rks_dense::hessenberg(ma, H.data(), ma, Q.data(), ma);
+  rks_dense::hessenberg_arrow(ma, c->brow, H.data(), ma, Q.data(), ma);
   if (rks_dense::schur(ma, H.data(), ma, Q.data(), ma) != 0) return RKS_EDENSE;
   const int want = c->k - q;
   rks_dense::reorder(ma, H.data(), ma, Q.data(), ma, ma, c->which, std::min(want + 1, ma));
@@ -406,20 +418,20 @@ int contract(rks_ctx* c) {
   for (int j = 0; j < ka; ++j)
     for (int l = 0; l < ma; ++l) Qp[l + (size_t)j * ma] = c->cs_h[q + l] * Qk[l + (size_t)j * ma];
   int ps = prof_begin(c, RKS_K_RESTART);
-  if (c->prec == RKS_PREC_DF) {
+  if (c->prec != RKS_PREC_FP64) {
     std::vector<float2> Q2h(Qp.size());
     for (size_t t = 0; t < Qp.size(); ++t) {
       float h = (float)Qp[t];
       Q2h[t] = make_float2(h, (float)(Qp[t] - (double)h));
     }
     CK(cudaMemcpyAsync(c->Q2, Q2h.data(), Q2h.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
-    rks::launch_df_rows_gemm(c->n, c->U2, c->ldu, q, ma, c->Q2, ka, q, m, c->stream);
+    rks::launch_df_rows_gemm(c->n, c->Ub, c->ldu, q, ma, c->Q2, ka, q, m, c->f32, c->stream);
     CK(cudaStreamSynchronize(c->stream));   // Q2h is a host temporary
   } else {
     CK(cudaMemcpyAsync(c->Qd, Qp.data(), Qp.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     rks::launch_rows_gemm(c->n, c->U, c->ldu, q, ma, c->Qd, ka, c->U, c->ldu, q, m, c->stream);
   }
-  prof_end(c, ps, RKS_K_RESTART, 1, (double)(ma + ka + 2) * sizeof(double) * c->n, 2.0 * c->n * ma * ka);
+  prof_end(c, ps, RKS_K_RESTART, 1, (double)(ma + ka + 2) * (c->f32 ? 4.0 : 8.0) * c->n, 2.0 * c->n * ma * ka);
   int rc = launch_err();
   if (rc) return rc;
   const double s_last_scale = c->cs_h[m];
@@ -431,7 +443,7 @@ int contract(rks_ctx* c) {
   CK(cudaMemcpyAsync(c->colscale, c->cs_h.data(), c->cs_h.size() * sizeof(double), cudaMemcpyHostToDevice,
                      c->stream));
   CK(cudaMemcpyAsync(c->S, c->S_h.data(), c->S_h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  if (c->prec == RKS_PREC_DF) {
+  if (c->prec != RKS_PREC_FP64) {
     c->S2_h.resize(c->S_h.size());
     for (size_t t = 0; t < c->S_h.size(); ++t) {
       float h = (float)c->S_h[t];
@@ -562,8 +574,8 @@ int finalize(rks_ctx* c) {
   const int np = (int)col.size();
   CK(cudaMemcpyAsync(c->Qd, Yr.data(), Yr.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   int ps = prof_begin(c, RKS_K_OTHER);
-  if (c->prec == RKS_PREC_DF) {
-    rks::launch_df2d_cols(c->n, c->U2, c->ldu, c->AX, c->ldu, kk, c->stream);
+  if (c->prec != RKS_PREC_FP64) {
+    rks::launch_df2d_cols(c->n, c->Ub, c->ldu, c->AX, c->ldu, kk, c->f32, c->stream);
     rks::launch_rows_gemm(c->n, c->AX, c->ldu, 0, kk, c->Qd, kk, c->X, c->ldu, 0, -1, c->stream);
   } else {
     rks::launch_rows_gemm(c->n, c->U, c->ldu, 0, kk, c->Qd, kk, c->X, c->ldu, 0, -1, c->stream);
@@ -601,7 +613,8 @@ void free_ctx(rks_ctx* c) {
   cudaFree(c->coef); cudaFree(c->flag); cudaFree(c->Qd); cudaFree(c->u1);
   cudaFree(c->X); cudaFree(c->AX); cudaFree(c->rsum); cudaFree(c->pcol); cudaFree(c->plam);
   cudaFree(c->vals2); cudaFree(c->U2); cudaFree(c->S2); cudaFree(c->nrs); cudaFree(c->sj); cudaFree(c->Q2);
-  cudaFree(c->rprev); cudaFree(c->znorm); cudaFree(c->tmp64);
+  cudaFree(c->rprev); cudaFree(c->znorm); cudaFree(c->tmp64); cudaFree(c->valsf); cudaFree(c->Uf);
+  cudaFree(c->otab); cudaFree(c->lsr1); cudaFree(c->lsz1);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -645,7 +658,7 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
   if (opts) o = *opts;
   if (o.zeta == 0) o.zeta = 8;
   if (o.conv != RKS_CONV_EIG && o.conv != RKS_CONV_NORM1) return RKS_EINVAL;
-  if (o.prec != RKS_PREC_DF && o.prec != RKS_PREC_FP64) return RKS_EINVAL;
+  if (o.prec != RKS_PREC_DF && o.prec != RKS_PREC_FP64 && o.prec != RKS_PREC_MIXED) return RKS_EINVAL;
   if (o.maxit <= 0) o.maxit = 1000;
   const int m = k + p;
   if (n <= 0 || !rowptr || !colind || !vals || k < 1 || p < 2 || (int64_t)m + 1 > n || d < m + 1 ||
@@ -717,14 +730,30 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
     if (c->norm1 == 0.0) c->norm1 = 1.0;
   }
   c->ldu = (n + 31) / 32 * 32;
-  if (c->prec == RKS_PREC_DF) {
+  if (c->prec != RKS_PREC_FP64) {
+    if (c->prec == RKS_PREC_MIXED) {
+      if ((rc = dalloc(&c->Uf, (size_t)c->ldu * (m + 1))) || (rc = dalloc(&c->valsf, c->nnz))) return fail(rc);
+      rks::launch_d2df(c->nnz, c->vals, c->valsf, true, c->stream);
+    }
     if ((rc = dalloc(&c->U2, (size_t)c->ldu * (m + 1))) || (rc = dalloc(&c->vals2, c->nnz)) ||
         (rc = dalloc(&c->S2, (size_t)d * (m + 1))) || (rc = dalloc(&c->nrs, m + 1)) || (rc = dalloc(&c->sj, 1)) ||
         (rc = dalloc(&c->Q2, (size_t)(m + 1) * (m + 1))) || (rc = dalloc(&c->rprev, m + 1)) ||
-        (rc = dalloc(&c->znorm, 1)) || (rc = dalloc(&c->tmp64, n)))
+        (rc = dalloc(&c->znorm, 1)) || (rc = dalloc(&c->tmp64, n)) ||
+        (rc = dalloc(&c->otab, (size_t)n * rks::omega_slots(o.zeta))) || (rc = dalloc(&c->lsr1, m + 1)) ||
+        (rc = dalloc(&c->lsz1, d)))
       return fail(rc);
-    rks::launch_d2df(c->nnz, c->vals, c->vals2, c->stream);
+    {
+      int bad = 0;
+      if (cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream) != cudaSuccess) return fail(RKS_ECUDA);
+      rks::launch_omega_table(n, d, o.zeta, seed, c->otab, c->flag, c->stream);
+      if (cudaMemcpyAsync(&bad, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return fail(RKS_ECUDA);
+      if (bad) return fail(RKS_EINVAL);
+    }
+    rks::launch_d2df(c->nnz, c->vals, c->vals2, false, c->stream);
     c->A2.n = n; c->A2.nnz = c->nnz; c->A2.rowptr = c->rowptr; c->A2.colind = c->colind; c->A2.vals = c->vals2;
+    c->Ub = c->U2;
     if (rks::configure_df_kernels() != cudaSuccess) return fail(RKS_ECUDA);
     if (rks::df_gemm_smem(m, k + 2) > 200 * 1024 || rks::df_small_smem(d, m + 1) > 200 * 1024) return fail(RKS_EINVAL);
   } else if ((rc = dalloc(&c->U, (size_t)c->ldu * (m + 1)))) {
@@ -750,14 +779,15 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
   return RKS_OK;
 }
 
-static int solve_impl(rks_ctx* c) {
+// Algorithm 1 from the start vector `start` (NULL: the user's u1 or the
+// library's generator) until the estimates reach c->tol (with the FP64
+// verification when verify > 0), `limit` restarts, or stagnation (if
+// stall > 0: no decrease of the largest estimate over `stall` restarts).
+// Sets *converged; leaves the Ritz pairs of the last contraction in c.
+static int run_alg1(rks_ctx* c, const double* start, int limit, double verify, int stall, bool* converged) {
   const int m = c->m, d = c->d;
-  c->solved = false;
-  c->q = 0; c->ja = 0; c->nmatvec = 0; c->restarts = 0; c->kk = 0;
-  std::memset(&c->stats, 0, sizeof(c->stats));
-  c->evused = 0;
-  c->hist.clear();
-  c->hist_lock.clear();
+  *converged = false;
+  c->q = 0; c->ja = 0; c->kk = 0;
   c->Ba.assign((size_t)(m + 1) * m, 0.0);
   c->Tqq.assign((size_t)(c->k + 2) * (c->k + 2), 0.0);
   c->Tqa.assign((size_t)(c->k + 2) * (m + 1), 0.0);
@@ -769,15 +799,15 @@ static int solve_impl(rks_ctx* c) {
   CK(cudaMemsetAsync(c->colscale, 0, (m + 1) * sizeof(double), c->stream));
   // start vector (Sec. 3.1, k = 0): u_1 = u~_1 / ||Omega u~_1||
   int ps = prof_begin(c, RKS_K_OTHER);
-  if (c->prec == RKS_PREC_DF) {
-    const double* src = c->u1;
+  if (c->prec != RKS_PREC_FP64) {
+    const double* src = start ? start : c->u1;
     if (!src) { rks::launch_start_vector(c->n, c->seed + 1, c->tmp64, c->stream); src = c->tmp64; }
-    rks::launch_d2df(c->n, src, c->U2, c->stream);
-    rks::launch_df_sketch_vec(c->n, c->U2, d, c->zeta, c->seed, c->s_raw, c->flag, c->stream);
+    rks::launch_d2df(c->n, src, c->Ub, c->f32, c->stream);
+    rks::launch_df_sketch_vec(c->n, c->Ub, d, c->zeta, c->otab, c->s_raw, c->f32, c->stream);
     CK(cudaMemsetAsync(c->znorm, 0, sizeof(double), c->stream));
     rks::launch_df_small(0, d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale, c->rprev, c->coef,
-                         m + 1, c->znorm, c->nrs, c->sj, c->flag, c->stream);
-    prof_end(c, ps, RKS_K_OTHER, c->u1 ? 3 : 4, 0.0, 0.0);
+                         m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1, c->flag, c->stream);
+    prof_end(c, ps, RKS_K_OTHER, src == c->tmp64 && !start ? 4 : 3, 0.0, 0.0);
   } else {
     if (c->u1) CK(cudaMemcpyAsync(c->U, c->u1, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     else rks::launch_start_vector(c->n, c->seed + 1, c->U, c->stream);
@@ -790,14 +820,15 @@ static int solve_impl(rks_ctx* c) {
   rc = expand(c);                      // Algorithm 1, initial expansion to m
   if (rc) return rc;
   if (c->opts.max_restarts < 0) { c->solved = true; return RKS_OK; }
-  const int limit = c->opts.max_restarts > 0 ? std::min(c->opts.maxit, c->opts.max_restarts) : c->opts.maxit;
-  bool converged = false;
-  const double tol0 = c->tol, eta0 = c->eta_lock;
+  int done = 0;
+  double best = 1e300;
+  int since_best = 0;
   while (true) {
     auto h0 = std::chrono::steady_clock::now();
     rc = contract(c);                  // Schur, reorder, truncate, whiten, lock, restart
     if (rc) return rc;
     ++c->restarts;
+    ++done;
     ritz(c);
     c->stats.host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
     double mx = 0.0;
@@ -805,30 +836,78 @@ static int solve_impl(rks_ctx* c) {
     c->hist.push_back(mx);
     c->hist_lock.push_back(c->q);
     if (c->q >= c->k || mx <= c->tol) {
-      converged = true;
-      if (c->opts.verify > 0) {        // FP64 verification of the true residuals
+      *converged = true;
+      if (verify > 0) {                // FP64 verification of the true residuals
         rc = finalize(c);
-        if (rc) break;
+        if (rc) return rc;
         double mr = 0.0;
         for (double v : c->resid) mr = std::max(mr, v);
-        if (mr > c->opts.verify && c->q < c->k && c->restarts < limit) {
+        if (mr > verify && c->q < c->k && done < limit) {
           c->tol *= 0.25;
           c->eta_lock *= 0.25;
-          converged = false;
+          *converged = false;
           rc = expand(c);
-          if (rc) break;
+          if (rc) return rc;
           continue;
         }
+        if (mr > verify) *converged = false;
       }
-      break;
+      return RKS_OK;
     }
-    if (c->restarts >= limit) break;
+    if (mx < 0.5 * best) { best = mx; since_best = 0; } else if (++since_best >= stall && stall > 0) return RKS_OK;
+    if (done >= limit) return RKS_OK;
     rc = expand(c);                    // Algorithm 2 from k to m
-    if (rc) break;
+    if (rc) return rc;
+  }
+}
+
+static int solve_impl(rks_ctx* c) {
+  c->solved = false;
+  c->nmatvec = 0; c->restarts = 0;
+  std::memset(&c->stats, 0, sizeof(c->stats));
+  c->evused = 0;
+  c->hist.clear();
+  c->hist_lock.clear();
+  const int limit = c->opts.max_restarts > 0 ? std::min(c->opts.maxit, c->opts.max_restarts) : c->opts.maxit;
+  const double tol0 = c->tol, eta0 = c->eta_lock;
+  bool converged = false;
+  int rc = RKS_OK;
+  if (c->prec == RKS_PREC_MIXED) {
+    // Phase 1: FP32 basis and values (compensated arithmetic), down to the
+    // FP32 floor or until the estimates stagnate.
+    c->f32 = true;
+    c->Ub = c->Uf;
+    c->A2.vals = c->valsf;
+    c->A2.f32 = true;
+    const double floor32 = c->opts.mixed_tol > 0 ? c->opts.mixed_tol : 64.0 * 5.9604644775390625e-08;
+    c->tol = std::max(tol0, floor32);
+    c->eta_lock = std::max(eta0, 0.5 * floor32);
+    bool conv1 = false;
+    rc = run_alg1(c, nullptr, limit, 0.0, 20, &conv1);
+    c->phase_restarts = c->restarts;
+    if (rc == RKS_OK && c->opts.max_restarts >= 0) {
+      // Phase 2 start vector: the sum of the FP32 Schur vectors (all wanted
+      // directions to FP32 accuracy), in FP64.
+      rks::launch_sum_cols_f32(c->n, c->Uf, c->ldu, c->kk, c->tmp64, c->stream);
+      rc = launch_err();
+    }
+    c->f32 = false;
+    c->Ub = c->U2;
+    c->A2.vals = c->vals2;
+    c->A2.f32 = false;
+    c->tol = tol0;
+    c->eta_lock = eta0;
+    if (rc == RKS_OK && c->opts.max_restarts >= 0) {
+      // Phase 2: double-float from that start vector, verified in FP64.
+      rc = run_alg1(c, c->tmp64, std::max(1, limit - c->restarts), c->opts.verify, 0, &converged);
+    }
+  } else {
+    rc = run_alg1(c, nullptr, limit, c->opts.verify, 0, &converged);
   }
   c->tol = tol0;
   c->eta_lock = eta0;
   if (rc) return rc;
+  if (c->opts.max_restarts < 0) { c->solved = true; return RKS_OK; }
   rc = finalize(c);
   if (rc) return rc;
   c->solved = true;
@@ -896,8 +975,8 @@ int rks_get_schur(rks_ctx* c, double* T, double* U, double* b) {
   if (b) std::memcpy(b, c->bfull.data(), sizeof(double) * kk);
   if (U) {
     const double* src = c->U;
-    if (c->prec == RKS_PREC_DF) {
-      rks::launch_df2d_cols(c->n, c->U2, c->ldu, c->AX, c->ldu, kk, c->stream);
+    if (c->prec != RKS_PREC_FP64) {
+      rks::launch_df2d_cols(c->n, c->Ub, c->ldu, c->AX, c->ldu, kk, c->f32, c->stream);
       src = c->AX;
     }
     CK(cudaMemcpy2DAsync(U, c->n * sizeof(double), src, c->ldu * sizeof(double), c->n * sizeof(double), kk,
@@ -934,12 +1013,18 @@ int rks_get_krylov(rks_ctx* c, int* ncols_out, double* U, double* S, double* H) 
   if (!c->solved) return RKS_ESTATE;
   const int nc = c->q + c->ja + 1;
   if (ncols_out) *ncols_out = nc;
-  if (U && c->prec == RKS_PREC_DF) {
+  if (U && c->prec != RKS_PREC_FP64 && !c->f32) {
     std::vector<float2> tmp((size_t)c->n * nc);
     CK(cudaMemcpy2DAsync(tmp.data(), c->n * sizeof(float2), c->U2, c->ldu * sizeof(float2), c->n * sizeof(float2), nc,
                          cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     for (size_t t = 0; t < tmp.size(); ++t) U[t] = (double)tmp[t].x + (double)tmp[t].y;
+  } else if (U && c->f32) {
+    std::vector<float> tmp((size_t)c->n * nc);
+    CK(cudaMemcpy2DAsync(tmp.data(), c->n * sizeof(float), c->Uf, c->ldu * sizeof(float), c->n * sizeof(float), nc,
+                         cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (size_t t = 0; t < tmp.size(); ++t) U[t] = (double)tmp[t];
   } else if (U) {
     CK(cudaMemcpy2DAsync(U, c->n * sizeof(double), c->U, c->ldu * sizeof(double), c->n * sizeof(double), nc,
                          cudaMemcpyDeviceToHost, c->stream));

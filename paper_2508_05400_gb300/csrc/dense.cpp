@@ -136,6 +136,35 @@ void hessenberg(int n, double* A, int lda, double* Q, int ldq) {
   }
 }
 
+void hessenberg_arrow(int n, int ka, double* A, int lda, double* Q, int ldq) {
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) at(Q, ldq, i, j) = (i == j) ? 1.0 : 0.0;
+  if (ka < 2 || ka >= n) {
+    if (ka >= n) hessenberg(n, A, lda, Q, ldq);
+    return;
+  }
+  // Row ka holds b in columns 0..ka-1; rows > ka are zero there.  Reduce from
+  // the bottom: for row i = ka, ka-1, ..., 2 zero (i, 0..i-2) with a reflector
+  // acting on columns (and, as a similarity, rows) 0..i-1.  Entries of rows
+  // > i in those columns are already zero, so they stay zero.
+  std::vector<double> x(n), v(n);
+  for (int i = ka; i >= 2; --i) {
+    const int len = i;              // indices 0..i-1, pivot at i-1
+    // reflector on the reversed row segment so that the last entry survives
+    for (int t = 0; t < len; ++t) x[t] = at(A, lda, i, len - 1 - t);
+    double beta;
+    house(x.data(), len, v.data(), &beta);
+    if (beta == 0.0) continue;
+    std::vector<double> vr(len);
+    for (int t = 0; t < len; ++t) vr[t] = v[len - 1 - t];
+    // A <- A P on columns 0..len-1 (rows 0..n-1), then A <- P A on rows 0..len-1
+    apply_right(A, lda, 0, len, 0, n - 1, vr.data(), beta);
+    apply_left(A, lda, 0, len, 0, n - 1, vr.data(), beta);
+    apply_right(Q, ldq, 0, len, 0, n - 1, vr.data(), beta);
+    for (int t = 0; t < len - 1; ++t) at(A, lda, i, t) = 0.0;
+  }
+}
+
 int standardize_2x2(int n, double* T, int ldt, double* Z, int ldz, int nz, int i) {
   double a = at(T, ldt, i, i), b = at(T, ldt, i, i + 1);
   double c = at(T, ldt, i + 1, i), d = at(T, ldt, i + 1, i + 1);

@@ -10,6 +10,10 @@ struct Block { int start, size; double re, im; };   // im >= 0 for a 2x2 pair
 
 // A (n x n) <- Q^T A Q upper Hessenberg; Q (n x n) is overwritten with Q.
 void hessenberg(int n, double* A, int lda, double* Q, int ldq);
+// Same result for a matrix that is upper Hessenberg except for row ka, which
+// may be full in columns 0..ka-1 (the restarted Rayleigh quotient
+// [T_k; b^T] of Algorithm 2 followed by Arnoldi columns): O(ka^3) work.
+void hessenberg_arrow(int n, int ka, double* A, int lda, double* Q, int ldq);
 // Real Schur form of an upper Hessenberg H (in place), Z <- Z * (QR rotations).
 // 2x2 blocks are standardised.  Returns 0, or -1 if the iteration did not converge.
 int schur(int n, double* H, int ldh, double* Z, int ldz);

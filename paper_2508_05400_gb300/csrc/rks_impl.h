@@ -24,25 +24,30 @@ struct CsrDF {
   int64_t n = 0, nnz = 0;
   const int32_t* rowptr = nullptr;
   const int32_t* colind = nullptr;
-  const float2* vals = nullptr;
+  const void* vals = nullptr;   // float2 pairs, or float when f32
+  bool f32 = false;             // FP32 values and FP32 basis (mixed precision)
 };
 
 cudaError_t configure_df_kernels();
 int df_small_smem(int d, int c);
 int df_gemm_smem(int nin, int nout);
-void launch_df_spmv_sketch(const CsrDF& A, const float2* x, float2* w, int d, int zeta, uint64_t seed,
-                           double* out_raw, int* flag, cudaStream_t st);
-void launch_df_update_sketch(int64_t n, float2* U, int64_t ldu, int c, const float2* nrs, const float2* sj,
-                             int d, int zeta, uint64_t seed, double* out_raw, int* flag, cudaStream_t st);
+void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, int d, int zeta, const uint16_t* otab,
+                           double* out_raw, cudaStream_t st);
+void launch_df_update_sketch(int64_t n, void* U, int64_t ldu, int c, const float2* nrs, const float2* sj,
+                             int d, int zeta, const uint16_t* otab, double* out_raw, bool f32, cudaStream_t st);
 void launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_raw, double* z_raw, double* S64,
                      float2* S2, double* colscale, double* rprev, double* coef, int ldcoef, double* znorm_prev,
-                     float2* nrs, float2* sj, int* flag, cudaStream_t st);
-void launch_d2df(int64_t n, const double* x, float2* y, cudaStream_t st);
-void launch_df2d_cols(int64_t n, const float2* x, int64_t ldx, double* y, int64_t ldy, int ncols, cudaStream_t st);
-void launch_df_sketch_vec(int64_t n, const float2* x, int d, int zeta, uint64_t seed, double* out_raw, int* flag,
-                          cudaStream_t st);
-void launch_df_rows_gemm(int64_t n, float2* U, int64_t ldu, int a0, int nin, const float2* Q, int nout, int c0,
-                         int move_src, cudaStream_t st);
+                     float2* nrs, float2* sj, float2* r1, float2* z1, int* flag, cudaStream_t st);
+void launch_omega_table(int64_t n, int d, int zeta, uint64_t seed, uint16_t* tab, int* flag, cudaStream_t st);
+int omega_slots(int zeta);
+void launch_d2df(int64_t n, const double* x, void* y, bool f32, cudaStream_t st);
+void launch_sum_cols_f32(int64_t n, const float* U, int64_t ldu, int ncols, double* y, cudaStream_t st);
+void launch_df2d_cols(int64_t n, const void* x, int64_t ldx, double* y, int64_t ldy, int ncols, bool f32,
+                      cudaStream_t st);
+void launch_df_sketch_vec(int64_t n, const void* x, int d, int zeta, const uint16_t* otab, double* out_raw,
+                          bool f32, cudaStream_t st);
+void launch_df_rows_gemm(int64_t n, void* U, int64_t ldu, int a0, int nin, const float2* Q, int nout, int c0,
+                         int move_src, bool f32, cudaStream_t st);
 
 void launch_sketch_pairs(int64_t n, int d, int zeta, uint64_t seed, int32_t* rows, int8_t* signs, int* flag,
                          cudaStream_t st);
