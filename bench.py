@@ -126,6 +126,17 @@ def cpu_sample(P, u1, restarts: int = 1) -> dict:
     return {"seconds": dt, "nmatvec": res.nmatvec, "restarts": res.restarts}
 
 
+def reduce_max_over_ranks(values, device, dist, world: int):
+    """Max of each value over the ranks (replicas run independently; the
+    slowest rank bounds the whole job).  No-op for world = 1."""
+    if world <= 1:
+        return list(values)
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -219,11 +230,7 @@ def run_ours(args) -> None:
         ev1.record(stream)
         barrier()
     ms_total = ev0.elapsed_time(ev1)
-    ms_step = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = reduce_max_over_ranks([ms_total / args.steps], dev, dist, world)[0]
     clocks = clk.summary()
 
     # roofline of the dominant kernel (live CUDA-event durations of the timed solves)
@@ -266,10 +273,8 @@ def run_ours(args) -> None:
     barrier()
     e2e_ms = statistics.mean(e2e_times) if e2e_times else None
     kk = P.k
-    if world > 1 and e2e_ms is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    if e2e_ms is not None:
+        e2e_ms = reduce_max_over_ranks([e2e_ms], dev, dist, world)[0]
     h2d = A.rowptr.nbytes + A.colind.nbytes + A.vals.nbytes + u1.nbytes
     d2h = 8 * A.n * kk + 3 * 8 * kk
 

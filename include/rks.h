@@ -47,7 +47,8 @@ typedef enum {
                            before k pairs converged (Sec. 2.1) */
   RKS_ENAN = -6,        /* a non-finite value appeared (e.g. NaN in A) */
   RKS_ESTATE = -7,      /* call out of order (e.g. rks_get_* before rks_solve) */
-  RKS_EDENSE = -8       /* the small dense Schur iteration failed */
+  RKS_EDENSE = -8,      /* the small dense Schur iteration failed */
+  RKS_ETIMEOUT = -9     /* a bounded device-side wait (grid barrier) timed out */
 } rks_status;
 
 /* Wanted part of the spectrum (Sec. 5: largest / smallest modulus; real part). */

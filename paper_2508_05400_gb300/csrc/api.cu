@@ -76,6 +76,7 @@ struct rks_ctx {
   double* rprev = nullptr;
   double* znorm = nullptr;
   uint16_t* otab = nullptr;  // packed Omega (rows + signs), built once from the hash
+  unsigned* bar = nullptr;   // grid-barrier state of the cooperative least squares
   float2* lsr1 = nullptr;    // least-squares scratch: first-pass coefficients (m+1)
   float2* lsz1 = nullptr;    // and the projected sketch (d)
   double* tmp64 = nullptr;
@@ -189,6 +190,7 @@ int read_flag(rks_ctx* c, int* f) {
 }
 
 int flag_status(int f) {
+  if (f & rks::RKS_FLAG_TIMEOUT) return RKS_ETIMEOUT;
   if (f & rks::RKS_FLAG_NAN) return RKS_ENAN;
   if (f & rks::RKS_FLAG_HASH) return RKS_EINVAL;
   if (f & rks::RKS_FLAG_BREAKDOWN) return RKS_EBREAKDOWN;
@@ -208,9 +210,10 @@ void expand_df_launches(rks_ctx* c, int c0) {
                                c->otab, c->z_raw, c->stream);
     prof_end(c, s, RKS_K_SPMV, 1, spmv_bytes, 2.0 * c->nnz);
     s = prof_begin(c, RKS_K_LS);
-    rks::launch_df_small(j, c->d, c->zscale, j > c0 ? 1 : 0, 1, c->s_raw, c->z_raw, c->S, c->S2, c->colscale,
-                         c->rprev, c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1, c->flag, c->stream);
-    prof_end(c, s, RKS_K_LS, 3, 3.0 * P * c->d * col, 6.0 * c->d * col);
+    const int nls = rks::launch_df_small(j, c->d, c->zscale, j > c0 ? 1 : 0, 1, c->s_raw, c->z_raw, c->S, c->S2,
+                                         c->colscale, c->rprev, c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1,
+                                         c->lsz1, c->flag, c->bar, c->stream);
+    prof_end(c, s, RKS_K_LS, nls, 3.0 * P * c->d * col, 6.0 * c->d * col);
     s = prof_begin(c, RKS_K_UPDATE);
     rks::launch_df_update_sketch(c->n, c->Ub, c->ldu, col, c->nrs, c->sj, c->d, c->zeta, c->otab, c->s_raw,
                                  c->f32, c->stream);
@@ -219,7 +222,7 @@ void expand_df_launches(rks_ctx* c, int c0) {
   }
   int s = prof_begin(c, RKS_K_FINISH);
   rks::launch_df_small(c->m, c->d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale, c->rprev,
-                       c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1, c->flag, c->stream);
+                       c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1, c->flag, c->bar, c->stream);
   prof_end(c, s, RKS_K_FINISH, 1, 3.0 * P * c->d, 2.0 * c->d);
 }
 
@@ -614,7 +617,7 @@ void free_ctx(rks_ctx* c) {
   cudaFree(c->X); cudaFree(c->AX); cudaFree(c->rsum); cudaFree(c->pcol); cudaFree(c->plam);
   cudaFree(c->vals2); cudaFree(c->U2); cudaFree(c->S2); cudaFree(c->nrs); cudaFree(c->sj); cudaFree(c->Q2);
   cudaFree(c->rprev); cudaFree(c->znorm); cudaFree(c->tmp64); cudaFree(c->valsf); cudaFree(c->Uf);
-  cudaFree(c->otab); cudaFree(c->lsr1); cudaFree(c->lsz1);
+  cudaFree(c->otab); cudaFree(c->lsr1); cudaFree(c->lsz1); cudaFree(c->bar);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -645,6 +648,7 @@ const char* rks_strerror(int s) {
     case RKS_ENAN: return "non-finite value encountered";
     case RKS_ESTATE: return "call out of order";
     case RKS_EDENSE: return "small dense Schur iteration failed";
+    case RKS_ETIMEOUT: return "a bounded device-side wait timed out";
     default: return "unknown status";
   }
 }
@@ -740,8 +744,9 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
         (rc = dalloc(&c->Q2, (size_t)(m + 1) * (m + 1))) || (rc = dalloc(&c->rprev, m + 1)) ||
         (rc = dalloc(&c->znorm, 1)) || (rc = dalloc(&c->tmp64, n)) ||
         (rc = dalloc(&c->otab, (size_t)n * rks::omega_slots(o.zeta))) || (rc = dalloc(&c->lsr1, m + 1)) ||
-        (rc = dalloc(&c->lsz1, d)))
+        (rc = dalloc(&c->lsz1, d)) || (rc = dalloc(&c->bar, 2)))
       return fail(rc);
+    if (cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), c->stream) != cudaSuccess) return fail(RKS_ECUDA);
     {
       int bad = 0;
       if (cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream) != cudaSuccess) return fail(RKS_ECUDA);
@@ -806,7 +811,7 @@ static int run_alg1(rks_ctx* c, const double* start, int limit, double verify, i
     rks::launch_df_sketch_vec(c->n, c->Ub, d, c->zeta, c->otab, c->s_raw, c->f32, c->stream);
     CK(cudaMemsetAsync(c->znorm, 0, sizeof(double), c->stream));
     rks::launch_df_small(0, d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale, c->rprev, c->coef,
-                         m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1, c->flag, c->stream);
+                         m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1, c->flag, c->bar, c->stream);
     prof_end(c, ps, RKS_K_OTHER, src == c->tmp64 && !start ? 4 : 3, 0.0, 0.0);
   } else {
     if (c->u1) CK(cudaMemcpyAsync(c->U, c->u1, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));

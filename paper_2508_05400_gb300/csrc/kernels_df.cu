@@ -23,6 +23,8 @@
 // recovered (TwoSum) and added, with xl, to lo.  The bins are folded into the
 // global FP64 d-vector with one FP64 atomic add per bin and CTA.
 
+#include <algorithm>
+
 #include "rks_impl.h"
 
 namespace rks {
@@ -244,8 +246,8 @@ __device__ __forceinline__ void ld2(const float* p, float2& a, float2& b) {
 
 // u~ = sj * w' + sum_{col < c} U[:, col] * nrs[col]  (nrs = -b .* scale, DF)
 // written to U[:, c]; out_raw += Omega-sums of u~.
-template <int MAXZ, class TU>
-__global__ void __launch_bounds__(512) k_df_update_sketch(
+template <int MAXZ, class TU, int UNR, int MINB>
+__global__ void __launch_bounds__(512, MINB) k_df_update_sketch(
     int64_t n, TU* __restrict__ U, int64_t ldu, int c, const float2* __restrict__ nrs,
     const float2* __restrict__ sj, int d, const uint16_t* __restrict__ otab, double* out_raw) {
   extern __shared__ float shf[];
@@ -268,12 +270,12 @@ __global__ void __launch_bounds__(512) k_df_update_sketch(
     }
     const TU* up = U + i;
     int col = 0;
-    for (; col + 8 <= c; col += 8) {
-      float2 a[8], b[8];
+    for (; col + UNR <= c; col += UNR) {
+      float2 a[UNR], b[UNR];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) ld2(up + (int64_t)(col + q) * ldu, a[q], b[q]);
+      for (int q = 0; q < UNR; ++q) ld2(up + (int64_t)(col + q) * ldu, a[q], b[q]);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 0; q < UNR; ++q) {
         const float2 r = rsh[col + q];
         df_mac(a[q].x, a[q].y, r.x, r.y, s0, t0);
         df_mac(b[q].x, b[q].y, r.x, r.y, s1, t1);
@@ -390,6 +392,148 @@ __global__ void __launch_bounds__(256) k_df_ls1(
   }
   df_warp_sum(s, t);
   if (lane == 0) r1[col] = df_norm(s, t);
+}
+
+// Grid-wide barrier of the cooperative least-squares kernel.  bar[0] counts
+// arrivals, bar[1] is the generation.  The wait is bounded (about a second of
+// clock cycles): on timeout the kernel records RKS_FLAG_TIMEOUT and goes on,
+// and the host reports the failure instead of the device hanging.  The
+// cooperative launch guarantees that all CTAs are resident, so the bound is
+// never reached in a correct run.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, int* flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == nblocks) {
+      bar[0] = 0u;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (clock64() - t0 > 4000000000ll) { atomicOr(flag, RKS_FLAG_TIMEOUT); break; }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// sum_r S2[r, col] * v[r] over r = lane, lane + 32, ... < d (DF), with the
+// loads of four rows issued before their products (L2 latency overlap).
+__device__ __forceinline__ void df_col_dot(const float2* __restrict__ sc, const float2* v, int d, int lane,
+                                           float& s, float& t) {
+  int r = lane;
+  for (; r + 96 < d; r += 128) {
+    const float2 a0 = sc[r], a1 = sc[r + 32], a2 = sc[r + 64], a3 = sc[r + 96];
+    const float2 b0 = v[r], b1 = v[r + 32], b2 = v[r + 64], b3 = v[r + 96];
+    df_mac(a0.x, a0.y, b0.x, b0.y, s, t);
+    df_mac(a1.x, a1.y, b1.x, b1.y, s, t);
+    df_mac(a2.x, a2.y, b2.x, b2.y, s, t);
+    df_mac(a3.x, a3.y, b3.x, b3.y, s, t);
+  }
+  for (; r < d; r += 32) {
+    const float2 a = sc[r], b = v[r];
+    df_mac(a.x, a.y, b.x, b.y, s, t);
+  }
+}
+
+// The three least-squares phases of k_df_ls1/2/3 in one cooperative launch.
+__global__ void __launch_bounds__(256) k_df_ls_coop(
+    int j, int d, double zscale, int finish, double* __restrict__ s_raw, double* __restrict__ z_raw,
+    double* __restrict__ S64, float2* __restrict__ S2, double* __restrict__ colscale, double* __restrict__ rprev,
+    double* __restrict__ coef, int ldcoef, double* __restrict__ znorm_prev, float2* __restrict__ nrs,
+    float2* __restrict__ sj, float2* __restrict__ r1, float2* __restrict__ z1, unsigned* bar, int* flag) {
+  extern __shared__ float2 zd[];   // d
+  __shared__ double red[33];
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  const int gw = blockIdx.x * nw + warp, tw = gridDim.x * nw;   // global warp index, warps in grid
+  const int c = j + 1;
+  double inv = 0.0;
+  if (finish) {
+    double ss = 0.0;
+    for (int r = tid; r < d; r += nt) { double v = s_raw[r] * zscale; ss = fma(v, v, ss); }
+    ss = block_sum_d(ss, red);
+    const double beta = sqrt(ss);
+    const bool finite = isfinite(beta);
+    const bool brk = finite && !(beta > 1e-14 * znorm_prev[0]);
+    inv = (finite && !brk) ? 1.0 / beta : 0.0;
+    if (blockIdx.x == 0) {
+      for (int r = tid; r < d; r += nt) {
+        double v = s_raw[r] * zscale * inv;
+        S64[r + (size_t)j * d] = v;
+        S2[r + (size_t)j * d] = df_from_double(v);
+      }
+      if (j >= 1) {
+        double* cc = coef + (size_t)(j - 1) * ldcoef;
+        for (int i = tid; i < j; i += nt) cc[i] = rprev[i];
+        if (tid == 0) cc[j] = beta;
+      }
+      if (tid == 0) {
+        colscale[j] = inv;
+        if (!finite) atomicOr(flag, RKS_FLAG_NAN);
+        else if (brk) atomicOr(flag, RKS_FLAG_BREAKDOWN);
+      }
+    }
+  }
+  const double scj = finish ? inv : colscale[j];
+  double zz = 0.0;
+  for (int r = tid; r < d; r += nt) {
+    double v = z_raw[r] * zscale * scj;
+    zz = fma(v, v, zz);
+    zd[r] = df_from_double(v);
+  }
+  zz = block_sum_d(zz, red);
+  // phase 1: r1 = S^T z (column j straight from the sums when just finished)
+  for (int col = gw; col < c; col += tw) {
+    float s = 0.f, t = 0.f;
+    if (finish && col == j) {
+      for (int r = lane; r < d; r += 32) {
+        float2 a = df_from_double(s_raw[r] * zscale * inv), b = zd[r];
+        df_mac(a.x, a.y, b.x, b.y, s, t);
+      }
+    } else {
+      df_col_dot(S2 + (size_t)col * d, zd, d, lane, s, t);
+    }
+    df_warp_sum(s, t);
+    if (lane == 0) r1[col] = df_norm(s, t);
+  }
+  grid_barrier(bar, gridDim.x, flag);
+  // phase 2: z1 = z - S r1 (S[:, j] was written by CTA 0 before the barrier)
+  for (int r = gw; r < d; r += tw) {
+    float s = 0.f, t = 0.f;
+    for (int col = lane; col < c; col += 32) {
+      float2 a = S2[r + (size_t)col * d], b = r1[col];
+      df_mac(a.x, a.y, b.x, b.y, s, t);
+    }
+    df_warp_sum(s, t);
+    if (lane == 0) {
+      float s2 = zd[r].x, t2 = zd[r].y;
+      df_add(-s, -t, s2, t2);
+      z1[r] = df_norm(s2, t2);
+    }
+  }
+  grid_barrier(bar, gridDim.x, flag);
+  // phase 3: r = r1 + S^T z1; clear the sums (no longer read)
+  if (blockIdx.x == 0) {
+    for (int r = tid; r < d; r += nt) { z_raw[r] = 0.0; s_raw[r] = 0.0; }
+    if (tid == 0) { sj[0] = df_from_double(scj); znorm_prev[0] = sqrt(zz); }
+  }
+  for (int col = gw; col < c; col += tw) {
+    float s = 0.f, t = 0.f;
+    df_col_dot(S2 + (size_t)col * d, z1, d, lane, s, t);
+    df_warp_sum(s, t);
+    if (lane == 0) {
+      df_add(r1[col].x, r1[col].y, s, t);
+      const double rd = df_to_double(df_norm(s, t));
+      rprev[col] = rd;
+      nrs[col] = df_from_double(-rd * colscale[col]);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(256) k_df_ls2(int j, int d, double zscale, double* __restrict__ s_raw,
@@ -524,6 +668,66 @@ __global__ void k_sum_cols_f32(int64_t n, const float* __restrict__ U, int64_t l
   }
 }
 
+// Restart product, in place: U[i, c0 + o] = sum_l U[i, a0 + l] Q[l, o] for
+// o < nout (<= 4 * MAXOP), then U[i, c0 + nout] = U[i, move_src].  A CTA of
+// 256 threads owns 64 rows; the 4 threads of a row split the outputs (up to
+// MAXOP DF accumulators each, in registers).  Every read of the CTA's rows
+// precedes the barrier, every write follows it, and no other CTA touches
+// these rows, so the in-place update is safe.
+template <class TU, int MAXOP>
+__global__ void __launch_bounds__(256) k_df_restart(int64_t n, TU* U, int64_t ldu, int a0, int nin,
+                                                    const float2* __restrict__ Q, int nout, int c0, int move_src) {
+  extern __shared__ float2 qs[];                  // nin x nout, column-major
+  for (int t = threadIdx.x; t < nin * nout; t += blockDim.x) qs[t] = Q[t];
+  __syncthreads();
+  const int r = threadIdx.x & 63, g = threadIdx.x >> 6;       // row in tile, output group
+  const int64_t i = blockIdx.x * (int64_t)64 + r;
+  const int per = (nout + 3) / 4;
+  const int o0 = g * per;
+  const int no = max(0, min(per, nout - o0));
+  float s[MAXOP], t[MAXOP];
+#pragma unroll
+  for (int o = 0; o < MAXOP; ++o) { s[o] = 0.f; t[o] = 0.f; }
+  TU mv{};
+  if (i < n) {
+    const TU* up = U + i + (int64_t)a0 * ldu;
+    int l = 0;
+    for (; l + 4 <= nin; l += 4) {          // four loads in flight per thread
+      float2 a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = ldv(up + (int64_t)(l + u) * ldu);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2* ql = qs + (l + u) + (size_t)o0 * nin;
+#pragma unroll
+        for (int o = 0; o < MAXOP; ++o)
+          if (o < no) {
+            const float2 q = ql[(size_t)o * nin];
+            df_mac(a[u].x, a[u].y, q.x, q.y, s[o], t[o]);
+          }
+      }
+    }
+    for (; l < nin; ++l) {
+      const float2 a = ldv(up + (int64_t)l * ldu);
+      const float2* ql = qs + l + (size_t)o0 * nin;
+#pragma unroll
+      for (int o = 0; o < MAXOP; ++o)
+        if (o < no) {
+          const float2 q = ql[(size_t)o * nin];
+          df_mac(a.x, a.y, q.x, q.y, s[o], t[o]);
+        }
+    }
+    if (move_src >= 0 && g == 0) mv = U[i + (int64_t)move_src * ldu];
+  }
+  __syncthreads();
+  if (i < n) {
+#pragma unroll
+    for (int o = 0; o < MAXOP; ++o)
+      if (o < no) stv(U + i + (int64_t)(c0 + o0 + o) * ldu, df_norm(s[o], t[o]));
+    if (move_src >= 0 && g == 0) U[i + (int64_t)(c0 + nout) * ldu] = mv;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -547,14 +751,18 @@ cudaError_t configure_df_kernels() {
   RKS_SMEM((k_df_spmv_sketch<16, TA, TU>));
   RKS_SMEM_T(float2, float2) RKS_SMEM_T(float, float)
 #undef RKS_SMEM_T
-  RKS_SMEM((k_df_update_sketch<4, float2>)); RKS_SMEM((k_df_update_sketch<8, float2>));
-  RKS_SMEM((k_df_update_sketch<16, float2>)); RKS_SMEM((k_df_update_sketch<4, float>));
-  RKS_SMEM((k_df_update_sketch<8, float>)); RKS_SMEM((k_df_update_sketch<16, float>));
+  constexpr int U8 = kDfUpdUnroll, MB = kDfUpdMinBlocks;
+  RKS_SMEM((k_df_update_sketch<4, float2, U8, MB>)); RKS_SMEM((k_df_update_sketch<8, float2, U8, MB>));
+  RKS_SMEM((k_df_update_sketch<16, float2, U8, MB>)); RKS_SMEM((k_df_update_sketch<4, float, U8, MB>));
+  RKS_SMEM((k_df_update_sketch<8, float, U8, MB>)); RKS_SMEM((k_df_update_sketch<16, float, U8, MB>));
   RKS_SMEM((k_df_sketch_vec<4, float2>)); RKS_SMEM((k_df_sketch_vec<8, float2>)); RKS_SMEM((k_df_sketch_vec<16, float2>));
   RKS_SMEM((k_df_sketch_vec<4, float>)); RKS_SMEM((k_df_sketch_vec<8, float>)); RKS_SMEM((k_df_sketch_vec<16, float>));
   RKS_SMEM(k_df_ls1);
+  RKS_SMEM(k_df_ls_coop);
   RKS_SMEM(k_df_rows_gemm<float2>);
   RKS_SMEM(k_df_rows_gemm<float>);
+  RKS_SMEM((k_df_restart<float2, 4>)); RKS_SMEM((k_df_restart<float2, 8>)); RKS_SMEM((k_df_restart<float2, 16>));
+  RKS_SMEM((k_df_restart<float, 4>)); RKS_SMEM((k_df_restart<float, 8>)); RKS_SMEM((k_df_restart<float, 16>));
 #undef RKS_SMEM
   if (e == cudaSuccess) done = true;
   return e;
@@ -588,12 +796,15 @@ void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, int d, int ze
 template <class TU>
 static void update_t(int64_t n, void* U, int64_t ldu, int c, const float2* nrs, const float2* sj, int d, int zeta,
                      const uint16_t* otab, double* out_raw, cudaStream_t st) {
-  const int g = df_grid((n + 1) / 2, 512);
+  constexpr int U8 = kDfUpdUnroll, MB = kDfUpdMinBlocks;
+  int64_t g64 = ((n + 1) / 2 + 511) / 512;
+  if (g64 > 152 * MB) g64 = 152 * MB;
+  const int g = (int)std::max<int64_t>(g64, 1);
   const size_t sm = (size_t)2 * d * sizeof(float) + (size_t)c * sizeof(float2) + 16;
   TU* u = static_cast<TU*>(U);
-  if (zeta <= 4) k_df_update_sketch<4, TU><<<g, 512, sm, st>>>(n, u, ldu, c, nrs, sj, d, otab, out_raw);
-  else if (zeta <= 8) k_df_update_sketch<8, TU><<<g, 512, sm, st>>>(n, u, ldu, c, nrs, sj, d, otab, out_raw);
-  else k_df_update_sketch<16, TU><<<g, 512, sm, st>>>(n, u, ldu, c, nrs, sj, d, otab, out_raw);
+  if (zeta <= 4) k_df_update_sketch<4, TU, U8, MB><<<g, 512, sm, st>>>(n, u, ldu, c, nrs, sj, d, otab, out_raw);
+  else if (zeta <= 8) k_df_update_sketch<8, TU, U8, MB><<<g, 512, sm, st>>>(n, u, ldu, c, nrs, sj, d, otab, out_raw);
+  else k_df_update_sketch<16, TU, U8, MB><<<g, 512, sm, st>>>(n, u, ldu, c, nrs, sj, d, otab, out_raw);
 }
 
 void launch_df_update_sketch(int64_t n, void* U, int64_t ldu, int c, const float2* nrs, const float2* sj,
@@ -602,17 +813,28 @@ void launch_df_update_sketch(int64_t n, void* U, int64_t ldu, int c, const float
   else update_t<float2>(n, U, ldu, c, nrs, sj, d, zeta, otab, out_raw, st);
 }
 
-void launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_raw, double* z_raw, double* S64,
-                     float2* S2, double* colscale, double* rprev, double* coef, int ldcoef, double* znorm_prev,
-                     float2* nrs, float2* sj, float2* r1, float2* z1, int* flag, cudaStream_t st) {
+int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_raw, double* z_raw, double* S64,
+                    float2* S2, double* colscale, double* rprev, double* coef, int ldcoef, double* znorm_prev,
+                    float2* nrs, float2* sj, float2* r1, float2* z1, int* flag, unsigned* bar, cudaStream_t st) {
   const size_t sm = (size_t)d * sizeof(float2);
   const int c = j + 1;
+  if (ls && bar) {
+    // one cooperative launch: warps over columns / rows, two grid barriers
+    int g = (std::max(c, d) + 7) / 8;
+    g = std::min(g, 48);
+    void* args[] = {&j, &d, &zscale, &finish, &s_raw, &z_raw, &S64, &S2, &colscale, &rprev, &coef, &ldcoef,
+                    &znorm_prev, &nrs, &sj, &r1, &z1, &bar, &flag};
+    if (cudaLaunchCooperativeKernel((const void*)k_df_ls_coop, dim3(g), dim3(256), args, sm, st) == cudaSuccess)
+      return 1;
+    (void)cudaGetLastError();   // not available: fall back to the three-kernel form below
+  }
   const int g1 = ls ? (c + 7) / 8 : 1;
   k_df_ls1<<<g1, 256, sm, st>>>(j, d, zscale, finish, ls, s_raw, z_raw, S64, S2, colscale, rprev, coef, ldcoef,
                                 znorm_prev, r1, flag);
-  if (!ls) return;
+  if (!ls) return 1;
   k_df_ls2<<<(d + 7) / 8, 256, 0, st>>>(j, d, zscale, s_raw, z_raw, S2, colscale, r1, z1);
   k_df_ls3<<<(c + 7) / 8, 256, 0, st>>>(j, d, z_raw, S2, colscale, r1, z1, rprev, nrs, sj);
+  return 3;
 }
 
 void launch_omega_table(int64_t n, int d, int zeta, uint64_t seed, uint16_t* tab, int* flag, cudaStream_t st) {
@@ -657,8 +879,24 @@ void launch_df_sketch_vec(int64_t n, const void* x, int d, int zeta, const uint1
   else sketch_vec_t<float2>(n, x, d, zeta, otab, out_raw, st);
 }
 
+template <class TU>
+static void restart_t(int64_t n, TU* U, int64_t ldu, int a0, int nin, const float2* Q, int nout, int c0,
+                      int move_src, cudaStream_t st) {
+  const size_t sm = (size_t)nin * nout * sizeof(float2);
+  const int g = (int)((n + 63) / 64);
+  const int per = (nout + 3) / 4;
+  if (per <= 4) k_df_restart<TU, 4><<<g, 256, sm, st>>>(n, U, ldu, a0, nin, Q, nout, c0, move_src);
+  else if (per <= 8) k_df_restart<TU, 8><<<g, 256, sm, st>>>(n, U, ldu, a0, nin, Q, nout, c0, move_src);
+  else k_df_restart<TU, 16><<<g, 256, sm, st>>>(n, U, ldu, a0, nin, Q, nout, c0, move_src);
+}
+
 void launch_df_rows_gemm(int64_t n, void* U, int64_t ldu, int a0, int nin, const float2* Q, int nout, int c0,
                          int move_src, bool f32, cudaStream_t st) {
+  if (nout <= 64) {        // register-tiled restart product
+    if (f32) restart_t<float>(n, static_cast<float*>(U), ldu, a0, nin, Q, nout, c0, move_src, st);
+    else restart_t<float2>(n, static_cast<float2*>(U), ldu, a0, nin, Q, nout, c0, move_src, st);
+    return;
+  }
   const size_t sm = (size_t)df_gemm_smem(nin, nout);
   const int g = (int)((n + 127) / 128);
   if (f32) k_df_rows_gemm<float><<<g, 128, sm, st>>>(n, static_cast<float*>(U), ldu, a0, nin, Q, nout, c0, move_src);

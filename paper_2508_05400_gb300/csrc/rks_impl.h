@@ -5,13 +5,17 @@
 
 namespace rks {
 
-enum : int { RKS_FLAG_NAN = 1, RKS_FLAG_BREAKDOWN = 2, RKS_FLAG_HASH = 4 };
+enum : int { RKS_FLAG_NAN = 1, RKS_FLAG_BREAKDOWN = 2, RKS_FLAG_HASH = 4, RKS_FLAG_TIMEOUT = 8 };
 
 // CTAs of the kernels that carry a sketch (one shared-memory bin set each,
 // folded into the global d-vector with one atomic per bin).
 constexpr int kSketchCtas = 152 * 2;
 // CTAs of the double-float streaming kernels (512 threads each).
 constexpr int kDfCtas = 152 * 2;
+// Update kernel: columns loaded per batch and resident CTAs per SM it is
+// compiled for (register budget 65536 / (512 * kDfUpdMinBlocks) per thread).
+constexpr int kDfUpdUnroll = 8;
+constexpr int kDfUpdMinBlocks = 2;
 
 struct Csr {
   int64_t n = 0, nnz = 0;
@@ -35,9 +39,9 @@ void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, int d, int ze
                            double* out_raw, cudaStream_t st);
 void launch_df_update_sketch(int64_t n, void* U, int64_t ldu, int c, const float2* nrs, const float2* sj,
                              int d, int zeta, const uint16_t* otab, double* out_raw, bool f32, cudaStream_t st);
-void launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_raw, double* z_raw, double* S64,
+int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_raw, double* z_raw, double* S64,
                      float2* S2, double* colscale, double* rprev, double* coef, int ldcoef, double* znorm_prev,
-                     float2* nrs, float2* sj, float2* r1, float2* z1, int* flag, cudaStream_t st);
+                     float2* nrs, float2* sj, float2* r1, float2* z1, int* flag, unsigned* bar, cudaStream_t st);
 void launch_omega_table(int64_t n, int d, int zeta, uint64_t seed, uint16_t* tab, int* flag, cudaStream_t st);
 int omega_slots(int zeta);
 void launch_d2df(int64_t n, const double* x, void* y, bool f32, cudaStream_t st);

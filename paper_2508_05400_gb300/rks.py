@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "librks.so")
 
 WHICH = {"LM": 0, "SM": 1, "LR": 2, "SR": 3}
 STATUS = {0: "RKS_OK", -1: "RKS_EINVAL", -2: "RKS_ENOMEM", -3: "RKS_ECUDA", -4: "RKS_ENOCONV",
-          -5: "RKS_EBREAKDOWN", -6: "RKS_ENAN", -7: "RKS_ESTATE", -8: "RKS_EDENSE"}
+          -5: "RKS_EBREAKDOWN", -6: "RKS_ENAN", -7: "RKS_ESTATE", -8: "RKS_EDENSE",
+          -9: "RKS_ETIMEOUT"}
 RKS_OK, RKS_EINVAL, RKS_ENOCONV = 0, -1, -4
 
 

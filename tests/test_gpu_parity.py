@@ -315,3 +315,36 @@ def test_invariant_start_vector_reports_breakdown():
         with pytest.raises(K().RKSError) as e:
             s.solve()
     assert e.value.code == -5
+
+
+# ---------------------------------------------------------------------------
+# Mixed precision: FP32 basis phase, then the double-float finish
+# ---------------------------------------------------------------------------
+
+def test_mixed_matches_oracle_2d():
+    N = 30
+    A = I.convdiff_2d(N, N, 1.0, 20.0, 10.0)
+    ex = np.sort(I.convdiff_2d_eigenvalues(N, N, 1.0, 20.0, 10.0))[::-1]
+    info, _ = _check_against_oracle(A, 6, 18, 64, 8, "LR", 1e-13, 1e-10, exact=ex, prec="mixed")
+    assert info["converged"] == 1
+
+
+def test_mixed_3d_lognormal_fp32_matrix():
+    # 3D upwind operator with a log-normal diffusivity, FP32 values (the 160^3
+    # workload's structure at 20^3); residual target on the ||A||_1 scale.
+    P = I.convdiff3d_problem(N=20, k=8, p=24, d=96)
+    u1 = I.start_vector(P.A.n, 1)
+    with K().Solver.from_csr(P.A, P.k, P.p, P.d, which=P.which, zeta=P.zeta, u1=u1, prec="mixed",
+                             **P.solver_opts()) as s:
+        info = s.solve(allow_noconv=False)
+        lam, X, res = s.eigpairs()
+    assert res.max() <= P.tol
+    Z = K().unpack_eigvecs(lam, X)
+    hres, _ = R.true_residuals(P.A.to_scipy(), Z, lam)   # FP32 values promoted exactly
+    assert hres.max() <= P.tol
+    o = P.solver_opts()
+    ores = R.rks(P.A.to_scipy(), P.k, P.p, P.d, u1, zeta=P.zeta, seed=0, which=P.which,
+                 tol=o["tol"], eta_lock=o["eta_lock"], conv="norm1")
+    assert ores.converged
+    # both find the same rightmost eigenvalues to the accuracy the residual allows
+    assert np.allclose(np.sort(lam.real)[::-1][:4], np.sort(ores.eigvals.real)[::-1][:4], rtol=1e-4)
