@@ -75,7 +75,10 @@ struct rks_ctx {
   float2* Q2 = nullptr;
   double* rprev = nullptr;
   double* znorm = nullptr;
-  uint16_t* otab = nullptr;  // packed Omega (rows + signs), built once from the hash
+  uint16_t* otab = nullptr;  // packed Omega (rows + signs) from the hash; freed once the tiles are built
+  rks::SketchTiles tiles;    // per-tile bin lists of Omega (deterministic sketch accumulation)
+  double* part_z = nullptr;  // G x d per-CTA partial sketches of A u (z') and of u~ (s~)
+  double* part_s = nullptr;
   unsigned* bar = nullptr;   // grid-barrier state of the cooperative least squares
   float2* lsr1 = nullptr;    // least-squares scratch: first-pass coefficients (m+1)
   float2* lsz1 = nullptr;    // and the projected sketch (d)
@@ -206,24 +209,24 @@ void expand_df_launches(rks_ctx* c, int c0) {
     int s = prof_begin(c, RKS_K_SPMV);
     const size_t es = c->f32 ? sizeof(float) : sizeof(float2);
     char* ub = static_cast<char*>(c->Ub);
-    rks::launch_df_spmv_sketch(c->A2, ub + (size_t)j * c->ldu * es, ub + (size_t)col * c->ldu * es, c->d, c->zeta,
-                               c->otab, c->z_raw, c->stream);
+    rks::launch_df_spmv_sketch(c->A2, ub + (size_t)j * c->ldu * es, ub + (size_t)col * c->ldu * es, c->tiles,
+                               c->part_z, c->stream);
     prof_end(c, s, RKS_K_SPMV, 1, spmv_bytes, 2.0 * c->nnz);
     s = prof_begin(c, RKS_K_LS);
     const int nls = rks::launch_df_small(j, c->d, c->zscale, j > c0 ? 1 : 0, 1, c->s_raw, c->z_raw, c->S, c->S2,
                                          c->colscale, c->rprev, c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1,
-                                         c->lsz1, c->flag, c->bar, c->stream);
+                                         c->lsz1, c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream);
     prof_end(c, s, RKS_K_LS, nls, 3.0 * P * c->d * col, 6.0 * c->d * col);
     s = prof_begin(c, RKS_K_UPDATE);
-    rks::launch_df_update_sketch(c->n, c->Ub, c->ldu, col, c->nrs, c->sj, c->d, c->zeta, c->otab, c->s_raw,
-                                 c->f32, c->stream);
+    rks::launch_df_update_sketch(c->Ub, c->ldu, col, c->nrs, c->sj, c->tiles, c->part_s, c->f32, c->stream);
     prof_end(c, s, RKS_K_UPDATE, 1, (col + 2) * (c->f32 ? 4.0 : P) * n, 2.0 * n * col);
     ++c->nmatvec;
   }
   int s = prof_begin(c, RKS_K_FINISH);
-  rks::launch_df_small(c->m, c->d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale, c->rprev,
-                       c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1, c->flag, c->bar, c->stream);
-  prof_end(c, s, RKS_K_FINISH, 1, 3.0 * P * c->d, 2.0 * c->d);
+  const int nf = rks::launch_df_small(c->m, c->d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale,
+                                      c->rprev, c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1,
+                                      c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream);
+  prof_end(c, s, RKS_K_FINISH, nf, 3.0 * P * c->d, 2.0 * c->d);
 }
 
 // Algorithm 2: extend from the last vector at column q+ja to column m.
@@ -552,7 +555,7 @@ int finalize(rks_ctx* c) {
     if (rc) return rc;
     rc = dalloc(&c->AX, (size_t)c->ldu * (c->k + 1));
     if (rc) return rc;
-    rc = dalloc(&c->rsum, (size_t)4 * (c->k + 1));
+    rc = dalloc(&c->rsum, (size_t)4 * (c->k + 1) * rks::kResidCtas);
     if (rc) return rc;
     rc = dalloc(&c->pcol, (size_t)2 * (c->k + 1));
     if (rc) return rc;
@@ -589,15 +592,16 @@ int finalize(rks_ctx* c) {
   for (int t = 0; t < np; ++t) { pc[t] = col[t]; pc[np + t] = colim[t]; pv[t] = pl_re[t]; pv[np + t] = pl_im[t]; }
   CK(cudaMemcpyAsync(c->pcol, pc.data(), pc.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->plam, pv.data(), pv.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemsetAsync(c->rsum, 0, sizeof(double) * 4 * np, c->stream));
-  rks::launch_resid_sums(c->n, c->X, c->AX, c->ldu, np, c->pcol, c->pcol + np, c->plam, c->plam + np, c->rsum,
-                         c->stream);
+  const int rg = rks::launch_resid_sums(c->n, c->X, c->AX, c->ldu, np, c->pcol, c->pcol + np, c->plam,
+                                        c->plam + np, c->rsum, c->stream);
   prof_end(c, ps, RKS_K_OTHER, 3, 0.0, 0.0);
   int rc = launch_err();
   if (rc) return rc;
-  std::vector<double> sums(4 * np);
-  CK(cudaMemcpyAsync(sums.data(), c->rsum, sums.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<double> part((size_t)4 * np * rg), sums(4 * np, 0.0);
+  CK(cudaMemcpyAsync(part.data(), c->rsum, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  for (int q = 0; q < 4 * np; ++q)
+    for (int g = 0; g < rg; ++g) sums[q] += part[(size_t)q * rg + g];
   prof_flush(c);
   c->resid.assign(kk, 0.0);
   for (int t = 0; t < np; ++t) {
@@ -618,6 +622,8 @@ void free_ctx(rks_ctx* c) {
   cudaFree(c->vals2); cudaFree(c->U2); cudaFree(c->S2); cudaFree(c->nrs); cudaFree(c->sj); cudaFree(c->Q2);
   cudaFree(c->rprev); cudaFree(c->znorm); cudaFree(c->tmp64); cudaFree(c->valsf); cudaFree(c->Uf);
   cudaFree(c->otab); cudaFree(c->lsr1); cudaFree(c->lsz1); cudaFree(c->bar);
+  rks::free_sketch_tiles(&c->tiles);
+  cudaFree(c->part_z); cudaFree(c->part_s);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -718,18 +724,19 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
     return fail(RKS_ECUDA);
   if (bad) return fail(RKS_EINVAL);
   c->A.n = n; c->A.nnz = c->nnz; c->A.rowptr = c->rowptr; c->A.colind = c->colind; c->A.vals = c->vals;
-  // ||A||_1
+  // ||A||_1: column sums of |a_ij| on the host, entries in storage order (the
+  // same bits on every run; FP64 atomics would add them in varying order)
   {
-    double* colsum = nullptr;
-    if ((rc = dalloc(&colsum, n))) return fail(rc);
-    cudaMemsetAsync(colsum, 0, n * sizeof(double), c->stream);
-    rks::launch_col_abs_sums(c->nnz, c->colind, c->vals, colsum, c->stream);
-    std::vector<double> h(n);
-    cudaError_t e = cudaMemcpyAsync(h.data(), colsum, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    std::vector<int32_t> ci(c->nnz);
+    std::vector<double> cv(c->nnz);
+    cudaError_t e = cudaMemcpyAsync(ci.data(), c->colind, c->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(cv.data(), c->vals, c->nnz * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    cudaFree(colsum);
     if (e != cudaSuccess) return fail(RKS_ECUDA);
-    c->norm1 = *std::max_element(h.begin(), h.end());
+    std::vector<double> colsum(n, 0.0);
+    for (int64_t p = 0; p < c->nnz; ++p) colsum[ci[p]] += std::fabs(cv[p]);
+    c->norm1 = n ? *std::max_element(colsum.begin(), colsum.end()) : 0.0;
     if (!std::isfinite(c->norm1)) return fail(RKS_ENAN);
     if (c->norm1 == 0.0) c->norm1 = 1.0;
   }
@@ -756,6 +763,13 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
         return fail(RKS_ECUDA);
       if (bad) return fail(RKS_EINVAL);
     }
+    if (rks::configure_df_kernels() != cudaSuccess) return fail(RKS_ECUDA);
+    if (rks::build_sketch_tiles(n, d, o.zeta, c->otab, &c->tiles, c->stream) != 0) return fail(RKS_ECUDA);
+    cudaFree(c->otab);
+    c->otab = nullptr;
+    if (rks::sketch_tile_smem(c->tiles, m + 1) > 200 * 1024) return fail(RKS_EINVAL);
+    if ((rc = dalloc(&c->part_z, (size_t)c->tiles.G * d)) || (rc = dalloc(&c->part_s, (size_t)c->tiles.G * d)))
+      return fail(rc);
     rks::launch_d2df(c->nnz, c->vals, c->vals2, false, c->stream);
     c->A2.n = n; c->A2.nnz = c->nnz; c->A2.rowptr = c->rowptr; c->A2.colind = c->colind; c->A2.vals = c->vals2;
     c->Ub = c->U2;
@@ -808,11 +822,12 @@ static int run_alg1(rks_ctx* c, const double* start, int limit, double verify, i
     const double* src = start ? start : c->u1;
     if (!src) { rks::launch_start_vector(c->n, c->seed + 1, c->tmp64, c->stream); src = c->tmp64; }
     rks::launch_d2df(c->n, src, c->Ub, c->f32, c->stream);
-    rks::launch_df_sketch_vec(c->n, c->Ub, d, c->zeta, c->otab, c->s_raw, c->f32, c->stream);
+    rks::launch_df_sketch_vec(c->Ub, c->tiles, c->part_s, c->f32, c->stream);
     CK(cudaMemsetAsync(c->znorm, 0, sizeof(double), c->stream));
-    rks::launch_df_small(0, d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale, c->rprev, c->coef,
-                         m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1, c->flag, c->bar, c->stream);
-    prof_end(c, ps, RKS_K_OTHER, src == c->tmp64 && !start ? 4 : 3, 0.0, 0.0);
+    const int nf = rks::launch_df_small(0, d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale,
+                                        c->rprev, c->coef, m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1,
+                                        c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream);
+    prof_end(c, ps, RKS_K_OTHER, (src == c->tmp64 && !start ? 3 : 2) + nf, 0.0, 0.0);
   } else {
     if (c->u1) CK(cudaMemcpyAsync(c->U, c->u1, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     else rks::launch_start_vector(c->n, c->seed + 1, c->U, c->stream);

@@ -395,16 +395,9 @@ __global__ void k_resid_sums(int64_t n, const double* __restrict__ X, const doub
     for (int q = 0; q < 4; ++q) {
       double v = lane < nw ? red[q][lane] : 0.0;
       for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) atomicAdd(&out[t * 4 + q], v);
+      if (lane == 0) out[((size_t)t * 4 + q) * gridDim.x + blockIdx.x] = v;   // summed on the host in CTA order
     }
   }
-}
-
-__global__ void k_col_abs_sums(int64_t nnz, const int32_t* __restrict__ colind,
-                               const double* __restrict__ vals, double* __restrict__ colsum) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
-       p += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&colsum[colind[p]], fabs(vals[p]));
 }
 
 __global__ void k_f32_to_f64(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
@@ -539,14 +532,12 @@ void launch_spmm(const Csr& A, const double* X, int64_t ldx, double* Y, int64_t 
   k_spmm<<<grid, 256, 0, st>>>(A.n, A.rowptr, A.colind, A.vals, X, ldx, Y, ldy, ncols);
 }
 
-void launch_resid_sums(int64_t n, const double* X, const double* AX, int64_t ld, int npairs, const int* col,
-                       const int* colim, const double* lre, const double* lim, double* out, cudaStream_t st) {
-  dim3 grid((unsigned)grid_for(n, 256, 152 * 2), (unsigned)npairs);
+int launch_resid_sums(int64_t n, const double* X, const double* AX, int64_t ld, int npairs, const int* col,
+                      const int* colim, const double* lre, const double* lim, double* out, cudaStream_t st) {
+  const int g = grid_for(n, 256, kResidCtas);
+  dim3 grid((unsigned)g, (unsigned)npairs);
   k_resid_sums<<<grid, 256, 0, st>>>(n, X, AX, ld, col, colim, lre, lim, out);
-}
-
-void launch_col_abs_sums(int64_t nnz, const int32_t* colind, const double* vals, double* colsum, cudaStream_t st) {
-  k_col_abs_sums<<<grid_for(nnz, 256, 152 * 8), 256, 0, st>>>(nnz, colind, vals, colsum);
+  return g;
 }
 
 void launch_f32_to_f64(int64_t n, const float* a, double* b, cudaStream_t st) {

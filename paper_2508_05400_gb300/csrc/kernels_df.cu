@@ -17,13 +17,18 @@
 //                     locked and active columns (Thm 4.3), z = z' / beta_j
 //   k_df_update_sketch u~_{j+1} = w'/beta_j - U b, s~_{j+1} = Omega u~_{j+1}
 //
-// Sketch accumulation: per-CTA bins hold (hi, lo) float pairs in shared
-// memory.  A contribution x = xh + xl is added with a returning FP32 atomic on
-// hi: from the returned old value the exact rounding error of old + xh is
-// recovered (TwoSum) and added, with xl, to lo.  The bins are folded into the
-// global FP64 d-vector with one FP64 atomic add per bin and CTA.
+// Sketch accumulation is deterministic: no atomics.  Each CTA owns a fixed,
+// contiguous range of rows, cut into tiles of at most kTileRows rows.  For
+// every tile a transposed copy of Omega restricted to the tile (the "bin
+// lists", built once by k_tiles_build) gives, per sketch row, the tile rows
+// that contribute to it and their signs, in a fixed order.  A tile's values
+// are staged in shared memory; then the threads that own the tile's sketch
+// rows sum their lists (DF, TwoSum) into per-CTA DF accumulators.  Each CTA
+// writes its d partial sums; the consumer adds the CTA partials in CTA order
+// (fold_group).  The result is the same bits on every run.
 
 #include <algorithm>
+#include <vector>
 
 #include "rks_impl.h"
 
@@ -115,66 +120,14 @@ __device__ __forceinline__ uint64_t mix64_df(uint64_t z) {
 
 // Packed Omega table: for column i, MAXZ uint16 entries (row in bits 0..14,
 // bit 15 set for a negative sign), written once by k_omega_table from the same
-// hash; unused slots (t >= zeta) are 0xFFFF.
-template <int MAXZ>
-struct OmegaRow { uint16_t e[MAXZ]; };
-
-template <int MAXZ>
-__device__ __forceinline__ OmegaRow<MAXZ> omega_load(const uint16_t* __restrict__ tab, int64_t i) {
-  OmegaRow<MAXZ> r;
-  if constexpr (MAXZ == 4) {
-    uint2 v = __ldg(reinterpret_cast<const uint2*>(tab) + i);
-    r.e[0] = v.x & 0xFFFF; r.e[1] = v.x >> 16; r.e[2] = v.y & 0xFFFF; r.e[3] = v.y >> 16;
-  } else {
-    const uint4* p = reinterpret_cast<const uint4*>(tab) + i * (MAXZ / 8);
-#pragma unroll
-    for (int q = 0; q < MAXZ / 8; ++q) {
-      uint4 v = __ldg(p + q);
-      r.e[8 * q + 0] = v.x & 0xFFFF; r.e[8 * q + 1] = v.x >> 16;
-      r.e[8 * q + 2] = v.y & 0xFFFF; r.e[8 * q + 3] = v.y >> 16;
-      r.e[8 * q + 4] = v.z & 0xFFFF; r.e[8 * q + 5] = v.z >> 16;
-      r.e[8 * q + 6] = v.w & 0xFFFF; r.e[8 * q + 7] = v.w >> 16;
-    }
-  }
-  return r;
-}
-
-// Add sign * (vh + vl) into the bins of the rows listed in `o`.
-template <int MAXZ>
-__device__ __forceinline__ void df_sketch_add_tab(float* bh, float* bl, const OmegaRow<MAXZ>& o, float vh,
-                                                  float vl) {
-#pragma unroll
-  for (int t = 0; t < MAXZ; ++t) {
-    const uint32_t e = o.e[t];
-    if (e == 0xFFFFu) continue;
-    const int row = e & 0x7FFF;
-    const float xh = (e & 0x8000u) ? -vh : vh;
-    const float xl = (e & 0x8000u) ? -vl : vl;
-    float old = atomicAdd(&bh[row], xh);
-    float s, er;
-    two_sum(old, xh, s, er);
-    atomicAdd(&bl[row], er + xl);
-  }
-}
-
-__device__ __forceinline__ void df_bins_zero(float* bh, float* bl, int d) {
-  for (int r = threadIdx.x; r < d; r += blockDim.x) { bh[r] = 0.f; bl[r] = 0.f; }
-  __syncthreads();
-}
-
-__device__ __forceinline__ void df_bins_flush(const float* bh, const float* bl, double* out, int d) {
-  __syncthreads();
-  for (int r = threadIdx.x; r < d; r += blockDim.x) {
-    double v = (double)bh[r] + (double)bl[r];
-    if (v != 0.0) atomicAdd(&out[r], v);
-  }
-}
+// hash; unused slots (t >= zeta) are 0xFFFF.  The tile bin lists are built
+// from it.
 
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
 
-// The packed Omega table (see OmegaRow) from the hash of rks.h.
+// The packed Omega table from the hash of rks.h.
 template <int MAXZ>
 __global__ void k_omega_table(int64_t n, int d, int zeta, uint64_t seed, uint16_t* __restrict__ tab, int* flag) {
   const uint64_t gamma = 0x9E3779B97F4A7C15ull;
@@ -205,30 +158,212 @@ __global__ void k_omega_table(int64_t n, int d, int zeta, uint64_t seed, uint16_
   }
 }
 
-// w'[i] = sum_p A_p x[col_p]  (A and x in DF); out_raw += Omega-sums of w'.
-template <int MAXZ, class TA, class TU>
-__global__ void __launch_bounds__(512) k_df_spmv_sketch(
-    int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-    const TA* __restrict__ vals, const TU* __restrict__ x, TU* __restrict__ w, int d,
-    const uint16_t* __restrict__ otab, double* out_raw) {
-  extern __shared__ float shf[];
-  float* bh = shf;
-  float* bl = shf + d;
-  df_bins_zero(bh, bl, d);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float s = 0.f, t = 0.f;
-    const int p0 = rowptr[i], p1 = rowptr[i + 1];
-    for (int p = p0; p < p1; ++p) {
-      float2 a = ldv(vals + p);
-      float2 xv = ldv(x + colind[p]);
-      df_mac(a.x, a.y, xv.x, xv.y, s, t);
-    }
-    const OmegaRow<MAXZ> o = omega_load<MAXZ>(otab, i);
-    float2 v = stv(w + i, df_norm(s, t));
-    df_sketch_add_tab<MAXZ>(bh, bl, o, v.x, v.y);
+// ---------------------------------------------------------------------------
+// tile bin lists (built once per context from the packed table)
+// ---------------------------------------------------------------------------
+
+// Largest number of entries of one sketch row within one tile (atomicMax into
+// *lmax; the per-bin counts are integers, so their order does not matter).
+template <int MAXZ>
+__global__ void __launch_bounds__(256) k_tiles_count(const int64_t* __restrict__ trow, int d,
+                                                     const uint16_t* __restrict__ otab, int* lmax) {
+  extern __shared__ int cnt[];   // d
+  const int64_t t = blockIdx.x;
+  for (int b = threadIdx.x; b < d; b += blockDim.x) cnt[b] = 0;
+  __syncthreads();
+  const int64_t q1 = trow[t + 1] * MAXZ;
+  for (int64_t q = trow[t] * MAXZ + threadIdx.x; q < q1; q += blockDim.x) {
+    const uint32_t e = otab[q];
+    if (e != 0xFFFFu) atomicAdd(&cnt[e & 0x7FFF], 1);
   }
-  df_bins_flush(bh, bl, out_raw, d);
+  __syncthreads();
+  int m = 0;
+  for (int b = threadIdx.x; b < d; b += blockDim.x) m = max(m, cnt[b]);
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(lmax, m);
+}
+
+// Bin lists of one tile (one CTA per tile), jagged-diagonal layout:
+//   positions p = 0..d-1 rank the sketch rows by entry count (descending,
+//   ties by row index); meta[t*d + p] = row | count << 16;
+//   slot s holds entry s of every position whose count exceeds s, the
+//   positions in order, from off[t*(L+1) + s] = sum_p min(count_p, s);
+//   an entry is (tile row) | 0x8000 for a negative sign.
+// The entries of a sketch row are listed in (32-row chunk, slot, lane) order,
+// fixed by the table alone.
+template <int MAXZ>
+__global__ void __launch_bounds__(256) k_tiles_build(const int64_t* __restrict__ trow, int d, int zeta, int L,
+                                                     const uint16_t* __restrict__ otab, uint32_t* __restrict__ meta,
+                                                     int* __restrict__ off, uint16_t* __restrict__ ent) {
+  extern __shared__ int sm[];
+  int* cnt = sm;          // d: entries per sketch row
+  int* rank = cnt + d;    // d: position of each sketch row
+  int* scnt = rank + d;   // d: counts by position
+  int* cur = scnt + d;    // d: fill cursor per sketch row
+  int* offs = cur + d;    // L + 1
+  const int64_t t = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t r0 = trow[t], r1 = trow[t + 1];
+  for (int b = tid; b < d; b += nt) { cnt[b] = 0; cur[b] = 0; }
+  __syncthreads();
+  for (int64_t q = r0 * MAXZ + tid; q < r1 * MAXZ; q += nt) {
+    const uint32_t e = otab[q];
+    if (e != 0xFFFFu) atomicAdd(&cnt[e & 0x7FFF], 1);
+  }
+  __syncthreads();
+  for (int b = tid; b < d; b += nt) {
+    const int cb = cnt[b];
+    int r = 0;
+    for (int b2 = 0; b2 < d; ++b2) {
+      const int c2 = cnt[b2];
+      r += (c2 > cb) || (c2 == cb && b2 < b);
+    }
+    rank[b] = r;
+  }
+  __syncthreads();
+  for (int b = tid; b < d; b += nt) {
+    scnt[rank[b]] = cnt[b];
+    meta[t * d + rank[b]] = (uint32_t)b | ((uint32_t)cnt[b] << 16);
+  }
+  __syncthreads();
+  for (int s = tid; s <= L; s += nt) {
+    int o = 0;
+    for (int p = 0; p < d; ++p) o += min(scnt[p], s);
+    offs[s] = o;
+    off[t * (L + 1) + s] = o;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int lane = tid;
+    uint16_t* et = ent + r0 * zeta;
+    const int rows = (int)(r1 - r0);
+    for (int c0 = 0; c0 < rows; c0 += 32) {
+      const int l = c0 + lane;
+      for (int s = 0; s < MAXZ; ++s) {
+        const uint32_t e = l < rows ? (uint32_t)otab[(r0 + l) * MAXZ + s] : 0xFFFFu;
+        const bool v = e != 0xFFFFu;
+        const uint32_t key = v ? (e & 0x7FFFu) : (0x10000u + lane);   // no two invalid lanes match
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        if (v) {
+          const int b = (int)(e & 0x7FFFu);
+          const int kk = cur[b] + __popc(grp & ((1u << lane) - 1u));
+          et[offs[kk] + rank[b]] = (uint16_t)(l | (e & 0x8000u));
+        }
+        __syncwarp();
+        if (v && lane == __ffs(grp) - 1) cur[e & 0x7FFFu] += __popc(grp);
+        __syncwarp();
+      }
+    }
+  }
+}
+
+// (s, e) += sign * vals[row] for one bin-list entry
+__device__ __forceinline__ void tile_add(uint32_t x, const float2* vals, float& s, float& e) {
+  const float2 v = vals[x & 0x7FFFu];
+  const uint32_t sg = (x & 0x8000u) << 16;
+  df_add(__uint_as_float(__float_as_uint(v.x) ^ sg), __uint_as_float(__float_as_uint(v.y) ^ sg), s, e);
+}
+
+// Sketch of one staged tile: acc[row] += sum over the row's bin list of
+// sign * vals[tile row], entries in their stored order.  H adjacent lanes
+// share a position (each takes every H-th entry) when d is small; their sums
+// are combined by a fixed xor tree.  A sketch row has one position per tile,
+// so acc[row] has one writer per tile.
+__device__ __forceinline__ void tile_gather(const SketchTiles& tv, int64_t t, int64_t r0, const float2* vals,
+                                            const int* offs, float2* acc) {
+  const int d = tv.d, H = tv.H, total = d * H;
+  const int lane = threadIdx.x & 31;
+  const uint32_t* __restrict__ meta = tv.meta + t * d;
+  const uint16_t* __restrict__ ent = tv.ent + r0 * tv.zeta;
+  for (int base = threadIdx.x & ~31; base < total; base += blockDim.x) {
+    const int pp = base + lane;
+    const int p = pp / H, h = pp - p * H;
+    float s = 0.f, e = 0.f;
+    int b = -1, cnt = 0;
+    if (pp < total) {
+      const uint32_t mt = __ldg(meta + p);
+      b = (int)(mt & 0xFFFFu);
+      cnt = (int)(mt >> 16);
+      int q = h;
+      for (; q + 3 * H < cnt; q += 4 * H) {
+        const uint32_t x0 = __ldg(ent + offs[q] + p), x1 = __ldg(ent + offs[q + H] + p);
+        const uint32_t x2 = __ldg(ent + offs[q + 2 * H] + p), x3 = __ldg(ent + offs[q + 3 * H] + p);
+        tile_add(x0, vals, s, e);
+        tile_add(x1, vals, s, e);
+        tile_add(x2, vals, s, e);
+        tile_add(x3, vals, s, e);
+      }
+      for (; q < cnt; q += H) tile_add(__ldg(ent + offs[q] + p), vals, s, e);
+    }
+    for (int o = 1; o < H; o <<= 1) {
+      const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+      const float e2 = __shfl_xor_sync(0xffffffffu, e, o);
+      float ss, er;
+      two_sum(s, s2, ss, er);
+      s = ss;
+      e = e + e2 + er;
+    }
+    if (h == 0 && cnt > 0) {
+      const float2 a = acc[b];
+      float as = a.x, ae = a.y;
+      df_add(s, e, as, ae);
+      acc[b] = df_norm(as, ae);
+    }
+  }
+}
+
+// Shared memory of a tile kernel: acc (d), two value buffers, the update's
+// coefficients (c), two slot-offset buffers.
+__host__ __device__ inline size_t tile_smem_bytes(int d, int L, int c) {
+  return ((size_t)d + 2 * kTileRows + c) * sizeof(float2) + (size_t)2 * (L + 1) * sizeof(int);
+}
+
+// Stage the slot offsets of tile t.
+__device__ __forceinline__ void tile_offsets(const SketchTiles& tv, int64_t t, int* of) {
+  const int L1 = tv.L + 1;
+  for (int q = threadIdx.x; q < L1; q += blockDim.x) of[q] = tv.off[t * L1 + q];
+}
+
+__device__ __forceinline__ void tile_write_part(const float2* acc, int d, double* part) {
+  __syncthreads();
+  for (int r = threadIdx.x; r < d; r += blockDim.x) part[(size_t)blockIdx.x * d + r] = df_to_double(acc[r]);
+}
+
+// w'[i] = sum_p A_p x[col_p] (DF) over the CTA's tiles; part[cta] = the
+// CTA's Omega-sums of w' as stored.
+template <class TA, class TU>
+__global__ void __launch_bounds__(512) k_df_spmv_sketch(
+    const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind, const TA* __restrict__ vals,
+    const TU* __restrict__ x, TU* __restrict__ w, const SketchTiles tv, double* __restrict__ part) {
+  extern __shared__ float2 sh2[];
+  const int d = tv.d, L1 = tv.L + 1;
+  float2* acc = sh2;
+  float2* vb = acc + d;
+  int* offs = reinterpret_cast<int*>(vb + 2 * kTileRows);
+  for (int r = threadIdx.x; r < d; r += blockDim.x) acc[r] = make_float2(0.f, 0.f);
+  const int t0 = tv.ctile[blockIdx.x], t1 = tv.ctile[blockIdx.x + 1];
+  for (int t = t0; t < t1; ++t) {
+    const int buf = (t - t0) & 1;
+    float2* v = vb + buf * kTileRows;
+    int* of = offs + buf * L1;
+    const int64_t r0 = tv.row[t];
+    const int rows = (int)(tv.row[t + 1] - r0);
+    for (int l = threadIdx.x; l < rows; l += blockDim.x) {
+      const int64_t i = r0 + l;
+      float s = 0.f, e = 0.f;
+      const int p0 = rowptr[i], p1 = rowptr[i + 1];
+      for (int p = p0; p < p1; ++p) {
+        const float2 a = ldv(vals + p);
+        const float2 xv = ldv(x + colind[p]);
+        df_mac(a.x, a.y, xv.x, xv.y, s, e);
+      }
+      v[l] = stv(w + i, df_norm(s, e));
+    }
+    tile_offsets(tv, t, of);
+    __syncthreads();
+    tile_gather(tv, t, r0, v, of, acc);
+  }
+  tile_write_part(acc, d, part);
 }
 
 // Vector load of two consecutive rows (i even, ld even): float4 = two pairs,
@@ -245,59 +380,96 @@ __device__ __forceinline__ void ld2(const float* p, float2& a, float2& b) {
 }
 
 // u~ = sj * w' + sum_{col < c} U[:, col] * nrs[col]  (nrs = -b .* scale, DF)
-// written to U[:, c]; out_raw += Omega-sums of u~.
-template <int MAXZ, class TU, int UNR, int MINB>
+// written to U[:, c]; part[cta] = the CTA's Omega-sums of u~ as stored.
+// A thread takes two consecutive rows (tile starts are even and ld is a
+// multiple of 32, so the pair load stays aligned and inside the column).
+template <class TU, int UNR, int MINB>
 __global__ void __launch_bounds__(512, MINB) k_df_update_sketch(
-    int64_t n, TU* __restrict__ U, int64_t ldu, int c, const float2* __restrict__ nrs,
-    const float2* __restrict__ sj, int d, const uint16_t* __restrict__ otab, double* out_raw) {
-  extern __shared__ float shf[];
-  float* bh = shf;
-  float* bl = shf + d;
-  float2* rsh = reinterpret_cast<float2*>(shf + 2 * d);
+    TU* __restrict__ U, int64_t ldu, int c, const float2* __restrict__ nrs, const float2* __restrict__ sj,
+    const SketchTiles tv, double* __restrict__ part) {
+  extern __shared__ float2 sh2[];
+  const int d = tv.d, L1 = tv.L + 1;
+  float2* acc = sh2;
+  float2* vb = acc + d;
+  float2* rsh = vb + 2 * kTileRows;
+  int* offs = reinterpret_cast<int*>(rsh + c);
   for (int col = threadIdx.x; col < c; col += blockDim.x) rsh[col] = nrs[col];
-  df_bins_zero(bh, bl, d);
+  for (int r = threadIdx.x; r < d; r += blockDim.x) acc[r] = make_float2(0.f, 0.f);
+  __syncthreads();
   const float2 sc = sj[0];
-  const int64_t npair = (n + 1) / 2;
-  for (int64_t pi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pi < npair;
-       pi += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = 2 * pi;          // rows i, i + 1 (ld is a multiple of 32: the pair stays aligned)
-    float s0 = 0.f, t0 = 0.f, s1 = 0.f, t1 = 0.f;
-    {
-      float2 w0, w1;
-      ld2(U + i + (int64_t)c * ldu, w0, w1);
-      df_mac(w0.x, w0.y, sc.x, sc.y, s0, t0);
-      df_mac(w1.x, w1.y, sc.x, sc.y, s1, t1);
-    }
-    const TU* up = U + i;
-    int col = 0;
-    for (; col + UNR <= c; col += UNR) {
-      float2 a[UNR], b[UNR];
-#pragma unroll
-      for (int q = 0; q < UNR; ++q) ld2(up + (int64_t)(col + q) * ldu, a[q], b[q]);
-#pragma unroll
-      for (int q = 0; q < UNR; ++q) {
-        const float2 r = rsh[col + q];
-        df_mac(a[q].x, a[q].y, r.x, r.y, s0, t0);
-        df_mac(b[q].x, b[q].y, r.x, r.y, s1, t1);
+  const int t0 = tv.ctile[blockIdx.x], t1 = tv.ctile[blockIdx.x + 1];
+  for (int t = t0; t < t1; ++t) {
+    const int buf = (t - t0) & 1;
+    float2* v = vb + buf * kTileRows;
+    int* of = offs + buf * L1;
+    const int64_t r0 = tv.row[t];
+    const int rows = (int)(tv.row[t + 1] - r0);
+    for (int l = 2 * threadIdx.x; l < rows; l += 2 * blockDim.x) {
+      const int64_t i = r0 + l;
+      float s0 = 0.f, t0a = 0.f, s1 = 0.f, t1a = 0.f;
+      {
+        float2 w0, w1;
+        ld2(U + i + (int64_t)c * ldu, w0, w1);
+        df_mac(w0.x, w0.y, sc.x, sc.y, s0, t0a);
+        df_mac(w1.x, w1.y, sc.x, sc.y, s1, t1a);
       }
+      const TU* up = U + i;
+      int col = 0;
+      for (; col + UNR <= c; col += UNR) {
+        float2 a[UNR], bb[UNR];
+#pragma unroll
+        for (int q = 0; q < UNR; ++q) ld2(up + (int64_t)(col + q) * ldu, a[q], bb[q]);
+#pragma unroll
+        for (int q = 0; q < UNR; ++q) {
+          const float2 r = rsh[col + q];
+          df_mac(a[q].x, a[q].y, r.x, r.y, s0, t0a);
+          df_mac(bb[q].x, bb[q].y, r.x, r.y, s1, t1a);
+        }
+      }
+      for (; col < c; ++col) {
+        float2 a, bb;
+        ld2(up + (int64_t)col * ldu, a, bb);
+        const float2 r = rsh[col];
+        df_mac(a.x, a.y, r.x, r.y, s0, t0a);
+        df_mac(bb.x, bb.y, r.x, r.y, s1, t1a);
+      }
+      v[l] = stv(U + i + (int64_t)c * ldu, df_norm(s0, t0a));
+      if (l + 1 < rows) v[l + 1] = stv(U + i + 1 + (int64_t)c * ldu, df_norm(s1, t1a));
     }
-    for (; col < c; ++col) {
-      float2 a, b;
-      ld2(up + (int64_t)col * ldu, a, b);
-      const float2 r = rsh[col];
-      df_mac(a.x, a.y, r.x, r.y, s0, t0);
-      df_mac(b.x, b.y, r.x, r.y, s1, t1);
-    }
-    const float2 v0 = stv(U + i + (int64_t)c * ldu, df_norm(s0, t0));
-    df_sketch_add_tab<MAXZ>(bh, bl, omega_load<MAXZ>(otab, i), v0.x, v0.y);
-    if (i + 1 < n) {
-      const float2 v1 = stv(U + i + 1 + (int64_t)c * ldu, df_norm(s1, t1));
-      df_sketch_add_tab<MAXZ>(bh, bl, omega_load<MAXZ>(otab, i + 1), v1.x, v1.y);
-    }
+    tile_offsets(tv, t, of);
+    __syncthreads();
+    tile_gather(tv, t, r0, v, of, acc);
   }
-  df_bins_flush(bh, bl, out_raw, d);
+  tile_write_part(acc, d, part);
 }
 
+// out[r] = sum over g < G of part[g * d + r] for the 32 sketch rows of group
+// grp: warp w of the CTA adds g = w, w + nw, ... in order, then warp 0 adds
+// the warp sums in warp order.  Fixed order for a fixed G (deterministic).
+__device__ void fold_group(const double* __restrict__ part, int d, int G, int grp, double* __restrict__ out,
+                           double* red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int r = grp * 32 + lane;
+  double v = 0.0;
+  if (r < d) {
+#pragma unroll 4
+    for (int g = warp; g < G; g += nw) v += part[(size_t)g * d + r];
+  }
+  red[threadIdx.x] = v;
+  __syncthreads();
+  if (warp == 0 && r < d) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w * 32 + lane];
+    out[r] = s;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_df_fold(const double* __restrict__ part, int d, int G,
+                                                 double* __restrict__ out) {
+  __shared__ double red[256];
+  fold_group(part, d, G, blockIdx.x, out, red);
+}
 
 // Least squares b = S^+ z of one Arnoldi step, CGS2 in the sketch, in three
 // multi-CTA kernels (8 warps per CTA):
@@ -357,10 +529,6 @@ __global__ void __launch_bounds__(256) k_df_ls1(
         colscale[j] = inv;
         if (!finite) atomicOr(flag, RKS_FLAG_NAN);
         else if (brk) atomicOr(flag, RKS_FLAG_BREAKDOWN);
-      }
-      if (!ls) {                      // finish only (single CTA): clear the sums here
-        __syncthreads();
-        for (int r = tid; r < d; r += nt) s_raw[r] = 0.0;
       }
     }
   }
@@ -447,12 +615,24 @@ __global__ void __launch_bounds__(256) k_df_ls_coop(
     int j, int d, double zscale, int finish, double* __restrict__ s_raw, double* __restrict__ z_raw,
     double* __restrict__ S64, float2* __restrict__ S2, double* __restrict__ colscale, double* __restrict__ rprev,
     double* __restrict__ coef, int ldcoef, double* __restrict__ znorm_prev, float2* __restrict__ nrs,
-    float2* __restrict__ sj, float2* __restrict__ r1, float2* __restrict__ z1, unsigned* bar, int* flag) {
+    float2* __restrict__ sj, float2* __restrict__ r1, float2* __restrict__ z1, const double* __restrict__ part_z,
+    const double* __restrict__ part_s, int G, unsigned* bar, int* flag) {
   extern __shared__ float2 zd[];   // d
   __shared__ double red[33];
+  __shared__ double fred[256];
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   const int gw = blockIdx.x * nw + warp, tw = gridDim.x * nw;   // global warp index, warps in grid
   const int c = j + 1;
+  // phase 0: z' and s~_j from the sketch kernels' per-CTA partial sums
+  {
+    const int gz = (d + 31) / 32;
+    const int ntask = finish ? 2 * gz : gz;
+    for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+      if (task < gz) fold_group(part_z, d, G, task, z_raw, fred);
+      else fold_group(part_s, d, G, task - gz, s_raw, fred);
+    }
+    grid_barrier(bar, gridDim.x, flag);
+  }
   double inv = 0.0;
   if (finish) {
     double ss = 0.0;
@@ -518,11 +698,8 @@ __global__ void __launch_bounds__(256) k_df_ls_coop(
     }
   }
   grid_barrier(bar, gridDim.x, flag);
-  // phase 3: r = r1 + S^T z1; clear the sums (no longer read)
-  if (blockIdx.x == 0) {
-    for (int r = tid; r < d; r += nt) { z_raw[r] = 0.0; s_raw[r] = 0.0; }
-    if (tid == 0) { sj[0] = df_from_double(scj); znorm_prev[0] = sqrt(zz); }
-  }
+  // phase 3: r = r1 + S^T z1
+  if (blockIdx.x == 0 && tid == 0) { sj[0] = df_from_double(scj); znorm_prev[0] = sqrt(zz); }
   for (int col = gw; col < c; col += tw) {
     float s = 0.f, t = 0.f;
     df_col_dot(S2 + (size_t)col * d, z1, d, lane, s, t);
@@ -542,8 +719,6 @@ __global__ void __launch_bounds__(256) k_df_ls2(int j, int d, double zscale, dou
                                                 float2* __restrict__ z1) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   const int c = j + 1;
-  if (blockIdx.x == 0)
-    for (int r = tid; r < d; r += blockDim.x) s_raw[r] = 0.0;   // no kernel of this step reads it again
   const int r = blockIdx.x * nw + warp;
   if (r >= d) return;
   float s = 0.f, t = 0.f;
@@ -567,10 +742,7 @@ __global__ void __launch_bounds__(256) k_df_ls3(int j, int d, double* __restrict
                                                 float2* __restrict__ sj) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   const int c = j + 1;
-  if (blockIdx.x == 0) {
-    for (int r = tid; r < d; r += blockDim.x) z_raw[r] = 0.0;   // read for the last time in k_df_ls2
-    if (tid == 0) sj[0] = df_from_double(colscale[j]);
-  }
+  if (blockIdx.x == 0 && tid == 0) sj[0] = df_from_double(colscale[j]);
   const int col = blockIdx.x * nw + warp;
   if (col >= c) return;
   float s = 0.f, t = 0.f;
@@ -606,20 +778,29 @@ __global__ void k_df2d_cols(int64_t n, const TU* __restrict__ x, int64_t ldx, do
     y[i + (int64_t)j * ldy] = df_to_double(ldv(x + i + (int64_t)j * ldx));
 }
 
-// sketch of a DF vector (start vector)
-template <int MAXZ, class TU>
-__global__ void __launch_bounds__(512) k_df_sketch_vec(int64_t n, const TU* __restrict__ x, int d,
-                                                       const uint16_t* __restrict__ otab, double* out_raw) {
-  extern __shared__ float shf[];
-  float* bh = shf;
-  float* bl = shf + d;
-  df_bins_zero(bh, bl, d);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float2 v = ldv(x + i);
-    df_sketch_add_tab<MAXZ>(bh, bl, omega_load<MAXZ>(otab, i), v.x, v.y);
+// part[cta] = the CTA's Omega-sums of a stored vector (start vector)
+template <class TU>
+__global__ void __launch_bounds__(512) k_df_sketch_vec(const TU* __restrict__ x, const SketchTiles tv,
+                                                       double* __restrict__ part) {
+  extern __shared__ float2 sh2[];
+  const int d = tv.d, L1 = tv.L + 1;
+  float2* acc = sh2;
+  float2* vb = acc + d;
+  int* offs = reinterpret_cast<int*>(vb + 2 * kTileRows);
+  for (int r = threadIdx.x; r < d; r += blockDim.x) acc[r] = make_float2(0.f, 0.f);
+  const int t0 = tv.ctile[blockIdx.x], t1 = tv.ctile[blockIdx.x + 1];
+  for (int t = t0; t < t1; ++t) {
+    const int buf = (t - t0) & 1;
+    float2* v = vb + buf * kTileRows;
+    int* of = offs + buf * L1;
+    const int64_t r0 = tv.row[t];
+    const int rows = (int)(tv.row[t + 1] - r0);
+    for (int l = threadIdx.x; l < rows; l += blockDim.x) v[l] = ldv(x + r0 + l);
+    tile_offsets(tv, t, of);
+    __syncthreads();
+    tile_gather(tv, t, r0, v, of, acc);
   }
-  df_bins_flush(bh, bl, out_raw, d);
+  tile_write_part(acc, d, part);
 }
 
 // Row-blocked DF product, in place: U[i, c0 + o] = sum_l U[i, a0 + l] Q[l, o]
@@ -746,17 +927,12 @@ cudaError_t configure_df_kernels() {
   const int big = 200 * 1024;
   cudaError_t e = cudaSuccess;
 #define RKS_SMEM(f) if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
-#define RKS_SMEM_T(TA, TU)                                                                          \
-  RKS_SMEM((k_df_spmv_sketch<4, TA, TU>)); RKS_SMEM((k_df_spmv_sketch<8, TA, TU>));                  \
-  RKS_SMEM((k_df_spmv_sketch<16, TA, TU>));
-  RKS_SMEM_T(float2, float2) RKS_SMEM_T(float, float)
-#undef RKS_SMEM_T
+  RKS_SMEM((k_df_spmv_sketch<float2, float2>)); RKS_SMEM((k_df_spmv_sketch<float, float>));
   constexpr int U8 = kDfUpdUnroll, MB = kDfUpdMinBlocks;
-  RKS_SMEM((k_df_update_sketch<4, float2, U8, MB>)); RKS_SMEM((k_df_update_sketch<8, float2, U8, MB>));
-  RKS_SMEM((k_df_update_sketch<16, float2, U8, MB>)); RKS_SMEM((k_df_update_sketch<4, float, U8, MB>));
-  RKS_SMEM((k_df_update_sketch<8, float, U8, MB>)); RKS_SMEM((k_df_update_sketch<16, float, U8, MB>));
-  RKS_SMEM((k_df_sketch_vec<4, float2>)); RKS_SMEM((k_df_sketch_vec<8, float2>)); RKS_SMEM((k_df_sketch_vec<16, float2>));
-  RKS_SMEM((k_df_sketch_vec<4, float>)); RKS_SMEM((k_df_sketch_vec<8, float>)); RKS_SMEM((k_df_sketch_vec<16, float>));
+  RKS_SMEM((k_df_update_sketch<float2, U8, MB>)); RKS_SMEM((k_df_update_sketch<float, U8, MB>));
+  RKS_SMEM(k_df_sketch_vec<float2>); RKS_SMEM(k_df_sketch_vec<float>);
+  RKS_SMEM(k_tiles_count<4>); RKS_SMEM(k_tiles_count<8>); RKS_SMEM(k_tiles_count<16>);
+  RKS_SMEM(k_tiles_build<4>); RKS_SMEM(k_tiles_build<8>); RKS_SMEM(k_tiles_build<16>);
   RKS_SMEM(k_df_ls1);
   RKS_SMEM(k_df_ls_coop);
   RKS_SMEM(k_df_rows_gemm<float2>);
@@ -771,70 +947,56 @@ cudaError_t configure_df_kernels() {
 int df_small_smem(int d, int c) { return (int)((size_t)d * sizeof(float2)); }
 int df_gemm_smem(int nin, int nout) { return (int)(((size_t)nin * nout + (size_t)128 * nout) * sizeof(float2)); }
 
-template <class TA, class TU>
-static void spmv_t(const CsrDF& A, const void* x, void* w, int d, int zeta, const uint16_t* otab, double* out_raw,
-                   cudaStream_t st) {
-  const int g = df_grid(A.n, 512);
-  const size_t sm = (size_t)2 * d * sizeof(float);
-  const TA* v = static_cast<const TA*>(A.vals);
-  const TU* xx = static_cast<const TU*>(x);
-  TU* ww = static_cast<TU*>(w);
-  if (zeta <= 4)
-    k_df_spmv_sketch<4, TA, TU><<<g, 512, sm, st>>>(A.n, A.rowptr, A.colind, v, xx, ww, d, otab, out_raw);
-  else if (zeta <= 8)
-    k_df_spmv_sketch<8, TA, TU><<<g, 512, sm, st>>>(A.n, A.rowptr, A.colind, v, xx, ww, d, otab, out_raw);
+void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, const SketchTiles& t, double* part,
+                           cudaStream_t st) {
+  const size_t sm = tile_smem_bytes(t.d, t.L, 0);
+  if (A.f32)
+    k_df_spmv_sketch<float, float><<<t.G, 512, sm, st>>>(A.rowptr, A.colind, static_cast<const float*>(A.vals),
+                                                         static_cast<const float*>(x), static_cast<float*>(w), t,
+                                                         part);
   else
-    k_df_spmv_sketch<16, TA, TU><<<g, 512, sm, st>>>(A.n, A.rowptr, A.colind, v, xx, ww, d, otab, out_raw);
+    k_df_spmv_sketch<float2, float2><<<t.G, 512, sm, st>>>(A.rowptr, A.colind, static_cast<const float2*>(A.vals),
+                                                           static_cast<const float2*>(x), static_cast<float2*>(w),
+                                                           t, part);
 }
 
-void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, int d, int zeta, const uint16_t* otab,
-                           double* out_raw, cudaStream_t st) {
-  if (A.f32) spmv_t<float, float>(A, x, w, d, zeta, otab, out_raw, st);
-  else spmv_t<float2, float2>(A, x, w, d, zeta, otab, out_raw, st);
-}
-
-template <class TU>
-static void update_t(int64_t n, void* U, int64_t ldu, int c, const float2* nrs, const float2* sj, int d, int zeta,
-                     const uint16_t* otab, double* out_raw, cudaStream_t st) {
+void launch_df_update_sketch(void* U, int64_t ldu, int c, const float2* nrs, const float2* sj, const SketchTiles& t,
+                             double* part, bool f32, cudaStream_t st) {
   constexpr int U8 = kDfUpdUnroll, MB = kDfUpdMinBlocks;
-  int64_t g64 = ((n + 1) / 2 + 511) / 512;
-  if (g64 > 152 * MB) g64 = 152 * MB;
-  const int g = (int)std::max<int64_t>(g64, 1);
-  const size_t sm = (size_t)2 * d * sizeof(float) + (size_t)c * sizeof(float2) + 16;
-  TU* u = static_cast<TU*>(U);
-  if (zeta <= 4) k_df_update_sketch<4, TU, U8, MB><<<g, 512, sm, st>>>(n, u, ldu, c, nrs, sj, d, otab, out_raw);
-  else if (zeta <= 8) k_df_update_sketch<8, TU, U8, MB><<<g, 512, sm, st>>>(n, u, ldu, c, nrs, sj, d, otab, out_raw);
-  else k_df_update_sketch<16, TU, U8, MB><<<g, 512, sm, st>>>(n, u, ldu, c, nrs, sj, d, otab, out_raw);
-}
-
-void launch_df_update_sketch(int64_t n, void* U, int64_t ldu, int c, const float2* nrs, const float2* sj,
-                             int d, int zeta, const uint16_t* otab, double* out_raw, bool f32, cudaStream_t st) {
-  if (f32) update_t<float>(n, U, ldu, c, nrs, sj, d, zeta, otab, out_raw, st);
-  else update_t<float2>(n, U, ldu, c, nrs, sj, d, zeta, otab, out_raw, st);
+  const size_t sm = tile_smem_bytes(t.d, t.L, c);
+  if (f32)
+    k_df_update_sketch<float, U8, MB><<<t.G, 512, sm, st>>>(static_cast<float*>(U), ldu, c, nrs, sj, t, part);
+  else
+    k_df_update_sketch<float2, U8, MB><<<t.G, 512, sm, st>>>(static_cast<float2*>(U), ldu, c, nrs, sj, t, part);
 }
 
 int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_raw, double* z_raw, double* S64,
                     float2* S2, double* colscale, double* rprev, double* coef, int ldcoef, double* znorm_prev,
-                    float2* nrs, float2* sj, float2* r1, float2* z1, int* flag, unsigned* bar, cudaStream_t st) {
+                    float2* nrs, float2* sj, float2* r1, float2* z1, const double* part_z, const double* part_s,
+                    int G, int* flag, unsigned* bar, cudaStream_t st) {
   const size_t sm = (size_t)d * sizeof(float2);
   const int c = j + 1;
   if (ls && bar) {
-    // one cooperative launch: warps over columns / rows, two grid barriers
+    // one cooperative launch: partial-sum fold, then warps over columns / rows, three grid barriers
     int g = (std::max(c, d) + 7) / 8;
     g = std::min(g, 48);
     void* args[] = {&j, &d, &zscale, &finish, &s_raw, &z_raw, &S64, &S2, &colscale, &rprev, &coef, &ldcoef,
-                    &znorm_prev, &nrs, &sj, &r1, &z1, &bar, &flag};
+                    &znorm_prev, &nrs, &sj, &r1, &z1, &part_z, &part_s, &G, &bar, &flag};
     if (cudaLaunchCooperativeKernel((const void*)k_df_ls_coop, dim3(g), dim3(256), args, sm, st) == cudaSuccess)
       return 1;
-    (void)cudaGetLastError();   // not available: fall back to the three-kernel form below
+    (void)cudaGetLastError();   // not available: fall back to the kernels below
   }
+  const int gf = (d + 31) / 32;
+  int nl = 0;
+  if (finish) { k_df_fold<<<gf, 256, 0, st>>>(part_s, d, G, s_raw); ++nl; }
+  if (ls) { k_df_fold<<<gf, 256, 0, st>>>(part_z, d, G, z_raw); ++nl; }
   const int g1 = ls ? (c + 7) / 8 : 1;
   k_df_ls1<<<g1, 256, sm, st>>>(j, d, zscale, finish, ls, s_raw, z_raw, S64, S2, colscale, rprev, coef, ldcoef,
                                 znorm_prev, r1, flag);
-  if (!ls) return 1;
+  if (!ls) return nl + 1;
   k_df_ls2<<<(d + 7) / 8, 256, 0, st>>>(j, d, zscale, s_raw, z_raw, S2, colscale, r1, z1);
   k_df_ls3<<<(c + 7) / 8, 256, 0, st>>>(j, d, z_raw, S2, colscale, r1, z1, rprev, nrs, sj);
-  return 3;
+  return nl + 3;
 }
 
 void launch_omega_table(int64_t n, int d, int zeta, uint64_t seed, uint16_t* tab, int* flag, cudaStream_t st) {
@@ -862,22 +1024,75 @@ void launch_df2d_cols(int64_t n, const void* x, int64_t ldx, double* y, int64_t 
   else k_df2d_cols<float2><<<grid, 256, 0, st>>>(n, static_cast<const float2*>(x), ldx, y, ldy, ncols);
 }
 
-template <class TU>
-static void sketch_vec_t(int64_t n, const void* x, int d, int zeta, const uint16_t* otab, double* out_raw,
-                         cudaStream_t st) {
-  const int g = df_grid(n, 512);
-  const size_t sm = (size_t)2 * d * sizeof(float);
-  const TU* xx = static_cast<const TU*>(x);
-  if (zeta <= 4) k_df_sketch_vec<4, TU><<<g, 512, sm, st>>>(n, xx, d, otab, out_raw);
-  else if (zeta <= 8) k_df_sketch_vec<8, TU><<<g, 512, sm, st>>>(n, xx, d, otab, out_raw);
-  else k_df_sketch_vec<16, TU><<<g, 512, sm, st>>>(n, xx, d, otab, out_raw);
+void launch_df_sketch_vec(const void* x, const SketchTiles& t, double* part, bool f32, cudaStream_t st) {
+  const size_t sm = tile_smem_bytes(t.d, t.L, 0);
+  if (f32) k_df_sketch_vec<float><<<t.G, 512, sm, st>>>(static_cast<const float*>(x), t, part);
+  else k_df_sketch_vec<float2><<<t.G, 512, sm, st>>>(static_cast<const float2*>(x), t, part);
 }
 
-void launch_df_sketch_vec(int64_t n, const void* x, int d, int zeta, const uint16_t* otab, double* out_raw,
-                          bool f32, cudaStream_t st) {
-  if (f32) sketch_vec_t<float>(n, x, d, zeta, otab, out_raw, st);
-  else sketch_vec_t<float2>(n, x, d, zeta, otab, out_raw, st);
+// Row ranges: G CTAs (at most kSketchCtas) own contiguous, even-aligned row
+// ranges of equal length (to within two rows); each range is cut into tiles
+// of at most kTileRows rows.  The partition depends on n only.
+int build_sketch_tiles(int64_t n, int d, int zeta, const uint16_t* otab, SketchTiles* out, cudaStream_t st) {
+  SketchTiles t;
+  t.n = n; t.d = d; t.zeta = zeta;
+  const int64_t npair = (n + 1) / 2;
+  int64_t G = std::min<int64_t>(kSketchCtas, std::max<int64_t>(1, (n + kTileRows - 1) / kTileRows));
+  G = std::max<int64_t>(1, std::min(G, npair));
+  std::vector<int> ctile(G + 1);
+  std::vector<int64_t> row;
+  for (int64_t g = 0; g < G; ++g) {
+    const int64_t a = 2 * (g * npair / G), b = std::min<int64_t>(n, 2 * ((g + 1) * npair / G));
+    ctile[g] = (int)row.size();
+    for (int64_t r = a; r < b; r += kTileRows) row.push_back(r);
+  }
+  ctile[G] = (int)row.size();
+  row.push_back(n);
+  t.G = (int)G;
+  t.ntile = (int)row.size() - 1;
+  t.H = 1;
+  while (t.H < 8 && (int64_t)d * t.H * 2 <= 512) t.H *= 2;
+  cudaError_t e = cudaMalloc(&t.row, row.size() * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&t.ctile, ctile.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(t.row, row.data(), row.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(t.ctile, ctile.data(), ctile.size() * sizeof(int), cudaMemcpyHostToDevice);
+  int* lmax = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&lmax, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(lmax, 0, sizeof(int), st);
+  const int slots = omega_slots(zeta);
+  const size_t smc = (size_t)d * sizeof(int);
+  if (e == cudaSuccess) {
+    if (slots == 4) k_tiles_count<4><<<t.ntile, 256, smc, st>>>(t.row, d, otab, lmax);
+    else if (slots == 8) k_tiles_count<8><<<t.ntile, 256, smc, st>>>(t.row, d, otab, lmax);
+    else k_tiles_count<16><<<t.ntile, 256, smc, st>>>(t.row, d, otab, lmax);
+    e = cudaGetLastError();
+  }
+  int L = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&L, lmax, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(lmax);
+  t.L = L;
+  if (e == cudaSuccess) e = cudaMalloc(&t.meta, (size_t)t.ntile * d * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&t.off, (size_t)t.ntile * (L + 1) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&t.ent, (size_t)n * zeta * sizeof(uint16_t));
+  const size_t smb = ((size_t)4 * d + L + 1) * sizeof(int);
+  if (e == cudaSuccess) {
+    if (slots == 4) k_tiles_build<4><<<t.ntile, 256, smb, st>>>(t.row, d, zeta, L, otab, t.meta, t.off, t.ent);
+    else if (slots == 8) k_tiles_build<8><<<t.ntile, 256, smb, st>>>(t.row, d, zeta, L, otab, t.meta, t.off, t.ent);
+    else k_tiles_build<16><<<t.ntile, 256, smb, st>>>(t.row, d, zeta, L, otab, t.meta, t.off, t.ent);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  *out = t;
+  return (int)e;
 }
+
+void free_sketch_tiles(SketchTiles* t) {
+  cudaFree(t->row); cudaFree(t->ctile); cudaFree(t->meta); cudaFree(t->off); cudaFree(t->ent);
+  *t = SketchTiles();
+}
+
+size_t sketch_tile_smem(const SketchTiles& t, int c) { return tile_smem_bytes(t.d, t.L, c); }
 
 template <class TU>
 static void restart_t(int64_t n, TU* U, int64_t ldu, int a0, int nin, const float2* Q, int nout, int c0,

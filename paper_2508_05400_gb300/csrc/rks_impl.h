@@ -7,15 +7,37 @@ namespace rks {
 
 enum : int { RKS_FLAG_NAN = 1, RKS_FLAG_BREAKDOWN = 2, RKS_FLAG_HASH = 4, RKS_FLAG_TIMEOUT = 8 };
 
-// CTAs of the kernels that carry a sketch (one shared-memory bin set each,
-// folded into the global d-vector with one atomic per bin).
+// CTAs of the kernels that carry a sketch (FP64 path: one shared-memory bin
+// set each, folded with one atomic per bin; DF path: one row range each).
 constexpr int kSketchCtas = 152 * 2;
 // CTAs of the double-float streaming kernels (512 threads each).
 constexpr int kDfCtas = 152 * 2;
+// CTAs of the final residual sums (partials added on the host in CTA order).
+constexpr int kResidCtas = 152 * 2;
 // Update kernel: columns loaded per batch and resident CTAs per SM it is
 // compiled for (register budget 65536 / (512 * kDfUpdMinBlocks) per thread).
 constexpr int kDfUpdUnroll = 8;
 constexpr int kDfUpdMinBlocks = 2;
+
+// Deterministic sketch accumulation: per-tile bin lists of Omega (built once
+// by build_sketch_tiles; layout in kernels_df.cu).  Device arrays:
+//   row[ntile + 1]          first row of each tile (row[ntile] = n)
+//   ctile[G + 1]            CTA g owns tiles ctile[g] .. ctile[g + 1] - 1
+//   meta[ntile * d]         per tile and position: sketch row | count << 16
+//   off[ntile * (L + 1)]    per tile: slot offsets of its entries
+//   ent[n * zeta]           tile t's entries at row[t] * zeta .. row[t + 1] * zeta
+// The sketch kernels run G CTAs and write G x d partial sums (FP64), which
+// are added in CTA order.
+constexpr int kTileRows = 1024;
+struct SketchTiles {
+  int64_t n = 0;
+  int d = 0, zeta = 0, G = 0, ntile = 0, L = 0, H = 1;   // L: largest list; H: threads per list
+  int64_t* row = nullptr;
+  int* ctile = nullptr;
+  uint32_t* meta = nullptr;
+  int* off = nullptr;
+  uint16_t* ent = nullptr;
+};
 
 struct Csr {
   int64_t n = 0, nnz = 0;
@@ -35,21 +57,24 @@ struct CsrDF {
 cudaError_t configure_df_kernels();
 int df_small_smem(int d, int c);
 int df_gemm_smem(int nin, int nout);
-void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, int d, int zeta, const uint16_t* otab,
-                           double* out_raw, cudaStream_t st);
-void launch_df_update_sketch(int64_t n, void* U, int64_t ldu, int c, const float2* nrs, const float2* sj,
-                             int d, int zeta, const uint16_t* otab, double* out_raw, bool f32, cudaStream_t st);
+void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, const SketchTiles& t, double* part,
+                           cudaStream_t st);
+void launch_df_update_sketch(void* U, int64_t ldu, int c, const float2* nrs, const float2* sj, const SketchTiles& t,
+                             double* part, bool f32, cudaStream_t st);
 int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_raw, double* z_raw, double* S64,
-                     float2* S2, double* colscale, double* rprev, double* coef, int ldcoef, double* znorm_prev,
-                     float2* nrs, float2* sj, float2* r1, float2* z1, int* flag, unsigned* bar, cudaStream_t st);
+                    float2* S2, double* colscale, double* rprev, double* coef, int ldcoef, double* znorm_prev,
+                    float2* nrs, float2* sj, float2* r1, float2* z1, const double* part_z, const double* part_s,
+                    int G, int* flag, unsigned* bar, cudaStream_t st);
+int build_sketch_tiles(int64_t n, int d, int zeta, const uint16_t* otab, SketchTiles* out, cudaStream_t st);
+void free_sketch_tiles(SketchTiles* t);
+size_t sketch_tile_smem(const SketchTiles& t, int c);
 void launch_omega_table(int64_t n, int d, int zeta, uint64_t seed, uint16_t* tab, int* flag, cudaStream_t st);
 int omega_slots(int zeta);
 void launch_d2df(int64_t n, const double* x, void* y, bool f32, cudaStream_t st);
 void launch_sum_cols_f32(int64_t n, const float* U, int64_t ldu, int ncols, double* y, cudaStream_t st);
 void launch_df2d_cols(int64_t n, const void* x, int64_t ldx, double* y, int64_t ldy, int ncols, bool f32,
                       cudaStream_t st);
-void launch_df_sketch_vec(int64_t n, const void* x, int d, int zeta, const uint16_t* otab, double* out_raw,
-                          bool f32, cudaStream_t st);
+void launch_df_sketch_vec(const void* x, const SketchTiles& t, double* part, bool f32, cudaStream_t st);
 void launch_df_rows_gemm(int64_t n, void* U, int64_t ldu, int a0, int nin, const float2* Q, int nout, int c0,
                          int move_src, bool f32, cudaStream_t st);
 
@@ -73,9 +98,9 @@ int rows_gemm_smem(int nin, int nout, int threads);
 void launch_rows_gemm(int64_t n, const double* A, int64_t lda, int a0, int nin, const double* B, int nout,
                       double* C, int64_t ldc, int c0, int move_src, cudaStream_t st);
 void launch_spmm(const Csr& A, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncols, cudaStream_t st);
-void launch_resid_sums(int64_t n, const double* X, const double* AX, int64_t ld, int npairs, const int* col,
-                       const int* colim, const double* lre, const double* lim, double* out, cudaStream_t st);
-void launch_col_abs_sums(int64_t nnz, const int32_t* colind, const double* vals, double* colsum, cudaStream_t st);
+// Writes per-CTA partial sums out[(pair * 4 + q) * G + cta]; returns G (<= kResidCtas).
+int launch_resid_sums(int64_t n, const double* X, const double* AX, int64_t ld, int npairs, const int* col,
+                      const int* colim, const double* lre, const double* lim, double* out, cudaStream_t st);
 void launch_f32_to_f64(int64_t n, const float* a, double* b, cudaStream_t st);
 void launch_fill(int64_t n, double v, double* a, cudaStream_t st);
 void launch_check_csr(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind, int* bad,
