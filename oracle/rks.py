@@ -261,14 +261,20 @@ def whiten(st: RKSState) -> None:
     st.Tqa = st.Tqa @ Rinv
 
 
-def contract(st: RKSState, k: int, which: str):
+def contract(st: RKSState, k: int, which: str, keep: int = 0):
     """Alg. 1 contraction: Schur form, reordering, truncation of the active part.
 
+    The active part keeps its k - q best Schur vectors (Alg. 1 truncates to
+    k), or, with ``keep`` > 0, max(k - q, min(keep, ma // 2)) of them: after
+    q vectors are locked the restart still carries up to ``keep`` active
+    directions (a thick restart, Sec. 2.3's truncation with a larger size).
     Returns (T_a, b_a, Q) where Q (ma x ka) are the kept Schur vectors.
     """
     ma = st.ja
     Ba, b = st.Ba[:ma, :], st.Ba[ma, :]
     want = k - st.q
+    if keep:
+        want = max(want, min(keep, ma // 2))
     # sort enough blocks to cover ``want`` columns plus a possible pair
     T, Q = ordered_schur(Ba, which, nsort=min(want + 1, ma))
     ka = min(truncation_size(T, want), ma - 1)
@@ -355,6 +361,15 @@ class RKSResult:
     history: list = field(default_factory=list)
 
 
+def n_wanted(lam: np.ndarray, k: int) -> int:
+    """How many leading sorted Ritz values are reported: k, or k + 1 when the
+    k-th is the first member of a complex pair (pairs are never split)."""
+    nw = min(k, lam.size)
+    if 0 < nw < lam.size and lam[nw - 1].imag > 0:
+        nw += 1
+    return nw
+
+
 def norm1(A: sp.spmatrix) -> float:
     return float(np.abs(A).sum(axis=0).max())
 
@@ -372,13 +387,15 @@ def rks(A, k: int, p: int, d: int, u1: np.ndarray, *, zeta: int = 8, seed: int =
         which: str = "LM", tol: float = 1e-10, lock_vectors: bool = True,
         eta_lock: float | None = None, maxit: int = 1000, Omega=None,
         whiten_tol: float = 1e-10, max_restarts: int | None = None,
-        conv: str = "eig") -> RKSResult:
+        conv: str = "eig", keep: int = 0) -> RKSResult:
     """Algorithm 1 (rKS) with the deflation of Sec. 4.
 
     ``max_restarts`` (if given) stops after that many contractions whatever the
     estimates say (the paper's fixed-iteration runs, Sec. 5).  ``conv`` picks
     the convergence quantity: "eig" (|b^T y|/|lambda|, Eq. 4.8) or "norm1"
     (|b^T y|/||A||_1, see ``ritz``), and the matching locking threshold.
+    ``keep`` > 0 selects the thick restart of ``contract``.  Convergence and
+    the returned pairs concern the n_wanted best Ritz pairs of the full T.
     """
     A = sp.csr_matrix(A, dtype=np.float64)
     norm_a = norm1(A) if conv == "norm1" else None
@@ -394,7 +411,7 @@ def rks(A, k: int, p: int, d: int, u1: np.ndarray, *, zeta: int = 8, seed: int =
     restarts = 0
     limit = maxit if max_restarts is None else min(maxit, max_restarts)
     while True:
-        contract(st, k, which)                   # Schur, reorder, truncate
+        contract(st, k, which, keep)             # Schur, reorder, truncate
         restarts += 1
         ja = st.ja
         if ja and whiten_tol is not None:
@@ -405,8 +422,9 @@ def rks(A, k: int, p: int, d: int, u1: np.ndarray, *, zeta: int = 8, seed: int =
             lock(st, k, eta_lock, norm_a)
         T, b, _ = full_T(st)
         lam, Y, est = ritz(T, b, which, norm_a)  # Alg. 1, Ritz pairs + Eq. 4.8
+        est = est[:n_wanted(lam, k)]
         history.append(float(est.max()) if est.size else 0.0)
-        if st.q >= k or np.all(est <= tol):
+        if np.all(est <= tol):
             converged = True
             break
         if restarts >= limit:
@@ -414,6 +432,8 @@ def rks(A, k: int, p: int, d: int, u1: np.ndarray, *, zeta: int = 8, seed: int =
         extend(st, m - st.q)                     # Alg. 1, extension
     T, b, U = full_T(st)
     lam, Y, est = ritz(T, b, which, norm_a)
+    nw = n_wanted(lam, k)
+    lam, Y, est = lam[:nw], Y[:, :nw], est[:nw]
     X = U @ Y
     res, rq = true_residuals(A, X, lam)
     return RKSResult(eigvals=lam, X=X, resid=res, est=est, lam_rq=rq, T=T, U=U, b=b,

@@ -152,6 +152,44 @@ def test_convdiff_kronecker_closed_form(lock):
     assert res.resid.max() < 1e-13
 
 
+def test_thick_restart_keeps_closed_form_and_saves_matvecs():
+    # keep > 0 retains extra active Schur vectors after locking: the same
+    # closed-form eigenvalues, with fewer products with A than truncating to k
+    N = 30
+    A = I.convdiff_2d(N, N, 1.0, 20.0, 10.0).to_scipy()
+    ex = np.sort(I.convdiff_2d_eigenvalues(N, N, 1.0, 20.0, 10.0))[::-1][:6]
+    u1 = I.start_vector(N * N, 1)
+    base = R.rks(A, 6, 18, 64, u1, zeta=8, seed=0, which="LR", tol=1e-13)
+    thick = R.rks(A, 6, 18, 64, u1, zeta=8, seed=0, which="LR", tol=1e-13, keep=6)
+    assert base.converged and thick.converged
+    assert thick.eigvals.size == 6
+    assert np.max(np.abs(thick.eigvals - ex) / np.abs(ex)) < 1e-10
+    assert thick.resid.max() < 1e-13
+    assert thick.nmatvec < base.nmatvec
+    # the full decomposition it ends on is still a Krylov decomposition
+    r = A @ thick.U - thick.U @ thick.T - np.outer(thick.u, thick.b)
+    assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(A @ thick.U)
+
+
+def test_contract_keep_size():
+    # the kept active count is max(k - q, min(keep, ma // 2)) with ma = m - q
+    # active columns, one more when a complex pair straddles the cut
+    A = I.convdiff_2d(12, 11, 1.0, 20.0, 10.0).to_scipy()
+    Om = omega_matrix(132, 48, 8, 0)
+    for keep, qlock, expect in [(0, 0, 4), (4, 0, 4), (6, 0, 6), (4, 2, 4), (10, 2, 9), (20, 2, 9)]:
+        st = R.start(A, Om, I.start_vector(132, 1))
+        R.extend(st, 20)
+        if qlock:   # lock the two leading vectors: the active part then has 18 columns
+            R.contract(st, qlock, "LR")
+            R.lock(st, qlock, 1e300)
+            assert st.q == qlock
+            R.extend(st, 20 - qlock)
+        Ta, bk, Qk = R.contract(st, 4, "LR", keep)
+        assert Qk.shape[1] - expect in (0, 1)
+        if Qk.shape[1] == expect + 1:        # only for a pair at the cut
+            assert R.schur_blocks(Ta)[-1][1] == 2
+
+
 def _planted_spectrum_matrix(n, seed):
     """A = X D X^{-1} with known eigenvalues (including complex pairs), X well conditioned."""
     rng = np.random.default_rng(seed)
