@@ -108,6 +108,11 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+DTYPES = {"fp64": "f64",
+          "df": "df64 (fp32 pair, 48-bit significand; fp64 sketch/LS/Schur/residuals)",
+          "mixed": "f32 basis (split-bf16 tensor-core restart) then df64; fp64 sketch/LS/Schur/residuals"}
+
+
 def _problem():
     from paper_2508_05400_gb300 import inputs as I
     P = I.convdiff2d_problem()
@@ -185,6 +190,7 @@ def run_ours(args) -> None:
 
     P, u1 = _problem()
     A = P.A
+    keep = P.k if args.keep < 0 else args.keep
     stream = torch.cuda.current_stream(dev)
     # inputs resident in HBM before the timed region
     d_rowptr = torch.from_numpy(A.rowptr).to(dev)
@@ -194,7 +200,7 @@ def run_ours(args) -> None:
     solver = rks.Solver(A.n, d_rowptr, d_colind, d_vals, P.k, P.p, P.d, which=P.which,
                         seed=P.omega_seed, zeta=P.zeta, u1=d_u1, device=True,
                         stream=stream.cuda_stream, profile=True, prec=args.prec, maxit=args.maxit,
-                        **P.solver_opts())
+                        keep=keep, **P.solver_opts())
     X_dev = torch.empty((P.k + 1, A.n), dtype=torch.float64, device=dev)
 
     def step():
@@ -265,10 +271,9 @@ def run_ours(args) -> None:
         t0 = time.perf_counter()
         with rks.Solver(A.n, h_rowptr, h_colind, h_vals, P.k, P.p, P.d, which=P.which,
                         seed=P.omega_seed, zeta=P.zeta, u1=h_u1, stream=stream.cuda_stream,
-                        prec=args.prec, maxit=args.maxit, **P.solver_opts()) as s2:
+                        prec=args.prec, maxit=args.maxit, keep=keep, **P.solver_opts()) as s2:
             s2.solve(allow_noconv=False)
             s2.eigpairs(X_out=h_X)
-            kk = s2.nkept
         e2e_times.append((time.perf_counter() - t0) * 1e3)
     barrier()
     e2e_ms = statistics.mean(e2e_times) if e2e_times else None
@@ -282,10 +287,10 @@ def run_ours(args) -> None:
     line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.prec == "fp64" else "df64 (fp32 pair, 48-bit significand; fp64 sketch/LS/Schur/residuals)",
+            "dtype": DTYPES[args.prec],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "k": P.k, "p": P.p, "d": P.d,
-                       "zeta": P.zeta, "prec": args.prec, "parallelism": f"replicas{world}",
+                       "zeta": P.zeta, "prec": args.prec, "keep": keep, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (basis 648 MB, A 80 MB)"},
             "roofline": roofline,
             "spmv_rgs_gbs": path_bytes / (path_ms * 1e-3) / 1e9 if path_ms else None,
@@ -323,7 +328,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--maxit", type=int, default=4000, help="restart limit of each solve")
-    ap.add_argument("--prec", default="df", choices=["df", "fp64"],
+    ap.add_argument("--keep", type=int, default=-1,
+                    help="active Schur vectors a restart keeps after locking (thick restart); "
+                         "-1: k; 0: k - q as in Algorithm 1")
+    ap.add_argument("--prec", default="df", choices=["df", "fp64", "mixed"],
                     help="arithmetic of the n-dimensional work (see include/rks.h)")
     args = ap.parse_args()
     if args.impl == "reference":

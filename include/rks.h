@@ -94,6 +94,14 @@ typedef struct {
                           fails, divide tol and eta_lock by 4 and continue the
                           restarts from the current decomposition (bounded
                           by maxit); 0: no check (default) */
+  int keep;            /* 0 (default): a restart keeps the k - q best active
+                          Schur vectors (Algorithm 1 truncates to k, q locked).
+                          1..k: thick restart, it keeps
+                          max(k - q, min(keep, (m - q) / 2)) of them, so that
+                          after locking the restart still carries up to keep
+                          active directions.  Either way convergence and the
+                          reported Ritz pairs concern the rks_nwanted best
+                          Ritz pairs of the kept decomposition. */
 } rks_opts;
 
 enum { RKS_PREC_DF = 0, RKS_PREC_FP64 = 1, RKS_PREC_MIXED = 2 };
@@ -168,25 +176,31 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
 int rks_solve(rks_ctx* c, rks_info* info);
 
 /* The rKS decomposition A U = U T + u b^T of the last solve (Def. 2.9), with
- * kk = rks_nkept(c) columns (k, or k + 1 when a complex pair straddles the
- * cut).  T: kk x kk (host, FP64); U: n x kk FP64 (host or device per
- * mem_device), unit sketch norm columns ||Omega U e_i|| = 1; b: kk (host).
- * Any pointer may be NULL. */
+ * kk = rks_nkept(c) columns: the q locked and the active Schur vectors kept
+ * at the last restart (k, or k + 1 when a complex pair straddles the cut; up
+ * to q + keep with opts.keep > 0).  T: kk x kk (host, FP64); U: n x kk FP64
+ * (host or device per mem_device), unit sketch norm columns
+ * ||Omega U e_i|| = 1; b: kk (host).  Any pointer may be NULL. */
 int rks_get_schur(rks_ctx* c, double* T, double* U, double* b);
 
 /* Number of columns kk of the decomposition returned by rks_get_schur. */
 int rks_nkept(const rks_ctx* c);
 
-/* Ritz pairs of the last solve, best first (Sec. 4.1): lam_re, lam_im (kk,
- * host); X (n x kk FP64, host or device per mem_device) in LAPACK dgeev real
+/* Number nw of Ritz pairs reported by rks_get_eigpairs and
+ * rks_get_estimates: the best k of the kept decomposition, k + 1 when the
+ * k-th is the first member of a complex pair (at most kk). */
+int rks_nwanted(const rks_ctx* c);
+
+/* Ritz pairs of the last solve, best first (Sec. 4.1): lam_re, lam_im (nw,
+ * host); X (n x nw FP64, host or device per mem_device) in LAPACK dgeev real
  * packing: a conjugate pair occupies columns (j, j+1) = (Re x, Im x) of the
- * eigenvector of the member with Im > 0; resid (kk, host) =
+ * eigenvector of the member with Im > 0; resid (nw, host) =
  * ||A x - lambda x|| / (||A||_1 ||x||) computed in FP64 on the device.  Any
  * pointer may be NULL. */
 int rks_get_eigpairs(rks_ctx* c, double* lam_re, double* lam_im, double* X, double* resid);
 
 /* Residual estimates |b^T y_i| / |lambda_i| (Eq. 4.8) of the last solve, in
- * the order of rks_get_eigpairs (kk values, host). */
+ * the order of rks_get_eigpairs (nw values, host). */
 int rks_get_estimates(rks_ctx* c, double* est);
 
 /* The sketch-orthonormal Krylov decomposition as it stands (for tests of
@@ -254,6 +268,21 @@ int rks_sketch_apply(int64_t n, int d, int zeta, uint64_t seed, const double* x,
  * RKS_OK, RKS_EINVAL (arguments, or the hash draw cap reached) or RKS_ECUDA. */
 int rks_sketch_apply_noalloc(int64_t n, int d, int zeta, uint64_t seed, const double* x, double* z,
                              void* stream);
+
+/* ---- Restart product on the tensor cores (Eq. 3.5) ------------------ */
+
+/* out = U Q for an FP32 basis, the restart product U_k = U Q' of the
+ * mixed-precision path, on the tcgen05 tensor cores: U and Q are split into
+ * three bf16 terms each, the six leading split products are accumulated in
+ * FP32 (FP32-class accuracy).  out[i + o*ldu] = sum_l U[i + l*ldu] *
+ * Q[l + o*nin] for i < n, o < nout.  U, out: device FP32 arrays with leading
+ * dimension ldu >= n; out may equal U (each 128-row tile is read before it is
+ * written).  Q: host FP64, nin x nout column-major, 1 <= nin <= 256,
+ * 1 <= nout <= 64.  Runs on `stream` (NULL: default stream) and synchronises
+ * it.  Returns RKS_OK, RKS_EINVAL (sizes, NULL pointers), RKS_ENOMEM,
+ * RKS_ECUDA, or RKS_ETIMEOUT if a bounded device wait gave up. */
+int rks_basis_product_f32(int64_t n, const float* U, int64_t ldu, int nin, const double* Q, int nout, float* out,
+                          void* stream);
 
 /* ---- Host-side small dense FP64 steps (Algorithm 1 contraction) ------ */
 

@@ -18,7 +18,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 CXX = os.environ.get("CXX", "g++")
 
-SOURCES = ["kernels.cu", "kernels_df.cu", "api.cu", "noalloc.cu", "dense.cpp"]
+SOURCES = ["kernels.cu", "kernels_df.cu", "restart_tc.cu", "api.cu", "noalloc.cu", "dense.cpp"]
 
 
 def _cmd(src: str) -> list[str]:

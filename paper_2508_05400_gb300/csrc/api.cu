@@ -66,6 +66,8 @@ struct rks_ctx {
   float2* U2 = nullptr;
   float* valsf = nullptr;  // mixed precision: FP32 values and basis
   float* Uf = nullptr;
+  void* qimg = nullptr;     // mixed precision: bf16 split image of Q' for the tensor-core restart
+  std::vector<uint16_t> qimg_h;
   void* Ub = nullptr;      // basis in use: U2 or Uf
   bool f32 = false;        // basis in use is FP32
   int phase_restarts = 0;
@@ -99,7 +101,8 @@ struct rks_ctx {
   int evused = 0;
   // results
   bool solved = false;
-  int kk = 0;
+  int kk = 0;               // columns of the kept decomposition (locked + active)
+  int nw = 0;               // reported Ritz pairs: the best k (k + 1 for a pair at the cut)
   std::vector<double> Tfull, bfull, lre, lim, est, resid;
   std::vector<double> hist;
   std::vector<int> hist_lock;
@@ -337,7 +340,10 @@ int contract(rks_ctx* c) {
   }
   rks_dense::hessenberg_arrow(ma, c->brow, H.data(), ma, Q.data(), ma);
   if (rks_dense::schur(ma, H.data(), ma, Q.data(), ma) != 0) return RKS_EDENSE;
-  const int want = c->k - q;
+  // Algorithm 1 keeps the k - q best active Schur vectors; with opts.keep > 0
+  // the restart is thick: up to keep active vectors even after locking
+  int want = c->k - q;
+  if (c->opts.keep > 0) want = std::max(want, std::min(c->opts.keep, ma / 2));
   rks_dense::reorder(ma, H.data(), ma, Q.data(), ma, ma, c->which, std::min(want + 1, ma));
   // truncation size: blocks covering `want` columns, pairs kept whole
   int ka = 0;
@@ -424,7 +430,16 @@ int contract(rks_ctx* c) {
   for (int j = 0; j < ka; ++j)
     for (int l = 0; l < ma; ++l) Qp[l + (size_t)j * ma] = c->cs_h[q + l] * Qk[l + (size_t)j * ma];
   int ps = prof_begin(c, RKS_K_RESTART);
-  if (c->prec != RKS_PREC_FP64) {
+  if (c->f32 && c->qimg && rks::tc_restart_supported(ma, ka)) {
+    // FP32 basis: split-BF16 product on the tensor cores
+    rks::tc_restart_bimage(ma, ka, Qp.data(), c->qimg_h);
+    CK(cudaMemcpyAsync(c->qimg, c->qimg_h.data(), c->qimg_h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                       c->stream));
+    float* U0 = c->Uf + (size_t)q * c->ldu;
+    rks::launch_tc_restart_f32(c->n, U0, U0, c->ldu, ma, ka, c->qimg, c->Uf + (size_t)m * c->ldu,
+                               c->Uf + (size_t)(q + ka) * c->ldu, c->flag, c->stream);
+    CK(cudaStreamSynchronize(c->stream));   // the image is a host buffer reused next restart
+  } else if (c->prec != RKS_PREC_FP64) {
     std::vector<float2> Q2h(Qp.size());
     for (size_t t = 0; t < Qp.size(); ++t) {
       float h = (float)Qp[t];
@@ -545,15 +560,21 @@ void ritz(rks_ctx* c) {
     double al = std::hypot(lre[o], lim[o]);
     c->est[t] = std::abs(bty) / std::max(c->opts.conv == RKS_CONV_NORM1 ? c->norm1 : al, 1e-300);
   }
+  int nw = std::min(c->k, kk);
+  if (nw > 0 && nw < kk && c->lim[nw - 1] > 0) ++nw;   // never split a complex pair
+  c->nw = nw;
 }
 
 // Ritz vectors X = U Y (real packing), A X and FP64 residuals.
 int finalize(rks_ctx* c) {
-  const int kk = c->kk;
+  const int kk = c->kk, nw = c->nw;
   if (!c->X) {
-    int rc = dalloc(&c->X, (size_t)c->ldu * (c->k + 1));
+    // X holds the nw <= k + 1 Ritz vectors; AX also serves as FP64 scratch
+    // for the kk <= min(m, 2k + 1) kept basis columns
+    const int ncx = std::min(c->m + 1, 2 * c->k + 2);
+    int rc = dalloc(&c->X, (size_t)c->ldu * ncx);
     if (rc) return rc;
-    rc = dalloc(&c->AX, (size_t)c->ldu * (c->k + 1));
+    rc = dalloc(&c->AX, (size_t)c->ldu * ncx);
     if (rc) return rc;
     rc = dalloc(&c->rsum, (size_t)4 * (c->k + 1) * rks::kResidCtas);
     if (rc) return rc;
@@ -562,11 +583,11 @@ int finalize(rks_ctx* c) {
     rc = dalloc(&c->plam, (size_t)2 * (c->k + 1));
     if (rc) return rc;
   }
-  std::vector<double> Yr((size_t)kk * kk);
+  std::vector<double> Yr((size_t)kk * nw);
   std::vector<int> col, colim;
   std::vector<double> pl_re, pl_im;
-  for (int t = 0; t < kk;) {
-    bool pair = c->lim[t] > 0 && t + 1 < kk;
+  for (int t = 0; t < nw;) {
+    bool pair = c->lim[t] > 0 && t + 1 < nw;
     for (int i = 0; i < kk; ++i) {
       Yr[i + (size_t)t * kk] = c->Y[i + (size_t)t * kk].real();
       if (pair) Yr[i + (size_t)(t + 1) * kk] = c->Y[i + (size_t)t * kk].imag();
@@ -582,11 +603,11 @@ int finalize(rks_ctx* c) {
   int ps = prof_begin(c, RKS_K_OTHER);
   if (c->prec != RKS_PREC_FP64) {
     rks::launch_df2d_cols(c->n, c->Ub, c->ldu, c->AX, c->ldu, kk, c->f32, c->stream);
-    rks::launch_rows_gemm(c->n, c->AX, c->ldu, 0, kk, c->Qd, kk, c->X, c->ldu, 0, -1, c->stream);
+    rks::launch_rows_gemm(c->n, c->AX, c->ldu, 0, kk, c->Qd, nw, c->X, c->ldu, 0, -1, c->stream);
   } else {
-    rks::launch_rows_gemm(c->n, c->U, c->ldu, 0, kk, c->Qd, kk, c->X, c->ldu, 0, -1, c->stream);
+    rks::launch_rows_gemm(c->n, c->U, c->ldu, 0, kk, c->Qd, nw, c->X, c->ldu, 0, -1, c->stream);
   }
-  rks::launch_spmm(c->A, c->X, c->ldu, c->AX, c->ldu, kk, c->stream);
+  rks::launch_spmm(c->A, c->X, c->ldu, c->AX, c->ldu, nw, c->stream);
   std::vector<int> pc(2 * np);
   std::vector<double> pv(2 * np);
   for (int t = 0; t < np; ++t) { pc[t] = col[t]; pc[np + t] = colim[t]; pv[t] = pl_re[t]; pv[np + t] = pl_im[t]; }
@@ -603,7 +624,7 @@ int finalize(rks_ctx* c) {
   for (int q = 0; q < 4 * np; ++q)
     for (int g = 0; g < rg; ++g) sums[q] += part[(size_t)q * rg + g];
   prof_flush(c);
-  c->resid.assign(kk, 0.0);
+  c->resid.assign(nw, 0.0);
   for (int t = 0; t < np; ++t) {
     double res = std::sqrt(sums[4 * t]) / (c->norm1 * std::sqrt(std::max(sums[4 * t + 1], 1e-300)));
     c->resid[col[t]] = res;
@@ -621,7 +642,7 @@ void free_ctx(rks_ctx* c) {
   cudaFree(c->X); cudaFree(c->AX); cudaFree(c->rsum); cudaFree(c->pcol); cudaFree(c->plam);
   cudaFree(c->vals2); cudaFree(c->U2); cudaFree(c->S2); cudaFree(c->nrs); cudaFree(c->sj); cudaFree(c->Q2);
   cudaFree(c->rprev); cudaFree(c->znorm); cudaFree(c->tmp64); cudaFree(c->valsf); cudaFree(c->Uf);
-  cudaFree(c->otab); cudaFree(c->lsr1); cudaFree(c->lsz1); cudaFree(c->bar);
+  cudaFree(c->otab); cudaFree(c->lsr1); cudaFree(c->lsz1); cudaFree(c->bar); cudaFree(c->qimg);
   rks::free_sketch_tiles(&c->tiles);
   cudaFree(c->part_z); cudaFree(c->part_s);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
@@ -670,6 +691,7 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
   if (o.conv != RKS_CONV_EIG && o.conv != RKS_CONV_NORM1) return RKS_EINVAL;
   if (o.prec != RKS_PREC_DF && o.prec != RKS_PREC_FP64 && o.prec != RKS_PREC_MIXED) return RKS_EINVAL;
   if (o.maxit <= 0) o.maxit = 1000;
+  if (o.keep < 0 || o.keep > k) return RKS_EINVAL;
   const int m = k + p;
   if (n <= 0 || !rowptr || !colind || !vals || k < 1 || p < 2 || (int64_t)m + 1 > n || d < m + 1 ||
       o.zeta < 1 || o.zeta > 16 || d < 2 * o.zeta || d > 8192 || which < 0 || which > 3 || !(tol > 0) ||
@@ -744,6 +766,8 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
   if (c->prec != RKS_PREC_FP64) {
     if (c->prec == RKS_PREC_MIXED) {
       if ((rc = dalloc(&c->Uf, (size_t)c->ldu * (m + 1))) || (rc = dalloc(&c->valsf, c->nnz))) return fail(rc);
+      if (cudaMalloc(&c->qimg, rks::kTcImageBytes) != cudaSuccess) return fail(RKS_ENOMEM);
+      if (rks::configure_tc_kernels() != cudaSuccess) return fail(RKS_ECUDA);
       rks::launch_d2df(c->nnz, c->vals, c->valsf, true, c->stream);
     }
     if ((rc = dalloc(&c->U2, (size_t)c->ldu * (m + 1))) || (rc = dalloc(&c->vals2, c->nnz)) ||
@@ -806,7 +830,7 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
 static int run_alg1(rks_ctx* c, const double* start, int limit, double verify, int stall, bool* converged) {
   const int m = c->m, d = c->d;
   *converged = false;
-  c->q = 0; c->ja = 0; c->kk = 0;
+  c->q = 0; c->ja = 0; c->kk = 0; c->nw = 0;
   c->Ba.assign((size_t)(m + 1) * m, 0.0);
   c->Tqq.assign((size_t)(c->k + 2) * (c->k + 2), 0.0);
   c->Tqa.assign((size_t)(c->k + 2) * (m + 1), 0.0);
@@ -852,17 +876,17 @@ static int run_alg1(rks_ctx* c, const double* start, int limit, double verify, i
     ritz(c);
     c->stats.host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
     double mx = 0.0;
-    for (double e : c->est) mx = std::max(mx, e);
+    for (int t = 0; t < c->nw; ++t) mx = std::max(mx, c->est[t]);
     c->hist.push_back(mx);
     c->hist_lock.push_back(c->q);
-    if (c->q >= c->k || mx <= c->tol) {
+    if (mx <= c->tol) {
       *converged = true;
       if (verify > 0) {                // FP64 verification of the true residuals
         rc = finalize(c);
         if (rc) return rc;
         double mr = 0.0;
         for (double v : c->resid) mr = std::max(mr, v);
-        if (mr > verify && c->q < c->k && done < limit) {
+        if (mr > verify && c->q < c->k && done < limit) {   // locked vectors are final
           c->tol *= 0.25;
           c->eta_lock *= 0.25;
           *converged = false;
@@ -952,7 +976,7 @@ int rks_solve(rks_ctx* c, rks_info* info) {
     info->nmatvec = c->nmatvec;
     double me = 0.0, mr = 0.0;
     int nc = 0;
-    for (size_t i = 0; i < c->est.size() && c->restarts > 0; ++i) {
+    for (size_t i = 0; i < (size_t)c->nw && i < c->est.size() && c->restarts > 0; ++i) {
       me = std::max(me, c->est[i]);
       if (c->est[i] <= c->tol) ++nc;
     }
@@ -969,6 +993,8 @@ int rks_solve(rks_ctx* c, rks_info* info) {
 }
 
 int rks_nkept(const rks_ctx* c) { return c ? c->kk : 0; }
+
+int rks_nwanted(const rks_ctx* c) { return c ? c->nw : 0; }
 
 int rks_get_history(const rks_ctx* c, double* hist, int* nlock, int cap) {
   if (!c || cap < 0) return RKS_EINVAL;
@@ -1009,12 +1035,12 @@ int rks_get_schur(rks_ctx* c, double* T, double* U, double* b) {
 int rks_get_eigpairs(rks_ctx* c, double* lam_re, double* lam_im, double* X, double* resid) {
   if (!c) return RKS_EINVAL;
   if (!c->solved || c->kk == 0) return RKS_ESTATE;
-  const int kk = c->kk;
-  if (lam_re) std::memcpy(lam_re, c->lre.data(), sizeof(double) * kk);
-  if (lam_im) std::memcpy(lam_im, c->lim.data(), sizeof(double) * kk);
-  if (resid) std::memcpy(resid, c->resid.data(), sizeof(double) * kk);
+  const int nw = c->nw;
+  if (lam_re) std::memcpy(lam_re, c->lre.data(), sizeof(double) * nw);
+  if (lam_im) std::memcpy(lam_im, c->lim.data(), sizeof(double) * nw);
+  if (resid) std::memcpy(resid, c->resid.data(), sizeof(double) * nw);
   if (X) {
-    CK(cudaMemcpy2DAsync(X, c->n * sizeof(double), c->X, c->ldu * sizeof(double), c->n * sizeof(double), kk,
+    CK(cudaMemcpy2DAsync(X, c->n * sizeof(double), c->X, c->ldu * sizeof(double), c->n * sizeof(double), nw,
                          c->opts.mem_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
@@ -1024,7 +1050,7 @@ int rks_get_eigpairs(rks_ctx* c, double* lam_re, double* lam_im, double* X, doub
 int rks_get_estimates(rks_ctx* c, double* est) {
   if (!c || !est) return RKS_EINVAL;
   if (!c->solved || c->kk == 0) return RKS_ESTATE;
-  std::memcpy(est, c->est.data(), sizeof(double) * c->kk);
+  std::memcpy(est, c->est.data(), sizeof(double) * c->nw);
   return RKS_OK;
 }
 
@@ -1103,6 +1129,32 @@ int rks_sketch_pairs(int64_t n, int d, int zeta, uint64_t seed, int32_t* rows, i
   cudaFree(flag);
   if (e != cudaSuccess) return RKS_ECUDA;
   return f ? RKS_EINVAL : RKS_OK;
+}
+
+int rks_basis_product_f32(int64_t n, const float* U, int64_t ldu, int nin, const double* Q, int nout, float* out,
+                          void* stream) {
+  if (n <= 0 || ldu < n || !U || !Q || !out || !rks::tc_restart_supported(nin, nout)) return RKS_EINVAL;
+  if (rks::configure_tc_kernels() != cudaSuccess) return RKS_ECUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<uint16_t> img;
+  rks::tc_restart_bimage(nin, nout, Q, img);
+  void* dimg = nullptr;
+  int* flag = nullptr;
+  if (cudaMalloc(&dimg, img.size() * sizeof(uint16_t)) != cudaSuccess) return RKS_ENOMEM;
+  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) { cudaFree(dimg); return RKS_ENOMEM; }
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dimg, img.data(), img.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    rks::launch_tc_restart_f32(n, U, out, ldu, nin, nout, dimg, nullptr, nullptr, flag, st);
+    e = cudaGetLastError();
+  }
+  int f = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&f, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dimg);
+  cudaFree(flag);
+  if (e != cudaSuccess) return RKS_ECUDA;
+  return (f & rks::RKS_FLAG_TIMEOUT) ? RKS_ETIMEOUT : RKS_OK;
 }
 
 int rks_sketch_apply(int64_t n, int d, int zeta, uint64_t seed, const double* x, double* z, void* stream) {

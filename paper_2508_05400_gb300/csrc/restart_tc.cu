@@ -1,0 +1,313 @@
+// Restart product U_k = U Q' (Eq. 3.5) of an FP32 basis on the fifth-generation
+// tensor cores of sm_103a (tcgen05.mma, accumulators in tensor memory).
+//
+// Split-BF16: an FP32 value u is the exact sum u1 + u2 + u3 of three bf16
+// numbers (u1 = bf16(u), u2 = bf16(u - u1), u3 = bf16(u - u1 - u2); each
+// remainder is exact in FP32); Q' is split the same way on the host.  The
+// product keeps the six terms u_i q_j with i + j <= 4 (the dropped ones are
+// below 2^-32 |u| |q|); every bf16 x bf16 product is exact and the sums are
+// FP32 in tensor memory, so the result has FP32-class accuracy.
+//
+// One CTA (256 threads) owns tiles of 128 rows; per tile the K dimension
+// (the nin input columns, padded to kKc) streams through two shared-memory
+// stages of 32 columns: all threads load and split a stage (FP32 loads,
+// coalesced along the rows) into the canonical K-major no-swizzle layout,
+// thread 0 issues 2 x 6 MMAs of 128 x N x 16 on it and commits them to the
+// stage's mbarrier, which the next load of that stage waits for.  The
+// epilogue reads the 128 x N FP32 accumulator with tcgen05.ld (warps 0-3 and
+// 4-7 take alternate 16-column groups of their lane quarter) and writes the
+// outputs; every read of a tile's rows precedes its writes, so the product
+// may be formed in place.  All waits are bounded (RKS_FLAG_TIMEOUT).
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "rks_impl.h"
+
+namespace rks {
+
+namespace {
+
+constexpr int kM = 128;           // rows per tile (MMA M)
+constexpr int kKc = 32;           // input columns per stage (two MMA K-steps)
+constexpr int kThreads = 256;
+constexpr int kStageSplit = kM * kKc * 2;   // bytes of one split of one stage
+constexpr int kStage = 3 * kStageSplit;
+constexpr int kTmemCols = 64;
+
+// Byte offset of element (r, k) of a K-major, no-swizzle tile with `rows`
+// rows: K sub-tiles of 16, each of rows/8 groups (stride SBO = 256 B) of two
+// 8 x 16-byte core matrices along K (stride LBO = 128 B).
+__host__ __device__ inline uint32_t canon_off(int r, int k, int rows) {
+  return (uint32_t)((k >> 4) * rows * 32 + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: start address, LBO, SBO (all >> 4),
+// descriptor version 1 (bits 46-48), no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+         (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t idesc_bf16(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Bounded wait for the completion of the mbarrier phase with this parity.
+__device__ bool mbar_wait(uint32_t mbar, uint32_t parity, int* flag) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P1;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > 2000000000ll) {
+      atomicOr(flag, RKS_FLAG_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ uint32_t bf16_bits(__nv_bfloat16 h) { return (uint32_t)__bfloat16_as_ushort(h); }
+
+// The six split products (i, j) with i + j <= 4, splits numbered 1..3 (0..2 here).
+__host__ __device__ constexpr int pair_a(int p) { return p == 2 || p == 4 ? 1 : (p == 5 ? 2 : 0); }
+__host__ __device__ constexpr int pair_b(int p) { return p == 1 || p == 4 ? 1 : (p == 3 ? 2 : 0); }
+
+// out[i, o] = sum_l in[i, l] Q'[l, o] for i < n, o < nout; then, when mvsrc
+// is given, mvdst[i] = mvsrc[i].  bimg: the three bf16 splits of Q' (Kp x N,
+// zero padded) in the canonical layout, split j at byte j * Kp * N * 2.
+__global__ void __launch_bounds__(kThreads, 1) k_tc_restart_f32(int64_t n, const float* in, float* out, int64_t ldu,
+                                                                int nin, int Kp, int N, int nout,
+                                                                const uint4* __restrict__ bimg, const float* mvsrc,
+                                                                float* mvdst, int* flag) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int bbytes = 3 * Kp * N * 2;
+  uint8_t* sB = smem;
+  uint8_t* sA = smem + ((bbytes + 1023) & ~1023);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sA + 2 * kStage);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
+
+  for (int t = tid; t < bbytes / 16; t += kThreads) reinterpret_cast<uint4*>(sB)[t] = bimg[t];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < 3; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + s)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = idesc_bf16(N);
+  const uint32_t sA32 = smem_u32(sA), sB32 = smem_u32(sB);
+  const int nk = Kp / kKc;
+  const int64_t ntiles = (n + kM - 1) / kM;
+  int g = 0;                 // stages filled so far (all tiles)
+  uint32_t dpar = 0;         // parity of the accumulator-done barrier
+  bool ok = true;
+  const int r = tid & (kM - 1), kh = tid >> 7;   // loader: row, half of the stage's 32 columns
+
+  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int64_t i = tile * kM + r;
+    for (int kc = 0; kc < nk && ok; ++kc, ++g) {
+      const int s = g & 1;
+      if (g >= 2) ok = mbar_wait(smem_u32(mbar + s), (uint32_t)(((g - 2) >> 1) & 1), flag);
+      ok = __syncthreads_and(ok);
+      if (!ok) break;
+      // load and split 16 columns of one row
+      float v[16];
+      const int l0 = kc * kKc + kh * 16;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int l = l0 + u;
+        v[u] = (i < n && l < nin) ? in[i + (int64_t)l * ldu] : 0.f;
+      }
+      uint8_t* st = sA + s * kStage;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t w[3][4];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+          uint32_t p[3][2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float x = v[h * 8 + u + e];
+            const __nv_bfloat16 a = __float2bfloat16_rn(x);
+            const float r1 = x - __bfloat162float(a);
+            const __nv_bfloat16 b = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+            p[0][e] = bf16_bits(a);
+            p[1][e] = bf16_bits(b);
+            p[2][e] = bf16_bits(c);
+          }
+#pragma unroll
+          for (int q = 0; q < 3; ++q) w[q][u >> 1] = p[q][0] | (p[q][1] << 16);
+        }
+        const uint32_t off = canon_off(r, kh * 16 + h * 8, kM);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          *reinterpret_cast<uint4*>(st + q * kStageSplit + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        fence_after();
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const int ks = kc * 2 + kk;   // K-step of 16 within the padded K
+#pragma unroll
+          for (int pr = 0; pr < 6; ++pr) {
+            const uint64_t a = sdesc(sA32 + s * kStage + pair_a(pr) * kStageSplit + kk * kM * 32);
+            const uint64_t b = sdesc(sB32 + pair_b(pr) * Kp * N * 2 + ks * N * 32);
+            mma_bf16(tmem, a, b, idesc, (kc | kk | pr) ? 1u : 0u);
+          }
+        }
+        mma_commit(smem_u32(mbar + s));
+        if (kc == nk - 1) mma_commit(smem_u32(mbar + 2));
+      }
+    }
+    if (!ok) break;
+    // epilogue
+    ok = mbar_wait(smem_u32(mbar + 2), dpar, flag);
+    dpar ^= 1u;
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    fence_after();
+    const int q4 = warp & 3;
+    const int64_t ir = tile * kM + q4 * 32 + lane;
+    float mv = 0.f;
+    if (mvsrc && warp < 4 && ir < n) mv = mvsrc[ir];
+    for (int cg = warp >> 2; cg < N / 16; cg += 2) {
+      float acc[16];
+      tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(cg * 16), acc);
+      if (ir < n) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int o = cg * 16 + j;
+          if (o < nout) out[ir + (int64_t)o * ldu] = acc[j];
+        }
+      }
+    }
+    if (mvsrc && warp < 4 && ir < n) mvdst[ir] = mv;
+    fence_before();
+    __syncthreads();   // accumulator read before the next tile's first MMA
+  }
+  // Every issued MMA has completed unless a wait gave up; then thread 0 waits
+  // (bounded again) for the last commit of each barrier before the tensor
+  // memory is released.
+  if (!ok && tid == 0) {
+    const int c0 = (g + 1) / 2, c1 = g / 2;      // commits made to the two stage barriers
+    if (c0 > 0) (void)mbar_wait(smem_u32(mbar + 0), (uint32_t)((c0 - 1) & 1), flag);
+    if (c1 > 0) (void)mbar_wait(smem_u32(mbar + 1), (uint32_t)((c1 - 1) & 1), flag);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+uint16_t host_bf16(float x) {   // round to nearest even (finite inputs)
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+double host_bf16_value(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+}  // namespace
+
+bool tc_restart_supported(int nin, int nout) { return nin >= 1 && nin <= 256 && nout >= 1 && nout <= 64; }
+
+size_t tc_restart_smem(int nin, int nout) {
+  const int Kp = (nin + kKc - 1) / kKc * kKc, N = (nout + 15) / 16 * 16;
+  return (size_t)((3 * Kp * N * 2 + 1023) & ~1023) + 2 * kStage + 64;
+}
+
+// Host image of the three bf16 splits of Q (nin x nout, column-major FP64).
+void tc_restart_bimage(int nin, int nout, const double* Q, std::vector<uint16_t>& img) {
+  const int Kp = (nin + kKc - 1) / kKc * kKc, N = (nout + 15) / 16 * 16;
+  img.assign((size_t)3 * Kp * N, 0);
+  for (int o = 0; o < nout; ++o)
+    for (int l = 0; l < nin; ++l) {
+      double rem = Q[l + (size_t)o * nin];
+      for (int s = 0; s < 3; ++s) {
+        const uint16_t h = host_bf16((float)rem);
+        rem -= host_bf16_value(h);
+        img[(size_t)s * Kp * N + canon_off(o, l, N) / 2] = h;
+      }
+    }
+}
+
+cudaError_t configure_tc_kernels() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_restart_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+void launch_tc_restart_f32(int64_t n, const float* in, float* out, int64_t ldu, int nin, int nout, const void* bimg,
+                           const float* mvsrc, float* mvdst, int* flag, cudaStream_t st) {
+  const int Kp = (nin + kKc - 1) / kKc * kKc, N = (nout + 15) / 16 * 16;
+  const int64_t ntiles = (n + kM - 1) / kM;
+  const int g = (int)std::min<int64_t>(ntiles, 152 * 2);
+  k_tc_restart_f32<<<g, kThreads, tc_restart_smem(nin, nout), st>>>(n, in, out, ldu, nin, Kp, N, nout,
+                                                                      static_cast<const uint4*>(bimg), mvsrc, mvdst,
+                                                                      flag);
+}
+
+}  // namespace rks

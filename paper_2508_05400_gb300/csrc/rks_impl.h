@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace rks {
 
 enum : int { RKS_FLAG_NAN = 1, RKS_FLAG_BREAKDOWN = 2, RKS_FLAG_HASH = 4, RKS_FLAG_TIMEOUT = 8 };
@@ -77,6 +79,16 @@ void launch_df2d_cols(int64_t n, const void* x, int64_t ldx, double* y, int64_t 
 void launch_df_sketch_vec(const void* x, const SketchTiles& t, double* part, bool f32, cudaStream_t st);
 void launch_df_rows_gemm(int64_t n, void* U, int64_t ldu, int a0, int nin, const float2* Q, int nout, int c0,
                          int move_src, bool f32, cudaStream_t st);
+
+// Tensor-core restart product for an FP32 basis (restart_tc.cu):
+// out[:, o] = sum_l in[:, l] Q[l, o], in place allowed, then mvdst = mvsrc.
+bool tc_restart_supported(int nin, int nout);
+size_t tc_restart_smem(int nin, int nout);
+void tc_restart_bimage(int nin, int nout, const double* Q, std::vector<uint16_t>& img);
+cudaError_t configure_tc_kernels();
+void launch_tc_restart_f32(int64_t n, const float* in, float* out, int64_t ldu, int nin, int nout, const void* bimg,
+                           const float* mvsrc, float* mvdst, int* flag, cudaStream_t st);
+constexpr size_t kTcImageBytes = (size_t)3 * 256 * 64 * 2;   // largest split image of Q'
 
 void launch_sketch_pairs(int64_t n, int d, int zeta, uint64_t seed, int32_t* rows, int8_t* signs, int* flag,
                          cudaStream_t st);

@@ -32,7 +32,7 @@ class Opts(C.Structure):
     _fields_ = [("zeta", C.c_int), ("maxit", C.c_int), ("lock", C.c_int), ("mem_device", C.c_int),
                 ("stream", C.c_void_p), ("u1", C.c_void_p), ("eta_lock", C.c_double),
                 ("max_restarts", C.c_int), ("profile", C.c_int), ("conv", C.c_int),
-                ("prec", C.c_int), ("mixed_tol", C.c_double), ("verify", C.c_double)]
+                ("prec", C.c_int), ("mixed_tol", C.c_double), ("verify", C.c_double), ("keep", C.c_int)]
 
 
 CONV = {"eig": 0, "norm1": 1}
@@ -99,8 +99,12 @@ def lib() -> C.CDLL:
         L.rks_get_history.restype = C.c_int
         L.rks_nkept.argtypes = [_P]
         L.rks_nkept.restype = C.c_int
+        L.rks_nwanted.argtypes = [_P]
+        L.rks_nwanted.restype = C.c_int
         L.rks_norm1.argtypes = [_P]
         L.rks_norm1.restype = C.c_double
+        L.rks_basis_product_f32.argtypes = [C.c_int64, _P, C.c_int64, C.c_int, _P, C.c_int, _P, _P]
+        L.rks_basis_product_f32.restype = C.c_int
         L.rks_destroy.argtypes = [_P]
         L.rks_destroy.restype = None
         L.rks_sketch_pairs.argtypes = [C.c_int64, C.c_int, C.c_int, C.c_uint64, _P, _P, _P]
@@ -155,7 +159,7 @@ class Solver:
     def __init__(self, n, rowptr, colind, vals, k, p, d, which="LM", tol=1e-10, seed=0, *,
                  zeta=8, maxit=1000, lock=True, u1=None, eta_lock=0.0, max_restarts=0,
                  device=False, stream=None, profile=False, conv="eig", verify=0.0, prec="df",
-                 mixed_tol=0.0):
+                 mixed_tol=0.0, keep=0):
         L = lib()
         self.n, self.k, self.p, self.d = int(n), int(k), int(p), int(d)
         self.device = bool(device)
@@ -184,6 +188,7 @@ class Solver:
         o.verify = float(verify)
         o.prec = PREC[prec]
         o.mixed_tol = float(mixed_tol)
+        o.keep = int(keep)
         h = _P()
         _check(L.rks_create(C.byref(h), self.n, _ptr(rowptr), _ptr(colind), _ptr(vals), vdt,
                             self.k, self.p, self.d, WHICH[which] if isinstance(which, str) else int(which),
@@ -221,6 +226,10 @@ class Solver:
         return lib().rks_nkept(self._h)
 
     @property
+    def nwanted(self) -> int:
+        return lib().rks_nwanted(self._h)
+
+    @property
     def norm1(self) -> float:
         return lib().rks_norm1(self._h)
 
@@ -234,8 +243,8 @@ class Solver:
         return T, U, b
 
     def eigpairs(self, X_out=None, want_vectors=True):
-        """(lam complex[kk], X real-packed n x kk or None, resid[kk])."""
-        kk = self.nkept
+        """(lam complex[nw], X real-packed n x nw or None, resid[nw]), best first."""
+        kk = self.nwanted
         lre, lim, res = np.zeros(kk), np.zeros(kk), np.zeros(kk)
         X = None
         if want_vectors:
@@ -245,7 +254,7 @@ class Solver:
         return lre + 1j * lim, X, res
 
     def estimates(self) -> np.ndarray:
-        e = np.zeros(self.nkept)
+        e = np.zeros(self.nwanted)
         _check(lib().rks_get_estimates(self._h, e.ctypes.data), "rks_get_estimates")
         return e
 
@@ -327,6 +336,19 @@ def sketch_apply_noalloc(x, z, d: int, zeta: int, seed: int) -> int:
     import torch
     stream = torch.cuda.current_stream().cuda_stream
     return lib().rks_sketch_apply_noalloc(x.numel(), d, zeta, seed, x.data_ptr(), z.data_ptr(), stream)
+
+
+def basis_product_f32(U, ldu: int, n: int, nin: int, Q: np.ndarray, out) -> None:
+    """out = U Q on the tensor cores (split-BF16) for an FP32 basis.
+
+    U, out: CUDA float32 tensors holding column-major n x nin / n x nout data
+    with leading dimension ldu (out may be U); Q: nin x nout FP64 host array.
+    """
+    import torch
+    Qf = np.asfortranarray(Q, dtype=np.float64)
+    stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().rks_basis_product_f32(n, U.data_ptr(), ldu, nin, Qf.ctypes.data, Qf.shape[1], out.data_ptr(),
+                                       stream), "rks_basis_product_f32")
 
 
 def host_ordered_schur(B: np.ndarray, which: str, nsort: int):

@@ -130,7 +130,7 @@ def _run_gpu(A, k, p, d, zeta, which, tol, **kw):
 def _check_against_oracle(A, k, p, d, zeta, which, tol, lam_tol, exact=None, **kw):
     info, lam, X, res, T, U, b, est = _run_gpu(A, k, p, d, zeta, which, tol, **kw)
     ores = R.rks(A.to_scipy(), k, p, d, I.start_vector(A.n, 1), zeta=zeta, seed=0,
-                 which=which, tol=tol, lock_vectors=kw.get("lock", True))
+                 which=which, tol=tol, lock_vectors=kw.get("lock", True), keep=kw.get("keep", 0))
     assert info["converged"] == 1 and ores.converged
     kk = min(lam.size, ores.eigvals.size, k)
     rel = np.abs(lam[:kk] - ores.eigvals[:kk]) / np.abs(ores.eigvals[:kk])
@@ -197,7 +197,7 @@ def test_device_pointer_mode_matches_host_mode(gpu):
     with K().Solver(A.n, t(A.rowptr), t(A.colind), t(A.vals), 6, 18, 64, which="LR", tol=1e-12,
                     u1=t(u1), device=True) as s:
         s.solve()
-        X_d = gpu.zeros((s.nkept, A.n), dtype=gpu.float64, device="cuda")
+        X_d = gpu.zeros((s.nwanted, A.n), dtype=gpu.float64, device="cuda")
         lam_d, _, _ = s.eigpairs(X_out=X_d)
     # the same inputs give the same bits whichever memory they came from
     assert np.array_equal(lam_d, lam_h)
@@ -262,6 +262,30 @@ def test_convdiff_1000_full_size(prec):
     near = np.array([np.min(np.abs(ex[:60] - l)) / abs(l) for l in lam.real])
     assert near.max() < 0.15
     assert np.median(near) < 0.01
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_thick_restart_matches_oracle(prec):
+    # keep > 0: the same thick restart as the oracle, the closed-form spectrum
+    N = 30
+    A = I.convdiff_2d(N, N, 1.0, 20.0, 10.0)
+    ex = np.sort(I.convdiff_2d_eigenvalues(N, N, 1.0, 20.0, 10.0))[::-1]
+    info, ores = _check_against_oracle(A, 6, 18, 64, 8, "LR", 1e-13, 1e-10, exact=ex, prec=prec, keep=6)
+    assert info["nmatvec"] < R.rks(A.to_scipy(), 6, 18, 64, I.start_vector(A.n, 1), zeta=8, seed=0,
+                                   which="LR", tol=1e-13).nmatvec
+    with K().Solver.from_csr(A, 6, 18, 64, which="LR", tol=1e-13, zeta=8, u1=I.start_vector(A.n, 1),
+                             prec=prec, keep=6) as s:
+        s.solve()
+        assert s.nwanted == 6 and s.nkept >= 6
+        T, U, b = s.schur()
+        lam, X, res = s.eigpairs()
+        assert lam.size == 6 and X.shape == (A.n, 6)
+    # the kept decomposition A U = U T + u b^T: A U - U T is the rank-one u b^T,
+    # so it vanishes on the complement of b
+    AU = A.to_scipy() @ U
+    r = AU - U @ T
+    Pb = np.eye(b.size) - np.outer(b, b) / (b @ b)
+    assert np.linalg.norm(r @ Pb) <= 1e-10 * np.linalg.norm(AU)
 
 
 @pytest.mark.parametrize("prec", PRECS)
