@@ -34,13 +34,14 @@ WORKLOAD = ("convdiff2d_1000: 2D upwind convection-diffusion 1000x1000 (n=1e6), 
 # Products with A that rKS needs on this workload (measured by this solver on a
 # GB300; the method's count, used to scale the bounded CPU samples).
 NMATVEC_WORKLOAD = None
-# DRAM traffic per launch of the dominant kernel from one ncu capture (bytes),
-# valid only for the kernel source it was measured on (sha256 prefix of kernels.cu).
+# DRAM traffic of the dominant kernel from one ncu capture, as a ratio to the
+# algorithmic bytes of the captured launch (applied to the mean launch), valid
+# only for the kernel source it was measured on (sha256 prefix of kernels_df.cu).
 NCU_TRAFFIC = {}
 
 
 def _kernel_hash() -> str:
-    with open(os.path.join(ROOT, "paper_2508_05400_gb300", "csrc", "kernels.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2508_05400_gb300", "csrc", "kernels_df.cu"), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
@@ -200,7 +201,7 @@ def run_ours(args) -> None:
     solver = rks.Solver(A.n, d_rowptr, d_colind, d_vals, P.k, P.p, P.d, which=P.which,
                         seed=P.omega_seed, zeta=P.zeta, u1=d_u1, device=True,
                         stream=stream.cuda_stream, profile=True, prec=args.prec, maxit=args.maxit,
-                        keep=keep, **P.solver_opts())
+                        keep=keep, ortho=args.ortho, **P.solver_opts())
     X_dev = torch.empty((P.k + 1, A.n), dtype=torch.float64, device=dev)
 
     def step():
@@ -249,8 +250,8 @@ def run_ours(args) -> None:
     achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
     traffic = None
     rec = NCU_TRAFFIC.get(dom)
-    if rec and rec.get("kernels_sha") == _kernel_hash():
-        traffic = rec["bytes_per_launch"]
+    if rec and rec.get("kernels_sha") == _kernel_hash() and args.prec == "df":
+        traffic = rec["ratio"] * bytes_per_launch
     path = ("spmv_sketch", "ls", "update_sketch", "finish")
     path_bytes = sum(agg[c]["bytes"] for c in path)
     path_ms = sum(agg[c]["ms"] for c in path)
@@ -271,7 +272,8 @@ def run_ours(args) -> None:
         t0 = time.perf_counter()
         with rks.Solver(A.n, h_rowptr, h_colind, h_vals, P.k, P.p, P.d, which=P.which,
                         seed=P.omega_seed, zeta=P.zeta, u1=h_u1, stream=stream.cuda_stream,
-                        prec=args.prec, maxit=args.maxit, keep=keep, **P.solver_opts()) as s2:
+                        prec=args.prec, maxit=args.maxit, keep=keep, ortho=args.ortho,
+                        **P.solver_opts()) as s2:
             s2.solve(allow_noconv=False)
             s2.eigpairs(X_out=h_X)
         e2e_times.append((time.perf_counter() - t0) * 1e3)
@@ -290,7 +292,8 @@ def run_ours(args) -> None:
             "dtype": DTYPES[args.prec],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "k": P.k, "p": P.p, "d": P.d,
-                       "zeta": P.zeta, "prec": args.prec, "keep": keep, "parallelism": f"replicas{world}",
+                       "zeta": P.zeta, "prec": args.prec, "keep": keep, "ortho": args.ortho,
+                       "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (basis 648 MB, A 80 MB)"},
             "roofline": roofline,
             "spmv_rgs_gbs": path_bytes / (path_ms * 1e-3) / 1e9 if path_ms else None,
@@ -328,6 +331,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--maxit", type=int, default=4000, help="restart limit of each solve")
+    ap.add_argument("--ortho", default="sketch", choices=["sketch", "cgs2"],
+                    help="sketch: randomized Gram-Schmidt (rKS); cgs2: the Krylov-Schur baseline "
+                         "with Euclidean CGS2 (DF only)")
     ap.add_argument("--keep", type=int, default=-1,
                     help="active Schur vectors a restart keeps after locking (thick restart); "
                          "-1: k; 0: k - q as in Algorithm 1")

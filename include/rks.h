@@ -102,7 +102,15 @@ typedef struct {
                           active directions.  Either way convergence and the
                           reported Ritz pairs concern the rks_nwanted best
                           Ritz pairs of the kept decomposition. */
+  int ortho;           /* RKS_ORTHO_SKETCH (default): randomized Gram-Schmidt
+                          in the sketch (the method).  RKS_ORTHO_CGS2: the
+                          Krylov-Schur baseline the paper compares against
+                          (KS-CGS2, Sec. 5): Euclidean classical Gram-Schmidt
+                          with reorthogonalisation, same storage and kernels,
+                          no sketch; RKS_PREC_DF only. */
 } rks_opts;
+
+enum { RKS_ORTHO_SKETCH = 0, RKS_ORTHO_CGS2 = 1 };
 
 enum { RKS_PREC_DF = 0, RKS_PREC_FP64 = 1, RKS_PREC_MIXED = 2 };
 

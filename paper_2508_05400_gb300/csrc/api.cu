@@ -81,6 +81,7 @@ struct rks_ctx {
   rks::SketchTiles tiles;    // per-tile bin lists of Omega (deterministic sketch accumulation)
   double* part_z = nullptr;  // G x d per-CTA partial sketches of A u (z') and of u~ (s~)
   double* part_s = nullptr;
+  double* part_d = nullptr;  // Euclidean CGS2 baseline: G x (m+1) partial dot products
   unsigned* bar = nullptr;   // grid-barrier state of the cooperative least squares
   float2* lsr1 = nullptr;    // least-squares scratch: first-pass coefficients (m+1)
   float2* lsz1 = nullptr;    // and the projected sketch (d)
@@ -232,11 +233,45 @@ void expand_df_launches(rks_ctx* c, int c0) {
   prof_end(c, s, RKS_K_FINISH, nf, 3.0 * P * c->d, 2.0 * c->d);
 }
 
+// Krylov-Schur with Euclidean CGS2 (the paper's KS-CGS2 comparison method,
+// Sec. 5), same storage and kernels without the sketch: per step the SpMV,
+// two passes of (dot products with every basis column, update), and the norm.
+void expand_ks_launches(rks_ctx* c, int c0) {
+  const double n = (double)c->n, P = 8.0;
+  const double spmv_bytes = (double)c->nnz * (P + 4) + 4.0 * (n + 1) + 2 * P * n;
+  const int G = c->tiles.G;
+  for (int j = c0; j < c->m; ++j) {
+    const int col = j + 1;
+    char* ub = static_cast<char*>(c->Ub);
+    const size_t es = sizeof(float2);
+    int s = prof_begin(c, RKS_K_SPMV);
+    rks::launch_df_spmv(c->A2, ub + (size_t)j * c->ldu * es, ub + (size_t)col * c->ldu * es, c->tiles, c->stream);
+    prof_end(c, s, RKS_K_SPMV, 1, spmv_bytes, 2.0 * c->nnz);
+    for (int pass = 1; pass <= 2; ++pass) {
+      s = prof_begin(c, RKS_K_LS);
+      rks::launch_df_dots(c->Ub, c->ldu, col, col, c->tiles, c->part_d, c->stream);
+      rks::launch_ks_coef(pass, j, col, G, c->part_d, c->colscale, c->rprev, c->nrs, c->sj, c->stream);
+      prof_end(c, s, RKS_K_LS, 2, (col + 1) * P * n, 2.0 * n * col);
+      s = prof_begin(c, RKS_K_UPDATE);
+      rks::launch_df_update_plain(c->Ub, c->ldu, col, c->nrs, c->sj, c->tiles, pass == 2 ? c->part_s : nullptr,
+                                  c->stream);
+      prof_end(c, s, RKS_K_UPDATE, 1, (col + 2) * P * n, 2.0 * n * col);
+    }
+    s = prof_begin(c, RKS_K_FINISH);
+    rks::launch_ks_finish(j, G, c->part_s, 1e-14 * c->norm1, c->colscale, c->rprev, c->coef, c->m + 1, c->flag,
+                          c->stream);
+    prof_end(c, s, RKS_K_FINISH, 1, 8.0 * G, 2.0 * G);
+    ++c->nmatvec;
+  }
+}
+
 // Algorithm 2: extend from the last vector at column q+ja to column m.
 int expand(rks_ctx* c) {
   const int c0 = c->q + c->ja;
   c->brow = c->ja;
-  if (c->prec != RKS_PREC_FP64) {
+  if (c->opts.ortho == RKS_ORTHO_CGS2) {
+    expand_ks_launches(c, c0);
+  } else if (c->prec != RKS_PREC_FP64) {
     expand_df_launches(c, c0);
   } else
   {
@@ -386,7 +421,7 @@ int contract(rks_ctx* c) {
       acc -= (a == bb) ? 1.0 : 0.0;
       gerr += acc * acc;
     }
-  if (ka > 0 && std::sqrt(gerr) > 1e-10) {
+  if (c->opts.ortho != RKS_ORTHO_CGS2 && ka > 0 && std::sqrt(gerr) > 1e-10) {
     std::vector<double> R((size_t)ka * ka), Rinv((size_t)ka * ka, 0.0);
     house_qr(d, ka, Sa.data(), R.data());
     for (int j = 0; j < ka; ++j) {          // Rinv by back substitution
@@ -644,7 +679,7 @@ void free_ctx(rks_ctx* c) {
   cudaFree(c->rprev); cudaFree(c->znorm); cudaFree(c->tmp64); cudaFree(c->valsf); cudaFree(c->Uf);
   cudaFree(c->otab); cudaFree(c->lsr1); cudaFree(c->lsz1); cudaFree(c->bar); cudaFree(c->qimg);
   rks::free_sketch_tiles(&c->tiles);
-  cudaFree(c->part_z); cudaFree(c->part_s);
+  cudaFree(c->part_z); cudaFree(c->part_s); cudaFree(c->part_d);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -692,6 +727,8 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
   if (o.prec != RKS_PREC_DF && o.prec != RKS_PREC_FP64 && o.prec != RKS_PREC_MIXED) return RKS_EINVAL;
   if (o.maxit <= 0) o.maxit = 1000;
   if (o.keep < 0 || o.keep > k) return RKS_EINVAL;
+  if (o.ortho != RKS_ORTHO_SKETCH && o.ortho != RKS_ORTHO_CGS2) return RKS_EINVAL;
+  if (o.ortho == RKS_ORTHO_CGS2 && o.prec != RKS_PREC_DF) return RKS_EINVAL;
   const int m = k + p;
   if (n <= 0 || !rowptr || !colind || !vals || k < 1 || p < 2 || (int64_t)m + 1 > n || d < m + 1 ||
       o.zeta < 1 || o.zeta > 16 || d < 2 * o.zeta || d > 8192 || which < 0 || which > 3 || !(tol > 0) ||
@@ -792,7 +829,8 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
     cudaFree(c->otab);
     c->otab = nullptr;
     if (rks::sketch_tile_smem(c->tiles, m + 1) > 200 * 1024) return fail(RKS_EINVAL);
-    if ((rc = dalloc(&c->part_z, (size_t)c->tiles.G * d)) || (rc = dalloc(&c->part_s, (size_t)c->tiles.G * d)))
+    if ((rc = dalloc(&c->part_z, (size_t)c->tiles.G * d)) || (rc = dalloc(&c->part_s, (size_t)c->tiles.G * d)) ||
+        (rc = dalloc(&c->part_d, (size_t)c->tiles.G * (m + 1))))
       return fail(rc);
     rks::launch_d2df(c->nnz, c->vals, c->vals2, false, c->stream);
     c->A2.n = n; c->A2.nnz = c->nnz; c->A2.rowptr = c->rowptr; c->A2.colind = c->colind; c->A2.vals = c->vals2;
@@ -846,12 +884,19 @@ static int run_alg1(rks_ctx* c, const double* start, int limit, double verify, i
     const double* src = start ? start : c->u1;
     if (!src) { rks::launch_start_vector(c->n, c->seed + 1, c->tmp64, c->stream); src = c->tmp64; }
     rks::launch_d2df(c->n, src, c->Ub, c->f32, c->stream);
-    rks::launch_df_sketch_vec(c->Ub, c->tiles, c->part_s, c->f32, c->stream);
-    CK(cudaMemsetAsync(c->znorm, 0, sizeof(double), c->stream));
-    const int nf = rks::launch_df_small(0, d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale,
-                                        c->rprev, c->coef, m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1,
-                                        c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream);
-    prof_end(c, ps, RKS_K_OTHER, (src == c->tmp64 && !start ? 3 : 2) + nf, 0.0, 0.0);
+    if (c->opts.ortho == RKS_ORTHO_CGS2) {   // Euclidean normalisation of the start vector
+      rks::launch_df_dots(c->Ub, c->ldu, 1, 0, c->tiles, c->part_d, c->stream);
+      rks::launch_ks_finish(-1, c->tiles.G, c->part_d, 0.0, c->colscale, c->rprev, c->coef, m + 1, c->flag,
+                            c->stream);
+      prof_end(c, ps, RKS_K_OTHER, src == c->tmp64 && !start ? 4 : 3, 0.0, 0.0);
+    } else {
+      rks::launch_df_sketch_vec(c->Ub, c->tiles, c->part_s, c->f32, c->stream);
+      CK(cudaMemsetAsync(c->znorm, 0, sizeof(double), c->stream));
+      const int nf = rks::launch_df_small(0, d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale,
+                                          c->rprev, c->coef, m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1,
+                                          c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream);
+      prof_end(c, ps, RKS_K_OTHER, (src == c->tmp64 && !start ? 3 : 2) + nf, 0.0, 0.0);
+    }
   } else {
     if (c->u1) CK(cudaMemcpyAsync(c->U, c->u1, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     else rks::launch_start_vector(c->n, c->seed + 1, c->U, c->stream);

@@ -274,6 +274,22 @@ int schur(int n, double* H, int ldh, double* Z, int ldz) {
   return 0;
 }
 
+// Diagonal blocks of T starting in [i0, i1) (a 2x2 block is never split).
+static void scan_blocks(const double* T, int ldt, int i0, int i1, int n, std::vector<Block>& out) {
+  int i = i0;
+  while (i < i1) {
+    if (i + 1 < n && at(T, ldt, i + 1, i) != 0.0) {
+      double a = at(T, ldt, i, i), b = at(T, ldt, i, i + 1), c = at(T, ldt, i + 1, i), d = at(T, ldt, i + 1, i + 1);
+      double p = 0.5 * (a - d), disc = p * p + b * c;
+      out.push_back({i, 2, 0.5 * (a + d), disc < 0 ? std::sqrt(-disc) : 0.0});
+      i += 2;
+    } else {
+      out.push_back({i, 1, at(T, ldt, i, i), 0.0});
+      i += 1;
+    }
+  }
+}
+
 std::vector<Block> blocks(int n, const double* T, int ldt) {
   std::vector<Block> out;
   int i = 0;
@@ -328,7 +344,44 @@ bool small_solve(int s, double M[4][4], double r[4]) {
 
 }  // namespace
 
+// Exchange of two adjacent 1x1 blocks a = T(j,j), c = T(j+1,j+1): the rotation
+// whose first column is the eigenvector (b, c - a) of [[a, b], [0, c]] for c
+// brings c to the top (G^T T G = [[c, *], [0, a]]).
+static void swap_singles(int n, double* T, int ldt, double* Z, int ldz, int nz, int j) {
+  const double a = at(T, ldt, j, j), b = at(T, ldt, j, j + 1), c = at(T, ldt, j + 1, j + 1);
+  const double x = b, y = c - a;
+  const double r = std::hypot(x, y);
+  if (r == 0.0) return;                       // equal diagonal, b = 0: already in order
+  const double cs = x / r, sn = y / r;
+  for (int col = j; col < n; ++col) {         // rows j, j+1 <- G^T rows
+    const double t0 = at(T, ldt, j, col), t1 = at(T, ldt, j + 1, col);
+    at(T, ldt, j, col) = cs * t0 + sn * t1;
+    at(T, ldt, j + 1, col) = -sn * t0 + cs * t1;
+  }
+  for (int row = 0; row <= j + 1; ++row) {    // columns j, j+1 <- columns G
+    const double t0 = at(T, ldt, row, j), t1 = at(T, ldt, row, j + 1);
+    at(T, ldt, row, j) = cs * t0 + sn * t1;
+    at(T, ldt, row, j + 1) = -sn * t0 + cs * t1;
+  }
+  if (Z) {
+    double* z0 = Z + (size_t)j * ldz;
+    double* z1 = Z + (size_t)(j + 1) * ldz;
+    for (int row = 0; row < nz; ++row) {
+      const double t0 = z0[row], t1 = z1[row];
+      z0[row] = cs * t0 + sn * t1;
+      z1[row] = -sn * t0 + cs * t1;
+    }
+  }
+  at(T, ldt, j, j) = c;
+  at(T, ldt, j + 1, j + 1) = a;
+  at(T, ldt, j + 1, j) = 0.0;
+}
+
 int swap_blocks(int n, double* T, int ldt, double* Z, int ldz, int nz, int j, int p, int q) {
+  if (p == 1 && q == 1) {
+    swap_singles(n, T, ldt, Z, ldz, nz, j);
+    return 0;
+  }
   const int s = p + q;
   // Sylvester: T11 X - X T22 = -T12, X is p x q; unknown index x(i,l) = i + p*l
   double M[4][4] = {{0}}, r[4] = {0};
@@ -446,16 +499,18 @@ int reorder(int n, double* T, int ldt, double* Z, int ldz, int nz, int which, in
     if (best < 0) break;
     // bubble block `best` up to position `top`
     int t = best;
+    std::vector<Block> loc;
     while (bl[t].start > top) {
-      const int up_start = bl[t - 1].start, up_size = bl[t - 1].size;
+      const int up_start = bl[t - 1].start, up_size = bl[t - 1].size, s = up_size + bl[t].size;
       int rc = swap_blocks(n, T, ldt, Z, ldz, nz, up_start, up_size, bl[t].size);
       if (rc != 0) { ++fails; break; }
-      bl = blocks(n, T, ldt);
-      // the moved block now starts at up_start
-      int pos = up_start;
-      t = -1;
-      for (size_t u = 0; u < bl.size(); ++u) if (bl[u].start == pos) t = (int)u;
-      if (t < 0) break;
+      // only the two swapped blocks changed: rescan their rows (the moved
+      // block now starts at up_start; a 2x2 block may have split)
+      loc.clear();
+      scan_blocks(T, ldt, up_start, up_start + s, n, loc);
+      bl.erase(bl.begin() + (t - 1), bl.begin() + (t + 1));
+      bl.insert(bl.begin() + (t - 1), loc.begin(), loc.end());
+      t = t - 1;
     }
     if (t < 0) break;
     top = bl[t].start + bl[t].size;

@@ -24,8 +24,8 @@
 // that contribute to it and their signs, in a fixed order.  A tile's values
 // are staged in shared memory; then the threads that own the tile's sketch
 // rows sum their lists (DF, TwoSum) into per-CTA DF accumulators.  Each CTA
-// writes its d partial sums; the consumer adds the CTA partials in CTA order
-// (fold_group).  The result is the same bits on every run.
+// writes its d partial sums; the consumer adds the CTA partials in a fixed
+// order (fold_row).  The result is the same bits on every run.
 
 #include <algorithm>
 #include <vector>
@@ -265,35 +265,34 @@ __device__ __forceinline__ void tile_add(uint32_t x, const float2* vals, float& 
 }
 
 // Sketch of one staged tile: acc[row] += sum over the row's bin list of
-// sign * vals[tile row], entries in their stored order.  H adjacent lanes
-// share a position (each takes every H-th entry) when d is small; their sums
-// are combined by a fixed xor tree.  A sketch row has one position per tile,
-// so acc[row] has one writer per tile.
-__device__ __forceinline__ void tile_gather(const SketchTiles& tv, int64_t t, int64_t r0, const float2* vals,
-                                            const int* offs, float2* acc) {
-  const int d = tv.d, H = tv.H, total = d * H;
+// sign * vals[tile row], entries in their stored order.  The tile's slot
+// offsets (offs), positions (ms) and entries (es) are in shared memory.
+// H adjacent lanes share a position (each takes every H-th entry) when d is
+// small; their sums are combined by a fixed xor tree.  A sketch row has one
+// position per tile, so acc[row] has one writer per tile.
+__device__ __forceinline__ void tile_gather(int d, int H, const float2* vals, const int* offs, const uint32_t* ms,
+                                            const uint16_t* es, float2* acc) {
+  const int total = d * H;
   const int lane = threadIdx.x & 31;
-  const uint32_t* __restrict__ meta = tv.meta + t * d;
-  const uint16_t* __restrict__ ent = tv.ent + r0 * tv.zeta;
   for (int base = threadIdx.x & ~31; base < total; base += blockDim.x) {
     const int pp = base + lane;
     const int p = pp / H, h = pp - p * H;
     float s = 0.f, e = 0.f;
     int b = -1, cnt = 0;
     if (pp < total) {
-      const uint32_t mt = __ldg(meta + p);
+      const uint32_t mt = ms[p];
       b = (int)(mt & 0xFFFFu);
       cnt = (int)(mt >> 16);
       int q = h;
       for (; q + 3 * H < cnt; q += 4 * H) {
-        const uint32_t x0 = __ldg(ent + offs[q] + p), x1 = __ldg(ent + offs[q + H] + p);
-        const uint32_t x2 = __ldg(ent + offs[q + 2 * H] + p), x3 = __ldg(ent + offs[q + 3 * H] + p);
+        const uint32_t x0 = es[offs[q] + p], x1 = es[offs[q + H] + p];
+        const uint32_t x2 = es[offs[q + 2 * H] + p], x3 = es[offs[q + 3 * H] + p];
         tile_add(x0, vals, s, e);
         tile_add(x1, vals, s, e);
         tile_add(x2, vals, s, e);
         tile_add(x3, vals, s, e);
       }
-      for (; q < cnt; q += H) tile_add(__ldg(ent + offs[q] + p), vals, s, e);
+      for (; q < cnt; q += H) tile_add(es[offs[q] + p], vals, s, e);
     }
     for (int o = 1; o < H; o <<= 1) {
       const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
@@ -312,16 +311,49 @@ __device__ __forceinline__ void tile_gather(const SketchTiles& tv, int64_t t, in
   }
 }
 
-// Shared memory of a tile kernel: acc (d), two value buffers, the update's
-// coefficients (c), two slot-offset buffers.
-__host__ __device__ inline size_t tile_smem_bytes(int d, int L, int c) {
-  return ((size_t)d + 2 * kTileRows + c) * sizeof(float2) + (size_t)2 * (L + 1) * sizeof(int);
+// Shared memory of a tile kernel: DF accumulators (d), two value buffers,
+// the update's coefficients (c), then two buffers each of the tile's entries,
+// positions and slot offsets.
+struct TileSmem {
+  size_t acc, vb, rsh, es, ms, offs, total;
+};
+
+__host__ __device__ inline TileSmem tile_smem_layout(int d, int L, int c, int zeta) {
+  TileSmem s;
+  size_t o = 0;
+  s.acc = o; o += (size_t)d * sizeof(float2);
+  s.vb = o; o += (size_t)2 * kTileRows * sizeof(float2);
+  s.rsh = o; o += (size_t)c * sizeof(float2);
+  o = (o + 15) & ~(size_t)15;
+  s.es = o; o += (size_t)2 * kTileRows * zeta * sizeof(uint16_t);
+  s.ms = o; o += (size_t)2 * d * sizeof(uint32_t);
+  s.offs = o; o += (size_t)2 * (L + 1) * sizeof(int);
+  s.total = o;
+  return s;
 }
 
-// Stage the slot offsets of tile t.
-__device__ __forceinline__ void tile_offsets(const SketchTiles& tv, int64_t t, int* of) {
-  const int L1 = tv.L + 1;
+__host__ __device__ inline size_t tile_smem_bytes(int d, int L, int c, int zeta) {
+  return tile_smem_layout(d, L, c, zeta).total;
+}
+
+// Stage tile t's slot offsets, positions and entries (coalesced copies; the
+// entries with 16-byte loads when aligned).
+__device__ __forceinline__ void tile_stage(const SketchTiles& tv, int64_t t, int64_t r0, int rows, int* of,
+                                           uint32_t* ms, uint16_t* es) {
+  const int L1 = tv.L + 1, d = tv.d;
   for (int q = threadIdx.x; q < L1; q += blockDim.x) of[q] = tv.off[t * L1 + q];
+  const uint32_t* mg = tv.meta + t * d;
+  for (int q = threadIdx.x; q < d; q += blockDim.x) ms[q] = __ldg(mg + q);
+  const uint16_t* src = tv.ent + r0 * tv.zeta;
+  const int cnt = rows * tv.zeta;
+  int q0 = 0;
+  if (((r0 * tv.zeta) & 7) == 0) {
+    const int nv = cnt >> 3;
+    for (int q = threadIdx.x; q < nv; q += blockDim.x)
+      reinterpret_cast<uint4*>(es)[q] = __ldg(reinterpret_cast<const uint4*>(src) + q);
+    q0 = nv << 3;
+  }
+  for (int q = q0 + threadIdx.x; q < cnt; q += blockDim.x) es[q] = src[q];
 }
 
 __device__ __forceinline__ void tile_write_part(const float2* acc, int d, double* part) {
@@ -330,40 +362,68 @@ __device__ __forceinline__ void tile_write_part(const float2* acc, int d, double
 }
 
 // w'[i] = sum_p A_p x[col_p] (DF) over the CTA's tiles; part[cta] = the
-// CTA's Omega-sums of w' as stored.
-template <class TA, class TU>
+// CTA's Omega-sums of w' as stored.  512 threads; thread l takes the tile
+// rows l and l + 512 together, four entries of each per round, so that the
+// loads of both rows are in flight at once (the products of a row are still
+// accumulated in entry order).
+// SK = false: the plain SpMV (Krylov-Schur with Euclidean CGS2), no sketch.
+template <class TA, class TU, bool SK>
 __global__ void __launch_bounds__(512) k_df_spmv_sketch(
     const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind, const TA* __restrict__ vals,
     const TU* __restrict__ x, TU* __restrict__ w, const SketchTiles tv, double* __restrict__ part) {
-  extern __shared__ float2 sh2[];
+  static_assert(kTileRows == 1024, "two rows per thread of a 512-thread CTA");
+  extern __shared__ __align__(16) uint8_t smraw[];
   const int d = tv.d, L1 = tv.L + 1;
-  float2* acc = sh2;
-  float2* vb = acc + d;
-  int* offs = reinterpret_cast<int*>(vb + 2 * kTileRows);
-  for (int r = threadIdx.x; r < d; r += blockDim.x) acc[r] = make_float2(0.f, 0.f);
+  const TileSmem lay = tile_smem_layout(d, tv.L, 0, tv.zeta);
+  float2* acc = reinterpret_cast<float2*>(smraw + lay.acc);
+  if (SK)
+    for (int r = threadIdx.x; r < d; r += blockDim.x) acc[r] = make_float2(0.f, 0.f);
   const int t0 = tv.ctile[blockIdx.x], t1 = tv.ctile[blockIdx.x + 1];
   for (int t = t0; t < t1; ++t) {
     const int buf = (t - t0) & 1;
-    float2* v = vb + buf * kTileRows;
-    int* of = offs + buf * L1;
+    float2* v = reinterpret_cast<float2*>(smraw + lay.vb) + buf * kTileRows;
+    int* of = reinterpret_cast<int*>(smraw + lay.offs) + buf * L1;
+    uint32_t* ms = reinterpret_cast<uint32_t*>(smraw + lay.ms) + buf * d;
+    uint16_t* es = reinterpret_cast<uint16_t*>(smraw + lay.es) + (size_t)buf * kTileRows * tv.zeta;
     const int64_t r0 = tv.row[t];
     const int rows = (int)(tv.row[t + 1] - r0);
-    for (int l = threadIdx.x; l < rows; l += blockDim.x) {
-      const int64_t i = r0 + l;
-      float s = 0.f, e = 0.f;
-      const int p0 = rowptr[i], p1 = rowptr[i + 1];
-      for (int p = p0; p < p1; ++p) {
-        const float2 a = ldv(vals + p);
-        const float2 xv = ldv(x + colind[p]);
-        df_mac(a.x, a.y, xv.x, xv.y, s, e);
+    if (SK) tile_stage(tv, t, r0, rows, of, ms, es);
+    const int la = threadIdx.x, lb = threadIdx.x + 512;
+    int pa = 0, ea = 0, pb = 0, eb = 0;
+    if (la < rows) { pa = rowptr[r0 + la]; ea = rowptr[r0 + la + 1]; }
+    if (lb < rows) { pb = rowptr[r0 + lb]; eb = rowptr[r0 + lb + 1]; }
+    float sa = 0.f, ta = 0.f, sb = 0.f, tb = 0.f;
+    const int len = max(ea - pa, eb - pb);
+    for (int q = 0; q < len; q += 4) {
+      int ca[4], cb[4];
+      float2 va[4], vbv[4], xa[4], xb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int p = pa + q + u, p2 = pb + q + u;
+        ca[u] = p < ea ? colind[p] : -1;
+        cb[u] = p2 < eb ? colind[p2] : -1;
+        va[u] = p < ea ? ldv(vals + p) : make_float2(0.f, 0.f);
+        vbv[u] = p2 < eb ? ldv(vals + p2) : make_float2(0.f, 0.f);
       }
-      v[l] = stv(w + i, df_norm(s, e));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xa[u] = ca[u] >= 0 ? ldv(x + ca[u]) : make_float2(0.f, 0.f);
+        xb[u] = cb[u] >= 0 ? ldv(x + cb[u]) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (ca[u] >= 0) df_mac(va[u].x, va[u].y, xa[u].x, xa[u].y, sa, ta);
+        if (cb[u] >= 0) df_mac(vbv[u].x, vbv[u].y, xb[u].x, xb[u].y, sb, tb);
+      }
     }
-    tile_offsets(tv, t, of);
-    __syncthreads();
-    tile_gather(tv, t, r0, v, of, acc);
+    if (la < rows) v[la] = stv(w + r0 + la, df_norm(sa, ta));
+    if (lb < rows) v[lb] = stv(w + r0 + lb, df_norm(sb, tb));
+    if (SK) {
+      __syncthreads();
+      tile_gather(d, tv.H, v, of, ms, es, acc);
+    }
   }
-  tile_write_part(acc, d, part);
+  if (SK) tile_write_part(acc, d, part);
 }
 
 // Vector load of two consecutive rows (i even, ld even): float4 = two pairs,
@@ -383,27 +443,35 @@ __device__ __forceinline__ void ld2(const float* p, float2& a, float2& b) {
 // written to U[:, c]; part[cta] = the CTA's Omega-sums of u~ as stored.
 // A thread takes two consecutive rows (tile starts are even and ld is a
 // multiple of 32, so the pair load stays aligned and inside the column).
-template <class TU, int UNR, int MINB>
+// MODE 1: with the sketch; MODE 0: plain update (Euclidean CGS2); MODE 2:
+// plain update, and part[cta] = the CTA's sum of squares of u~ as stored
+// (FP64, fixed reduction order).
+template <class TU, int UNR, int MINB, int MODE>
 __global__ void __launch_bounds__(512, MINB) k_df_update_sketch(
     TU* __restrict__ U, int64_t ldu, int c, const float2* __restrict__ nrs, const float2* __restrict__ sj,
     const SketchTiles tv, double* __restrict__ part) {
-  extern __shared__ float2 sh2[];
+  constexpr bool SK = MODE == 1;
+  extern __shared__ __align__(16) uint8_t smraw[];
   const int d = tv.d, L1 = tv.L + 1;
-  float2* acc = sh2;
-  float2* vb = acc + d;
-  float2* rsh = vb + 2 * kTileRows;
-  int* offs = reinterpret_cast<int*>(rsh + c);
+  const TileSmem lay = tile_smem_layout(d, tv.L, c, tv.zeta);
+  float2* acc = reinterpret_cast<float2*>(smraw + lay.acc);
+  float2* rsh = reinterpret_cast<float2*>(smraw + lay.rsh);
   for (int col = threadIdx.x; col < c; col += blockDim.x) rsh[col] = nrs[col];
-  for (int r = threadIdx.x; r < d; r += blockDim.x) acc[r] = make_float2(0.f, 0.f);
+  if (SK)
+    for (int r = threadIdx.x; r < d; r += blockDim.x) acc[r] = make_float2(0.f, 0.f);
+  double ss = 0.0;
   __syncthreads();
   const float2 sc = sj[0];
   const int t0 = tv.ctile[blockIdx.x], t1 = tv.ctile[blockIdx.x + 1];
   for (int t = t0; t < t1; ++t) {
     const int buf = (t - t0) & 1;
-    float2* v = vb + buf * kTileRows;
-    int* of = offs + buf * L1;
+    float2* v = reinterpret_cast<float2*>(smraw + lay.vb) + buf * kTileRows;
+    int* of = reinterpret_cast<int*>(smraw + lay.offs) + buf * L1;
+    uint32_t* ms = reinterpret_cast<uint32_t*>(smraw + lay.ms) + buf * d;
+    uint16_t* es = reinterpret_cast<uint16_t*>(smraw + lay.es) + (size_t)buf * kTileRows * tv.zeta;
     const int64_t r0 = tv.row[t];
     const int rows = (int)(tv.row[t + 1] - r0);
+    if (SK) tile_stage(tv, t, r0, rows, of, ms, es);
     for (int l = 2 * threadIdx.x; l < rows; l += 2 * blockDim.x) {
       const int64_t i = r0 + l;
       float s0 = 0.f, t0a = 0.f, s1 = 0.f, t1a = 0.f;
@@ -433,42 +501,142 @@ __global__ void __launch_bounds__(512, MINB) k_df_update_sketch(
         df_mac(a.x, a.y, r.x, r.y, s0, t0a);
         df_mac(bb.x, bb.y, r.x, r.y, s1, t1a);
       }
-      v[l] = stv(U + i + (int64_t)c * ldu, df_norm(s0, t0a));
-      if (l + 1 < rows) v[l + 1] = stv(U + i + 1 + (int64_t)c * ldu, df_norm(s1, t1a));
+      const float2 v0 = stv(U + i + (int64_t)c * ldu, df_norm(s0, t0a));
+      v[l] = v0;
+      if (MODE == 2) { const double x = df_to_double(v0); ss = fma(x, x, ss); }
+      if (l + 1 < rows) {
+        const float2 v1 = stv(U + i + 1 + (int64_t)c * ldu, df_norm(s1, t1a));
+        v[l + 1] = v1;
+        if (MODE == 2) { const double x = df_to_double(v1); ss = fma(x, x, ss); }
+      }
     }
-    tile_offsets(tv, t, of);
+    if (SK) {
+      __syncthreads();
+      tile_gather(d, tv.H, v, of, ms, es, acc);
+    }
+  }
+  if (SK) tile_write_part(acc, d, part);
+  if (MODE == 2) {
+    __shared__ double red[32];
+    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
     __syncthreads();
-    tile_gather(tv, t, r0, v, of, acc);
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+      part[blockIdx.x] = s;
+    }
   }
-  tile_write_part(acc, d, part);
 }
 
-// out[r] = sum over g < G of part[g * d + r] for the 32 sketch rows of group
-// grp: warp w of the CTA adds g = w, w + nw, ... in order, then warp 0 adds
-// the warp sums in warp order.  Fixed order for a fixed G (deterministic).
-__device__ void fold_group(const double* __restrict__ part, int d, int G, int grp, double* __restrict__ out,
-                           double* red) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int r = grp * 32 + lane;
+// Euclidean CGS2 (Krylov-Schur baseline): part[cta * c + l] = the CTA's
+// partial of U[:, l]^T U[:, cv] for l < c (DF products, FP64 per CTA, fixed
+// order).  Columns go in groups of 8 (U read once); U[:, cv] is re-read per
+// group (from L2).
+template <class TU>
+__global__ void __launch_bounds__(512) k_df_dots(const TU* __restrict__ U, int64_t ldu, int c, int cv,
+                                                 const SketchTiles tv, double* __restrict__ part) {
+  __shared__ float2 red[16][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t0 = tv.ctile[blockIdx.x], t1 = tv.ctile[blockIdx.x + 1];
+  const TU* vcol = U + (int64_t)cv * ldu;
+  for (int g0 = 0; g0 < c; g0 += 8) {
+    const int ng = min(8, c - g0);
+    float s[8], e[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { s[q] = 0.f; e[q] = 0.f; }
+    for (int t = t0; t < t1; ++t) {
+      const int64_t r0 = tv.row[t];
+      const int rows = (int)(tv.row[t + 1] - r0);
+      for (int l = 2 * threadIdx.x; l < rows; l += 2 * blockDim.x) {
+        const int64_t i = r0 + l;
+        float2 x0, x1;
+        ld2(vcol + i, x0, x1);
+        if (l + 1 >= rows) x1 = make_float2(0.f, 0.f);
+        float2 a[8], b[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < ng) ld2(U + i + (int64_t)(g0 + q) * ldu, a[q], b[q]);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < ng) {
+            df_mac(a[q].x, a[q].y, x0.x, x0.y, s[q], e[q]);
+            df_mac(b[q].x, b[q].y, x1.x, x1.y, s[q], e[q]);
+          }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      df_warp_sum(s[q], e[q]);
+      if (lane == 0) red[warp][q] = df_norm(s[q], e[q]);
+    }
+    __syncthreads();
+    if (threadIdx.x < ng) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += df_to_double(red[w][threadIdx.x]);
+      part[(size_t)blockIdx.x * c + g0 + threadIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Coefficients of one CGS2 pass from the folded dots g_l = u~_l^T v:
+// pass 1 (v = w' = A u~_j): b_l = cs_l cs_j g_l, rprev = b, sj = cs_j;
+// pass 2 (v = u~): b_l = cs_l g_l, rprev += b, sj = 1; nrs_l = -b_l cs_l.
+// One CTA; the G partials of each l are added in CTA order.
+__global__ void __launch_bounds__(256) k_ks_coef(int pass, int j, int c, int G, const double* __restrict__ part,
+                                                 const double* __restrict__ colscale, double* __restrict__ rprev,
+                                                 float2* __restrict__ nrs, float2* __restrict__ sj) {
+  for (int l = threadIdx.x; l < c; l += blockDim.x) {
+    double g = 0.0;
+    for (int q = 0; q < G; ++q) g += part[(size_t)q * c + l];
+    const double b = pass == 1 ? colscale[l] * colscale[j] * g : colscale[l] * g;
+    rprev[l] = pass == 1 ? b : rprev[l] + b;
+    nrs[l] = df_from_double(-b * colscale[l]);
+  }
+  if (threadIdx.x == 0) sj[0] = df_from_double(pass == 1 ? colscale[j] : 1.0);
+}
+
+// End of a CGS2 step j: beta = ||u~|| from the G sum-of-squares partials,
+// colscale[j + 1] = 1/beta, coefficient column j = (rprev_0..j, beta); beta
+// <= thr is a breakdown.  With j < 0 only the start vector's scale.
+__global__ void k_ks_finish(int j, int G, const double* __restrict__ part, double thr,
+                            double* __restrict__ colscale, const double* __restrict__ rprev, double* __restrict__ coef,
+                            int ldcoef, int* flag) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double ss = 0.0;
+  for (int q = 0; q < G; ++q) ss += part[q];
+  const double beta = sqrt(ss);
+  const bool finite = isfinite(beta);
+  const bool brk = finite && !(beta > thr);
+  colscale[j + 1] = (finite && !brk) ? 1.0 / beta : 0.0;
+  if (j >= 0) {
+    double* cc = coef + (size_t)j * ldcoef;
+    for (int i = 0; i <= j; ++i) cc[i] = rprev[i];
+    cc[j + 1] = beta;
+  }
+  if (!finite) atomicOr(flag, RKS_FLAG_NAN);
+  else if (brk) atomicOr(flag, RKS_FLAG_BREAKDOWN);
+}
+
+// sum over g < G of part[g * d + r] by one warp: lane l adds g = l, l + 32,
+// ... in order, then a fixed xor tree adds the 32 lane sums (every lane ends
+// with the total).  The same order on every run.
+__device__ __forceinline__ double fold_row(const double* __restrict__ part, int d, int G, int r, int lane) {
   double v = 0.0;
-  if (r < d) {
-#pragma unroll 4
-    for (int g = warp; g < G; g += nw) v += part[(size_t)g * d + r];
-  }
-  red[threadIdx.x] = v;
-  __syncthreads();
-  if (warp == 0 && r < d) {
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += red[w * 32 + lane];
-    out[r] = s;
-  }
-  __syncthreads();
+#pragma unroll 8
+  for (int g = lane; g < G; g += 32) v += part[(size_t)g * d + r];
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
+// out = the CTA-ordered sum of the sketch kernels' partials (warp per row)
 __global__ void __launch_bounds__(256) k_df_fold(const double* __restrict__ part, int d, int G,
                                                  double* __restrict__ out) {
-  __shared__ double red[256];
-  fold_group(part, d, G, blockIdx.x, out, red);
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= d) return;
+  const double v = fold_row(part, d, G, r, lane);
+  if (lane == 0) out[r] = v;
 }
 
 // Least squares b = S^+ z of one Arnoldi step, CGS2 in the sketch, in three
@@ -619,17 +787,19 @@ __global__ void __launch_bounds__(256) k_df_ls_coop(
     const double* __restrict__ part_s, int G, unsigned* bar, int* flag) {
   extern __shared__ float2 zd[];   // d
   __shared__ double red[33];
-  __shared__ double fred[256];
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   const int gw = blockIdx.x * nw + warp, tw = gridDim.x * nw;   // global warp index, warps in grid
   const int c = j + 1;
   // phase 0: z' and s~_j from the sketch kernels' per-CTA partial sums
   {
-    const int gz = (d + 31) / 32;
-    const int ntask = finish ? 2 * gz : gz;
-    for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
-      if (task < gz) fold_group(part_z, d, G, task, z_raw, fred);
-      else fold_group(part_s, d, G, task - gz, s_raw, fred);
+    const int nb = finish ? 2 * d : d;
+    for (int r = gw; r < nb; r += tw) {
+      const bool isz = r < d;
+      const double v = fold_row(isz ? part_z : part_s, d, G, isz ? r : r - d, lane);
+      if (lane == 0) {
+        if (isz) z_raw[r] = v;
+        else s_raw[r - d] = v;
+      }
     }
     grid_barrier(bar, gridDim.x, flag);
   }
@@ -782,23 +952,24 @@ __global__ void k_df2d_cols(int64_t n, const TU* __restrict__ x, int64_t ldx, do
 template <class TU>
 __global__ void __launch_bounds__(512) k_df_sketch_vec(const TU* __restrict__ x, const SketchTiles tv,
                                                        double* __restrict__ part) {
-  extern __shared__ float2 sh2[];
+  extern __shared__ __align__(16) uint8_t smraw[];
   const int d = tv.d, L1 = tv.L + 1;
-  float2* acc = sh2;
-  float2* vb = acc + d;
-  int* offs = reinterpret_cast<int*>(vb + 2 * kTileRows);
+  const TileSmem lay = tile_smem_layout(d, tv.L, 0, tv.zeta);
+  float2* acc = reinterpret_cast<float2*>(smraw + lay.acc);
   for (int r = threadIdx.x; r < d; r += blockDim.x) acc[r] = make_float2(0.f, 0.f);
   const int t0 = tv.ctile[blockIdx.x], t1 = tv.ctile[blockIdx.x + 1];
   for (int t = t0; t < t1; ++t) {
     const int buf = (t - t0) & 1;
-    float2* v = vb + buf * kTileRows;
-    int* of = offs + buf * L1;
+    float2* v = reinterpret_cast<float2*>(smraw + lay.vb) + buf * kTileRows;
+    int* of = reinterpret_cast<int*>(smraw + lay.offs) + buf * L1;
+    uint32_t* ms = reinterpret_cast<uint32_t*>(smraw + lay.ms) + buf * d;
+    uint16_t* es = reinterpret_cast<uint16_t*>(smraw + lay.es) + (size_t)buf * kTileRows * tv.zeta;
     const int64_t r0 = tv.row[t];
     const int rows = (int)(tv.row[t + 1] - r0);
+    tile_stage(tv, t, r0, rows, of, ms, es);
     for (int l = threadIdx.x; l < rows; l += blockDim.x) v[l] = ldv(x + r0 + l);
-    tile_offsets(tv, t, of);
     __syncthreads();
-    tile_gather(tv, t, r0, v, of, acc);
+    tile_gather(d, tv.H, v, of, ms, es, acc);
   }
   tile_write_part(acc, d, part);
 }
@@ -927,9 +1098,11 @@ cudaError_t configure_df_kernels() {
   const int big = 200 * 1024;
   cudaError_t e = cudaSuccess;
 #define RKS_SMEM(f) if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
-  RKS_SMEM((k_df_spmv_sketch<float2, float2>)); RKS_SMEM((k_df_spmv_sketch<float, float>));
+  RKS_SMEM((k_df_spmv_sketch<float2, float2, true>)); RKS_SMEM((k_df_spmv_sketch<float, float, true>));
+  RKS_SMEM((k_df_spmv_sketch<float2, float2, false>));
   constexpr int U8 = kDfUpdUnroll, MB = kDfUpdMinBlocks;
-  RKS_SMEM((k_df_update_sketch<float2, U8, MB>)); RKS_SMEM((k_df_update_sketch<float, U8, MB>));
+  RKS_SMEM((k_df_update_sketch<float2, U8, MB, 1>)); RKS_SMEM((k_df_update_sketch<float, U8, MB, 1>));
+  RKS_SMEM((k_df_update_sketch<float2, U8, MB, 0>)); RKS_SMEM((k_df_update_sketch<float2, U8, MB, 2>));
   RKS_SMEM(k_df_sketch_vec<float2>); RKS_SMEM(k_df_sketch_vec<float>);
   RKS_SMEM(k_tiles_count<4>); RKS_SMEM(k_tiles_count<8>); RKS_SMEM(k_tiles_count<16>);
   RKS_SMEM(k_tiles_build<4>); RKS_SMEM(k_tiles_build<8>); RKS_SMEM(k_tiles_build<16>);
@@ -949,25 +1122,55 @@ int df_gemm_smem(int nin, int nout) { return (int)(((size_t)nin * nout + (size_t
 
 void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, const SketchTiles& t, double* part,
                            cudaStream_t st) {
-  const size_t sm = tile_smem_bytes(t.d, t.L, 0);
+  const size_t sm = tile_smem_bytes(t.d, t.L, 0, t.zeta);
   if (A.f32)
-    k_df_spmv_sketch<float, float><<<t.G, 512, sm, st>>>(A.rowptr, A.colind, static_cast<const float*>(A.vals),
-                                                         static_cast<const float*>(x), static_cast<float*>(w), t,
-                                                         part);
+    k_df_spmv_sketch<float, float, true><<<t.G, 512, sm, st>>>(
+        A.rowptr, A.colind, static_cast<const float*>(A.vals), static_cast<const float*>(x), static_cast<float*>(w),
+        t, part);
   else
-    k_df_spmv_sketch<float2, float2><<<t.G, 512, sm, st>>>(A.rowptr, A.colind, static_cast<const float2*>(A.vals),
-                                                           static_cast<const float2*>(x), static_cast<float2*>(w),
-                                                           t, part);
+    k_df_spmv_sketch<float2, float2, true><<<t.G, 512, sm, st>>>(
+        A.rowptr, A.colind, static_cast<const float2*>(A.vals), static_cast<const float2*>(x),
+        static_cast<float2*>(w), t, part);
+}
+
+void launch_df_spmv(const CsrDF& A, const void* x, void* w, const SketchTiles& t, cudaStream_t st) {
+  const size_t sm = tile_smem_bytes(t.d, t.L, 0, t.zeta);
+  k_df_spmv_sketch<float2, float2, false><<<t.G, 512, sm, st>>>(
+      A.rowptr, A.colind, static_cast<const float2*>(A.vals), static_cast<const float2*>(x), static_cast<float2*>(w),
+      t, nullptr);
+}
+
+void launch_df_update_plain(void* U, int64_t ldu, int c, const float2* nrs, const float2* sj, const SketchTiles& t,
+                            double* norm_part, cudaStream_t st) {
+  constexpr int U8 = kDfUpdUnroll, MB = kDfUpdMinBlocks;
+  const size_t sm = tile_smem_bytes(t.d, t.L, c, t.zeta);
+  float2* u = static_cast<float2*>(U);
+  if (norm_part) k_df_update_sketch<float2, U8, MB, 2><<<t.G, 512, sm, st>>>(u, ldu, c, nrs, sj, t, norm_part);
+  else k_df_update_sketch<float2, U8, MB, 0><<<t.G, 512, sm, st>>>(u, ldu, c, nrs, sj, t, nullptr);
+}
+
+void launch_df_dots(const void* U, int64_t ldu, int c, int cv, const SketchTiles& t, double* part, cudaStream_t st) {
+  k_df_dots<float2><<<t.G, 512, 0, st>>>(static_cast<const float2*>(U), ldu, c, cv, t, part);
+}
+
+void launch_ks_coef(int pass, int j, int c, int G, const double* part, const double* colscale, double* rprev,
+                    float2* nrs, float2* sj, cudaStream_t st) {
+  k_ks_coef<<<1, 256, 0, st>>>(pass, j, c, G, part, colscale, rprev, nrs, sj);
+}
+
+void launch_ks_finish(int j, int G, const double* part, double thr, double* colscale,
+                      const double* rprev, double* coef, int ldcoef, int* flag, cudaStream_t st) {
+  k_ks_finish<<<1, 32, 0, st>>>(j, G, part, thr, colscale, rprev, coef, ldcoef, flag);
 }
 
 void launch_df_update_sketch(void* U, int64_t ldu, int c, const float2* nrs, const float2* sj, const SketchTiles& t,
                              double* part, bool f32, cudaStream_t st) {
   constexpr int U8 = kDfUpdUnroll, MB = kDfUpdMinBlocks;
-  const size_t sm = tile_smem_bytes(t.d, t.L, c);
+  const size_t sm = tile_smem_bytes(t.d, t.L, c, t.zeta);
   if (f32)
-    k_df_update_sketch<float, U8, MB><<<t.G, 512, sm, st>>>(static_cast<float*>(U), ldu, c, nrs, sj, t, part);
+    k_df_update_sketch<float, U8, MB, 1><<<t.G, 512, sm, st>>>(static_cast<float*>(U), ldu, c, nrs, sj, t, part);
   else
-    k_df_update_sketch<float2, U8, MB><<<t.G, 512, sm, st>>>(static_cast<float2*>(U), ldu, c, nrs, sj, t, part);
+    k_df_update_sketch<float2, U8, MB, 1><<<t.G, 512, sm, st>>>(static_cast<float2*>(U), ldu, c, nrs, sj, t, part);
 }
 
 int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_raw, double* z_raw, double* S64,
@@ -986,7 +1189,7 @@ int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_r
       return 1;
     (void)cudaGetLastError();   // not available: fall back to the kernels below
   }
-  const int gf = (d + 31) / 32;
+  const int gf = (d + 7) / 8;
   int nl = 0;
   if (finish) { k_df_fold<<<gf, 256, 0, st>>>(part_s, d, G, s_raw); ++nl; }
   if (ls) { k_df_fold<<<gf, 256, 0, st>>>(part_z, d, G, z_raw); ++nl; }
@@ -1025,7 +1228,7 @@ void launch_df2d_cols(int64_t n, const void* x, int64_t ldx, double* y, int64_t 
 }
 
 void launch_df_sketch_vec(const void* x, const SketchTiles& t, double* part, bool f32, cudaStream_t st) {
-  const size_t sm = tile_smem_bytes(t.d, t.L, 0);
+  const size_t sm = tile_smem_bytes(t.d, t.L, 0, t.zeta);
   if (f32) k_df_sketch_vec<float><<<t.G, 512, sm, st>>>(static_cast<const float*>(x), t, part);
   else k_df_sketch_vec<float2><<<t.G, 512, sm, st>>>(static_cast<const float2*>(x), t, part);
 }
@@ -1092,7 +1295,7 @@ void free_sketch_tiles(SketchTiles* t) {
   *t = SketchTiles();
 }
 
-size_t sketch_tile_smem(const SketchTiles& t, int c) { return tile_smem_bytes(t.d, t.L, c); }
+size_t sketch_tile_smem(const SketchTiles& t, int c) { return tile_smem_bytes(t.d, t.L, c, t.zeta); }
 
 template <class TU>
 static void restart_t(int64_t n, TU* U, int64_t ldu, int a0, int nin, const float2* Q, int nout, int c0,

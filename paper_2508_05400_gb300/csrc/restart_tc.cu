@@ -11,7 +11,8 @@
 // One CTA (256 threads) owns tiles of 128 rows; per tile the K dimension
 // (the nin input columns, padded to kKc) streams through two shared-memory
 // stages of 32 columns: all threads load and split a stage (FP32 loads,
-// coalesced along the rows) into the canonical K-major no-swizzle layout,
+// coalesced along the rows, issued one stage ahead into registers) into the
+// canonical K-major no-swizzle layout,
 // thread 0 issues 2 x 6 MMAs of 128 x N x 16 on it and commits them to the
 // stage's mbarrier, which the next load of that stage waits for.  The
 // epilogue reads the 128 x N FP32 accumulator with tcgen05.ld (warps 0-3 and
@@ -119,7 +120,7 @@ __host__ __device__ constexpr int pair_b(int p) { return p == 1 || p == 4 ? 1 : 
 // out[i, o] = sum_l in[i, l] Q'[l, o] for i < n, o < nout; then, when mvsrc
 // is given, mvdst[i] = mvsrc[i].  bimg: the three bf16 splits of Q' (Kp x N,
 // zero padded) in the canonical layout, split j at byte j * Kp * N * 2.
-__global__ void __launch_bounds__(kThreads, 1) k_tc_restart_f32(int64_t n, const float* in, float* out, int64_t ldu,
+__global__ void __launch_bounds__(kThreads, 3) k_tc_restart_f32(int64_t n, const float* in, float* out, int64_t ldu,
                                                                 int nin, int Kp, int N, int nout,
                                                                 const uint4* __restrict__ bimg, const float* mvsrc,
                                                                 float* mvdst, int* flag) {
@@ -155,21 +156,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_restart_f32(int64_t n, const
   bool ok = true;
   const int r = tid & (kM - 1), kh = tid >> 7;   // loader: row, half of the stage's 32 columns
 
-  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+  // the 16 values (one row, half a stage) that this thread loads for stage kc of a tile
+  auto load16 = [&](int64_t tile, int kc, float* v) {
     const int64_t i = tile * kM + r;
+    const int l0 = kc * kKc + kh * 16;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int l = l0 + u;
+      v[u] = (tile < ntiles && i < n && l < nin) ? in[i + (int64_t)l * ldu] : 0.f;
+    }
+  };
+  float v[16], vn[16];
+  load16(blockIdx.x, 0, v);
+  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     for (int kc = 0; kc < nk && ok; ++kc, ++g) {
       const int s = g & 1;
+      // the next stage's loads go out before this stage is split and consumed
+      if (kc + 1 < nk) load16(tile, kc + 1, vn);
+      else load16(tile + gridDim.x, 0, vn);
       if (g >= 2) ok = mbar_wait(smem_u32(mbar + s), (uint32_t)(((g - 2) >> 1) & 1), flag);
       ok = __syncthreads_and(ok);
       if (!ok) break;
-      // load and split 16 columns of one row
-      float v[16];
-      const int l0 = kc * kKc + kh * 16;
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int l = l0 + u;
-        v[u] = (i < n && l < nin) ? in[i + (int64_t)l * ldu] : 0.f;
-      }
       uint8_t* st = sA + s * kStage;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -213,6 +220,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_restart_f32(int64_t n, const
         mma_commit(smem_u32(mbar + s));
         if (kc == nk - 1) mma_commit(smem_u32(mbar + 2));
       }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = vn[u];
     }
     if (!ok) break;
     // epilogue
@@ -304,8 +313,15 @@ void launch_tc_restart_f32(int64_t n, const float* in, float* out, int64_t ldu, 
                            const float* mvsrc, float* mvdst, int* flag, cudaStream_t st) {
   const int Kp = (nin + kKc - 1) / kKc * kKc, N = (nout + 15) / 16 * 16;
   const int64_t ntiles = (n + kM - 1) / kM;
-  const int g = (int)std::min<int64_t>(ntiles, 152 * 2);
-  k_tc_restart_f32<<<g, kThreads, tc_restart_smem(nin, nout), st>>>(n, in, out, ldu, nin, Kp, N, nout,
+  const size_t sm = tc_restart_smem(nin, nout);
+  int per_sm = 1, sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_restart_f32, kThreads, sm) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  per_sm = std::min(per_sm, 512 / kTmemCols);   // tensor memory columns per SM
+  const int g = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
+  k_tc_restart_f32<<<g, kThreads, sm, st>>>(n, in, out, ldu, nin, Kp, N, nout,
                                                                       static_cast<const uint4*>(bimg), mvsrc, mvdst,
                                                                       flag);
 }

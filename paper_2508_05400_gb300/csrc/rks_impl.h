@@ -67,6 +67,15 @@ int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_r
                     float2* S2, double* colscale, double* rprev, double* coef, int ldcoef, double* znorm_prev,
                     float2* nrs, float2* sj, float2* r1, float2* z1, const double* part_z, const double* part_s,
                     int G, int* flag, unsigned* bar, cudaStream_t st);
+// Krylov-Schur baseline with Euclidean CGS2 (no sketch), DF basis.
+void launch_df_spmv(const CsrDF& A, const void* x, void* w, const SketchTiles& t, cudaStream_t st);
+void launch_df_update_plain(void* U, int64_t ldu, int c, const float2* nrs, const float2* sj, const SketchTiles& t,
+                            double* norm_part, cudaStream_t st);
+void launch_df_dots(const void* U, int64_t ldu, int c, int cv, const SketchTiles& t, double* part, cudaStream_t st);
+void launch_ks_coef(int pass, int j, int c, int G, const double* part, const double* colscale, double* rprev,
+                    float2* nrs, float2* sj, cudaStream_t st);
+void launch_ks_finish(int j, int G, const double* part, double thr, double* colscale,
+                      const double* rprev, double* coef, int ldcoef, int* flag, cudaStream_t st);
 int build_sketch_tiles(int64_t n, int d, int zeta, const uint16_t* otab, SketchTiles* out, cudaStream_t st);
 void free_sketch_tiles(SketchTiles* t);
 size_t sketch_tile_smem(const SketchTiles& t, int c);

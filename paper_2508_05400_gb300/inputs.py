@@ -311,3 +311,32 @@ def convdiff3d_problem(N: int = 160, k: int = 50, p: int = 100, d: int = 600,
     nu = lognormal_field((N, N, N), 1.0, field_seed)
     A = convdiff_3d(N, N, N, nu, (10.0, 5.0, 2.0), dtype=np.float32)
     return Problem(f"convdiff3d_{N}", A, k, p, d, 8, "LR", tol, conv="norm1")
+
+
+def uneven_convdiff2d_problem(i: int, seed0: int = 1000, k: int = 8, p: int = 24, d: int = 64,
+                              tol: float = 1e-8) -> Problem:
+    """Problem i of the batch of uneven 2D convection-diffusion operators.
+
+    Seed seed0 + i draws (from SplitMix64 uniforms, in this order) the grid
+    sides a, b ~ U{70..450}, the convection (bx, by) ~ U[0, 30]^2, then the
+    log-normal diffusivity exp(g), g ~ N(0,1) per node; FP32 values, LR.
+    """
+    s = seed0 + i
+    u = uniform01(s, 4)
+    a, b = 70 + int(u[0] * 381), 70 + int(u[1] * 381)
+    bx, by = 30.0 * u[2], 30.0 * u[3]
+    nu = lognormal_field((b, a), 1.0, s + 7919)
+    A = convdiff_2d(a, b, nu, bx, by, dtype=np.float32)
+    return Problem(f"uneven2d_{i}_{a}x{b}", A, k, p, d, 8, "LR", tol, conv="norm1")
+
+
+def grf_convdiff2d_problem(i: int, seed0: int = 20000, N: int = 512, k: int = 16, p: int = 48,
+                           d: int = 192, tol: float = 1e-8) -> Problem:
+    """Member i of the parametric 2D family on an N x N grid: seed seed0 + i
+    draws (bx, by) ~ U[0, 50]^2 and the diffusivity exp(GRF), correlation
+    length 0.1 (held-out members use seed0 = 20000, training ones 10000)."""
+    s = seed0 + i
+    u = uniform01(s, 2)
+    nu = np.exp(gaussian_random_field(N, N, 0.1, s + 7919))
+    A = convdiff_2d(N, N, nu, 50.0 * u[0], 50.0 * u[1])
+    return Problem(f"grf2d_{N}_{s}", A, k, p, d, 8, "LR", tol, conv="norm1")

@@ -32,11 +32,12 @@ class Opts(C.Structure):
     _fields_ = [("zeta", C.c_int), ("maxit", C.c_int), ("lock", C.c_int), ("mem_device", C.c_int),
                 ("stream", C.c_void_p), ("u1", C.c_void_p), ("eta_lock", C.c_double),
                 ("max_restarts", C.c_int), ("profile", C.c_int), ("conv", C.c_int),
-                ("prec", C.c_int), ("mixed_tol", C.c_double), ("verify", C.c_double), ("keep", C.c_int)]
+                ("prec", C.c_int), ("mixed_tol", C.c_double), ("verify", C.c_double), ("keep", C.c_int), ("ortho", C.c_int)]
 
 
 CONV = {"eig": 0, "norm1": 1}
 PREC = {"df": 0, "fp64": 1, "mixed": 2}
+ORTHO = {"sketch": 0, "cgs2": 1}
 
 
 KCLASSES = ("spmv_sketch", "ls", "update_sketch", "finish", "restart", "other")
@@ -159,7 +160,7 @@ class Solver:
     def __init__(self, n, rowptr, colind, vals, k, p, d, which="LM", tol=1e-10, seed=0, *,
                  zeta=8, maxit=1000, lock=True, u1=None, eta_lock=0.0, max_restarts=0,
                  device=False, stream=None, profile=False, conv="eig", verify=0.0, prec="df",
-                 mixed_tol=0.0, keep=0):
+                 mixed_tol=0.0, keep=0, ortho="sketch"):
         L = lib()
         self.n, self.k, self.p, self.d = int(n), int(k), int(p), int(d)
         self.device = bool(device)
@@ -189,6 +190,7 @@ class Solver:
         o.prec = PREC[prec]
         o.mixed_tol = float(mixed_tol)
         o.keep = int(keep)
+        o.ortho = ORTHO[ortho]
         h = _P()
         _check(L.rks_create(C.byref(h), self.n, _ptr(rowptr), _ptr(colind), _ptr(vals), vdt,
                             self.k, self.p, self.d, WHICH[which] if isinstance(which, str) else int(which),

@@ -96,3 +96,31 @@ def test_grf_statistics():
     # neighbouring nodes are strongly correlated at ell = 0.1, h = 1/65
     c = np.corrcoef(g[:, :-1].ravel(), g[:, 1:].ravel())[0, 1]
     assert c > 0.8
+
+
+def test_uneven_batch_problems():
+    # 256 problems: sides in [70, 450], log-uneven sizes, FP32 values, seeded
+    sizes = []
+    for i in (0, 1, 2, 255):
+        P = I.uneven_convdiff2d_problem(i)
+        a, b = (int(x) for x in P.name.split("_")[-1].split("x"))
+        assert 70 <= a <= 450 and 70 <= b <= 450 and P.A.n == a * b
+        assert P.A.vals.dtype == np.float32 and P.A.nnz == 5 * a * b - 2 * (a + b)
+        assert (P.k, P.p, P.d, P.zeta, P.which) == (8, 24, 64, 8, "LR")
+        sizes.append(P.A.n)
+    again = I.uneven_convdiff2d_problem(2)
+    assert np.array_equal(again.A.vals, I.uneven_convdiff2d_problem(2).A.vals)
+    assert len(set(sizes)) == 4
+
+
+def test_grf_family_member():
+    P = I.grf_convdiff2d_problem(0, N=64)
+    assert P.A.n == 64 * 64 and P.A.nnz == 5 * 64 * 64 - 4 * 64
+    A = P.A.to_scipy()
+    # the diffusive part is a weighted graph Laplacian: A + A^T has non-positive
+    # row sums only through the convection and boundary terms (off-diagonals >= 0)
+    off = A - sp.diags(A.diagonal())
+    assert off.min() >= 0
+    assert np.all(A.diagonal() < 0)
+    assert I.grf_convdiff2d_problem(0, N=64).A.vals.tobytes() == P.A.vals.tobytes()
+    assert I.grf_convdiff2d_problem(1, N=64).A.vals.tobytes() != P.A.vals.tobytes()
