@@ -237,6 +237,43 @@ void rks_destroy(rks_ctx* c);
 /* Static message for a status code. */
 const char* rks_strerror(int status);
 
+/* ---- Batched solve of independent problems --------------------------- */
+
+/* Many independent problems (e.g. a batch of uneven operators) solved
+ * concurrently: one context per problem, each on a stream of its own, up to
+ * nthreads problems in flight with their small dense steps on separate host
+ * threads.  The kernels are deterministic, so every problem's results are the
+ * bits of a solve of that problem alone. */
+typedef struct rks_batch rks_batch;
+
+/* One context per problem i < count from its CSR arrays (rowptr[i], colind[i],
+ * vals[i]; host or device pointers per opts.mem_device) and n[i]; every other
+ * argument is shared and means what it means for rks_create.  opts.stream and
+ * opts.u1 must be NULL (each context creates its stream and draws its start
+ * vector from seed + 1).  Contexts are created on up to nthreads host threads.
+ * On failure nothing is kept and the first failing status in problem order is
+ * returned. */
+int rks_create_batched(rks_batch** out, int count, const int64_t* n, const int32_t* const* rowptr,
+                       const int32_t* const* colind, const void* const* vals, int vals_dtype, int k, int p,
+                       int d, int which, double tol, uint64_t seed, const rks_opts* opts, int nthreads);
+
+/* rks_solve of every problem, up to nthreads at a time; infos (count entries,
+ * may be NULL) receives each problem's rks_info.  Returns RKS_OK, RKS_ENOCONV
+ * when some problem did not converge (its results are partial) and no other
+ * error occurred, else the first other failing status in problem order;
+ * rks_batch_status gives each problem's own status. */
+int rks_solve_batched(rks_batch* b, int nthreads, rks_info* infos);
+
+/* Number of problems; the context of problem i (borrowed: valid until
+ * rks_destroy_batched, for rks_get_eigpairs and the other getters; NULL if i
+ * is out of range); the status of its last create or solve. */
+int rks_batch_count(const rks_batch* b);
+rks_ctx* rks_batch_get(rks_batch* b, int i);
+int rks_batch_status(const rks_batch* b, int i);
+
+/* Free every context of the batch.  Safe on NULL. */
+void rks_destroy_batched(rks_batch* b);
+
 /* ---- Sketch primitives (Sec. 5 setup; Def. 1.1) ---------------------- */
 
 /* The (row, sign) pairs of Omega: for column i and slot t < zeta,

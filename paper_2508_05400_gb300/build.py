@@ -18,7 +18,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 CXX = os.environ.get("CXX", "g++")
 
-SOURCES = ["kernels.cu", "kernels_df.cu", "restart_tc.cu", "api.cu", "noalloc.cu", "dense.cpp"]
+SOURCES = ["kernels.cu", "kernels_df.cu", "restart_tc.cu", "api.cu", "batch.cu", "noalloc.cu", "dense.cpp"]
 
 
 def _cmd(src: str) -> list[str]:
@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"build failed: {' '.join(c)}\n{r.stdout}\n{r.stderr}")
     objs = [os.path.join(BUILD, os.path.splitext(s)[0] + ".o") for s in SOURCES]
     tmp = LIB + ".tmp"
-    link = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+    link = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(link)}\n{r.stdout}\n{r.stderr}")

@@ -106,6 +106,19 @@ def lib() -> C.CDLL:
         L.rks_norm1.restype = C.c_double
         L.rks_basis_product_f32.argtypes = [C.c_int64, _P, C.c_int64, C.c_int, _P, C.c_int, _P, _P]
         L.rks_basis_product_f32.restype = C.c_int
+        L.rks_create_batched.argtypes = [C.POINTER(_P), C.c_int, _P, _P, _P, _P, C.c_int, C.c_int, C.c_int,
+                                         C.c_int, C.c_int, C.c_double, C.c_uint64, C.POINTER(Opts), C.c_int]
+        L.rks_create_batched.restype = C.c_int
+        L.rks_solve_batched.argtypes = [_P, C.c_int, _P]
+        L.rks_solve_batched.restype = C.c_int
+        L.rks_batch_count.argtypes = [_P]
+        L.rks_batch_count.restype = C.c_int
+        L.rks_batch_get.argtypes = [_P, C.c_int]
+        L.rks_batch_get.restype = _P
+        L.rks_batch_status.argtypes = [_P, C.c_int]
+        L.rks_batch_status.restype = C.c_int
+        L.rks_destroy_batched.argtypes = [_P]
+        L.rks_destroy_batched.restype = None
         L.rks_destroy.argtypes = [_P]
         L.rks_destroy.restype = None
         L.rks_sketch_pairs.argtypes = [C.c_int64, C.c_int, C.c_int, C.c_uint64, _P, _P, _P]
@@ -276,7 +289,8 @@ class Solver:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().rks_destroy(self._h)
+            if not getattr(self, "_borrowed", False):
+                lib().rks_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -370,3 +384,79 @@ def host_quasi_eig(T: np.ndarray):
     _check(lib().rks_host_quasi_eig(n, Tf.ctypes.data, lre.ctypes.data, lim.ctypes.data,
                                     Yr.ctypes.data, Yi.ctypes.data), "rks_host_quasi_eig")
     return lre + 1j * lim, Yr + 1j * Yi
+
+
+class Batch:
+    """Independent problems solved concurrently (rks_create_batched).
+
+    ``problems``: list of ``inputs.CSR`` (host arrays, one value type); the
+    other arguments are shared and mean what they mean for ``Solver``.
+    ``member(i)`` gives a Solver view of problem i (eigpairs, history, ...),
+    valid while the batch lives.
+    """
+
+    def __init__(self, problems, k, p, d, which="LM", tol=1e-10, seed=0, *, nthreads=16, zeta=8, maxit=1000,
+                 lock=True, eta_lock=0.0, conv="eig", verify=0.0, prec="df", keep=0, ortho="sketch"):
+        L = lib()
+        self.count = len(problems)
+        self._keep = [(_host(A.rowptr, np.int32), _host(A.colind, np.int32), np.ascontiguousarray(A.vals))
+                      for A in problems]
+        vdt = 0 if self._keep[0][2].dtype == np.float64 else 1
+        if any((0 if a[2].dtype == np.float64 else 1) != vdt for a in self._keep):
+            raise ValueError("all problems must share one value type")
+        ns = np.array([A.n for A in problems], dtype=np.int64)
+        ptrs = [np.array([a[j].ctypes.data for a in self._keep], dtype=np.uint64) for j in range(3)]
+        self._arrays = (ns, *ptrs)
+        o = Opts()
+        L.rks_opts_default(C.byref(o))
+        o.zeta, o.maxit, o.lock = int(zeta), int(maxit), int(bool(lock))
+        o.eta_lock, o.conv, o.verify = float(eta_lock), CONV[conv], float(verify)
+        o.prec, o.keep, o.ortho = PREC[prec], int(keep), ORTHO[ortho]
+        self.n = ns
+        self.k, self.p, self.d = int(k), int(p), int(d)
+        h = _P()
+        _check(L.rks_create_batched(C.byref(h), self.count, ns.ctypes.data, ptrs[0].ctypes.data,
+                                    ptrs[1].ctypes.data, ptrs[2].ctypes.data, vdt, self.k, self.p, self.d,
+                                    WHICH[which] if isinstance(which, str) else int(which), float(tol),
+                                    int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(o), int(nthreads)),
+               "rks_create_batched")
+        self._h = h
+
+    def solve(self, nthreads=16, allow_noconv=True):
+        infos = (Info * self.count)()
+        rc = lib().rks_solve_batched(self._h, int(nthreads), C.cast(infos, _P))
+        _check(rc, "rks_solve_batched", ok=(RKS_OK, RKS_ENOCONV) if allow_noconv else (RKS_OK,))
+        out = []
+        for i in range(self.count):
+            d = infos[i].as_dict()
+            d["status"] = STATUS.get(lib().rks_batch_status(self._h, i), None)
+            out.append(d)
+        return out
+
+    def member(self, i) -> "Solver":
+        s = Solver.__new__(Solver)
+        s.n, s.k, s.p, s.d = int(self.n[i]), self.k, self.p, self.d
+        s.device = False
+        s._borrowed = True
+        s._batch = self
+        s._h = lib().rks_batch_get(self._h, int(i))
+        if not s._h:
+            raise IndexError(i)
+        return s
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rks_destroy_batched(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
