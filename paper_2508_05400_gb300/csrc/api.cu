@@ -84,7 +84,8 @@ struct rks_ctx {
   double* part_d = nullptr;  // Euclidean CGS2 baseline: G x (m+1) partial dot products
   unsigned* bar = nullptr;   // grid-barrier state of the cooperative least squares
   float2* lsr1 = nullptr;    // least-squares scratch: first-pass coefficients (m+1)
-  float2* lsz1 = nullptr;    // and the projected sketch (d)
+  float2* M2 = nullptr;      // Gram matrix S^T S of the sketched basis (DF, (m+1) x (m+1))
+  std::vector<float2> M2_h;
   double* tmp64 = nullptr;
   // host state
   double norm1 = 0;
@@ -219,7 +220,7 @@ void expand_df_launches(rks_ctx* c, int c0) {
     s = prof_begin(c, RKS_K_LS);
     const int nls = rks::launch_df_small(j, c->d, c->zscale, j > c0 ? 1 : 0, 1, c->s_raw, c->z_raw, c->S, c->S2,
                                          c->colscale, c->rprev, c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1,
-                                         c->lsz1, c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream);
+                                         c->M2, c->m + 1, c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream);
     prof_end(c, s, RKS_K_LS, nls, 3.0 * P * c->d * col, 6.0 * c->d * col);
     s = prof_begin(c, RKS_K_UPDATE);
     rks::launch_df_update_sketch(c->Ub, c->ldu, col, c->nrs, c->sj, c->tiles, c->part_s, c->f32, c->stream);
@@ -228,7 +229,7 @@ void expand_df_launches(rks_ctx* c, int c0) {
   }
   int s = prof_begin(c, RKS_K_FINISH);
   const int nf = rks::launch_df_small(c->m, c->d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale,
-                                      c->rprev, c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1,
+                                      c->rprev, c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->M2, c->m + 1,
                                       c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream);
   prof_end(c, s, RKS_K_FINISH, nf, 3.0 * P * c->d, 2.0 * c->d);
 }
@@ -499,6 +500,25 @@ int contract(rks_ctx* c) {
   CK(cudaMemcpyAsync(c->colscale, c->cs_h.data(), c->cs_h.size() * sizeof(double), cudaMemcpyHostToDevice,
                      c->stream));
   CK(cudaMemcpyAsync(c->S, c->S_h.data(), c->S_h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (c->M2 && c->opts.ortho != RKS_ORTHO_CGS2) {
+    // Gram matrix of the kept sketches (locked, active and the last vector)
+    // for the least squares of the next expansion
+    const int nc = q + ka + 1, ldm = m + 1;
+    c->M2_h.assign((size_t)ldm * ldm, make_float2(0.f, 0.f));
+    for (int b2 = 0; b2 < nc; ++b2)
+      for (int a2 = 0; a2 <= b2; ++a2) {
+        const double* x = &c->S_h[(size_t)a2 * d];
+        const double* y = &c->S_h[(size_t)b2 * d];
+        double acc = 0.0;
+        for (int i = 0; i < d; ++i) acc += x[i] * y[i];
+        const float h = (float)acc;
+        const float2 v = make_float2(h, (float)(acc - (double)h));
+        c->M2_h[a2 + (size_t)b2 * ldm] = v;
+        c->M2_h[b2 + (size_t)a2 * ldm] = v;
+      }
+    CK(cudaMemcpyAsync(c->M2, c->M2_h.data(), c->M2_h.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                       c->stream));
+  }
   if (c->prec != RKS_PREC_FP64) {
     c->S2_h.resize(c->S_h.size());
     for (size_t t = 0; t < c->S_h.size(); ++t) {
@@ -677,7 +697,7 @@ void free_ctx(rks_ctx* c) {
   cudaFree(c->X); cudaFree(c->AX); cudaFree(c->rsum); cudaFree(c->pcol); cudaFree(c->plam);
   cudaFree(c->vals2); cudaFree(c->U2); cudaFree(c->S2); cudaFree(c->nrs); cudaFree(c->sj); cudaFree(c->Q2);
   cudaFree(c->rprev); cudaFree(c->znorm); cudaFree(c->tmp64); cudaFree(c->valsf); cudaFree(c->Uf);
-  cudaFree(c->otab); cudaFree(c->lsr1); cudaFree(c->lsz1); cudaFree(c->bar); cudaFree(c->qimg);
+  cudaFree(c->otab); cudaFree(c->lsr1); cudaFree(c->M2); cudaFree(c->bar); cudaFree(c->qimg);
   rks::free_sketch_tiles(&c->tiles);
   cudaFree(c->part_z); cudaFree(c->part_s); cudaFree(c->part_d);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
@@ -812,7 +832,7 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
         (rc = dalloc(&c->Q2, (size_t)(m + 1) * (m + 1))) || (rc = dalloc(&c->rprev, m + 1)) ||
         (rc = dalloc(&c->znorm, 1)) || (rc = dalloc(&c->tmp64, n)) ||
         (rc = dalloc(&c->otab, (size_t)n * rks::omega_slots(o.zeta))) || (rc = dalloc(&c->lsr1, m + 1)) ||
-        (rc = dalloc(&c->lsz1, d)) || (rc = dalloc(&c->bar, 2)))
+        (rc = dalloc(&c->M2, (size_t)(m + 1) * (m + 1))) || (rc = dalloc(&c->bar, 2)))
       return fail(rc);
     if (cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), c->stream) != cudaSuccess) return fail(RKS_ECUDA);
     {
@@ -893,7 +913,7 @@ static int run_alg1(rks_ctx* c, const double* start, int limit, double verify, i
       rks::launch_df_sketch_vec(c->Ub, c->tiles, c->part_s, c->f32, c->stream);
       CK(cudaMemsetAsync(c->znorm, 0, sizeof(double), c->stream));
       const int nf = rks::launch_df_small(0, d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale,
-                                          c->rprev, c->coef, m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->lsz1,
+                                          c->rprev, c->coef, m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->M2, c->m + 1,
                                           c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream);
       prof_end(c, ps, RKS_K_OTHER, (src == c->tmp64 && !start ? 3 : 2) + nf, 0.0, 0.0);
     }

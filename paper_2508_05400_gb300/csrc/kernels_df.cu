@@ -639,15 +639,21 @@ __global__ void __launch_bounds__(256) k_df_fold(const double* __restrict__ part
   if (lane == 0) out[r] = v;
 }
 
-// Least squares b = S^+ z of one Arnoldi step, CGS2 in the sketch, in three
-// multi-CTA kernels (8 warps per CTA):
-//   k_df_ls1  finish column j if requested (beta_j = ||s~_j||, S[:, j] in FP64
-//             and DF, colscale[j] = 1/beta_j, coefficient column j-1, flags:
-//             every CTA computes beta_j itself, CTA 0 writes), then
-//             r1 = S^T z (warp per column; column j read from s_raw directly);
-//   k_df_ls2  z1 = z - S r1 (warp per row);
-//   k_df_ls3  r = r1 + S^T z1 (warp per column), rprev = r (FP64),
-//             nrs = -r .* colscale (DF), sj = colscale[j].
+// Least squares b = S^+ z of one Arnoldi step (Alg. 2, Thm 4.3: against the
+// locked and active sketches together), CGS2 in the sketch written through the
+// Gram matrix M = S^T S: r1 = S^T z, r = r1 + S^T (z - S r1) = 2 r1 - M r1
+// (the same quantity; M is the identity up to rounding).  M is kept on the
+// device: the host sets it after every restart, and finishing column j adds
+// its row M[:, j] = S^T s_j.  Phases (8 warps per CTA):
+//   A  finish column j if requested (beta_j = ||s~_j||, S[:, j] in FP64 and
+//      DF, colscale[j] = 1/beta_j, coefficient column j-1, flags: every CTA
+//      computes beta_j itself, CTA 0 writes); then per column (one warp)
+//      r1 = S^T z and, when finishing, the new row of M;
+//   B  per column (one warp) r = 2 r1 - M r1, rprev = r (FP64),
+//      nrs = -r .* colscale (DF), sj = colscale[j].
+// k_df_ls_coop runs the fold of the sketch partials, A and B in one
+// cooperative launch (two grid barriers); k_df_ls1 (A) and k_df_ls_gram (B)
+// are the separate-launch form.
 // z = z_raw * zscale * colscale[j] (z_raw is the sketch of the unscaled w').
 
 __device__ double block_sum_d(double v, double* red) {
@@ -665,12 +671,66 @@ __device__ double block_sum_d(double v, double* red) {
   return red[32];
 }
 
+// Phase A for one column (one warp): r1[col] = S[:, col]^T z (if want_r1)
+// and, when column j is being finished (sjd = its DF values), the Gram entries
+// M[col, j] = M[j, col] = S[:, col]^T s_j.  Column j itself reads sjd.
+__device__ __forceinline__ void ls_phase_a(int col, int j, int d, int finish, int want_r1, const float2* S2,
+                                           const float2* zd, const float2* sjd, float2* r1, float2* M2, int ldm,
+                                           int lane) {
+  const float2* sc = (finish && col == j) ? sjd : S2 + (size_t)col * d;
+  float s = 0.f, t = 0.f, g = 0.f, ge = 0.f;
+#pragma unroll 4
+  for (int r = lane; r < d; r += 32) {
+    const float2 a = sc[r];
+    if (want_r1) {
+      const float2 b = zd[r];
+      df_mac(a.x, a.y, b.x, b.y, s, t);
+    }
+    if (finish) {
+      const float2 b = sjd[r];
+      df_mac(a.x, a.y, b.x, b.y, g, ge);
+    }
+  }
+  if (want_r1) df_warp_sum(s, t);
+  if (finish) df_warp_sum(g, ge);
+  if (lane == 0) {
+    if (want_r1) r1[col] = df_norm(s, t);
+    if (finish) {
+      const float2 m = df_norm(g, ge);
+      M2[col + (size_t)j * ldm] = m;
+      M2[j + (size_t)col * ldm] = m;
+    }
+  }
+}
+
+// Phase B for one column (one warp): r = 2 r1[col] - sum_l M[l, col] r1[l].
+__device__ __forceinline__ void ls_phase_b(int col, int c, const float2* M2, int ldm, const float2* r1,
+                                           const double* colscale, double* rprev, float2* nrs, int lane) {
+  const float2* mc = M2 + (size_t)col * ldm;
+  float s = 0.f, t = 0.f;
+#pragma unroll 4
+  for (int l = lane; l < c; l += 32) {
+    const float2 a = mc[l], b = r1[l];
+    df_mac(a.x, a.y, b.x, b.y, s, t);
+  }
+  df_warp_sum(s, t);
+  if (lane == 0) {
+    const float2 rc = r1[col];
+    float hs = 2.f * rc.x, ht = 2.f * rc.y;   // exact doubling
+    df_add(-s, -t, hs, ht);
+    const double rd = df_to_double(df_norm(hs, ht));
+    rprev[col] = rd;
+    nrs[col] = df_from_double(-rd * colscale[col]);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_df_ls1(
     int j, int d, double zscale, int finish, int ls, double* __restrict__ s_raw, const double* __restrict__ z_raw,
     double* __restrict__ S64, float2* __restrict__ S2, double* __restrict__ colscale,
     const double* __restrict__ rprev, double* __restrict__ coef, int ldcoef, double* __restrict__ znorm_prev,
-    float2* __restrict__ r1, int* flag) {
-  extern __shared__ float2 zd[];   // d
+    float2* __restrict__ r1, float2* __restrict__ M2, int ldm, int* flag) {
+  extern __shared__ float2 zd[];   // d: z; then d: s_j (when finishing)
+  float2* sjd = zd + d;
   __shared__ double red[33];
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   double inv = 0.0;
@@ -682,6 +742,7 @@ __global__ void __launch_bounds__(256) k_df_ls1(
     const bool finite = isfinite(beta);
     const bool brk = finite && !(beta > 1e-14 * znorm_prev[0]);
     inv = (finite && !brk) ? 1.0 / beta : 0.0;
+    for (int r = tid; r < d; r += nt) sjd[r] = df_from_double(s_raw[r] * zscale * inv);
     if (blockIdx.x == 0) {
       for (int r = tid; r < d; r += nt) {
         double v = s_raw[r] * zscale * inv;
@@ -700,34 +761,35 @@ __global__ void __launch_bounds__(256) k_df_ls1(
       }
     }
   }
-  if (!ls) return;
-  const double scj = finish ? inv : colscale[j];
-  double zz = 0.0;
-  for (int r = tid; r < d; r += nt) {
-    double v = z_raw[r] * zscale * scj;
-    zz = fma(v, v, zz);
-    zd[r] = df_from_double(v);
+  if (!ls && !finish) return;
+  if (ls) {
+    const double scj = finish ? inv : colscale[j];
+    double zz = 0.0;
+    for (int r = tid; r < d; r += nt) {
+      double v = z_raw[r] * zscale * scj;
+      zz = fma(v, v, zz);
+      zd[r] = df_from_double(v);
+    }
+    zz = block_sum_d(zz, red);
+    if (blockIdx.x == 0 && tid == 0) znorm_prev[0] = sqrt(zz);
   }
-  zz = block_sum_d(zz, red);            // also orders the zd writes before their use
-  if (blockIdx.x == 0 && tid == 0) znorm_prev[0] = sqrt(zz);
+  __syncthreads();
   const int c = j + 1;
+  for (int col = blockIdx.x * nw + warp; col < c; col += gridDim.x * nw)
+    ls_phase_a(col, j, d, finish, ls, S2, zd, sjd, r1, M2, ldm, lane);
+}
+
+// Phase B as its own launch (warp per column); CTA 0 also sets sj.
+__global__ void __launch_bounds__(256) k_df_ls_gram(int j, const float2* __restrict__ M2, int ldm,
+                                                    const float2* __restrict__ r1,
+                                                    const double* __restrict__ colscale,
+                                                    double* __restrict__ rprev, float2* __restrict__ nrs,
+                                                    float2* __restrict__ sj) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int c = j + 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sj[0] = df_from_double(colscale[j]);
   const int col = blockIdx.x * nw + warp;
-  if (col >= c) return;
-  float s = 0.f, t = 0.f;
-  if (finish && col == j) {             // the column finished above, straight from the sums
-    for (int r = lane; r < d; r += 32) {
-      float2 a = df_from_double(s_raw[r] * zscale * inv), b = zd[r];
-      df_mac(a.x, a.y, b.x, b.y, s, t);
-    }
-  } else {
-    const float2* sc = S2 + (size_t)col * d;
-    for (int r = lane; r < d; r += 32) {
-      float2 a = sc[r], b = zd[r];
-      df_mac(a.x, a.y, b.x, b.y, s, t);
-    }
-  }
-  df_warp_sum(s, t);
-  if (lane == 0) r1[col] = df_norm(s, t);
+  if (col < c) ls_phase_b(col, c, M2, ldm, r1, colscale, rprev, nrs, lane);
 }
 
 // Grid-wide barrier of the cooperative least-squares kernel.  bar[0] counts
@@ -759,38 +821,20 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, in
   __syncthreads();
 }
 
-// sum_r S2[r, col] * v[r] over r = lane, lane + 32, ... < d (DF), with the
-// loads of four rows issued before their products (L2 latency overlap).
-__device__ __forceinline__ void df_col_dot(const float2* __restrict__ sc, const float2* v, int d, int lane,
-                                           float& s, float& t) {
-  int r = lane;
-  for (; r + 96 < d; r += 128) {
-    const float2 a0 = sc[r], a1 = sc[r + 32], a2 = sc[r + 64], a3 = sc[r + 96];
-    const float2 b0 = v[r], b1 = v[r + 32], b2 = v[r + 64], b3 = v[r + 96];
-    df_mac(a0.x, a0.y, b0.x, b0.y, s, t);
-    df_mac(a1.x, a1.y, b1.x, b1.y, s, t);
-    df_mac(a2.x, a2.y, b2.x, b2.y, s, t);
-    df_mac(a3.x, a3.y, b3.x, b3.y, s, t);
-  }
-  for (; r < d; r += 32) {
-    const float2 a = sc[r], b = v[r];
-    df_mac(a.x, a.y, b.x, b.y, s, t);
-  }
-}
-
-// The three least-squares phases of k_df_ls1/2/3 in one cooperative launch.
+// Fold of the sketch partials, phase A and phase B in one cooperative launch.
 __global__ void __launch_bounds__(256) k_df_ls_coop(
     int j, int d, double zscale, int finish, double* __restrict__ s_raw, double* __restrict__ z_raw,
     double* __restrict__ S64, float2* __restrict__ S2, double* __restrict__ colscale, double* __restrict__ rprev,
     double* __restrict__ coef, int ldcoef, double* __restrict__ znorm_prev, float2* __restrict__ nrs,
-    float2* __restrict__ sj, float2* __restrict__ r1, float2* __restrict__ z1, const double* __restrict__ part_z,
-    const double* __restrict__ part_s, int G, unsigned* bar, int* flag) {
-  extern __shared__ float2 zd[];   // d
+    float2* __restrict__ sj, float2* __restrict__ r1, float2* __restrict__ M2, int ldm,
+    const double* __restrict__ part_z, const double* __restrict__ part_s, int G, unsigned* bar, int* flag) {
+  extern __shared__ float2 zd[];   // d: z; then d: s_j (when finishing)
+  float2* sjd = zd + d;
   __shared__ double red[33];
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   const int gw = blockIdx.x * nw + warp, tw = gridDim.x * nw;   // global warp index, warps in grid
   const int c = j + 1;
-  // phase 0: z' and s~_j from the sketch kernels' per-CTA partial sums
+  // z' and s~_j from the sketch kernels' per-CTA partial sums
   {
     const int nb = finish ? 2 * d : d;
     for (int r = gw; r < nb; r += tw) {
@@ -812,6 +856,7 @@ __global__ void __launch_bounds__(256) k_df_ls_coop(
     const bool finite = isfinite(beta);
     const bool brk = finite && !(beta > 1e-14 * znorm_prev[0]);
     inv = (finite && !brk) ? 1.0 / beta : 0.0;
+    for (int r = tid; r < d; r += nt) sjd[r] = df_from_double(s_raw[r] * zscale * inv);
     if (blockIdx.x == 0) {
       for (int r = tid; r < d; r += nt) {
         double v = s_raw[r] * zscale * inv;
@@ -837,97 +882,13 @@ __global__ void __launch_bounds__(256) k_df_ls_coop(
     zz = fma(v, v, zz);
     zd[r] = df_from_double(v);
   }
-  zz = block_sum_d(zz, red);
-  // phase 1: r1 = S^T z (column j straight from the sums when just finished)
-  for (int col = gw; col < c; col += tw) {
-    float s = 0.f, t = 0.f;
-    if (finish && col == j) {
-      for (int r = lane; r < d; r += 32) {
-        float2 a = df_from_double(s_raw[r] * zscale * inv), b = zd[r];
-        df_mac(a.x, a.y, b.x, b.y, s, t);
-      }
-    } else {
-      df_col_dot(S2 + (size_t)col * d, zd, d, lane, s, t);
-    }
-    df_warp_sum(s, t);
-    if (lane == 0) r1[col] = df_norm(s, t);
-  }
+  zz = block_sum_d(zz, red);            // also orders the zd and sjd writes before their use
+  // phase A
+  for (int col = gw; col < c; col += tw) ls_phase_a(col, j, d, finish, 1, S2, zd, sjd, r1, M2, ldm, lane);
   grid_barrier(bar, gridDim.x, flag);
-  // phase 2: z1 = z - S r1 (S[:, j] was written by CTA 0 before the barrier)
-  for (int r = gw; r < d; r += tw) {
-    float s = 0.f, t = 0.f;
-    for (int col = lane; col < c; col += 32) {
-      float2 a = S2[r + (size_t)col * d], b = r1[col];
-      df_mac(a.x, a.y, b.x, b.y, s, t);
-    }
-    df_warp_sum(s, t);
-    if (lane == 0) {
-      float s2 = zd[r].x, t2 = zd[r].y;
-      df_add(-s, -t, s2, t2);
-      z1[r] = df_norm(s2, t2);
-    }
-  }
-  grid_barrier(bar, gridDim.x, flag);
-  // phase 3: r = r1 + S^T z1
+  // phase B
   if (blockIdx.x == 0 && tid == 0) { sj[0] = df_from_double(scj); znorm_prev[0] = sqrt(zz); }
-  for (int col = gw; col < c; col += tw) {
-    float s = 0.f, t = 0.f;
-    df_col_dot(S2 + (size_t)col * d, z1, d, lane, s, t);
-    df_warp_sum(s, t);
-    if (lane == 0) {
-      df_add(r1[col].x, r1[col].y, s, t);
-      const double rd = df_to_double(df_norm(s, t));
-      rprev[col] = rd;
-      nrs[col] = df_from_double(-rd * colscale[col]);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(256) k_df_ls2(int j, int d, double zscale, double* __restrict__ s_raw,
-                                                const double* __restrict__ z_raw, const float2* __restrict__ S2,
-                                                const double* __restrict__ colscale, const float2* __restrict__ r1,
-                                                float2* __restrict__ z1) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  const int c = j + 1;
-  const int r = blockIdx.x * nw + warp;
-  if (r >= d) return;
-  float s = 0.f, t = 0.f;
-  for (int col = lane; col < c; col += 32) {
-    float2 a = S2[r + (size_t)col * d], b = r1[col];
-    df_mac(a.x, a.y, b.x, b.y, s, t);
-  }
-  df_warp_sum(s, t);
-  if (lane == 0) {
-    float2 zr = df_from_double(z_raw[r] * zscale * colscale[j]);
-    float s2 = zr.x, t2 = zr.y;
-    df_add(-s, -t, s2, t2);
-    z1[r] = df_norm(s2, t2);
-  }
-}
-
-__global__ void __launch_bounds__(256) k_df_ls3(int j, int d, double* __restrict__ z_raw,
-                                                const float2* __restrict__ S2, const double* __restrict__ colscale,
-                                                const float2* __restrict__ r1, const float2* __restrict__ z1,
-                                                double* __restrict__ rprev, float2* __restrict__ nrs,
-                                                float2* __restrict__ sj) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  const int c = j + 1;
-  if (blockIdx.x == 0 && tid == 0) sj[0] = df_from_double(colscale[j]);
-  const int col = blockIdx.x * nw + warp;
-  if (col >= c) return;
-  float s = 0.f, t = 0.f;
-  const float2* sc = S2 + (size_t)col * d;
-  for (int r = lane; r < d; r += 32) {
-    float2 a = sc[r], b = z1[r];
-    df_mac(a.x, a.y, b.x, b.y, s, t);
-  }
-  df_warp_sum(s, t);
-  if (lane == 0) {
-    df_add(r1[col].x, r1[col].y, s, t);
-    const double rd = df_to_double(df_norm(s, t));
-    rprev[col] = rd;
-    nrs[col] = df_from_double(-rd * colscale[col]);
-  }
+  for (int col = gw; col < c; col += tw) ls_phase_b(col, c, M2, ldm, r1, colscale, rprev, nrs, lane);
 }
 
 // y = x (FP64) in the storage type
@@ -1117,7 +1078,7 @@ cudaError_t configure_df_kernels() {
   return e;
 }
 
-int df_small_smem(int d, int c) { return (int)((size_t)d * sizeof(float2)); }
+int df_small_smem(int d, int c) { return (int)((size_t)2 * d * sizeof(float2)); }
 int df_gemm_smem(int nin, int nout) { return (int)(((size_t)nin * nout + (size_t)128 * nout) * sizeof(float2)); }
 
 void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, const SketchTiles& t, double* part,
@@ -1175,16 +1136,16 @@ void launch_df_update_sketch(void* U, int64_t ldu, int c, const float2* nrs, con
 
 int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_raw, double* z_raw, double* S64,
                     float2* S2, double* colscale, double* rprev, double* coef, int ldcoef, double* znorm_prev,
-                    float2* nrs, float2* sj, float2* r1, float2* z1, const double* part_z, const double* part_s,
-                    int G, int* flag, unsigned* bar, cudaStream_t st) {
-  const size_t sm = (size_t)d * sizeof(float2);
+                    float2* nrs, float2* sj, float2* r1, float2* M2, int ldm, const double* part_z,
+                    const double* part_s, int G, int* flag, unsigned* bar, cudaStream_t st) {
+  const size_t sm = (size_t)2 * d * sizeof(float2);
   const int c = j + 1;
   if (ls && bar) {
-    // one cooperative launch: partial-sum fold, then warps over columns / rows, three grid barriers
+    // one cooperative launch: partial-sum fold, phases A and B, two grid barriers
     int g = (std::max(c, d) + 7) / 8;
     g = std::min(g, 48);
     void* args[] = {&j, &d, &zscale, &finish, &s_raw, &z_raw, &S64, &S2, &colscale, &rprev, &coef, &ldcoef,
-                    &znorm_prev, &nrs, &sj, &r1, &z1, &part_z, &part_s, &G, &bar, &flag};
+                    &znorm_prev, &nrs, &sj, &r1, &M2, &ldm, &part_z, &part_s, &G, &bar, &flag};
     if (cudaLaunchCooperativeKernel((const void*)k_df_ls_coop, dim3(g), dim3(256), args, sm, st) == cudaSuccess)
       return 1;
     (void)cudaGetLastError();   // not available: fall back to the kernels below
@@ -1195,11 +1156,10 @@ int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_r
   if (ls) { k_df_fold<<<gf, 256, 0, st>>>(part_z, d, G, z_raw); ++nl; }
   const int g1 = ls ? (c + 7) / 8 : 1;
   k_df_ls1<<<g1, 256, sm, st>>>(j, d, zscale, finish, ls, s_raw, z_raw, S64, S2, colscale, rprev, coef, ldcoef,
-                                znorm_prev, r1, flag);
+                                znorm_prev, r1, M2, ldm, flag);
   if (!ls) return nl + 1;
-  k_df_ls2<<<(d + 7) / 8, 256, 0, st>>>(j, d, zscale, s_raw, z_raw, S2, colscale, r1, z1);
-  k_df_ls3<<<(c + 7) / 8, 256, 0, st>>>(j, d, z_raw, S2, colscale, r1, z1, rprev, nrs, sj);
-  return nl + 3;
+  k_df_ls_gram<<<(c + 7) / 8, 256, 0, st>>>(j, M2, ldm, r1, colscale, rprev, nrs, sj);
+  return nl + 2;
 }
 
 void launch_omega_table(int64_t n, int d, int zeta, uint64_t seed, uint16_t* tab, int* flag, cudaStream_t st) {

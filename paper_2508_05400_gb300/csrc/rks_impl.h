@@ -65,8 +65,8 @@ void launch_df_update_sketch(void* U, int64_t ldu, int c, const float2* nrs, con
                              double* part, bool f32, cudaStream_t st);
 int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_raw, double* z_raw, double* S64,
                     float2* S2, double* colscale, double* rprev, double* coef, int ldcoef, double* znorm_prev,
-                    float2* nrs, float2* sj, float2* r1, float2* z1, const double* part_z, const double* part_s,
-                    int G, int* flag, unsigned* bar, cudaStream_t st);
+                    float2* nrs, float2* sj, float2* r1, float2* M2, int ldm, const double* part_z,
+                    const double* part_s, int G, int* flag, unsigned* bar, cudaStream_t st);
 // Krylov-Schur baseline with Euclidean CGS2 (no sketch), DF basis.
 void launch_df_spmv(const CsrDF& A, const void* x, void* w, const SketchTiles& t, cudaStream_t st);
 void launch_df_update_plain(void* U, int64_t ldu, int c, const float2* nrs, const float2* sj, const SketchTiles& t,
