@@ -108,6 +108,15 @@ typedef struct {
                           (KS-CGS2, Sec. 5): Euclidean classical Gram-Schmidt
                           with reorthogonalisation, same storage and kernels,
                           no sketch; RKS_PREC_DF only. */
+  int tc_restart;      /* 1 (default): the restart product U_k = U Q' (Eq. 3.5)
+                          runs on the tensor cores where its sizes allow
+                          (at most 64 output columns, 256 input columns for
+                          the FP32 basis and 192 for the double-float basis,
+                          and the digit image of Q' in shared memory):
+                          split-BF16 products for the FP32 basis, exact 7-bit
+                          digit products (FP64-class) for the double-float
+                          basis;
+                          0: the SIMT kernels. */
 } rks_opts;
 
 enum { RKS_ORTHO_SKETCH = 0, RKS_ORTHO_CGS2 = 1 };
@@ -328,6 +337,22 @@ int rks_sketch_apply_noalloc(int64_t n, int d, int zeta, uint64_t seed, const do
  * RKS_ECUDA, or RKS_ETIMEOUT if a bounded device wait gave up. */
 int rks_basis_product_f32(int64_t n, const float* U, int64_t ldu, int nin, const double* Q, int nout, float* out,
                           void* stream);
+
+/* out = U Q as the double-float restart forms it on the tensor cores: every
+ * row of U is a 47-bit fixed-point integer at the row's own power-of-two
+ * scale, every column of Q one at the column's scale; both are cut into seven
+ * digits (a signed top digit and six of 7 bits), whose 34 leading digit-pair
+ * products are accumulated in FP32 (exactly where it matters) and recombined
+ * in double-float, then FP64.  Accuracy: about 2^-46 of the row's largest
+ * |U[i, l]| times sum_l |Q[l, o]|.  U, out: device FP64 arrays with leading
+ * dimension ldu >= n (U is read as ldu x nin values and rounded to
+ * double-float pairs); Q: host FP64, nin x nout column-major,
+ * 1 <= nin <= 192, 1 <= nout <= 64, and the digit
+ * image of Q must fit in shared memory (else RKS_EINVAL).  Allocates its
+ * scratch, runs on `stream` and synchronises it.  Returns RKS_OK,
+ * RKS_EINVAL, RKS_ENOMEM, RKS_ECUDA or RKS_ETIMEOUT. */
+int rks_basis_product_df(int64_t n, const double* U, int64_t ldu, int nin, const double* Q, int nout, double* out,
+                         void* stream);
 
 /* ---- Host-side small dense FP64 steps (Algorithm 1 contraction) ------ */
 

@@ -68,6 +68,12 @@ struct rks_ctx {
   float* Uf = nullptr;
   void* qimg = nullptr;     // mixed precision: bf16 split image of Q' for the tensor-core restart
   std::vector<uint16_t> qimg_h;
+  void* qimg_df = nullptr;  // double-float basis: digit image of Q', column exponents, row exponents
+  int* fexp_d = nullptr;
+  int* pexp_d = nullptr;     // power-of-two part of the input columns' scales
+  int* rexp_d = nullptr;     // per-row exponents (n)
+  std::vector<int> fexp_h, pexp_h;
+  std::vector<double> Qr_h;
   void* Ub = nullptr;      // basis in use: U2 or Uf
   bool f32 = false;        // basis in use is FP32
   int phase_restarts = 0;
@@ -475,6 +481,30 @@ int contract(rks_ctx* c) {
     rks::launch_tc_restart_f32(c->n, U0, U0, c->ldu, ma, ka, c->qimg, c->Uf + (size_t)m * c->ldu,
                                c->Uf + (size_t)(q + ka) * c->ldu, c->flag, c->stream);
     CK(cudaStreamSynchronize(c->stream));   // the image is a host buffer reused next restart
+  } else if (c->prec != RKS_PREC_FP64 && !c->f32 && c->qimg_df && rks::tc_restart_df_supported(ma, ka)) {
+    // double-float basis: exact digit products on the tensor cores.  The power
+    // of two of each column scale goes onto U (an exact exponent offset in the
+    // digit split), the rest (in [1, 2)) stays in Q'.
+    c->pexp_h.assign(ma, 0);
+    c->Qr_h.assign(Qp.size(), 0.0);
+    for (int l = 0; l < ma; ++l) {
+      int E = 0;
+      if (c->cs_h[q + l] != 0.0) std::frexp(c->cs_h[q + l], &E);
+      c->pexp_h[l] = c->cs_h[q + l] != 0.0 ? E - 1 : 0;
+      for (int j = 0; j < ka; ++j)
+        c->Qr_h[l + (size_t)j * ma] = std::ldexp(Qp[l + (size_t)j * ma], -c->pexp_h[l]);
+    }
+    rks::tc_restart_df_bimage(ma, ka, c->Qr_h.data(), c->qimg_h, c->fexp_h);
+    CK(cudaMemcpyAsync(c->pexp_d, c->pexp_h.data(), c->pexp_h.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(c->qimg_df, c->qimg_h.data(), c->qimg_h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(c->fexp_d, c->fexp_h.data(), c->fexp_h.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       c->stream));
+    float2* U0 = c->U2 + (size_t)q * c->ldu;
+    rks::launch_tc_restart_df(c->n, U0, U0, c->ldu, ma, ka, c->qimg_df, c->fexp_d, c->pexp_d, c->rexp_d,
+                              c->U2 + (size_t)m * c->ldu, c->U2 + (size_t)(q + ka) * c->ldu, c->flag, c->stream);
+    CK(cudaStreamSynchronize(c->stream));   // the image is a host buffer reused next restart
   } else if (c->prec != RKS_PREC_FP64) {
     std::vector<float2> Q2h(Qp.size());
     for (size_t t = 0; t < Qp.size(); ++t) {
@@ -698,6 +728,7 @@ void free_ctx(rks_ctx* c) {
   cudaFree(c->vals2); cudaFree(c->U2); cudaFree(c->S2); cudaFree(c->nrs); cudaFree(c->sj); cudaFree(c->Q2);
   cudaFree(c->rprev); cudaFree(c->znorm); cudaFree(c->tmp64); cudaFree(c->valsf); cudaFree(c->Uf);
   cudaFree(c->otab); cudaFree(c->lsr1); cudaFree(c->M2); cudaFree(c->bar); cudaFree(c->qimg);
+  cudaFree(c->qimg_df); cudaFree(c->fexp_d); cudaFree(c->pexp_d); cudaFree(c->rexp_d);
   rks::free_sketch_tiles(&c->tiles);
   cudaFree(c->part_z); cudaFree(c->part_s); cudaFree(c->part_d);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
@@ -717,6 +748,7 @@ void rks_opts_default(rks_opts* o) {
   o->zeta = 8;
   o->maxit = 1000;
   o->lock = 1;
+  o->tc_restart = 1;
 }
 
 const char* rks_strerror(int s) {
@@ -823,7 +855,7 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
   if (c->prec != RKS_PREC_FP64) {
     if (c->prec == RKS_PREC_MIXED) {
       if ((rc = dalloc(&c->Uf, (size_t)c->ldu * (m + 1))) || (rc = dalloc(&c->valsf, c->nnz))) return fail(rc);
-      if (cudaMalloc(&c->qimg, rks::kTcImageBytes) != cudaSuccess) return fail(RKS_ENOMEM);
+      if (o.tc_restart && cudaMalloc(&c->qimg, rks::kTcImageBytes) != cudaSuccess) return fail(RKS_ENOMEM);
       if (rks::configure_tc_kernels() != cudaSuccess) return fail(RKS_ECUDA);
       rks::launch_d2df(c->nnz, c->vals, c->valsf, true, c->stream);
     }
@@ -834,6 +866,14 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
         (rc = dalloc(&c->otab, (size_t)n * rks::omega_slots(o.zeta))) || (rc = dalloc(&c->lsr1, m + 1)) ||
         (rc = dalloc(&c->M2, (size_t)(m + 1) * (m + 1))) || (rc = dalloc(&c->bar, 2)))
       return fail(rc);
+    if (o.tc_restart && rks::tc_restart_df_supported(m, k + 1)) {
+      if (rks::configure_tc_kernels() != cudaSuccess) return fail(RKS_ECUDA);
+      if (cudaMalloc(&c->qimg_df, rks::kTcDfImageBytes) != cudaSuccess ||
+          cudaMalloc(&c->fexp_d, 64 * sizeof(int)) != cudaSuccess ||
+          cudaMalloc(&c->pexp_d, 256 * sizeof(int)) != cudaSuccess ||
+          cudaMalloc(&c->rexp_d, (size_t)n * sizeof(int)) != cudaSuccess)
+        return fail(RKS_ENOMEM);
+    }
     if (cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), c->stream) != cudaSuccess) return fail(RKS_ECUDA);
     {
       int bad = 0;
@@ -1219,6 +1259,49 @@ int rks_basis_product_f32(int64_t n, const float* U, int64_t ldu, int nin, const
   cudaFree(dimg);
   cudaFree(flag);
   if (e != cudaSuccess) return RKS_ECUDA;
+  return (f & rks::RKS_FLAG_TIMEOUT) ? RKS_ETIMEOUT : RKS_OK;
+}
+
+int rks_basis_product_df(int64_t n, const double* U, int64_t ldu, int nin, const double* Q, int nout, double* out,
+                         void* stream) {
+  if (n <= 0 || ldu < n || !U || !Q || !out || !rks::tc_restart_df_supported(nin, nout)) return RKS_EINVAL;
+  if (rks::configure_tc_kernels() != cudaSuccess) return RKS_ECUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<uint16_t> img;
+  std::vector<int> fexp;
+  rks::tc_restart_df_bimage(nin, nout, Q, img, fexp);
+  float2 *Ud = nullptr, *Od = nullptr;
+  void* dimg = nullptr;
+  int *dfexp = nullptr, *flag = nullptr, *pexp = nullptr, *rexp = nullptr;
+  int rc = RKS_OK;
+  if (cudaMalloc(&Ud, (size_t)ldu * nin * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&Od, (size_t)ldu * nout * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&dimg, img.size() * sizeof(uint16_t)) != cudaSuccess ||
+      cudaMalloc(&dfexp, fexp.size() * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&pexp, (size_t)nin * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&rexp, (size_t)n * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&flag, sizeof(int)) != cudaSuccess)
+    rc = RKS_ENOMEM;
+  int f = 0;
+  if (rc == RKS_OK) {
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pexp, 0, (size_t)nin * sizeof(int), st);   // unscaled columns
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dimg, img.data(), img.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dfexp, fexp.data(), fexp.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+      rks::launch_d2df((int64_t)ldu * nin, U, Ud, false, st);   // the basis as double-float pairs
+      rks::launch_tc_restart_df(n, Ud, Od, ldu, nin, nout, dimg, dfexp, pexp, rexp, nullptr, nullptr, flag, st);
+      rks::launch_df2d_cols(n, Od, ldu, out, ldu, nout, false, st);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&f, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = RKS_ECUDA;
+  }
+  cudaFree(Ud); cudaFree(Od); cudaFree(dimg); cudaFree(dfexp); cudaFree(pexp); cudaFree(rexp); cudaFree(flag);
+  if (rc != RKS_OK) return rc;
   return (f & rks::RKS_FLAG_TIMEOUT) ? RKS_ETIMEOUT : RKS_OK;
 }
 

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -112,6 +113,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 __device__ __forceinline__ uint32_t bf16_bits(__nv_bfloat16 h) { return (uint32_t)__bfloat16_as_ushort(h); }
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
 
 // The six split products (i, j) with i + j <= 4, splits numbered 1..3 (0..2 here).
 __host__ __device__ constexpr int pair_a(int p) { return p == 2 || p == 4 ? 1 : (p == 5 ? 2 : 0); }
@@ -263,6 +270,235 @@ __global__ void __launch_bounds__(kThreads, 3) k_tc_restart_f32(int64_t n, const
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
+// ---------------------------------------------------------------------------
+// Double-float basis: exact split products (Ozaki-type) on the tensor cores
+// ---------------------------------------------------------------------------
+//
+// A DF value v = hi + lo of row i is written, relative to the row scale 2^e_i
+// (|v| < 2^(e_i - 1) for every input column), as the 47-bit fixed-point
+// integer V = round(v 2^(48 - e_i)) = sum_s d_s 2^(42 - 7s), a signed top
+// digit d_0 (|d_0| <= 32) and six 7-bit digits (0..127), all exact in bf16;
+// Q' likewise per column with scale 2^f_o (digits c_t, built on the host).
+// Then
+//   sum_l v_l q_l = 2^(e_i + f_o - 12) sum_g 2^(-7g) G_g,
+//   G_g = sum_{s + t = g} sum_l d_s(i, l) c_t(l, o),
+// with integer G_g.  The 34 digit pairs with s + t <= 7 go to 8 accumulators
+// (8 x N tensor-memory columns; the dropped pairs are below 5 * 2^-51 of
+// the scale).  For K <= 192 every group of weight above 2^-35 stays below
+// 2^24, so the bf16 MMAs with FP32 accumulation in tensor memory sum it
+// exactly; a lighter group may round by a unit or two, far below 2^-48.
+// The epilogue combines the groups in DF.  K streams through two shared-
+// memory stages of one K-step (16 input columns x 7 digit slices); Q'
+// (7 slices, all K) stays resident.
+
+constexpr int kDfDigits = 7;
+constexpr int kDfThreads = 512;
+constexpr int kDfGroups = 8;
+constexpr int kDfStepSplit = kM * 16 * 2;                 // one digit slice of one K-step
+constexpr int kDfStage = kDfDigits * kDfStepSplit;        // 28 KB
+
+// Largest biased exponent of the hi parts of row i over the nin columns, each
+// column taken times 2^pexp[l] (its power-of-two scale; zero entries skipped).
+__global__ void k_row_exp(int64_t n, const float2* __restrict__ in, int64_t ldu, int nin,
+                          const int* __restrict__ pexp, int* __restrict__ rexp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int em = -100000;
+#pragma unroll 8
+    for (int l = 0; l < nin; ++l) {
+      const int E = (int)((__float_as_uint(in[i + (int64_t)l * ldu].x) >> 23) & 0xFFu);
+      if (E != 0) em = max(em, E + pexp[l]);
+    }
+    rexp[i] = em;
+  }
+}
+
+// round(x 2^(48 - e)) with e = emax - 125, from the bits of x (|result| <= 2^47 + 1);
+// a column scale 2^p is applied by passing emax - p
+__device__ __forceinline__ int64_t fixed48(float x, int emax) {
+  const uint32_t b = __float_as_uint(x);
+  int E = (int)((b >> 23) & 0xFFu);
+  uint32_t m = b & 0x7FFFFFu;
+  if (E == 0) E = 1; else m |= 0x800000u;
+  const int sh = E - emax + 23;                  // E - 102 - e
+  int64_t V;
+  if (sh >= 0) V = (int64_t)m << min(sh, 40);   // sh <= 23 except for an all-zero row (m = 0)
+  else if (sh > -26) V = (int64_t)((m + (1u << (-sh - 1))) >> -sh);
+  else V = 0;
+  return (b >> 31) ? -V : V;
+}
+
+// out[i, o] = sum_l in[i, l] 2^pexp[l] Q'[l, o] (DF) for i < n, o < nout;
+// then, when mvsrc is given, mvdst[i] = mvsrc[i].  bimg: the digit slices of
+// Q' (Kp x N,
+// canonical layout, slice t at byte t * Kp * N * 2); fexp[o] = f_o; rexp[i]
+// from k_row_exp.  Every read of a tile's rows precedes its writes (in place).
+__global__ void __launch_bounds__(kDfThreads, 1) k_tc_restart_df(int64_t n, const float2* in, float2* out,
+                                                                 int64_t ldu, int nin, int Kp, int N, int nout,
+                                                                 const uint4* __restrict__ bimg,
+                                                                 const int* __restrict__ fexp,
+                                                                 const int* __restrict__ pexp,
+                                                                 const int* __restrict__ rexp,
+                                                                 const float2* mvsrc, float2* mvdst, int tcols,
+                                                                 int* flag) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int bbytes = kDfDigits * Kp * N * 2;
+  uint8_t* sB = smem;
+  uint8_t* sA = smem + ((bbytes + 1023) & ~1023);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sA + 2 * kDfStage);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
+  int* sp = reinterpret_cast<int*>(mbar + 4);            // column power-of-two scales (Kp)
+
+  for (int t = tid; t < bbytes / 16; t += kDfThreads) reinterpret_cast<uint4*>(sB)[t] = bimg[t];
+  for (int t = tid; t < Kp; t += kDfThreads) sp[t] = t < nin ? pexp[t] : 0;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < 3; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + s)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = idesc_bf16(N);
+  const uint32_t sA32 = smem_u32(sA), sB32 = smem_u32(sB);
+  const int nk = Kp / 16;
+  const int64_t ntiles = (n + kM - 1) / kM;
+  int g = 0;                 // stages filled so far (all tiles)
+  uint32_t dpar = 0;         // parity of the accumulator-done barrier
+  bool ok = true;
+  const int r = tid & (kM - 1), kq = tid >> 7;   // loader: row, quarter of the K-step's 16 columns
+
+  auto load4 = [&](int64_t tile, int kc, float2* v) {
+    const int64_t i = tile * kM + r;
+    const int l0 = kc * 16 + kq * 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int l = l0 + u;
+      v[u] = (tile < ntiles && i < n && l < nin) ? in[i + (int64_t)l * ldu] : make_float2(0.f, 0.f);
+    }
+  };
+  float2 v[4], vn[4];
+  load4(blockIdx.x, 0, v);
+  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int64_t irow = tile * kM + r;
+    const int emax = irow < n ? rexp[irow] : 0;
+    for (int kc = 0; kc < nk && ok; ++kc, ++g) {
+      const int s = g & 1;
+      if (kc + 1 < nk) load4(tile, kc + 1, vn);
+      else load4(tile + gridDim.x, 0, vn);
+      if (g >= 2) ok = mbar_wait(smem_u32(mbar + s), (uint32_t)(((g - 2) >> 1) & 1), flag);
+      ok = __syncthreads_and(ok);
+      if (!ok) break;
+      // digits of 4 values of one row
+      uint32_t w[kDfDigits][2];
+#pragma unroll
+      for (int u = 0; u < 4; u += 2) {
+        uint32_t pk[kDfDigits][2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const float2 x = v[u + e];
+          const int ep = emax - sp[kc * 16 + kq * 4 + u + e];
+          const int64_t V = fixed48(x.x, ep) + fixed48(x.y, ep);
+          pk[0][e] = bf16_bits(__float2bfloat16_rn((float)(int)(V >> 42)));
+#pragma unroll
+          for (int q = 1; q < kDfDigits; ++q)
+            pk[q][e] = bf16_bits(__float2bfloat16_rn((float)(int)((V >> (42 - 7 * q)) & 127)));
+        }
+#pragma unroll
+        for (int q = 0; q < kDfDigits; ++q) w[q][u >> 1] = pk[q][0] | (pk[q][1] << 16);
+      }
+      uint8_t* st = sA + s * kDfStage;
+      const uint32_t off = canon_off(r, kq * 4, kM);
+#pragma unroll
+      for (int q = 0; q < kDfDigits; ++q)
+        *reinterpret_cast<uint2*>(st + q * kDfStepSplit + off) = make_uint2(w[q][0], w[q][1]);
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        fence_after();
+        const bool first = kc == 0;
+#pragma unroll
+        for (int gg = 0; gg < kDfGroups; ++gg)
+#pragma unroll
+          for (int sa = gg < kDfDigits ? 0 : gg - kDfDigits + 1; sa <= gg && sa < kDfDigits; ++sa) {
+            const int tb = gg - sa;
+            const int sa0 = gg < kDfDigits ? 0 : gg - kDfDigits + 1;   // first pair of the group
+            const uint64_t a = sdesc(sA32 + s * kDfStage + sa * kDfStepSplit);
+            const uint64_t b = sdesc(sB32 + tb * Kp * N * 2 + kc * N * 32);
+            mma_bf16(tmem + (uint32_t)(gg * N), a, b, idesc, (first && sa == sa0) ? 0u : 1u);
+          }
+        mma_commit(smem_u32(mbar + s));
+        if (kc == nk - 1) mma_commit(smem_u32(mbar + 2));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = vn[u];
+    }
+    if (!ok) break;
+    // epilogue: sum_g 2^(-7g) G_g in DF, times 2^(e_i + f_o - 12)
+    ok = mbar_wait(smem_u32(mbar + 2), dpar, flag);
+    dpar ^= 1u;
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    fence_after();
+    const int q4 = warp & 3;
+    const int64_t ir = tile * kM + q4 * 32 + lane;
+    const int er = ir < n ? rexp[ir] - 125 : 0;
+    float2 mv = make_float2(0.f, 0.f);
+    if (mvsrc && warp < 4 && ir < n) mv = mvsrc[ir];
+    for (int cg = warp >> 2; cg < N / 16; cg += kDfThreads / 128) {
+      float hs[16], ls[16];
+      {
+        float gv[16];
+        tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((kDfGroups - 1) * N + cg * 16), gv);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) { hs[jj] = gv[jj]; ls[jj] = 0.f; }
+      }
+      for (int gg = kDfGroups - 2; gg >= 0; --gg) {
+        float gv[16];
+        tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(gg * N + cg * 16), gv);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const float sh = hs[jj] * 0.0078125f, sl = ls[jj] * 0.0078125f;   // exact scaling by 2^-7
+          float s2, e2;
+          two_sum_f(gv[jj], sh, s2, e2);
+          hs[jj] = s2;
+          ls[jj] = e2 + sl;
+        }
+      }
+      if (ir < n) {
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int o = cg * 16 + jj;
+          if (o < nout) {
+            const int sc = er + fexp[o] - 12;
+            float h, l;
+            two_sum_f(hs[jj], ls[jj], h, l);
+            out[ir + (int64_t)o * ldu] = make_float2(ldexpf(h, sc), ldexpf(l, sc));
+          }
+        }
+      }
+    }
+    if (mvsrc && warp < 4 && ir < n) mvdst[ir] = mv;
+    fence_before();
+    __syncthreads();
+  }
+  if (!ok && tid == 0) {
+    const int c0 = (g + 1) / 2, c1 = g / 2;
+    if (c0 > 0) (void)mbar_wait(smem_u32(mbar + 0), (uint32_t)((c0 - 1) & 1), flag);
+    if (c1 > 0) (void)mbar_wait(smem_u32(mbar + 1), (uint32_t)((c1 - 1) & 1), flag);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+}
+
 uint16_t host_bf16(float x) {   // round to nearest even (finite inputs)
   uint32_t u;
   std::memcpy(&u, &x, 4);
@@ -301,10 +537,70 @@ void tc_restart_bimage(int nin, int nout, const double* Q, std::vector<uint16_t>
     }
 }
 
+// ---- double-float basis ----
+
+static int df_kp(int nin) { return (nin + 15) / 16 * 16; }
+static int df_n(int nout) { return (nout + 15) / 16 * 16; }
+
+size_t tc_restart_df_smem(int nin, int nout) {
+  const size_t b = (size_t)kDfDigits * df_kp(nin) * df_n(nout) * 2;
+  return ((b + 1023) & ~(size_t)1023) + 2 * kDfStage + 64 + (size_t)df_kp(nin) * sizeof(int);
+}
+
+bool tc_restart_df_supported(int nin, int nout) {
+  return nin >= 1 && nin <= 192 && nout >= 1 && nout <= 64 && tc_restart_df_smem(nin, nout) <= kTcDfSmemMax;
+}
+
+// Digit image of Q (nin x nout, column-major FP64) and the column exponents:
+// |Q[:, o]| < 2^(f_o - 1), W = round(Q 2^(48 - f_o)) = sum_t c_t 2^(42 - 7t).
+void tc_restart_df_bimage(int nin, int nout, const double* Q, std::vector<uint16_t>& img, std::vector<int>& fexp) {
+  const int Kp = df_kp(nin), N = df_n(nout);
+  img.assign((size_t)kDfDigits * Kp * N, 0);
+  fexp.assign(N, 0);
+  for (int o = 0; o < nout; ++o) {
+    double mx = 0.0;
+    for (int l = 0; l < nin; ++l) mx = std::max(mx, std::fabs(Q[l + (size_t)o * nin]));
+    int E2 = 0;
+    if (mx > 0.0) std::frexp(mx, &E2);          // mx < 2^E2
+    const int f = E2 + 1;
+    fexp[o] = f;
+    for (int l = 0; l < nin; ++l) {
+      const int64_t W = std::llround(std::ldexp(Q[l + (size_t)o * nin], 48 - f));
+      for (int t = 0; t < kDfDigits; ++t) {
+        const int dgt = t == 0 ? (int)(W >> 42) : (int)((W >> (42 - 7 * t)) & 127);
+        img[(size_t)t * Kp * N + canon_off(o, l, N) / 2] = host_bf16((float)dgt);
+      }
+    }
+  }
+}
+
+void launch_tc_restart_df(int64_t n, const float2* in, float2* out, int64_t ldu, int nin, int nout, const void* bimg,
+                          const int* fexp, const int* pexp, int* rexp, const float2* mvsrc, float2* mvdst, int* flag,
+                          cudaStream_t st) {
+  const int Kp = df_kp(nin), N = df_n(nout);
+  int tcols = 32;
+  while (tcols < kDfGroups * N) tcols *= 2;
+  const int64_t ntiles = (n + kM - 1) / kM;
+  const size_t sm = tc_restart_df_smem(nin, nout);
+  int sms = 152, dev = 0, per_sm = 1;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_restart_df, kDfThreads, sm) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  per_sm = std::min(per_sm, 512 / tcols);          // tensor memory columns per SM
+  const int ge = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+  k_row_exp<<<std::max(ge, 1), 256, 0, st>>>(n, in, ldu, nin, pexp, rexp);
+  const int g = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
+  k_tc_restart_df<<<g, kDfThreads, sm, st>>>(n, in, out, ldu, nin, Kp, N, nout, static_cast<const uint4*>(bimg),
+                                             fexp, pexp, rexp, mvsrc, mvdst, tcols, flag);
+}
+
 cudaError_t configure_tc_kernels() {
   static bool done = false;
   if (done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_tc_restart_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_restart_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcDfSmemMax);
   if (e == cudaSuccess) done = true;
   return e;
 }

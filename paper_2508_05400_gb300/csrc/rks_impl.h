@@ -98,6 +98,17 @@ cudaError_t configure_tc_kernels();
 void launch_tc_restart_f32(int64_t n, const float* in, float* out, int64_t ldu, int nin, int nout, const void* bimg,
                            const float* mvsrc, float* mvdst, int* flag, cudaStream_t st);
 constexpr size_t kTcImageBytes = (size_t)3 * 256 * 64 * 2;   // largest split image of Q'
+// Double-float basis: exact digit products on the tensor cores (restart_tc.cu).
+constexpr size_t kTcDfSmemMax = 227 * 1024;
+constexpr size_t kTcDfImageBytes = (size_t)8 * 256 * 64 * 2;  // largest digit image of Q'
+bool tc_restart_df_supported(int nin, int nout);
+size_t tc_restart_df_smem(int nin, int nout);
+void tc_restart_df_bimage(int nin, int nout, const double* Q, std::vector<uint16_t>& img, std::vector<int>& fexp);
+// out = in diag(2^pexp) Q (pexp: nin device ints, the input columns'
+// power-of-two scales; rexp: n device ints of scratch).
+void launch_tc_restart_df(int64_t n, const float2* in, float2* out, int64_t ldu, int nin, int nout, const void* bimg,
+                          const int* fexp, const int* pexp, int* rexp, const float2* mvsrc, float2* mvdst, int* flag,
+                          cudaStream_t st);
 
 void launch_sketch_pairs(int64_t n, int d, int zeta, uint64_t seed, int32_t* rows, int8_t* signs, int* flag,
                          cudaStream_t st);

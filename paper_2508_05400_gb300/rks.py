@@ -32,7 +32,8 @@ class Opts(C.Structure):
     _fields_ = [("zeta", C.c_int), ("maxit", C.c_int), ("lock", C.c_int), ("mem_device", C.c_int),
                 ("stream", C.c_void_p), ("u1", C.c_void_p), ("eta_lock", C.c_double),
                 ("max_restarts", C.c_int), ("profile", C.c_int), ("conv", C.c_int),
-                ("prec", C.c_int), ("mixed_tol", C.c_double), ("verify", C.c_double), ("keep", C.c_int), ("ortho", C.c_int)]
+                ("prec", C.c_int), ("mixed_tol", C.c_double), ("verify", C.c_double), ("keep", C.c_int), ("ortho", C.c_int),
+                ("tc_restart", C.c_int)]
 
 
 CONV = {"eig": 0, "norm1": 1}
@@ -119,6 +120,8 @@ def lib() -> C.CDLL:
         L.rks_batch_status.restype = C.c_int
         L.rks_destroy_batched.argtypes = [_P]
         L.rks_destroy_batched.restype = None
+        L.rks_basis_product_df.argtypes = [C.c_int64, _P, C.c_int64, C.c_int, _P, C.c_int, _P, _P]
+        L.rks_basis_product_df.restype = C.c_int
         L.rks_destroy.argtypes = [_P]
         L.rks_destroy.restype = None
         L.rks_sketch_pairs.argtypes = [C.c_int64, C.c_int, C.c_int, C.c_uint64, _P, _P, _P]
@@ -173,7 +176,7 @@ class Solver:
     def __init__(self, n, rowptr, colind, vals, k, p, d, which="LM", tol=1e-10, seed=0, *,
                  zeta=8, maxit=1000, lock=True, u1=None, eta_lock=0.0, max_restarts=0,
                  device=False, stream=None, profile=False, conv="eig", verify=0.0, prec="df",
-                 mixed_tol=0.0, keep=0, ortho="sketch"):
+                 mixed_tol=0.0, keep=0, ortho="sketch", tc_restart=True):
         L = lib()
         self.n, self.k, self.p, self.d = int(n), int(k), int(p), int(d)
         self.device = bool(device)
@@ -204,6 +207,7 @@ class Solver:
         o.mixed_tol = float(mixed_tol)
         o.keep = int(keep)
         o.ortho = ORTHO[ortho]
+        o.tc_restart = int(bool(tc_restart))
         h = _P()
         _check(L.rks_create(C.byref(h), self.n, _ptr(rowptr), _ptr(colind), _ptr(vals), vdt,
                             self.k, self.p, self.d, WHICH[which] if isinstance(which, str) else int(which),
@@ -365,6 +369,18 @@ def basis_product_f32(U, ldu: int, n: int, nin: int, Q: np.ndarray, out) -> None
     stream = torch.cuda.current_stream().cuda_stream
     _check(lib().rks_basis_product_f32(n, U.data_ptr(), ldu, nin, Qf.ctypes.data, Qf.shape[1], out.data_ptr(),
                                        stream), "rks_basis_product_f32")
+
+
+def basis_product_df(U, ldu: int, n: int, nin: int, Q: np.ndarray, out) -> None:
+    """out = U Q with the double-float restart's exact digit products on the
+    tensor cores.  U, out: CUDA float64 tensors holding column-major n x nin /
+    n x nout data with leading dimension ldu; Q: nin x nout FP64 host array.
+    """
+    import torch
+    Qf = np.asfortranarray(Q, dtype=np.float64)
+    stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().rks_basis_product_df(n, U.data_ptr(), ldu, nin, Qf.ctypes.data, Qf.shape[1], out.data_ptr(),
+                                      stream), "rks_basis_product_df")
 
 
 def host_ordered_schur(B: np.ndarray, which: str, nsort: int):
