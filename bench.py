@@ -33,11 +33,15 @@ WORKLOAD = ("convdiff2d_1000: 2D upwind convection-diffusion 1000x1000 (n=1e6), 
             "FP64 CSR; k=20 LR, p=60, d=320, zeta=8, tol=1e-8, locking")
 # Products with A that rKS needs on this workload (measured by this solver on a
 # GB300; the method's count, used to scale the bounded CPU samples).
-NMATVEC_WORKLOAD = None
+NMATVEC_WORKLOAD = 7535
 # DRAM traffic of the dominant kernel from one ncu capture, as a ratio to the
 # algorithmic bytes of the captured launch (applied to the mean launch), valid
 # only for the kernel source it was measured on (sha256 prefix of kernels_df.cu).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # two launches of k_df_update_sketch at c = 64, 65 in the third restart (profiles/df_kernels_convdiff1000.md):
+    # DRAM 541.9 / 547.2 MB against 528 / 536 MB of algorithmic bytes (the bin lists of Omega are the rest)
+    "update_sketch": {"kernels_sha": "e137dfb28ad01379", "ratio": 1.025},
+}
 
 
 def _kernel_hash() -> str:
