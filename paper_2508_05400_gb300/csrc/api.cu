@@ -420,15 +420,23 @@ int contract(rks_ctx* c) {
       for (int i = 0; i < d; ++i) dst[i] += w * src[i];
     }
   // whitening when the sketch lost orthonormality (Sec. 3.3, Eqs. 3.7-3.8)
+  // (the Gram matrix of the kept sketches, reused below for the device copy
+  // of S^T S unless whitening changes them)
+  const bool sketched = c->opts.ortho != RKS_ORTHO_CGS2;
+  std::vector<double> Gsa((size_t)ka * ka, 0.0);
   double gerr = 0.0;
-  for (int a = 0; a < ka; ++a)
-    for (int bb = 0; bb < ka; ++bb) {
-      double acc = 0.0;
-      for (int i = 0; i < d; ++i) acc += Sa[i + (size_t)a * d] * Sa[i + (size_t)bb * d];
-      acc -= (a == bb) ? 1.0 : 0.0;
-      gerr += acc * acc;
-    }
-  if (c->opts.ortho != RKS_ORTHO_CGS2 && ka > 0 && std::sqrt(gerr) > 1e-10) {
+  if (sketched)
+    for (int bb = 0; bb < ka; ++bb)
+      for (int a = 0; a <= bb; ++a) {
+        double acc = 0.0;
+        for (int i = 0; i < d; ++i) acc += Sa[i + (size_t)a * d] * Sa[i + (size_t)bb * d];
+        Gsa[a + (size_t)bb * ka] = Gsa[bb + (size_t)a * ka] = acc;
+        const double e = acc - ((a == bb) ? 1.0 : 0.0);
+        gerr += (a == bb ? 1.0 : 2.0) * e * e;
+      }
+  bool whitened = false;
+  if (sketched && ka > 0 && std::sqrt(gerr) > 1e-10) {
+    whitened = true;
     std::vector<double> R((size_t)ka * ka), Rinv((size_t)ka * ka, 0.0);
     house_qr(d, ka, Sa.data(), R.data());
     for (int j = 0; j < ka; ++j) {          // Rinv by back substitution
@@ -537,10 +545,14 @@ int contract(rks_ctx* c) {
     c->M2_h.assign((size_t)ldm * ldm, make_float2(0.f, 0.f));
     for (int b2 = 0; b2 < nc; ++b2)
       for (int a2 = 0; a2 <= b2; ++a2) {
-        const double* x = &c->S_h[(size_t)a2 * d];
-        const double* y = &c->S_h[(size_t)b2 * d];
         double acc = 0.0;
-        for (int i = 0; i < d; ++i) acc += x[i] * y[i];
+        if (!whitened && a2 >= q && b2 < q + ka) {
+          acc = Gsa[(a2 - q) + (size_t)(b2 - q) * ka];   // both active: computed above
+        } else {
+          const double* x = &c->S_h[(size_t)a2 * d];
+          const double* y = &c->S_h[(size_t)b2 * d];
+          for (int i = 0; i < d; ++i) acc += x[i] * y[i];
+        }
         const float h = (float)acc;
         const float2 v = make_float2(h, (float)(acc - (double)h));
         c->M2_h[a2 + (size_t)b2 * ldm] = v;

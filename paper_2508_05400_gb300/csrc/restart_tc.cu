@@ -312,6 +312,12 @@ __global__ void k_row_exp(int64_t n, const float2* __restrict__ in, int64_t ldu,
   }
 }
 
+// bf16 bits of a small integer 0 <= d < 256 on the full-rate pipes: the
+// float 2^23 + d minus 2^23 is d exactly, and its low 16 bits are zero.
+__device__ __forceinline__ uint32_t small_bf16(int d) {
+  return __float_as_uint(__int_as_float(0x4B000000 | d) - 8388608.0f) >> 16;
+}
+
 // round(x 2^(48 - e)) with e = emax - 125, from the bits of x (|result| <= 2^47 + 1);
 // a column scale 2^p is applied by passing emax - p
 __device__ __forceinline__ int64_t fixed48(float x, int emax) {
@@ -405,10 +411,17 @@ __global__ void __launch_bounds__(kDfThreads, 1) k_tc_restart_df(int64_t n, cons
           const float2 x = v[u + e];
           const int ep = emax - sp[kc * 16 + kq * 4 + u + e];
           const int64_t V = fixed48(x.x, ep) + fixed48(x.y, ep);
-          pk[0][e] = bf16_bits(__float2bfloat16_rn((float)(int)(V >> 42)));
-#pragma unroll
-          for (int q = 1; q < kDfDigits; ++q)
-            pk[q][e] = bf16_bits(__float2bfloat16_rn((float)(int)((V >> (42 - 7 * q)) & 127)));
+          // digits from two 32-bit halves: bits 21..47 (signed) and 0..20
+          const int vh = (int)(V >> 21);
+          const int vl = (int)(V & 0x1FFFFF);
+          const int d0 = vh >> 21;                                   // -32 .. 32
+          pk[0][e] = __float_as_uint(__int_as_float(0x4B000000 | (d0 + 128)) - 8388736.0f) >> 16;
+          pk[1][e] = small_bf16((vh >> 14) & 127);
+          pk[2][e] = small_bf16((vh >> 7) & 127);
+          pk[3][e] = small_bf16(vh & 127);
+          pk[4][e] = small_bf16(vl >> 14);
+          pk[5][e] = small_bf16((vl >> 7) & 127);
+          pk[6][e] = small_bf16(vl & 127);
         }
 #pragma unroll
         for (int q = 0; q < kDfDigits; ++q) w[q][u >> 1] = pk[q][0] | (pk[q][1] << 16);
