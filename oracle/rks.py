@@ -28,6 +28,9 @@ The code follows the paper's algorithms step by step, in its notation:
   estimates |b^T y| / |lambda| (Sec. 4.1, Eq. 4.8), then extension.
 * Locking (Sec. 4.4, Eq. 4.21): a leading block of active Schur vectors whose
   entries of b are below the threshold is moved to U_q and its b set to zero.
+* Aggressive deflation (option; Sec. 4.3, after Thm 4.3): before locking,
+  the active Schur form is reordered so that every block whose Ritz
+  estimate |b^T y| is below the locking threshold leads.
 * Whitening (Sec. 3.3, Eqs. 3.7-3.8): S_k = QR (Householder),
   U <- U R^{-1}, T <- R T R^{-1}, b^T <- b^T R^{-1}.
 
@@ -288,6 +291,66 @@ def contract(st: RKSState, k: int, which: str, keep: int = 0):
     return Ta, bk, Qk
 
 
+def block_eigvec(T: np.ndarray, start: int, size: int):
+    """Eigenvalue and unit eigenvector y of a quasi-triangular T for its
+    diagonal block at ``start`` (the Im >= 0 member of a pair).
+
+    T is block upper triangular, so y is zero below the block, the block's own
+    eigenvector inside it, and above it the solution of
+    (T_11 - lambda I) x = -T_12 v (the first start + size entries are the only
+    nonzero ones: the observation of the remark after Eq. 4.21).
+    """
+    lam = block_eigenvalue(T, start, size)
+    e = start + size
+    if size == 1:
+        v = np.ones(1, dtype=complex)
+    else:
+        w, V = np.linalg.eig(T[start:e, start:e])
+        v = V[:, np.argmax(w.imag)]
+    y = np.zeros(T.shape[0], dtype=complex)
+    y[start:e] = v
+    if start:
+        y[:start] = np.linalg.solve(T[:start, :start] - lam * np.eye(start), -(T[:start, start:e] @ v))
+    return lam, y / np.linalg.norm(y)
+
+
+def aggressive_reorder(st: RKSState, eta_lock: float, norm_a: float | None = None) -> int:
+    """Aggressive deflation (Sec. 4.3, after Thm 4.3): reorder the active part
+    so that every converged Schur block comes first, ready to be locked.
+
+    The factorization can be reordered by any orthogonal similarity that keeps
+    T_a quasi-triangular; moving a block to the front makes its eigenvector
+    the leading Schur vector, whose entry of b is then b^T y (unit y).  A
+    block counts as converged when |b^T y| is below the locking threshold of
+    ``lock`` (the same scale).  Converged blocks move to the front in their
+    current order and the others follow in theirs (LAPACK dtrsen); U_a, S_a,
+    b and T_qa take the same rotation.  Returns the number of converged
+    columns; nothing moves when they already lead or a swap is refused.
+    """
+    ja = st.ja
+    if ja == 0:
+        return 0
+    Ta, b = st.Ba[:ja, :], st.Ba[ja, :]
+    scale = np.finfo(float).eps * np.linalg.norm(Ta)
+    select = np.zeros(ja, dtype=np.int32)
+    for s, z in schur_blocks(Ta):
+        lam, y = block_eigvec(Ta, s, z)
+        thr = eta_lock * (norm_a if norm_a is not None else max(abs(lam), scale))
+        if abs(b @ y) <= thr:
+            select[s:s + z] = 1
+    nsel = int(select.sum())
+    if nsel == 0 or np.all(select[:nsel] == 1):
+        return nsel
+    T2, Z, _, _, _, _, _, info = dtrsen(select, Ta, np.eye(ja), job="N")
+    if info != 0:
+        return 0
+    st.Ba = np.vstack([T2, b @ Z])
+    st.Ua = np.asfortranarray(np.hstack([st.Ua[:, :ja] @ Z, st.Ua[:, ja:]]))
+    st.Sa = np.asfortranarray(np.hstack([st.Sa[:, :ja] @ Z, st.Sa[:, ja:]]))
+    st.Tqa = st.Tqa @ Z
+    return nsel
+
+
 def lock(st: RKSState, k: int, eta_lock: float, norm_a: float | None = None) -> int:
     """Sec. 4.4 locking: move the leading active blocks with small |b| to U_q.
 
@@ -359,6 +422,7 @@ class RKSResult:
     nlocked: int
     converged: bool
     history: list = field(default_factory=list)
+    locked: list = field(default_factory=list)   # q after each restart
 
 
 def n_wanted(lam: np.ndarray, k: int) -> int:
@@ -387,14 +451,16 @@ def rks(A, k: int, p: int, d: int, u1: np.ndarray, *, zeta: int = 8, seed: int =
         which: str = "LM", tol: float = 1e-10, lock_vectors: bool = True,
         eta_lock: float | None = None, maxit: int = 1000, Omega=None,
         whiten_tol: float = 1e-10, max_restarts: int | None = None,
-        conv: str = "eig", keep: int = 0) -> RKSResult:
+        conv: str = "eig", keep: int = 0, aggressive: bool = False) -> RKSResult:
     """Algorithm 1 (rKS) with the deflation of Sec. 4.
 
     ``max_restarts`` (if given) stops after that many contractions whatever the
     estimates say (the paper's fixed-iteration runs, Sec. 5).  ``conv`` picks
     the convergence quantity: "eig" (|b^T y|/|lambda|, Eq. 4.8) or "norm1"
     (|b^T y|/||A||_1, see ``ritz``), and the matching locking threshold.
-    ``keep`` > 0 selects the thick restart of ``contract``.  Convergence and
+    ``keep`` > 0 selects the thick restart of ``contract``; ``aggressive``
+    moves converged Schur blocks to the front before locking
+    (``aggressive_reorder``).  Convergence and
     the returned pairs concern the n_wanted best Ritz pairs of the full T.
     """
     A = sp.csr_matrix(A, dtype=np.float64)
@@ -407,6 +473,7 @@ def rks(A, k: int, p: int, d: int, u1: np.ndarray, *, zeta: int = 8, seed: int =
     st = start(A, Omega, np.asarray(u1, dtype=np.float64))
     extend(st, m)                                # Alg. 1, first line
     history = []
+    locked = []
     converged = False
     restarts = 0
     limit = maxit if max_restarts is None else min(maxit, max_restarts)
@@ -419,7 +486,10 @@ def rks(A, k: int, p: int, d: int, u1: np.ndarray, *, zeta: int = 8, seed: int =
             if np.linalg.norm(G - np.eye(ja)) > whiten_tol:
                 whiten(st)
         if lock_vectors:
+            if aggressive:
+                aggressive_reorder(st, eta_lock, norm_a)
             lock(st, k, eta_lock, norm_a)
+        locked.append(st.q)
         T, b, _ = full_T(st)
         lam, Y, est = ritz(T, b, which, norm_a)  # Alg. 1, Ritz pairs + Eq. 4.8
         est = est[:n_wanted(lam, k)]
@@ -439,4 +509,4 @@ def rks(A, k: int, p: int, d: int, u1: np.ndarray, *, zeta: int = 8, seed: int =
     return RKSResult(eigvals=lam, X=X, resid=res, est=est, lam_rq=rq, T=T, U=U, b=b,
                      u=st.Ua[:, st.ja].copy(), S=np.hstack([st.Sq, st.Sa[:, :st.ja]]),
                      s=st.Sa[:, st.ja].copy(), restarts=restarts, nmatvec=st.nmatvec,
-                     nlocked=st.q, converged=converged, history=history)
+                     nlocked=st.q, converged=converged, history=history, locked=locked)

@@ -382,3 +382,151 @@ def test_planted_missing_coupling_breaks_eigenvalues(monkeypatch):
                 tol=1e-13, maxit=80)
     assert res.nlocked > 1
     assert res.resid.max() > 1e-8
+
+
+def test_block_eigvec_against_library_eig():
+    # The eigenvector of a quasi-triangular T for its i-th diagonal block is
+    # zero below that block (remark after Eq. 4.21) and is, up to a phase, the
+    # eigenvector LAPACK returns for the same eigenvalue.
+    import scipy.linalg as sla
+    rng = np.random.default_rng(3)
+    T, _ = sla.schur(rng.standard_normal((14, 14)), output="real")
+    lam_all, V = np.linalg.eig(T)
+    nb2 = 0
+    for s, z in R.schur_blocks(T):
+        nb2 += z == 2
+        lam, y = R.block_eigvec(T, s, z)
+        assert np.linalg.norm(T @ y - lam * y) < 1e-12 * np.linalg.norm(T)
+        assert np.all(y[s + z:] == 0) and abs(np.linalg.norm(y) - 1) < 1e-14
+        v = V[:, np.argmin(np.abs(lam_all - lam))]
+        assert abs(abs(np.vdot(v, y)) - 1) < 1e-10
+    assert nb2 >= 2                       # the case covers complex pairs
+
+
+def _exterior_pair_matrix(n=300, seed=5, isolated=None):
+    """A normal matrix whose eigenvalue 1.0 sits just outside a disk of
+    eigenvalues (slow to converge) and whose pair 0.9 +- 5i is isolated
+    (fast): under LR the pair is wanted after 1.0 but converges first.
+    ``isolated`` adds one more real eigenvalue far to the right (converges,
+    and locks, first)."""
+    rng = np.random.default_rng(seed)
+    lead = ([isolated] if isolated is not None else []) + [1.0]
+    h = len(lead) + 2
+    nb = (n - h) // 2
+    r = np.sqrt(rng.uniform(0, 1, nb)); th = rng.uniform(0, np.pi, nb)
+    Blk = np.zeros((n, n))
+    for i, v in enumerate(lead):
+        Blk[i, i] = v
+    Blk[h - 2:h, h - 2:h] = [[0.9, 5.0], [-5.0, 0.9]]
+    for t in range(nb):
+        a, b = -0.05 + r[t] * np.cos(th[t]), r[t] * np.sin(th[t])
+        i = h + 2 * t
+        Blk[i:i + 2, i:i + 2] = [[a, b], [-b, a]]
+    if n - h - 2 * nb:
+        Blk[n - 1, n - 1] = -0.5
+    Qx, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return Qx @ Blk @ Qx.T
+
+
+@pytest.mark.parametrize("isolated", [None, 3.0])
+def test_aggressive_reorder_moves_converged_block(isolated):
+    # Sec. 4.3 (after Thm 4.3): reordering the factorization to test another
+    # leading vector.  The reorder is an orthogonal similarity: the
+    # decomposition A U = U T + u b^T (locked part and coupling T_qa
+    # included) still holds, the spectrum of T_a is unchanged, the converged
+    # pair now leads, and its estimate |b^T y| is the same number before and
+    # after (b' = Z^T b, y' = Z^T y).
+    A = sp.csr_matrix(_exterior_pair_matrix(isolated=isolated))
+    n = A.shape[0]
+    k = 3 if isolated is None else 4
+    st = R.start(A, omega_matrix(n, 48, 8, 0), I.start_vector(n, 1))
+    R.extend(st, 15)
+    moved = False
+    for _ in range(8):
+        R.contract(st, k, "LR")
+        if isolated is not None and st.q == 0:
+            R.lock(st, k, 1e-12)          # the isolated eigenvalue locks first
+            R.extend(st, 15 - st.q)
+            continue
+        ja = st.ja
+        Ta, b = st.Ba[:ja, :].copy(), st.Ba[ja, :].copy()
+        blocks = R.schur_blocks(Ta)
+        est = {}
+        for s, z in blocks:
+            lam, y = R.block_eigvec(Ta, s, z)
+            est[s] = (lam, abs(b @ y))
+        nsel = R.aggressive_reorder(st, 1e-12)
+        Ta2, b2 = st.Ba[:ja, :], st.Ba[ja, :]
+        assert np.allclose(np.sort_complex(np.linalg.eigvals(Ta2)), np.sort_complex(np.linalg.eigvals(Ta)),
+                           atol=1e-12)
+        orth, sketch, rel = _decomposition_errors(st)
+        assert orth < 1e-11 and sketch < 1e-13 and rel < 1e-11
+        conv = [s for s, z in blocks if est[s][1] <= 1e-12 * max(abs(est[s][0]), 1e-300)]
+        assert nsel == sum(dict(blocks)[s] for s in conv)
+        if conv and conv[0] != 0:         # a converged block behind an unconverged one
+            lam0, y0 = R.block_eigvec(Ta2, 0, dict(R.schur_blocks(Ta2))[0])
+            assert abs(lam0 - est[conv[0]][0]) < 1e-12 * abs(lam0)
+            assert abs(abs(b2 @ y0) - est[conv[0]][1]) <= 1e-6 * est[conv[0]][1] + 1e-15
+            moved = True
+            break
+        R.extend(st, 15 - st.q)
+    assert moved and st.q == (0 if isolated is None else 1)
+
+
+def test_aggressive_deflation_locks_earlier_same_result():
+    # Plain locking waits for the leading Schur vector; aggressive deflation
+    # locks the converged pair as soon as it converges.  Same eigenvalues,
+    # same residual level (planted spectrum {1, 0.9 +- 5i}).
+    A = _exterior_pair_matrix()
+    n = A.shape[0]
+    plain = R.rks(A, 3, 12, 48, I.start_vector(n, 1), which="LR", tol=1e-12)
+    aggr = R.rks(A, 3, 12, 48, I.start_vector(n, 1), which="LR", tol=1e-12, aggressive=True)
+    assert plain.converged and aggr.converged
+    for res in (plain, aggr):
+        assert np.allclose(np.sort_complex(res.eigvals), np.sort_complex([1.0, 0.9 + 5j, 0.9 - 5j]), atol=1e-11)
+        assert res.resid.max() < 1e-13
+    first = lambda hist: next(t for t, q in enumerate(hist) if q > 0)
+    assert first(aggr.locked) < first(plain.locked)
+    assert aggr.locked[first(aggr.locked)] == 2       # the pair, locked whole
+
+
+@pytest.mark.parametrize("eta_lock", [1e-3, 1e-6])
+def test_locking_bound_sqrt_i_at_lock_time(eta_lock):
+    # Remark after Eq. 4.21: with |b_j| <= eta on the locked columns, the Ritz
+    # pair of the i-th diagonal block of T_qq (its eigenvector lives in the
+    # first i entries) has ||A U_q y - l U_q y|| = ||u|| |b^T y| (Eq. 4.20)
+    # <= sqrt(i) eta ||u||, with ||u|| <= 1/sqrt(1-eps).  Planted spectrum
+    # {1.6, 1.45, 1.3, 1.2} over a bulk in [-1, 1]; the first locking event
+    # takes two vectors at once, with |b| far above rounding.
+    n = 200
+    rng = np.random.default_rng(7)
+    lam_p = np.concatenate([[1.6, 1.45, 1.3, 1.2], rng.uniform(-1, 1, n - 4)])
+    Qx, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    X = Qx @ (np.eye(n) + 0.3 * np.triu(rng.standard_normal((n, n)), 1) / np.sqrt(n))
+    A = sp.csr_matrix(X @ np.diag(lam_p) @ np.linalg.inv(X))
+    Om = omega_matrix(n, 48, 8, 0)
+    st = R.start(A, Om, I.start_vector(n, 1))
+    R.extend(st, 12)
+    for _ in range(20):
+        R.contract(st, 4, "LM")
+        ja = st.ja
+        b_before = st.Ba[ja, :].copy()
+        u = st.Ua[:, ja].copy()
+        r = R.lock(st, 4, eta_lock)
+        if r:
+            break
+        R.extend(st, 12 - st.q)
+    assert r >= 2 and st.q == r            # first locking event, several vectors
+    eta = np.abs(b_before[:r]).max()
+    Qb, _ = np.linalg.qr(np.hstack([st.Uq, u[:, None]]))
+    sv = np.linalg.svd(Om @ Qb, compute_uv=False)
+    eps = max(sv.max() ** 2 - 1, 1 - sv.min() ** 2)
+    assert eps < 1 and np.linalg.norm(u) <= 1 / np.sqrt(1 - eps) * (1 + 1e-12)
+    for s, z in R.schur_blocks(st.Tqq):
+        lam, y = R.block_eigvec(st.Tqq, s, z)
+        assert np.all(y[s + z:] == 0)
+        x = st.Uq @ y
+        res = np.linalg.norm(A @ x - lam * x)
+        ident = np.linalg.norm(u) * abs(b_before[:r] @ y)
+        assert abs(res - ident) <= 1e-7 * ident + 1e-13 * abs(lam)
+        assert res <= np.sqrt(s + z) * eta / np.sqrt(1 - eps) * (1 + 1e-9)
