@@ -205,7 +205,7 @@ def run_ours(args) -> None:
     solver = rks.Solver(A.n, d_rowptr, d_colind, d_vals, P.k, P.p, P.d, which=P.which,
                         seed=P.omega_seed, zeta=P.zeta, u1=d_u1, device=True,
                         stream=stream.cuda_stream, profile=True, prec=args.prec, maxit=args.maxit,
-                        keep=keep, ortho=args.ortho, **P.solver_opts())
+                        keep=keep, ortho=args.ortho, aggressive=args.aggressive, **P.solver_opts())
     X_dev = torch.empty((P.k + 1, A.n), dtype=torch.float64, device=dev)
 
     def step():
@@ -277,7 +277,7 @@ def run_ours(args) -> None:
         with rks.Solver(A.n, h_rowptr, h_colind, h_vals, P.k, P.p, P.d, which=P.which,
                         seed=P.omega_seed, zeta=P.zeta, u1=h_u1, stream=stream.cuda_stream,
                         prec=args.prec, maxit=args.maxit, keep=keep, ortho=args.ortho,
-                        **P.solver_opts()) as s2:
+                        aggressive=args.aggressive, **P.solver_opts()) as s2:
             s2.solve(allow_noconv=False)
             s2.eigpairs(X_out=h_X)
         e2e_times.append((time.perf_counter() - t0) * 1e3)
@@ -297,6 +297,7 @@ def run_ours(args) -> None:
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "k": P.k, "p": P.p, "d": P.d,
                        "zeta": P.zeta, "prec": args.prec, "keep": keep, "ortho": args.ortho,
+                       "aggressive": bool(args.aggressive),
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (basis 648 MB, A 80 MB)"},
             "roofline": roofline,
@@ -341,6 +342,8 @@ def main():
     ap.add_argument("--keep", type=int, default=-1,
                     help="active Schur vectors a restart keeps after locking (thick restart); "
                          "-1: k; 0: k - q as in Algorithm 1")
+    ap.add_argument("--aggressive", action="store_true",
+                    help="aggressive deflation: converged Schur blocks move to the front and lock")
     ap.add_argument("--prec", default="df", choices=["df", "fp64", "mixed"],
                     help="arithmetic of the n-dimensional work (see include/rks.h)")
     args = ap.parse_args()

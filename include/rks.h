@@ -117,6 +117,15 @@ typedef struct {
                           digit products (FP64-class) for the double-float
                           basis;
                           0: the SIMT kernels. */
+  int aggressive;      /* 1: aggressive deflation (Sec. 4.3, after Thm 4.3):
+                          before locking, the active Schur form is reordered
+                          (orthogonal swaps of diagonal blocks) so that every
+                          block whose Ritz estimate |b^T y| is below the
+                          locking threshold leads, converged blocks in their
+                          order, then the others in theirs; the leading ones
+                          then lock as usual.  Needs lock = 1.  Nothing moves
+                          if a swap is refused.  0 (default): only a leading
+                          prefix of converged Schur vectors locks. */
 } rks_opts;
 
 enum { RKS_ORTHO_SKETCH = 0, RKS_ORTHO_CGS2 = 1 };
@@ -362,6 +371,15 @@ int rks_basis_product_df(int64_t n, const double* U, int64_t ldu, int nin, const
  * are m x m host arrays.  Returns RKS_OK, RKS_EINVAL or RKS_EDENSE.  Runs on
  * the host only (no GPU needed). */
 int rks_host_ordered_schur(int m, const double* B, int which, int nsort, double* T, double* Q);
+
+/* Reorder a quasi-triangular T (n x n, column-major, host, in place) by
+ * orthogonal swaps of adjacent diagonal blocks so that the blocks flagged in
+ * select (n ints, read at each block's first row) lead, keeping the order of
+ * the flagged blocks and of the others (the aggressive-deflation reorder,
+ * Sec. 4.3).  Z (n x n, host) is multiplied on the right by the rotations
+ * (pass the identity to get them).  Returns RKS_OK, RKS_EINVAL, or
+ * RKS_EDENSE with T and Z unchanged when a swap is refused.  Host only. */
+int rks_host_reorder_select(int n, double* T, const int* select, double* Z);
 
 /* Eigenvalues and unit 2-norm eigenvectors of a quasi-triangular T (n x n,
  * host): a 2x2 block gives the pair (Im > 0 first).  Y_re, Y_im: n x n host

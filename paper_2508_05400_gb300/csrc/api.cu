@@ -372,6 +372,67 @@ void house_qr(int d, int ka, double* S, double* R) {
 
 // Algorithm 1 contraction + whitening (Sec. 3.3) + locking (Sec. 4.4) +
 // restart product on the device.  Sets c->kk results of the Ritz step.
+// Locking threshold of an active block with eigenvalue modulus lam (Sec. 4.4):
+// eta_lock * |lambda| (floored at eps ||T_a||_F), or eta_lock * ||A||_1.
+double lock_threshold(const rks_ctx* c, double lam, double tn) {
+  const double scale = c->opts.conv == RKS_CONV_NORM1 ? c->norm1 : std::max(lam, 2.220446049250313e-16 * tn);
+  return c->eta_lock * scale;
+}
+
+// Aggressive deflation (Sec. 4.3, after Thm 4.3): reorder the active Schur
+// form T_a (ka x ka) so that the blocks whose Ritz estimate |b^T y| (unit y,
+// eigenvector of T_a) is below the locking threshold lead, in their order,
+// followed by the others in theirs.  The rotation Z goes onto b (Z^T b), the
+// kept Schur vectors Qk (ma x ka), the coupling T_qa (q x ka, leading
+// dimension ldt) and the kept sketches S_a (d x ka).  Returns true when
+// something moved; a refused swap leaves everything unchanged.
+bool aggressive_reorder(const rks_ctx* c, int ka, std::vector<double>& Ta, std::vector<double>& bk, int ma,
+                        std::vector<double>& Qk, int q, int ldt, std::vector<double>& Tqa, int d,
+                        std::vector<double>& Sa) {
+  if (ka < 2) return false;
+  const auto bl = rks_dense::blocks(ka, Ta.data(), ka);
+  std::vector<double> lre(ka), lim(ka);
+  std::vector<std::complex<double>> Y((size_t)ka * ka);
+  rks_dense::quasi_eig(ka, Ta.data(), ka, lre.data(), lim.data(), Y.data(), ka);
+  double tn = 0.0;
+  for (double v : Ta) tn += v * v;
+  tn = std::sqrt(tn);
+  std::vector<char> sel(bl.size(), 0);
+  for (size_t t = 0; t < bl.size(); ++t) {
+    std::complex<double> e = 0.0;   // column bl[t].start of Y: the block's eigenvector (Im >= 0)
+    for (int i = 0; i < ka; ++i) e += bk[i] * Y[i + (size_t)bl[t].start * ka];
+    sel[t] = std::abs(e) <= lock_threshold(c, std::hypot(bl[t].re, bl[t].im), tn);
+  }
+  size_t first_open = 0;
+  while (first_open < bl.size() && sel[first_open]) ++first_open;
+  bool behind = false;
+  for (size_t t = first_open; t < bl.size(); ++t) behind = behind || sel[t];
+  if (!behind) return false;
+  std::vector<double> T2 = Ta, Z((size_t)ka * ka, 0.0);
+  for (int i = 0; i < ka; ++i) Z[i + (size_t)i * ka] = 1.0;
+  if (rks_dense::reorder_select(ka, T2.data(), ka, Z.data(), ka, ka, sel) != 0) return false;
+  Ta = T2;
+  auto right = [&](std::vector<double>& X, int rows, int ldx) {   // X (rows x ka) <- X Z
+    std::vector<double> row(ka);
+    for (int r = 0; r < rows; ++r) {
+      for (int j = 0; j < ka; ++j) {
+        double acc = 0.0;
+        for (int l = 0; l < ka; ++l) acc += X[r + (size_t)l * ldx] * Z[l + (size_t)j * ka];
+        row[j] = acc;
+      }
+      for (int j = 0; j < ka; ++j) X[r + (size_t)j * ldx] = row[j];
+    }
+  };
+  right(Qk, ma, ma);
+  right(Tqa, q, ldt);
+  right(Sa, d, d);
+  std::vector<double> b2(ka, 0.0);
+  for (int j = 0; j < ka; ++j)
+    for (int l = 0; l < ka; ++l) b2[j] += bk[l] * Z[l + (size_t)j * ka];
+  bk = b2;
+  return true;
+}
+
 int contract(rks_ctx* c) {
   const int m = c->m, q = c->q, ma = c->ja, d = c->d;
   const int ldb = m + 1, ldt = c->k + 2;
@@ -475,6 +536,8 @@ int contract(rks_ctx* c) {
       Tqa_new = t3;
     }
   }
+  const bool reordered = c->opts.lock && c->opts.aggressive &&
+                         aggressive_reorder(c, ka, Ta, bk, ma, Qk, q, ldt, Tqa_new, d, Sa);
   // device restart: U[:, q..q+ka-1] = U[:, q..m-1] diag(colscale) Qk ; u -> column q+ka
   std::vector<double> Qp((size_t)ma * ka);
   for (int j = 0; j < ka; ++j)
@@ -546,7 +609,7 @@ int contract(rks_ctx* c) {
     for (int b2 = 0; b2 < nc; ++b2)
       for (int a2 = 0; a2 <= b2; ++a2) {
         double acc = 0.0;
-        if (!whitened && a2 >= q && b2 < q + ka) {
+        if (!whitened && !reordered && a2 >= q && b2 < q + ka) {
           acc = Gsa[(a2 - q) + (size_t)(b2 - q) * ka];   // both active: computed above
         } else {
           const double* x = &c->S_h[(size_t)a2 * d];
@@ -577,9 +640,7 @@ int contract(rks_ctx* c) {
     tn = std::sqrt(tn);
     for (const auto& B : rks_dense::blocks(ka, Ta.data(), ka)) {
       if (q + r + B.size > c->k) break;
-      double lam = std::hypot(B.re, B.im);
-      double scale = c->opts.conv == RKS_CONV_NORM1 ? c->norm1 : std::max(lam, 2.220446049250313e-16 * tn);
-      double thr = c->eta_lock * scale;
+      const double thr = lock_threshold(c, std::hypot(B.re, B.im), tn);
       bool ok = true;
       for (int t = 0; t < B.size; ++t) ok = ok && std::fabs(bk[B.start + t]) <= thr;
       if (!ok) break;
@@ -791,6 +852,7 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
   if (o.prec != RKS_PREC_DF && o.prec != RKS_PREC_FP64 && o.prec != RKS_PREC_MIXED) return RKS_EINVAL;
   if (o.maxit <= 0) o.maxit = 1000;
   if (o.keep < 0 || o.keep > k) return RKS_EINVAL;
+  if (o.aggressive != 0 && o.aggressive != 1) return RKS_EINVAL;
   if (o.ortho != RKS_ORTHO_SKETCH && o.ortho != RKS_ORTHO_CGS2) return RKS_EINVAL;
   if (o.ortho == RKS_ORTHO_CGS2 && o.prec != RKS_PREC_DF) return RKS_EINVAL;
   const int m = k + p;
@@ -1218,6 +1280,14 @@ int rks_host_ordered_schur(int m, const double* B, int which, int nsort, double*
   if (rks_dense::schur(m, T, m, Q, m) != 0) return RKS_EDENSE;
   rks_dense::reorder(m, T, m, Q, m, m, which, std::min(std::max(nsort, 0), m));
   return RKS_OK;
+}
+
+int rks_host_reorder_select(int n, double* T, const int* select, double* Z) {
+  if (n < 1 || !T || !select || !Z) return RKS_EINVAL;
+  const auto bl = rks_dense::blocks(n, T, n);
+  std::vector<char> sel(bl.size());
+  for (size_t t = 0; t < bl.size(); ++t) sel[t] = select[bl[t].start] != 0;
+  return rks_dense::reorder_select(n, T, n, Z, n, n, sel) == 0 ? RKS_OK : RKS_EDENSE;
 }
 
 int rks_host_quasi_eig(int n, const double* T, double* lam_re, double* lam_im, double* Y_re, double* Y_im) {

@@ -519,6 +519,41 @@ int reorder(int n, double* T, int ldt, double* Z, int ldz, int nz, int which, in
   return fails;
 }
 
+int reorder_select(int n, double* T, int ldt, double* Z, int ldz, int nz, const std::vector<char>& sel) {
+  std::vector<Block> bl = blocks(n, T, ldt);
+  if (sel.size() != bl.size()) return -1;
+  // work on copies so that a refused swap leaves T and Z as they were
+  std::vector<double> T2((size_t)n * n), Z2((size_t)nz * n);
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < n; ++i) T2[i + (size_t)j * n] = at(T, ldt, i, j);
+    for (int i = 0; i < nz; ++i) Z2[i + (size_t)j * nz] = at(Z, ldz, i, j);
+  }
+  std::vector<int> size(bl.size());
+  for (size_t t = 0; t < bl.size(); ++t) size[t] = bl[t].size;
+  std::vector<char> cur = sel;   // flags in the current block order
+  int placed = 0;                // flagged blocks already at the top
+  for (size_t t = 0; t < cur.size(); ++t) {
+    if (!cur[t]) continue;
+    int start = 0;                 // row of block t - 1 (recomputed as it moves)
+    for (int v = 0; v + 1 < (int)t; ++v) start += size[v];
+    for (int u = (int)t; u > placed; --u) {
+      if (swap_blocks(n, T2.data(), n, Z2.data(), nz, nz, start, size[u - 1], size[u]) != 0) return -1;
+      std::vector<Block> loc;
+      scan_blocks(T2.data(), n, start, start + size[u - 1] + size[u], n, loc);
+      if (loc.size() != 2 || loc[0].size != size[u] || loc[1].size != size[u - 1]) return -1;
+      std::swap(size[u], size[u - 1]);
+      std::swap(cur[u], cur[u - 1]);
+      if (u - 2 >= 0) start -= size[u - 2];
+    }
+    ++placed;
+  }
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < n; ++i) at(T, ldt, i, j) = T2[i + (size_t)j * n];
+    for (int i = 0; i < nz; ++i) at(Z, ldz, i, j) = Z2[i + (size_t)j * nz];
+  }
+  return 0;
+}
+
 int quasi_eig(int n, const double* T, int ldt, double* lam_re, double* lam_im,
               std::complex<double>* Y, int ldy) {
   std::vector<Block> bl = blocks(n, T, ldt);

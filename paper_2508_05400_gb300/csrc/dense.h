@@ -29,6 +29,12 @@ int swap_blocks(int n, double* T, int ldt, double* Z, int ldz, int nz, int j, in
 // Move the best `nsort` blocks (by key) to the top, best first.  Returns the
 // number of rejected swaps (0 when the ordering is complete).
 int reorder(int n, double* T, int ldt, double* Z, int ldz, int nz, int which, int nsort);
+// Move the diagonal blocks flagged in sel (one flag per block, in the order
+// of blocks(T)) to the top, keeping the order among the flagged blocks and
+// among the others (the ordering of LAPACK's dtrsen).  Z (nz rows) takes the
+// rotations.  Returns 0, or -1 (T and Z unchanged) if a swap is refused or
+// rounding splits a 2x2 block.
+int reorder_select(int n, double* T, int ldt, double* Z, int ldz, int nz, const std::vector<char>& sel);
 // Eigenvalues and unit 2-norm eigenvectors of a quasi-triangular T; a 2x2
 // block at (i, i+1) gives columns i (Im > 0) and i+1 (its conjugate).
 int quasi_eig(int n, const double* T, int ldt, double* lam_re, double* lam_im,

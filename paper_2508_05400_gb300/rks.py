@@ -33,7 +33,7 @@ class Opts(C.Structure):
                 ("stream", C.c_void_p), ("u1", C.c_void_p), ("eta_lock", C.c_double),
                 ("max_restarts", C.c_int), ("profile", C.c_int), ("conv", C.c_int),
                 ("prec", C.c_int), ("mixed_tol", C.c_double), ("verify", C.c_double), ("keep", C.c_int), ("ortho", C.c_int),
-                ("tc_restart", C.c_int)]
+                ("tc_restart", C.c_int), ("aggressive", C.c_int)]
 
 
 CONV = {"eig": 0, "norm1": 1}
@@ -132,6 +132,8 @@ def lib() -> C.CDLL:
         L.rks_sketch_apply_noalloc.restype = C.c_int
         L.rks_host_ordered_schur.argtypes = [C.c_int, _P, C.c_int, C.c_int, _P, _P]
         L.rks_host_ordered_schur.restype = C.c_int
+        L.rks_host_reorder_select.argtypes = [C.c_int, _P, _P, _P]
+        L.rks_host_reorder_select.restype = C.c_int
         L.rks_host_quasi_eig.argtypes = [C.c_int, _P, _P, _P, _P, _P]
         L.rks_host_quasi_eig.restype = C.c_int
         _lib = L
@@ -176,7 +178,8 @@ class Solver:
     def __init__(self, n, rowptr, colind, vals, k, p, d, which="LM", tol=1e-10, seed=0, *,
                  zeta=8, maxit=1000, lock=True, u1=None, eta_lock=0.0, max_restarts=0,
                  device=False, stream=None, profile=False, conv="eig", verify=0.0, prec="df",
-                 mixed_tol=0.0, keep=0, ortho="sketch", tc_restart=True):
+                 mixed_tol=0.0, keep=0, ortho="sketch", tc_restart=True,
+                 aggressive=False):
         L = lib()
         self.n, self.k, self.p, self.d = int(n), int(k), int(p), int(d)
         self.device = bool(device)
@@ -208,6 +211,7 @@ class Solver:
         o.keep = int(keep)
         o.ortho = ORTHO[ortho]
         o.tc_restart = int(bool(tc_restart))
+        o.aggressive = int(bool(aggressive))
         h = _P()
         _check(L.rks_create(C.byref(h), self.n, _ptr(rowptr), _ptr(colind), _ptr(vals), vdt,
                             self.k, self.p, self.d, WHICH[which] if isinstance(which, str) else int(which),
@@ -392,6 +396,18 @@ def host_ordered_schur(B: np.ndarray, which: str, nsort: int):
     return T, Q
 
 
+def host_reorder_select(T: np.ndarray, select):
+    """Flagged diagonal blocks of quasi-triangular T first (rks_host_reorder_select):
+    returns (T', Z) with T = Z T' Z^T."""
+    n = T.shape[0]
+    Tf = np.asfortranarray(T, dtype=np.float64).copy(order="F")
+    Z = np.asfortranarray(np.eye(n))
+    sel = np.ascontiguousarray(select, dtype=np.int32)
+    _check(lib().rks_host_reorder_select(n, Tf.ctypes.data, sel.ctypes.data, Z.ctypes.data),
+           "rks_host_reorder_select")
+    return Tf, Z
+
+
 def host_quasi_eig(T: np.ndarray):
     n = T.shape[0]
     Tf = np.asfortranarray(T, dtype=np.float64)
@@ -412,7 +428,8 @@ class Batch:
     """
 
     def __init__(self, problems, k, p, d, which="LM", tol=1e-10, seed=0, *, nthreads=16, zeta=8, maxit=1000,
-                 lock=True, eta_lock=0.0, conv="eig", verify=0.0, prec="df", keep=0, ortho="sketch"):
+                 lock=True, eta_lock=0.0, conv="eig", verify=0.0, prec="df", keep=0, ortho="sketch",
+                 aggressive=False):
         L = lib()
         self.count = len(problems)
         self._keep = [(_host(A.rowptr, np.int32), _host(A.colind, np.int32), np.ascontiguousarray(A.vals))
@@ -428,6 +445,7 @@ class Batch:
         o.zeta, o.maxit, o.lock = int(zeta), int(maxit), int(bool(lock))
         o.eta_lock, o.conv, o.verify = float(eta_lock), CONV[conv], float(verify)
         o.prec, o.keep, o.ortho = PREC[prec], int(keep), ORTHO[ortho]
+        o.aggressive = int(bool(aggressive))
         self.n = ns
         self.k, self.p, self.d = int(k), int(p), int(d)
         h = _P()

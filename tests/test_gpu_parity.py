@@ -180,6 +180,36 @@ def test_planted_spectrum(which, k, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("isolated", [None, 3.0])
+def test_aggressive_deflation_against_oracle(prec, isolated):
+    # Aggressive deflation (Sec. 4.3, after Thm 4.3): the pair 0.9 +- 5i
+    # converges before the wanted-first eigenvalue 1.0 and is reordered to the
+    # front and locked at the same restart as in the oracle, earlier than
+    # with plain locking; with ``isolated`` it happens after a first lock
+    # (non-empty coupling T_qa).  Same eigenvalues, FP64 residuals.
+    from test_oracle_rks import _exterior_pair_matrix
+    As = sp.csr_matrix(_exterior_pair_matrix(isolated=isolated))
+    n = As.shape[0]
+    A = I.CSR(n, As.indptr.astype(np.int32), As.indices.astype(np.int32), As.data)
+    k = 3 if isolated is None else 4
+    exact = np.array(([isolated] if isolated is not None else []) + [1.0, 0.9 + 5j, 0.9 - 5j])
+    u1 = I.start_vector(n, 1)
+    ores = R.rks(As, k, 12, 48, u1, which="LR", tol=1e-12, aggressive=True)
+    plain = R.rks(As, k, 12, 48, u1, which="LR", tol=1e-12)
+    first = lambda hist: next(t for t, q in enumerate(hist) if q > 0)
+    assert first(ores.locked) < first(plain.locked)
+    with K().Solver.from_csr(A, k, 12, 48, which="LR", tol=1e-12, u1=u1, prec=prec, aggressive=True) as s:
+        info = s.solve(allow_noconv=False)
+        lam, X, res = s.eigpairs()
+        _, nlock = s.history()
+    assert info["converged"] == 1
+    assert first(list(nlock)) == first(ores.locked)
+    assert nlock[first(ores.locked)] == ores.locked[first(ores.locked)]
+    assert np.max(np.abs(np.sort_complex(lam) - np.sort_complex(exact))) <= 1e-10
+    assert res.max() <= 1e-12
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_ragged_convdiff_mid_size(prec):
     # several CTAs and a ragged tail (n = 2773 rows), rectangular grid
     A = I.convdiff_2d(59, 47, 1.0, 20.0, 10.0)

@@ -93,3 +93,39 @@ def test_host_quasi_eig_matches_scipy(lib):
     for j in range(24):
         if lam[j].imag > 0:
             assert np.isclose(lam[j + 1], lam[j].conj())
+
+
+def test_host_reorder_select_matches_lapack_dtrsen(lib):
+    # The aggressive-deflation reorder (Sec. 4.3): flagged blocks first, both
+    # groups in their original order, as LAPACK dtrsen orders them.  Same
+    # block eigenvalue sequence, T = Z T' Z^T with Z orthogonal, and the same
+    # leading invariant subspace as dtrsen's.
+    import scipy.linalg as sla
+    from scipy.linalg.lapack import dtrsen
+    rng = np.random.default_rng(11)
+    for m in (6, 23, 60):
+        T0, _ = sla.schur(rng.standard_normal((m, m)), output="real")
+        blocks = R.schur_blocks(T0)
+        for trial in range(4):
+            flags = rng.random(len(blocks)) < 0.4
+            if trial == 0:
+                flags[:] = False; flags[-1] = True          # last block to the top
+            sel = np.zeros(m, dtype=np.int32)
+            for (s, z), f in zip(blocks, flags):
+                sel[s:s + z] = int(f)
+            T, Z = K.host_reorder_select(T0, sel)
+            To, Zo, *_, info = dtrsen(sel, T0, np.eye(m), job="N")
+            assert info == 0
+            assert np.linalg.norm(Z @ T @ Z.T - T0) < 1e-13 * m * np.linalg.norm(T0)
+            assert np.linalg.norm(Z.T @ Z - np.eye(m)) < 1e-13 * m
+            assert np.all(np.tril(T, -2) == 0)
+            lam = [R.block_eigenvalue(T, s, z) for s, z in R.schur_blocks(T)]
+            lamo = [R.block_eigenvalue(To, s, z) for s, z in R.schur_blocks(To)]
+            assert np.allclose(lam, lamo, atol=1e-10 * np.abs(lamo).max())
+            want = [R.block_eigenvalue(T0, s, z) for (s, z), f in zip(blocks, flags) if f]
+            want += [R.block_eigenvalue(T0, s, z) for (s, z), f in zip(blocks, flags) if not f]
+            assert np.allclose(lam, want, atol=1e-10 * np.abs(want).max())
+            kc = int(sel.sum())
+            if kc:
+                sv = np.linalg.svd(Z[:, :kc].T @ Zo[:, :kc], compute_uv=False)
+                assert sv.min() > 1 - 1e-8
