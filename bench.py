@@ -309,6 +309,7 @@ def run_ours(args) -> None:
             "solve": {"restarts": info["restarts"], "nmatvec": info["nmatvec"],
                       "nlocked": info["nlocked"], "max_resid": info["max_resid"],
                       "max_est": info["max_est"], "host_dense_ms_per_step": agg["host_ms"] / args.steps,
+                      "whitenings_per_step": agg["whitenings"] / args.steps,
                       "kernel_ms_per_step": {c: agg[c]["ms"] / args.steps for c in rks.KCLASSES}}}
     solver.close()
     if rank == 0 and not args.no_cpu_baseline:

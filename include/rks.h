@@ -175,6 +175,8 @@ typedef struct {
   double bytes[RKS_NK];
   double flops[RKS_NK];
   double host_ms;      /* host time in the small dense step (Schur ... locking) */
+  int64_t whitenings;  /* restarts that whitened the kept sketches (Sec. 3.3) */
+  int64_t reorders;    /* restarts whose aggressive deflation moved a block */
 } rks_stats;
 
 /* Counters of the last rks_solve (see rks_stats). */

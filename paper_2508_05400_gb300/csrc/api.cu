@@ -74,6 +74,12 @@ struct rks_ctx {
   int* rexp_d = nullptr;     // per-row exponents (n)
   std::vector<int> fexp_h, pexp_h;
   std::vector<double> Qr_h;
+  // rotation of the kept columns still to be applied on the device after the
+  // restart's host work (whitening, aggressive reorder): columns corr_q ..
+  // corr_q + corr_ka - 1 times corr (corr_ka x corr_ka); empty: none
+  std::vector<double> corr;
+  int corr_q = 0, corr_ka = 0;
+  bool up_M2 = false;      // the Gram matrix changed at the restart: upload it
   void* Ub = nullptr;      // basis in use: U2 or Uf
   bool f32 = false;        // basis in use is FP32
   int phase_restarts = 0;
@@ -383,11 +389,12 @@ double lock_threshold(const rks_ctx* c, double lam, double tn) {
 // form T_a (ka x ka) so that the blocks whose Ritz estimate |b^T y| (unit y,
 // eigenvector of T_a) is below the locking threshold lead, in their order,
 // followed by the others in theirs.  The rotation Z goes onto b (Z^T b), the
-// kept Schur vectors Qk (ma x ka), the coupling T_qa (q x ka, leading
-// dimension ldt) and the kept sketches S_a (d x ka).  Returns true when
-// something moved; a refused swap leaves everything unchanged.
-bool aggressive_reorder(const rks_ctx* c, int ka, std::vector<double>& Ta, std::vector<double>& bk, int ma,
-                        std::vector<double>& Qk, int q, int ldt, std::vector<double>& Tqa, int d,
+// pending right factor Cm of the kept columns (ka x ka; empty = identity),
+// the coupling T_qa (q x ka, leading dimension ldt) and the kept sketches
+// S_a (d x ka).  Returns true when something moved; a refused swap leaves
+// everything unchanged.
+bool aggressive_reorder(const rks_ctx* c, int ka, std::vector<double>& Ta, std::vector<double>& bk,
+                        std::vector<double>& Cm, int q, int ldt, std::vector<double>& Tqa, int d,
                         std::vector<double>& Sa) {
   if (ka < 2) return false;
   const auto bl = rks_dense::blocks(ka, Ta.data(), ka);
@@ -423,7 +430,11 @@ bool aggressive_reorder(const rks_ctx* c, int ka, std::vector<double>& Ta, std::
       for (int j = 0; j < ka; ++j) X[r + (size_t)j * ldx] = row[j];
     }
   };
-  right(Qk, ma, ma);
+  if (Cm.empty()) {
+    Cm.assign((size_t)ka * ka, 0.0);
+    for (int i = 0; i < ka; ++i) Cm[i + (size_t)i * ka] = 1.0;
+  }
+  right(Cm, ka, ka);
   right(Tqa, q, ldt);
   right(Sa, d, d);
   std::vector<double> b2(ka, 0.0);
@@ -431,6 +442,69 @@ bool aggressive_reorder(const rks_ctx* c, int ka, std::vector<double>& Ta, std::
     for (int l = 0; l < ka; ++l) b2[j] += bk[l] * Z[l + (size_t)j * ka];
   bk = b2;
   return true;
+}
+
+// U[:, a0 .. a0+nout-1] <- U[:, a0 .. a0+nin-1] diag(cs) Q in place (Eq. 3.5),
+// Q nin x nout (host FP64, column-major), cs the column scales of the inputs
+// (nullptr: ones); move_src >= 0 also copies column move_src to a0 + nout.
+// Tensor cores where the sizes allow, else the SIMT kernels.  The host images
+// are pageable, so each copy has taken its source when cudaMemcpyAsync
+// returns and nothing here waits for the kernel.
+int restart_launch(rks_ctx* c, int a0, int nin, const std::vector<double>& Q, const double* cs, int nout,
+                   int move_src) {
+  std::vector<double> Qp((size_t)nin * nout);
+  for (int j = 0; j < nout; ++j)
+    for (int l = 0; l < nin; ++l) Qp[l + (size_t)j * nin] = (cs ? cs[l] : 1.0) * Q[l + (size_t)j * nin];
+  const int ps = prof_begin(c, RKS_K_RESTART);
+  if (c->f32 && c->qimg && rks::tc_restart_supported(nin, nout)) {
+    // FP32 basis: split-BF16 product on the tensor cores
+    rks::tc_restart_bimage(nin, nout, Qp.data(), c->qimg_h);
+    CK(cudaMemcpyAsync(c->qimg, c->qimg_h.data(), c->qimg_h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                       c->stream));
+    float* U0 = c->Uf + (size_t)a0 * c->ldu;
+    rks::launch_tc_restart_f32(c->n, U0, U0, c->ldu, nin, nout, c->qimg,
+                               move_src >= 0 ? c->Uf + (size_t)move_src * c->ldu : nullptr,
+                               move_src >= 0 ? c->Uf + (size_t)(a0 + nout) * c->ldu : nullptr, c->flag, c->stream);
+  } else if (c->prec != RKS_PREC_FP64 && !c->f32 && c->qimg_df && rks::tc_restart_df_supported(nin, nout)) {
+    // double-float basis: exact digit products on the tensor cores.  The power
+    // of two of each column scale goes onto U (an exact exponent offset in the
+    // digit split), the rest (in [1, 2)) stays in Q'.
+    c->pexp_h.assign(nin, 0);
+    c->Qr_h.assign(Qp.size(), 0.0);
+    for (int l = 0; l < nin; ++l) {
+      const double sc = cs ? cs[l] : 1.0;
+      int E = 0;
+      if (sc != 0.0) std::frexp(sc, &E);
+      c->pexp_h[l] = sc != 0.0 ? E - 1 : 0;
+      for (int j = 0; j < nout; ++j)
+        c->Qr_h[l + (size_t)j * nin] = std::ldexp(Qp[l + (size_t)j * nin], -c->pexp_h[l]);
+    }
+    rks::tc_restart_df_bimage(nin, nout, c->Qr_h.data(), c->qimg_h, c->fexp_h);
+    CK(cudaMemcpyAsync(c->pexp_d, c->pexp_h.data(), c->pexp_h.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(c->qimg_df, c->qimg_h.data(), c->qimg_h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(c->fexp_d, c->fexp_h.data(), c->fexp_h.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       c->stream));
+    float2* U0 = c->U2 + (size_t)a0 * c->ldu;
+    rks::launch_tc_restart_df(c->n, U0, U0, c->ldu, nin, nout, c->qimg_df, c->fexp_d, c->pexp_d, c->rexp_d,
+                              move_src >= 0 ? c->U2 + (size_t)move_src * c->ldu : nullptr,
+                              move_src >= 0 ? c->U2 + (size_t)(a0 + nout) * c->ldu : nullptr, c->flag, c->stream);
+  } else if (c->prec != RKS_PREC_FP64) {
+    std::vector<float2> Q2h(Qp.size());
+    for (size_t t = 0; t < Qp.size(); ++t) {
+      float h = (float)Qp[t];
+      Q2h[t] = make_float2(h, (float)(Qp[t] - (double)h));
+    }
+    CK(cudaMemcpyAsync(c->Q2, Q2h.data(), Q2h.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
+    rks::launch_df_rows_gemm(c->n, c->Ub, c->ldu, a0, nin, c->Q2, nout, a0, move_src, c->f32, c->stream);
+  } else {
+    CK(cudaMemcpyAsync(c->Qd, Qp.data(), Qp.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    rks::launch_rows_gemm(c->n, c->U, c->ldu, a0, nin, c->Qd, nout, c->U, c->ldu, a0, move_src, c->stream);
+  }
+  prof_end(c, ps, RKS_K_RESTART, 1, (double)(nin + nout + (move_src >= 0 ? 2 : 0)) * (c->f32 ? 4.0 : 8.0) * c->n,
+           2.0 * c->n * nin * nout);
+  return launch_err();
 }
 
 int contract(rks_ctx* c) {
@@ -471,6 +545,14 @@ int contract(rks_ctx* c) {
       for (int l = 0; l < ma; ++l) acc += M(c->Tqa, ldt, i, l) * Qk[l + (size_t)j * ma];
       Tqa_new[i + (size_t)j * ldt] = acc;
     }
+  // The device restart (Eq. 3.5) starts now, with the truncated Schur vectors
+  // as they are; the host work below (sketches, whitening, aggressive reorder,
+  // Gram matrix, locking and, in the caller, the Ritz pairs) overlaps it.
+  // Whitening and the aggressive reorder rotate the kept columns once more:
+  // that ka x ka factor C goes to the device in upload_restart, as a second
+  // in-place product, before the next expansion.
+  int rc = restart_launch(c, q, ma, Qk, &c->cs_h[q], ka, m);
+  if (rc) return rc;
   // sketches of the kept columns: S_a <- S_a Qk ; last column moves to q+ka
   std::vector<double> Sa((size_t)d * ka, 0.0);
   for (int j = 0; j < ka; ++j)
@@ -482,7 +564,7 @@ int contract(rks_ctx* c) {
     }
   // whitening when the sketch lost orthonormality (Sec. 3.3, Eqs. 3.7-3.8)
   // (the Gram matrix of the kept sketches, reused below for the device copy
-  // of S^T S unless whitening changes them)
+  // of S^T S unless whitening or the reorder changes them)
   const bool sketched = c->opts.ortho != RKS_ORTHO_CGS2;
   std::vector<double> Gsa((size_t)ka * ka, 0.0);
   double gerr = 0.0;
@@ -495,9 +577,11 @@ int contract(rks_ctx* c) {
         const double e = acc - ((a == bb) ? 1.0 : 0.0);
         gerr += (a == bb ? 1.0 : 2.0) * e * e;
       }
+  std::vector<double> Cm;   // pending right factor of the kept columns (empty: none)
   bool whitened = false;
   if (sketched && ka > 0 && std::sqrt(gerr) > 1e-10) {
     whitened = true;
+    ++c->stats.whitenings;
     std::vector<double> R((size_t)ka * ka), Rinv((size_t)ka * ka, 0.0);
     house_qr(d, ka, Sa.data(), R.data());
     for (int j = 0; j < ka; ++j) {          // Rinv by back substitution
@@ -517,9 +601,7 @@ int contract(rks_ctx* c) {
           Z[i + (size_t)j * ldz] = acc;
         }
     };
-    std::vector<double> tmp((size_t)std::max(ma, ka) * ka);
-    matmul(ma, ka, ka, Qk.data(), ma, Rinv.data(), ka, tmp.data(), ma);
-    std::copy(tmp.begin(), tmp.begin() + (size_t)ma * ka, Qk.begin());
+    Cm = Rinv;
     std::vector<double> t2((size_t)ka * ka);
     matmul(ka, ka, ka, Ta.data(), ka, Rinv.data(), ka, t2.data(), ka);
     matmul(ka, ka, ka, R.data(), ka, t2.data(), ka, Ta.data(), ka);
@@ -537,71 +619,20 @@ int contract(rks_ctx* c) {
     }
   }
   const bool reordered = c->opts.lock && c->opts.aggressive &&
-                         aggressive_reorder(c, ka, Ta, bk, ma, Qk, q, ldt, Tqa_new, d, Sa);
-  // device restart: U[:, q..q+ka-1] = U[:, q..m-1] diag(colscale) Qk ; u -> column q+ka
-  std::vector<double> Qp((size_t)ma * ka);
-  for (int j = 0; j < ka; ++j)
-    for (int l = 0; l < ma; ++l) Qp[l + (size_t)j * ma] = c->cs_h[q + l] * Qk[l + (size_t)j * ma];
-  int ps = prof_begin(c, RKS_K_RESTART);
-  if (c->f32 && c->qimg && rks::tc_restart_supported(ma, ka)) {
-    // FP32 basis: split-BF16 product on the tensor cores
-    rks::tc_restart_bimage(ma, ka, Qp.data(), c->qimg_h);
-    CK(cudaMemcpyAsync(c->qimg, c->qimg_h.data(), c->qimg_h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
-                       c->stream));
-    float* U0 = c->Uf + (size_t)q * c->ldu;
-    rks::launch_tc_restart_f32(c->n, U0, U0, c->ldu, ma, ka, c->qimg, c->Uf + (size_t)m * c->ldu,
-                               c->Uf + (size_t)(q + ka) * c->ldu, c->flag, c->stream);
-    CK(cudaStreamSynchronize(c->stream));   // the image is a host buffer reused next restart
-  } else if (c->prec != RKS_PREC_FP64 && !c->f32 && c->qimg_df && rks::tc_restart_df_supported(ma, ka)) {
-    // double-float basis: exact digit products on the tensor cores.  The power
-    // of two of each column scale goes onto U (an exact exponent offset in the
-    // digit split), the rest (in [1, 2)) stays in Q'.
-    c->pexp_h.assign(ma, 0);
-    c->Qr_h.assign(Qp.size(), 0.0);
-    for (int l = 0; l < ma; ++l) {
-      int E = 0;
-      if (c->cs_h[q + l] != 0.0) std::frexp(c->cs_h[q + l], &E);
-      c->pexp_h[l] = c->cs_h[q + l] != 0.0 ? E - 1 : 0;
-      for (int j = 0; j < ka; ++j)
-        c->Qr_h[l + (size_t)j * ma] = std::ldexp(Qp[l + (size_t)j * ma], -c->pexp_h[l]);
-    }
-    rks::tc_restart_df_bimage(ma, ka, c->Qr_h.data(), c->qimg_h, c->fexp_h);
-    CK(cudaMemcpyAsync(c->pexp_d, c->pexp_h.data(), c->pexp_h.size() * sizeof(int), cudaMemcpyHostToDevice,
-                       c->stream));
-    CK(cudaMemcpyAsync(c->qimg_df, c->qimg_h.data(), c->qimg_h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
-                       c->stream));
-    CK(cudaMemcpyAsync(c->fexp_d, c->fexp_h.data(), c->fexp_h.size() * sizeof(int), cudaMemcpyHostToDevice,
-                       c->stream));
-    float2* U0 = c->U2 + (size_t)q * c->ldu;
-    rks::launch_tc_restart_df(c->n, U0, U0, c->ldu, ma, ka, c->qimg_df, c->fexp_d, c->pexp_d, c->rexp_d,
-                              c->U2 + (size_t)m * c->ldu, c->U2 + (size_t)(q + ka) * c->ldu, c->flag, c->stream);
-    CK(cudaStreamSynchronize(c->stream));   // the image is a host buffer reused next restart
-  } else if (c->prec != RKS_PREC_FP64) {
-    std::vector<float2> Q2h(Qp.size());
-    for (size_t t = 0; t < Qp.size(); ++t) {
-      float h = (float)Qp[t];
-      Q2h[t] = make_float2(h, (float)(Qp[t] - (double)h));
-    }
-    CK(cudaMemcpyAsync(c->Q2, Q2h.data(), Q2h.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
-    rks::launch_df_rows_gemm(c->n, c->Ub, c->ldu, q, ma, c->Q2, ka, q, m, c->f32, c->stream);
-    CK(cudaStreamSynchronize(c->stream));   // Q2h is a host temporary
-  } else {
-    CK(cudaMemcpyAsync(c->Qd, Qp.data(), Qp.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    rks::launch_rows_gemm(c->n, c->U, c->ldu, q, ma, c->Qd, ka, c->U, c->ldu, q, m, c->stream);
-  }
-  prof_end(c, ps, RKS_K_RESTART, 1, (double)(ma + ka + 2) * (c->f32 ? 4.0 : 8.0) * c->n, 2.0 * c->n * ma * ka);
-  int rc = launch_err();
-  if (rc) return rc;
+                         aggressive_reorder(c, ka, Ta, bk, Cm, q, ldt, Tqa_new, d, Sa);
+  if (reordered) ++c->stats.reorders;
+  c->corr = Cm;
+  c->corr_q = q;
+  c->corr_ka = ka;
+  // host copies of the new scales and sketches (uploaded in upload_restart)
   const double s_last_scale = c->cs_h[m];
   for (int j = 0; j < ka; ++j) c->cs_h[q + j] = 1.0;
   c->cs_h[q + ka] = s_last_scale;
   for (int j = q + ka + 1; j <= m; ++j) c->cs_h[j] = 0.0;
   for (int j = 0; j < ka; ++j) std::memcpy(&c->S_h[(size_t)(q + j) * d], &Sa[(size_t)j * d], d * sizeof(double));
   std::memmove(&c->S_h[(size_t)(q + ka) * d], &c->S_h[(size_t)m * d], d * sizeof(double));
-  CK(cudaMemcpyAsync(c->colscale, c->cs_h.data(), c->cs_h.size() * sizeof(double), cudaMemcpyHostToDevice,
-                     c->stream));
-  CK(cudaMemcpyAsync(c->S, c->S_h.data(), c->S_h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  if (c->M2 && c->opts.ortho != RKS_ORTHO_CGS2) {
+  c->up_M2 = c->M2 && sketched;
+  if (c->up_M2) {
     // Gram matrix of the kept sketches (locked, active and the last vector)
     // for the least squares of the next expansion
     const int nc = q + ka + 1, ldm = m + 1;
@@ -621,8 +652,6 @@ int contract(rks_ctx* c) {
         c->M2_h[a2 + (size_t)b2 * ldm] = v;
         c->M2_h[b2 + (size_t)a2 * ldm] = v;
       }
-    CK(cudaMemcpyAsync(c->M2, c->M2_h.data(), c->M2_h.size() * sizeof(float2), cudaMemcpyHostToDevice,
-                       c->stream));
   }
   if (c->prec != RKS_PREC_FP64) {
     c->S2_h.resize(c->S_h.size());
@@ -630,7 +659,6 @@ int contract(rks_ctx* c) {
       float h = (float)c->S_h[t];
       c->S2_h[t] = make_float2(h, (float)(c->S_h[t] - (double)h));
     }
-    CK(cudaMemcpyAsync(c->S2, c->S2_h.data(), c->S2_h.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
   }
   // locking: leading active blocks with small |b| (relative to |lambda|)
   int r = 0;
@@ -682,6 +710,26 @@ int contract(rks_ctx* c) {
     M(c->Ba, ldb, ka, j) = bk[j];
   }
   return RKS_OK;
+}
+
+// Second half of a restart, after the host work: the pending rotation of the
+// kept columns (whitening, aggressive reorder) as an in-place product, then
+// the new column scales, sketches and Gram matrix to the device.
+int upload_restart(rks_ctx* c) {
+  if (!c->corr.empty()) {
+    int rc = restart_launch(c, c->corr_q, c->corr_ka, c->corr, nullptr, c->corr_ka, -1);
+    if (rc) return rc;
+    c->corr.clear();
+  }
+  CK(cudaMemcpyAsync(c->colscale, c->cs_h.data(), c->cs_h.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     c->stream));
+  CK(cudaMemcpyAsync(c->S, c->S_h.data(), c->S_h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (c->up_M2)
+    CK(cudaMemcpyAsync(c->M2, c->M2_h.data(), c->M2_h.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                       c->stream));
+  if (c->prec != RKS_PREC_FP64)
+    CK(cudaMemcpyAsync(c->S2, c->S2_h.data(), c->S2_h.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
+  return launch_err();
 }
 
 // Ritz pairs of the full T = [[Tqq, Tqa], [0, T_a]] and estimates (Eq. 4.8).
@@ -1054,6 +1102,8 @@ static int run_alg1(rks_ctx* c, const double* start, int limit, double verify, i
     ++done;
     ritz(c);
     c->stats.host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
+    rc = upload_restart(c);            // pending rotation, scales, sketches, Gram matrix
+    if (rc) return rc;
     double mx = 0.0;
     for (int t = 0; t < c->nw; ++t) mx = std::max(mx, c->est[t]);
     c->hist.push_back(mx);

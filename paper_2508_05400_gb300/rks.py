@@ -46,12 +46,15 @@ KCLASSES = ("spmv_sketch", "ls", "update_sketch", "finish", "restart", "other")
 
 class Stats(C.Structure):
     _fields_ = [("launches", C.c_int64 * 6), ("ms", C.c_double * 6), ("bytes", C.c_double * 6),
-                ("flops", C.c_double * 6), ("host_ms", C.c_double)]
+                ("flops", C.c_double * 6), ("host_ms", C.c_double), ("whitenings", C.c_int64),
+                ("reorders", C.c_int64)]
 
     def as_dict(self) -> dict:
         out = {name: {"launches": self.launches[i], "ms": self.ms[i], "bytes": self.bytes[i],
                       "flops": self.flops[i]} for i, name in enumerate(KCLASSES)}
         out["host_ms"] = self.host_ms
+        out["whitenings"] = self.whitenings
+        out["reorders"] = self.reorders
         out["launches_total"] = int(sum(self.launches))
         return out
 
