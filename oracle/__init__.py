@@ -10,6 +10,9 @@ Modules:
   sketch  - the sparse-sign embedding Omega from its hash specification.
   rks     - Algorithm 1 (rKS) and Algorithm 2 (extension) with the locking of
             Sec. 4.2-4.3, residual estimates of Sec. 4.1, whitening of Sec. 3.3.
+  sketch_qr - the randomized QR factorisations of a block listed in Sec. 2
+            (randomized Gram-Schmidt, sketch and whiten, randomized
+            Cholesky QR).
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 (closed forms, brute force, invariants, published generator outputs); none is
