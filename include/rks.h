@@ -365,6 +365,38 @@ int rks_basis_product_f32(int64_t n, const float* U, int64_t ldu, int nin, const
 int rks_basis_product_df(int64_t n, const double* U, int64_t ldu, int nin, const double* Q, int nout, double* out,
                          void* stream);
 
+/* ---- Randomized QR of a block (Sec. 2) -------------------------------- */
+
+/* The randomized orthogonalisation processes Sec. 2 lists for building a
+ * sketch-orthonormal basis, applied to a tall and skinny block K (n x s):
+ * K = Q R with R upper triangular and a positive diagonal.
+ *   RKS_QR_RGS      randomized Gram-Schmidt, column by column (the process of
+ *                   Algorithm 2 without A): Omega Q orthonormal.
+ *   RKS_QR_WHITEN   sketch and whiten (Sec. 3.3 on the whole block):
+ *                   Omega K = Q_s R, Q = K R^{-1}: Omega Q orthonormal.
+ *   RKS_QR_RCHOLQR  randomized Cholesky QR: whiten, then Cholesky QR of the
+ *                   whitened block: Q orthonormal in the Euclidean sense.
+ * RGS and WHITEN compute the same (unique) factorisation in exact
+ * arithmetic, RCHOLQR the Euclidean QR of K.  Omega is the solver's
+ * sparse-sign embedding for (n, d, zeta, seed).  The n-dimensional work runs
+ * in double-float arithmetic on the device, the d x s and s x s work in FP64
+ * on the host. */
+enum { RKS_QR_RGS = 0, RKS_QR_WHITEN = 1, RKS_QR_RCHOLQR = 2 };
+#define RKS_SKETCH_QR_MAX_S 192
+
+/* K, Q: device FP64, column-major n x s with leading dimensions ldk, ldq >= n
+ * (Q may be K, with ldq = ldk).  R: host s x s (column-major, ld s), written
+ * with zeros below the diagonal.  S: host d x s or NULL; receives Omega Q
+ * (measured by sketching the computed Q; for RGS the sketches the process
+ * computed).  1 <= s <= min(RKS_SKETCH_QR_MAX_S, d, n), 1 <= zeta <= 16,
+ * 2 zeta <= d <= 8192.  Work buffers (about 16 n s bytes) are allocated and
+ * freed by the call; it runs on `stream` and synchronises it.  Returns
+ * RKS_OK, RKS_EINVAL, RKS_ENOMEM, RKS_ECUDA, RKS_EBREAKDOWN (a zero or
+ * non-finite diagonal of R: K is rank deficient) or RKS_EDENSE (RCHOLQR: the
+ * Gram matrix is not positive definite). */
+int rks_sketch_qr(int64_t n, int s, const double* K, int64_t ldk, int d, int zeta, uint64_t seed, int method,
+                  double* Q, int64_t ldq, double* R, double* S, void* stream);
+
 /* ---- Host-side small dense FP64 steps (Algorithm 1 contraction) ------ */
 
 /* Ordered real Schur form (Prop. 2.8) of the m x m matrix B (column-major,

@@ -18,7 +18,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 CXX = os.environ.get("CXX", "g++")
 
-SOURCES = ["kernels.cu", "kernels_df.cu", "restart_tc.cu", "api.cu", "batch.cu", "noalloc.cu", "dense.cpp"]
+SOURCES = ["kernels.cu", "kernels_df.cu", "restart_tc.cu", "api.cu", "batch.cu", "noalloc.cu", "sketch_qr.cu",
+           "dense.cpp"]
 
 
 def _cmd(src: str) -> list[str]:

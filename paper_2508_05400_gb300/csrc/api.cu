@@ -330,51 +330,6 @@ int expand(rks_ctx* c) {
   return RKS_OK;
 }
 
-// Householder QR of the d x ka matrix S (column-major, ld d), R upper
-// triangular with positive diagonal (ka x ka, ld ka); S is overwritten by Q.
-void house_qr(int d, int ka, double* S, double* R) {
-  std::vector<double> V((size_t)d * ka, 0.0), beta(ka, 0.0);
-  std::vector<double> A(S, S + (size_t)d * ka);
-  for (int j = 0; j < ka; ++j) {
-    double s = 0.0;
-    for (int i = j; i < d; ++i) s += A[i + (size_t)j * d] * A[i + (size_t)j * d];
-    double nrm = std::sqrt(s);
-    double x0 = A[j + (size_t)j * d];
-    double v0 = x0 >= 0 ? x0 + nrm : x0 - nrm;
-    double* v = &V[(size_t)j * d];
-    v[j] = 1.0;
-    double vtv = 1.0;
-    for (int i = j + 1; i < d; ++i) { v[i] = (v0 != 0.0) ? A[i + (size_t)j * d] / v0 : 0.0; vtv += v[i] * v[i]; }
-    beta[j] = (nrm == 0.0) ? 0.0 : 2.0 / vtv;
-    for (int cc = j; cc < ka; ++cc) {
-      double acc = 0.0;
-      for (int i = j; i < d; ++i) acc += v[i] * A[i + (size_t)cc * d];
-      acc *= beta[j];
-      for (int i = j; i < d; ++i) A[i + (size_t)cc * d] -= acc * v[i];
-    }
-  }
-  // R and explicit Q (first ka columns)
-  for (int j = 0; j < ka; ++j)
-    for (int i = 0; i < ka; ++i) R[i + (size_t)j * ka] = (i <= j) ? A[i + (size_t)j * d] : 0.0;
-  std::vector<double> Q((size_t)d * ka, 0.0);
-  for (int j = 0; j < ka; ++j) Q[j + (size_t)j * d] = 1.0;
-  for (int h = ka - 1; h >= 0; --h) {
-    const double* v = &V[(size_t)h * d];
-    for (int cc = 0; cc < ka; ++cc) {
-      double acc = 0.0;
-      for (int i = h; i < d; ++i) acc += v[i] * Q[i + (size_t)cc * d];
-      acc *= beta[h];
-      for (int i = h; i < d; ++i) Q[i + (size_t)cc * d] -= acc * v[i];
-    }
-  }
-  for (int j = 0; j < ka; ++j) {      // positive diagonal of R
-    if (R[j + (size_t)j * ka] < 0) {
-      for (int cc = j; cc < ka; ++cc) R[j + (size_t)cc * ka] = -R[j + (size_t)cc * ka];
-      for (int i = 0; i < d; ++i) Q[i + (size_t)j * d] = -Q[i + (size_t)j * d];
-    }
-  }
-  std::memcpy(S, Q.data(), Q.size() * sizeof(double));
-}
 
 // Algorithm 1 contraction + whitening (Sec. 3.3) + locking (Sec. 4.4) +
 // restart product on the device.  Sets c->kk results of the Ritz step.
@@ -583,7 +538,7 @@ int contract(rks_ctx* c) {
     whitened = true;
     ++c->stats.whitenings;
     std::vector<double> R((size_t)ka * ka), Rinv((size_t)ka * ka, 0.0);
-    house_qr(d, ka, Sa.data(), R.data());
+    rks_dense::house_qr(d, ka, Sa.data(), R.data());
     for (int j = 0; j < ka; ++j) {          // Rinv by back substitution
       Rinv[j + (size_t)j * ka] = 1.0 / R[j + (size_t)j * ka];
       for (int i = j - 1; i >= 0; --i) {

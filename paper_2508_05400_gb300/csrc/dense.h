@@ -35,6 +35,9 @@ int reorder(int n, double* T, int ldt, double* Z, int ldz, int nz, int which, in
 // rotations.  Returns 0, or -1 (T and Z unchanged) if a swap is refused or
 // rounding splits a 2x2 block.
 int reorder_select(int n, double* T, int ldt, double* Z, int ldz, int nz, const std::vector<char>& sel);
+// Householder QR of the d x ka matrix S (column-major, ld d): R (ka x ka,
+// upper triangular, positive diagonal); S is overwritten by the explicit Q.
+void house_qr(int d, int ka, double* S, double* R);
 // Eigenvalues and unit 2-norm eigenvectors of a quasi-triangular T; a 2x2
 // block at (i, i+1) gives columns i (Im > 0) and i+1 (its conjugate).
 int quasi_eig(int n, const double* T, int ldt, double* lam_re, double* lam_im,

@@ -1110,6 +1110,10 @@ void launch_df_update_plain(void* U, int64_t ldu, int c, const float2* nrs, cons
   else k_df_update_sketch<float2, U8, MB, 0><<<t.G, 512, sm, st>>>(u, ldu, c, nrs, sj, t, nullptr);
 }
 
+void launch_df_fold(const double* part, int d, int G, double* out, cudaStream_t st) {
+  k_df_fold<<<(d + 7) / 8, 256, 0, st>>>(part, d, G, out);
+}
+
 void launch_df_dots(const void* U, int64_t ldu, int c, int cv, const SketchTiles& t, double* part, cudaStream_t st) {
   k_df_dots<float2><<<t.G, 512, 0, st>>>(static_cast<const float2*>(U), ldu, c, cv, t, part);
 }

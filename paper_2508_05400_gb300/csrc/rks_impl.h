@@ -72,6 +72,8 @@ void launch_df_spmv(const CsrDF& A, const void* x, void* w, const SketchTiles& t
 void launch_df_update_plain(void* U, int64_t ldu, int c, const float2* nrs, const float2* sj, const SketchTiles& t,
                             double* norm_part, cudaStream_t st);
 void launch_df_dots(const void* U, int64_t ldu, int c, int cv, const SketchTiles& t, double* part, cudaStream_t st);
+// out[r] = sum over g < G of part[g * d + r] in a fixed order (r < d)
+void launch_df_fold(const double* part, int d, int G, double* out, cudaStream_t st);
 void launch_ks_coef(int pass, int j, int c, int G, const double* part, const double* colscale, double* rprev,
                     float2* nrs, float2* sj, cudaStream_t st);
 void launch_ks_finish(int j, int G, const double* part, double thr, double* colscale,

@@ -19,7 +19,7 @@ WHICH = {"LM": 0, "SM": 1, "LR": 2, "SR": 3}
 STATUS = {0: "RKS_OK", -1: "RKS_EINVAL", -2: "RKS_ENOMEM", -3: "RKS_ECUDA", -4: "RKS_ENOCONV",
           -5: "RKS_EBREAKDOWN", -6: "RKS_ENAN", -7: "RKS_ESTATE", -8: "RKS_EDENSE",
           -9: "RKS_ETIMEOUT"}
-RKS_OK, RKS_EINVAL, RKS_ENOCONV = 0, -1, -4
+RKS_OK, RKS_EINVAL, RKS_ENOCONV, RKS_EBREAKDOWN, RKS_EDENSE = 0, -1, -4, -5, -8
 
 
 class RKSError(RuntimeError):
@@ -125,6 +125,9 @@ def lib() -> C.CDLL:
         L.rks_destroy_batched.restype = None
         L.rks_basis_product_df.argtypes = [C.c_int64, _P, C.c_int64, C.c_int, _P, C.c_int, _P, _P]
         L.rks_basis_product_df.restype = C.c_int
+        L.rks_sketch_qr.argtypes = [C.c_int64, C.c_int, _P, C.c_int64, C.c_int, C.c_int, C.c_uint64, C.c_int, _P,
+                                    C.c_int64, _P, _P, _P]
+        L.rks_sketch_qr.restype = C.c_int
         L.rks_destroy.argtypes = [_P]
         L.rks_destroy.restype = None
         L.rks_sketch_pairs.argtypes = [C.c_int64, C.c_int, C.c_int, C.c_uint64, _P, _P, _P]
@@ -376,6 +379,26 @@ def basis_product_f32(U, ldu: int, n: int, nin: int, Q: np.ndarray, out) -> None
     stream = torch.cuda.current_stream().cuda_stream
     _check(lib().rks_basis_product_f32(n, U.data_ptr(), ldu, nin, Qf.ctypes.data, Qf.shape[1], out.data_ptr(),
                                        stream), "rks_basis_product_f32")
+
+
+QR_METHODS = {"rgs": 0, "whiten": 1, "rcholqr": 2}
+
+
+def sketch_qr(K, d: int, zeta: int = 8, seed: int = 0, method: str = "rgs", Q=None):
+    """Randomized QR of a block (rks_sketch_qr).  K: CUDA float64 tensor of
+    shape (s, n), row j = column j of the n x s block; Q (same shape, may be
+    K) receives the orthogonal factor.  Returns (Q, R, S): R the s x s upper
+    triangular factor, S = Omega Q (d x s), both host arrays."""
+    import torch
+    s, n = K.shape
+    if Q is None:
+        Q = torch.empty_like(K)
+    R, S = _fortran((s, s)), _fortran((d, s))
+    stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().rks_sketch_qr(n, s, K.data_ptr(), K.stride(0), d, zeta, int(seed) & 0xFFFFFFFFFFFFFFFF,
+                               QR_METHODS[method], Q.data_ptr(), Q.stride(0), R.ctypes.data, S.ctypes.data,
+                               stream), "rks_sketch_qr")
+    return Q, R, S
 
 
 def basis_product_df(U, ldu: int, n: int, nin: int, Q: np.ndarray, out) -> None:

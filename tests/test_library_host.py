@@ -129,3 +129,17 @@ def test_host_reorder_select_matches_lapack_dtrsen(lib):
             if kc:
                 sv = np.linalg.svd(Z[:, :kc].T @ Zo[:, :kc], compute_uv=False)
                 assert sv.min() > 1 - 1e-8
+
+
+@pytest.mark.parametrize("kw", [dict(s=0), dict(s=193), dict(d=15), dict(zeta=0), dict(zeta=17), dict(method=3),
+                                dict(ldk=99), dict(s=50, d=40), dict(nullK=True), dict(nullR=True)])
+def test_sketch_qr_rejects_bad_arguments_before_any_device_call(lib, kw):
+    # argument checks of rks_sketch_qr return before any CUDA call (no GPU here)
+    a = dict(n=100, s=8, ldk=100, d=32, zeta=8, method=0, ldq=100)
+    nullK, nullR = kw.pop("nullK", False), kw.pop("nullR", False)
+    a.update(kw)
+    fake = 0x1000      # never dereferenced: the call must fail first
+    R = np.zeros((max(a["s"], 1), max(a["s"], 1)))
+    rc = lib.rks_sketch_qr(a["n"], a["s"], None if nullK else fake, a["ldk"], a["d"], a["zeta"], 0, a["method"],
+                           fake, a["ldq"], None if nullR else R.ctypes.data, None, None)
+    assert rc == K.RKS_EINVAL
