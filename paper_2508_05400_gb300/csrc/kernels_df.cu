@@ -463,8 +463,13 @@ __global__ void __launch_bounds__(512, MINB) k_df_update_sketch(
   __syncthreads();
   const float2 sc = sj[0];
   const int t0 = tv.ctile[blockIdx.x], t1 = tv.ctile[blockIdx.x + 1];
-  for (int t = t0; t < t1; ++t) {
-    const int buf = (t - t0) & 1;
+  // The second half of the grid takes its tiles last to first: the two CTAs
+  // an SM holds (blocks b and b + G/2) then meet their short last tile at
+  // different times, and the SM keeps more loads in flight.
+  const bool rev = blockIdx.x >= gridDim.x / 2;
+  for (int tt = t0; tt < t1; ++tt) {
+    const int t = rev ? t1 - 1 - (tt - t0) : tt;
+    const int buf = (tt - t0) & 1;
     float2* v = reinterpret_cast<float2*>(smraw + lay.vb) + buf * kTileRows;
     int* of = reinterpret_cast<int*>(smraw + lay.offs) + buf * L1;
     uint32_t* ms = reinterpret_cast<uint32_t*>(smraw + lay.ms) + buf * d;

@@ -18,7 +18,7 @@ constexpr int kDfCtas = 152 * 2;
 constexpr int kResidCtas = 152 * 2;
 // Update kernel: columns loaded per batch and resident CTAs per SM it is
 // compiled for (register budget 65536 / (512 * kDfUpdMinBlocks) per thread).
-constexpr int kDfUpdUnroll = 8;
+constexpr int kDfUpdUnroll = 10;
 constexpr int kDfUpdMinBlocks = 2;
 
 // Deterministic sketch accumulation: per-tile bin lists of Omega (built once
