@@ -36,17 +36,29 @@ WORKLOAD = ("convdiff2d_1000: 2D upwind convection-diffusion 1000x1000 (n=1e6), 
 NMATVEC_WORKLOAD = 7535
 # DRAM traffic of the dominant kernel from one ncu capture, as a ratio to the
 # algorithmic bytes of the captured launch (applied to the mean launch), valid
-# only for the kernel source it was measured on (sha256 prefix of kernels_df.cu).
+# only for the kernel source it was measured on (see _kernel_hash).
 NCU_TRAFFIC = {
     # two launches of k_df_update_sketch at c = 64, 65 in the third restart (profiles/df_kernels_convdiff1000.md):
     # DRAM 541.6 / 547.1 MB against 528 / 536 MB of algorithmic bytes (the bin lists of Omega are the rest)
-    "update_sketch": {"kernels_sha": "d51a7bb47d8ee8ee", "ratio": 1.023},
+    "update_sketch": {"kernels_sha": "fdc1ba79cef500a9", "ratio": 1.023},
 }
 
 
-def _kernel_hash() -> str:
-    with open(os.path.join(ROOT, "paper_2508_05400_gb300", "csrc", "kernels_df.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def _kernel_hash():
+    """sha256 prefix of the update kernel's source: the kernel, the tile
+    helpers it inlines and its compile-time constants (None if not found)."""
+    csrc = os.path.join(ROOT, "paper_2508_05400_gb300", "csrc")
+    src = open(os.path.join(csrc, "kernels_df.cu")).read()
+    impl = open(os.path.join(csrc, "rks_impl.h")).read()
+    parts = []
+    for a, b in (("// (s, e) += sign * vals[row] for one bin-list entry", "// w'[i] = sum_p A_p x[col_p] (DF)"),
+                 ("// Vector load of two consecutive rows", "// Euclidean CGS2 (Krylov-Schur baseline)")):
+        i, j = src.find(a), src.find(b)
+        if i < 0 or j < i:
+            return None
+        parts.append(src[i:j])
+    parts += [ln for ln in impl.splitlines() if "kDfUpd" in ln or "kTileRows =" in ln]
+    return hashlib.sha256("\n".join(parts).encode()).hexdigest()[:16]
 
 
 def _peaks() -> dict:

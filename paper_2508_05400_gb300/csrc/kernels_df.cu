@@ -1150,9 +1150,12 @@ int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_r
   const size_t sm = (size_t)2 * d * sizeof(float2);
   const int c = j + 1;
   if (ls && bar) {
-    // one cooperative launch: partial-sum fold, phases A and B, two grid barriers
-    int g = (std::max(c, d) + 7) / 8;
-    g = std::min(g, 48);
+    // one cooperative launch: partial-sum fold, phases A and B, two grid
+    // barriers; a warp per folded row (the fold's L2 latency dominates, so one
+    // row per warp beats fewer CTAs with less barrier traffic)
+    const int nb = finish ? 2 * d : d;
+    int g = (std::max(c, nb) + 7) / 8;
+    g = std::min(g, 96);
     void* args[] = {&j, &d, &zscale, &finish, &s_raw, &z_raw, &S64, &S2, &colscale, &rprev, &coef, &ldcoef,
                     &znorm_prev, &nrs, &sj, &r1, &M2, &ldm, &part_z, &part_s, &G, &bar, &flag};
     if (cudaLaunchCooperativeKernel((const void*)k_df_ls_coop, dim3(g), dim3(256), args, sm, st) == cudaSuccess)
