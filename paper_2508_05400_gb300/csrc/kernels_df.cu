@@ -827,18 +827,54 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, in
 }
 
 // Fold of the sketch partials, phase A and phase B in one cooperative launch.
+// The kernel is a chain of L2 round trips, so everything that does not
+// depend on the fold is loaded before it: each warp's column of S (phase A)
+// and of M (phase B) into registers, z_raw together with s_raw.  The order of
+// every sum is that of ls_phase_a / ls_phase_b, so the results are the same
+// bits as theirs.
+constexpr int kLsPre = 12;          // entries per lane prefetched for phase A (d <= 384 fully)
+constexpr int kLsPreB = 4;          // for phase B (c <= 128 fully)
+constexpr int kLsStageMax = 2048;   // d up to which z_raw / s_raw are staged in shared memory
+
 __global__ void __launch_bounds__(256) k_df_ls_coop(
     int j, int d, double zscale, int finish, double* __restrict__ s_raw, double* __restrict__ z_raw,
     double* __restrict__ S64, float2* __restrict__ S2, double* __restrict__ colscale, double* __restrict__ rprev,
     double* __restrict__ coef, int ldcoef, double* __restrict__ znorm_prev, float2* __restrict__ nrs,
     float2* __restrict__ sj, float2* __restrict__ r1, float2* __restrict__ M2, int ldm,
     const double* __restrict__ part_z, const double* __restrict__ part_s, int G, unsigned* bar, int* flag) {
-  extern __shared__ float2 zd[];   // d: z; then d: s_j (when finishing)
+  extern __shared__ float2 zd[];   // d: z; d: s_j (when finishing); then 2d doubles: z_raw, s_raw
   float2* sjd = zd + d;
+  double* zst = reinterpret_cast<double*>(sjd + d);
+  double* sst = zst + d;
   __shared__ double red[33];
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   const int gw = blockIdx.x * nw + warp, tw = gridDim.x * nw;   // global warp index, warps in grid
   const int c = j + 1;
+  const bool stage = d <= kLsStageMax;
+  // prefetch (independent of the fold): this warp's first column
+  const int col0 = gw;
+  float2 pa[kLsPre], pb[kLsPreB];
+  double cs0 = 0.0;
+  const bool pre_a = col0 < c && !(finish && col0 == j);      // column j of S is new when finishing
+  const bool pre_b = col0 < c && !(finish && col0 == j);      // so is column j of M
+  if (pre_a) {
+    const float2* sc = S2 + (size_t)col0 * d;
+#pragma unroll
+    for (int i = 0; i < kLsPre; ++i) {
+      const int r = lane + 32 * i;
+      pa[i] = r < d ? sc[r] : make_float2(0.f, 0.f);
+    }
+  }
+  if (pre_b) {
+    const float2* mc = M2 + (size_t)col0 * ldm;
+#pragma unroll
+    for (int i = 0; i < kLsPreB; ++i) {
+      const int l = lane + 32 * i;
+      pb[i] = (l < c && !(finish && l == j)) ? mc[l] : make_float2(0.f, 0.f);
+    }
+    cs0 = colscale[col0];
+  }
+  const double zn_prev = znorm_prev[0];
   // z' and s~_j from the sketch kernels' per-CTA partial sums
   {
     const int nb = finish ? 2 * d : d;
@@ -852,19 +888,30 @@ __global__ void __launch_bounds__(256) k_df_ls_coop(
     }
     grid_barrier(bar, gridDim.x, flag);
   }
+  // z_raw and s_raw in one round trip
+  const double cs_j = finish ? 0.0 : colscale[j];
+  if (stage) {
+    for (int r = tid; r < d; r += nt) {
+      zst[r] = z_raw[r];
+      if (finish) sst[r] = s_raw[r];
+    }
+    __syncthreads();
+  }
+  const double* zsrc = stage ? zst : z_raw;
+  const double* ssrc = stage ? sst : s_raw;
   double inv = 0.0;
   if (finish) {
     double ss = 0.0;
-    for (int r = tid; r < d; r += nt) { double v = s_raw[r] * zscale; ss = fma(v, v, ss); }
+    for (int r = tid; r < d; r += nt) { double v = ssrc[r] * zscale; ss = fma(v, v, ss); }
     ss = block_sum_d(ss, red);
     const double beta = sqrt(ss);
     const bool finite = isfinite(beta);
-    const bool brk = finite && !(beta > 1e-14 * znorm_prev[0]);
+    const bool brk = finite && !(beta > 1e-14 * zn_prev);
     inv = (finite && !brk) ? 1.0 / beta : 0.0;
-    for (int r = tid; r < d; r += nt) sjd[r] = df_from_double(s_raw[r] * zscale * inv);
+    for (int r = tid; r < d; r += nt) sjd[r] = df_from_double(ssrc[r] * zscale * inv);
     if (blockIdx.x == 0) {
       for (int r = tid; r < d; r += nt) {
-        double v = s_raw[r] * zscale * inv;
+        double v = ssrc[r] * zscale * inv;
         S64[r + (size_t)j * d] = v;
         S2[r + (size_t)j * d] = df_from_double(v);
       }
@@ -880,20 +927,79 @@ __global__ void __launch_bounds__(256) k_df_ls_coop(
       }
     }
   }
-  const double scj = finish ? inv : colscale[j];
+  const double scj = finish ? inv : cs_j;
   double zz = 0.0;
   for (int r = tid; r < d; r += nt) {
-    double v = z_raw[r] * zscale * scj;
+    double v = zsrc[r] * zscale * scj;
     zz = fma(v, v, zz);
     zd[r] = df_from_double(v);
   }
   zz = block_sum_d(zz, red);            // also orders the zd and sjd writes before their use
-  // phase A
-  for (int col = gw; col < c; col += tw) ls_phase_a(col, j, d, finish, 1, S2, zd, sjd, r1, M2, ldm, lane);
+  // phase A: r1[col] = S[:, col]^T z and, when finishing, M[col, j] = S[:, col]^T s_j
+  float2 mnew = make_float2(0.f, 0.f);  // M[j, col0] computed here (finishing)
+  for (int col = gw; col < c; col += tw) {
+    if (col == col0 && pre_a) {
+      float s_ = 0.f, t_ = 0.f, g = 0.f, ge = 0.f;
+      int i = 0;
+#pragma unroll
+      for (int ii = 0; ii < kLsPre; ++ii, ++i) {
+        const int r = lane + 32 * ii;
+        if (r < d) {
+          const float2 a = pa[ii], b = zd[r];
+          df_mac(a.x, a.y, b.x, b.y, s_, t_);
+          if (finish) { const float2 e = sjd[r]; df_mac(a.x, a.y, e.x, e.y, g, ge); }
+        }
+      }
+      for (int r = lane + 32 * kLsPre; r < d; r += 32) {
+        const float2 a = S2[(size_t)col * d + r], b = zd[r];
+        df_mac(a.x, a.y, b.x, b.y, s_, t_);
+        if (finish) { const float2 e = sjd[r]; df_mac(a.x, a.y, e.x, e.y, g, ge); }
+      }
+      df_warp_sum(s_, t_);
+      if (finish) df_warp_sum(g, ge);
+      if (lane == 0) r1[col] = df_norm(s_, t_);
+      if (finish) {
+        mnew = df_norm(g, ge);
+        if (lane == 0) {
+          M2[col + (size_t)j * ldm] = mnew;
+          M2[j + (size_t)col * ldm] = mnew;
+        }
+      }
+    } else {
+      ls_phase_a(col, j, d, finish, 1, S2, zd, sjd, r1, M2, ldm, lane);
+    }
+  }
   grid_barrier(bar, gridDim.x, flag);
   // phase B
   if (blockIdx.x == 0 && tid == 0) { sj[0] = df_from_double(scj); znorm_prev[0] = sqrt(zz); }
-  for (int col = gw; col < c; col += tw) ls_phase_b(col, c, M2, ldm, r1, colscale, rprev, nrs, lane);
+  for (int col = gw; col < c; col += tw) {
+    if (col == col0 && pre_b) {
+      float s_ = 0.f, t_ = 0.f;
+#pragma unroll
+      for (int ii = 0; ii < kLsPreB; ++ii) {
+        const int l = lane + 32 * ii;
+        if (l < c) {
+          const float2 a = (finish && l == j) ? mnew : pb[ii], b = r1[l];
+          df_mac(a.x, a.y, b.x, b.y, s_, t_);
+        }
+      }
+      for (int l = lane + 32 * kLsPreB; l < c; l += 32) {
+        const float2 a = (finish && l == j) ? mnew : M2[l + (size_t)col * ldm], b = r1[l];
+        df_mac(a.x, a.y, b.x, b.y, s_, t_);
+      }
+      df_warp_sum(s_, t_);
+      if (lane == 0) {
+        const float2 rc = r1[col];
+        float hs = 2.f * rc.x, ht = 2.f * rc.y;   // exact doubling
+        df_add(-s_, -t_, hs, ht);
+        const double rd = df_to_double(df_norm(hs, ht));
+        rprev[col] = rd;
+        nrs[col] = df_from_double(-rd * cs0);
+      }
+    } else {
+      ls_phase_b(col, c, M2, ldm, r1, colscale, rprev, nrs, lane);
+    }
+  }
 }
 
 // y = x (FP64) in the storage type
@@ -1148,6 +1254,7 @@ int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_r
                     float2* nrs, float2* sj, float2* r1, float2* M2, int ldm, const double* part_z,
                     const double* part_s, int G, int* flag, unsigned* bar, cudaStream_t st) {
   const size_t sm = (size_t)2 * d * sizeof(float2);
+  const size_t sm_coop = sm + (d <= kLsStageMax ? (size_t)2 * d * sizeof(double) : 0);
   const int c = j + 1;
   if (ls && bar) {
     // one cooperative launch: partial-sum fold, phases A and B, two grid
@@ -1158,7 +1265,7 @@ int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_r
     g = std::min(g, 96);
     void* args[] = {&j, &d, &zscale, &finish, &s_raw, &z_raw, &S64, &S2, &colscale, &rprev, &coef, &ldcoef,
                     &znorm_prev, &nrs, &sj, &r1, &M2, &ldm, &part_z, &part_s, &G, &bar, &flag};
-    if (cudaLaunchCooperativeKernel((const void*)k_df_ls_coop, dim3(g), dim3(256), args, sm, st) == cudaSuccess)
+    if (cudaLaunchCooperativeKernel((const void*)k_df_ls_coop, dim3(g), dim3(256), args, sm_coop, st) == cudaSuccess)
       return 1;
     (void)cudaGetLastError();   // not available: fall back to the kernels below
   }
