@@ -65,6 +65,10 @@ struct rks_ctx {
   float2* vals2 = nullptr;
   float2* U2 = nullptr;
   float* valsf = nullptr;  // mixed precision: FP32 values and basis
+  int ell_w = 0;           // ELLPACK copy of A for the SpMV (0: not used)
+  int32_t* ell_col = nullptr;
+  float2* ell_val2 = nullptr;
+  float* ell_valf = nullptr;
   float* Uf = nullptr;
   void* qimg = nullptr;     // mixed precision: bf16 split image of Q' for the tensor-core restart
   std::vector<uint16_t> qimg_h;
@@ -801,6 +805,7 @@ void free_ctx(rks_ctx* c) {
   cudaFree(c->z_raw); cudaFree(c->s_raw); cudaFree(c->z1); cudaFree(c->r1); cudaFree(c->r); cudaFree(c->rs);
   cudaFree(c->coef); cudaFree(c->flag); cudaFree(c->Qd); cudaFree(c->u1);
   cudaFree(c->X); cudaFree(c->AX); cudaFree(c->rsum); cudaFree(c->pcol); cudaFree(c->plam);
+  cudaFree(c->ell_col); cudaFree(c->ell_val2); cudaFree(c->ell_valf);
   cudaFree(c->vals2); cudaFree(c->U2); cudaFree(c->S2); cudaFree(c->nrs); cudaFree(c->sj); cudaFree(c->Q2);
   cudaFree(c->rprev); cudaFree(c->znorm); cudaFree(c->tmp64); cudaFree(c->valsf); cudaFree(c->Uf);
   cudaFree(c->otab); cudaFree(c->lsr1); cudaFree(c->M2); cudaFree(c->bar); cudaFree(c->qimg);
@@ -924,6 +929,16 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
     if (e != cudaSuccess) return fail(RKS_ECUDA);
     std::vector<double> colsum(n, 0.0);
     for (int64_t p = 0; p < c->nnz; ++p) colsum[ci[p]] += std::fabs(cv[p]);
+    // widest row: an ELLPACK copy for the SpMV when the padding stays small
+    std::vector<int32_t> rp(n + 1);
+    if (cudaMemcpyAsync(rp.data(), c->rowptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return fail(RKS_ECUDA);
+    int wmax = 0;
+    for (int64_t i = 0; i < n; ++i) wmax = std::max(wmax, rp[i + 1] - rp[i]);
+    const int64_t slots = (n + 31) / 32 * 32 * (int64_t)wmax;
+    c->ell_w = (wmax >= 1 && wmax <= 16 && (double)slots <= 1.25 * (double)std::max<int64_t>(c->nnz, 1)) ? wmax : 0;
     c->norm1 = n ? *std::max_element(colsum.begin(), colsum.end()) : 0.0;
     if (!std::isfinite(c->norm1)) return fail(RKS_ENAN);
     if (c->norm1 == 0.0) c->norm1 = 1.0;
@@ -971,6 +986,19 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
       return fail(rc);
     rks::launch_d2df(c->nnz, c->vals, c->vals2, false, c->stream);
     c->A2.n = n; c->A2.nnz = c->nnz; c->A2.rowptr = c->rowptr; c->A2.colind = c->colind; c->A2.vals = c->vals2;
+    if (c->ell_w) {
+      const size_t slots = (size_t)((n + 31) / 32 * 32) * c->ell_w;
+      if ((rc = dalloc(&c->ell_col, slots)) || (rc = dalloc(&c->ell_val2, slots))) return fail(rc);
+      rks::launch_ell_fill(n, c->ell_w, c->rowptr, c->colind, c->vals2, false, c->ell_col, c->ell_val2, c->stream);
+      if (c->prec == RKS_PREC_MIXED) {
+        if ((rc = dalloc(&c->ell_valf, slots))) return fail(rc);
+        rks::launch_ell_fill(n, c->ell_w, c->rowptr, c->colind, c->valsf, true, c->ell_col, c->ell_valf, c->stream);
+      }
+      if ((rc = launch_err())) return fail(rc);
+      c->A2.W = c->ell_w;
+      c->A2.ecol = c->ell_col;
+      c->A2.evals = c->ell_val2;
+    }
     c->Ub = c->U2;
     if (rks::configure_df_kernels() != cudaSuccess) return fail(RKS_ECUDA);
     if (rks::df_gemm_smem(m, k + 2) > 200 * 1024 || rks::df_small_smem(d, m + 1) > 200 * 1024) return fail(RKS_EINVAL);
@@ -1106,6 +1134,7 @@ static int solve_impl(rks_ctx* c) {
     c->f32 = true;
     c->Ub = c->Uf;
     c->A2.vals = c->valsf;
+    c->A2.evals = c->ell_valf;
     c->A2.f32 = true;
     const double floor32 = c->opts.mixed_tol > 0 ? c->opts.mixed_tol : 64.0 * 5.9604644775390625e-08;
     c->tol = std::max(tol0, floor32);
@@ -1122,6 +1151,7 @@ static int solve_impl(rks_ctx* c) {
     c->f32 = false;
     c->Ub = c->U2;
     c->A2.vals = c->vals2;
+    c->A2.evals = c->ell_val2;
     c->A2.f32 = false;
     c->tol = tol0;
     c->eta_lock = eta0;

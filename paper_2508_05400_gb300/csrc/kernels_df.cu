@@ -426,6 +426,87 @@ __global__ void __launch_bounds__(512) k_df_spmv_sketch(
   if (SK) tile_write_part(acc, d, part);
 }
 
+// The SpMV+sketch of k_df_spmv_sketch on the ELLPACK copy of A (CsrDF): a
+// thread's entries sit at fixed offsets from its row index, so the loads of a
+// round need no row pointer first and each is one contiguous segment per warp.
+// Entries are taken in CSR order and padding (column -1) is skipped, so the
+// products and sums are those of the CSR kernel, bit for bit.
+template <class TA, class TU, bool SK>
+__global__ void __launch_bounds__(512) k_df_spmv_ell(
+    const int32_t* __restrict__ ecol, const TA* __restrict__ evals, int W,
+    const TU* __restrict__ x, TU* __restrict__ w, const SketchTiles tv, double* __restrict__ part) {
+  static_assert(kTileRows == 1024, "two rows per thread of a 512-thread CTA");
+  extern __shared__ __align__(16) uint8_t smraw[];
+  const int d = tv.d, L1 = tv.L + 1;
+  const TileSmem lay = tile_smem_layout(d, tv.L, 0, tv.zeta);
+  float2* acc = reinterpret_cast<float2*>(smraw + lay.acc);
+  if (SK)
+    for (int r = threadIdx.x; r < d; r += blockDim.x) acc[r] = make_float2(0.f, 0.f);
+  const int t0 = tv.ctile[blockIdx.x], t1 = tv.ctile[blockIdx.x + 1];
+  for (int t = t0; t < t1; ++t) {
+    const int buf = (t - t0) & 1;
+    float2* v = reinterpret_cast<float2*>(smraw + lay.vb) + buf * kTileRows;
+    int* of = reinterpret_cast<int*>(smraw + lay.offs) + buf * L1;
+    uint32_t* ms = reinterpret_cast<uint32_t*>(smraw + lay.ms) + buf * d;
+    uint16_t* es = reinterpret_cast<uint16_t*>(smraw + lay.es) + (size_t)buf * kTileRows * tv.zeta;
+    const int64_t r0 = tv.row[t];
+    const int rows = (int)(tv.row[t + 1] - r0);
+    if (SK) tile_stage(tv, t, r0, rows, of, ms, es);
+    const int la = threadIdx.x, lb = threadIdx.x + 512;
+    const bool oka = la < rows, okb = lb < rows;
+    const int64_t ia = r0 + la, ib = r0 + lb;
+    const int64_t ba = (((ia >> 5) * W) << 5) + (ia & 31), bb = (((ib >> 5) * W) << 5) + (ib & 31);
+    float sa = 0.f, ta = 0.f, sb = 0.f, tb = 0.f;
+    for (int q = 0; q < W; q += 4) {
+      int ca[4], cb[4];
+      float2 va[4], vbv[4], xa[4], xb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = q + u;
+        const int64_t oa = ba + ((int64_t)e << 5), ob = bb + ((int64_t)e << 5);
+        ca[u] = (oka && e < W) ? ecol[oa] : -1;
+        cb[u] = (okb && e < W) ? ecol[ob] : -1;
+        va[u] = (oka && e < W) ? ldv(evals + oa) : make_float2(0.f, 0.f);
+        vbv[u] = (okb && e < W) ? ldv(evals + ob) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xa[u] = ca[u] >= 0 ? ldv(x + ca[u]) : make_float2(0.f, 0.f);
+        xb[u] = cb[u] >= 0 ? ldv(x + cb[u]) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (ca[u] >= 0) df_mac(va[u].x, va[u].y, xa[u].x, xa[u].y, sa, ta);
+        if (cb[u] >= 0) df_mac(vbv[u].x, vbv[u].y, xb[u].x, xb[u].y, sb, tb);
+      }
+    }
+    if (oka) v[la] = stv(w + ia, df_norm(sa, ta));
+    if (okb) v[lb] = stv(w + ib, df_norm(sb, tb));
+    if (SK) {
+      __syncthreads();
+      tile_gather(d, tv.H, v, of, ms, es, acc);
+    }
+  }
+  if (SK) tile_write_part(acc, d, part);
+}
+
+// ELLPACK slots of row i (and the padding rows of the last slice)
+template <class TV>
+__global__ void k_ell_fill(int64_t n, int W, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                           const TV* __restrict__ vals, int32_t* __restrict__ ecol, TV* __restrict__ evals) {
+  const int64_t nrow = (n + 31) / 32 * 32;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrow; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p0 = i < n ? rowptr[i] : 0;
+    const int len = i < n ? (int)(rowptr[i + 1] - p0) : 0;
+    const int64_t b = (((i >> 5) * W) << 5) + (i & 31);
+    for (int e = 0; e < W; ++e) {
+      const int64_t o = b + ((int64_t)e << 5);
+      ecol[o] = e < len ? colind[p0 + e] : -1;
+      evals[o] = e < len ? vals[p0 + e] : TV();
+    }
+  }
+}
+
 // Vector load of two consecutive rows (i even, ld even): float4 = two pairs,
 // float2 = two FP32 values.
 __device__ __forceinline__ void ld2(const float2* p, float2& a, float2& b) {
@@ -1172,6 +1253,8 @@ cudaError_t configure_df_kernels() {
 #define RKS_SMEM(f) if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
   RKS_SMEM((k_df_spmv_sketch<float2, float2, true>)); RKS_SMEM((k_df_spmv_sketch<float, float, true>));
   RKS_SMEM((k_df_spmv_sketch<float2, float2, false>));
+  RKS_SMEM((k_df_spmv_ell<float2, float2, true>)); RKS_SMEM((k_df_spmv_ell<float, float, true>));
+  RKS_SMEM((k_df_spmv_ell<float2, float2, false>));
   constexpr int U8 = kDfUpdUnroll, MB = kDfUpdMinBlocks;
   RKS_SMEM((k_df_update_sketch<float2, U8, MB, 1>)); RKS_SMEM((k_df_update_sketch<float, U8, MB, 1>));
   RKS_SMEM((k_df_update_sketch<float2, U8, MB, 0>)); RKS_SMEM((k_df_update_sketch<float2, U8, MB, 2>));
@@ -1192,9 +1275,31 @@ cudaError_t configure_df_kernels() {
 int df_small_smem(int d, int c) { return (int)((size_t)2 * d * sizeof(float2)); }
 int df_gemm_smem(int nin, int nout) { return (int)(((size_t)nin * nout + (size_t)128 * nout) * sizeof(float2)); }
 
+void launch_ell_fill(int64_t n, int W, const int32_t* rowptr, const int32_t* colind, const void* vals, bool f32,
+                     int32_t* ecol, void* evals, cudaStream_t st) {
+  const int g = df_grid((n + 31) / 32 * 32, 256);
+  if (f32)
+    k_ell_fill<float><<<g, 256, 0, st>>>(n, W, rowptr, colind, static_cast<const float*>(vals), ecol,
+                                         static_cast<float*>(evals));
+  else
+    k_ell_fill<float2><<<g, 256, 0, st>>>(n, W, rowptr, colind, static_cast<const float2*>(vals), ecol,
+                                          static_cast<float2*>(evals));
+}
+
 void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, const SketchTiles& t, double* part,
                            cudaStream_t st) {
   const size_t sm = tile_smem_bytes(t.d, t.L, 0, t.zeta);
+  if (A.ecol) {
+    if (A.f32)
+      k_df_spmv_ell<float, float, true><<<t.G, 512, sm, st>>>(A.ecol, static_cast<const float*>(A.evals), A.W,
+                                                               static_cast<const float*>(x), static_cast<float*>(w),
+                                                               t, part);
+    else
+      k_df_spmv_ell<float2, float2, true><<<t.G, 512, sm, st>>>(A.ecol, static_cast<const float2*>(A.evals), A.W,
+                                                                 static_cast<const float2*>(x),
+                                                                 static_cast<float2*>(w), t, part);
+    return;
+  }
   if (A.f32)
     k_df_spmv_sketch<float, float, true><<<t.G, 512, sm, st>>>(
         A.rowptr, A.colind, static_cast<const float*>(A.vals), static_cast<const float*>(x), static_cast<float*>(w),
@@ -1207,6 +1312,12 @@ void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, const SketchT
 
 void launch_df_spmv(const CsrDF& A, const void* x, void* w, const SketchTiles& t, cudaStream_t st) {
   const size_t sm = tile_smem_bytes(t.d, t.L, 0, t.zeta);
+  if (A.ecol && !A.f32) {
+    k_df_spmv_ell<float2, float2, false><<<t.G, 512, sm, st>>>(A.ecol, static_cast<const float2*>(A.evals), A.W,
+                                                                static_cast<const float2*>(x),
+                                                                static_cast<float2*>(w), t, nullptr);
+    return;
+  }
   k_df_spmv_sketch<float2, float2, false><<<t.G, 512, sm, st>>>(
       A.rowptr, A.colind, static_cast<const float2*>(A.vals), static_cast<const float2*>(x), static_cast<float2*>(w),
       t, nullptr);

@@ -54,7 +54,18 @@ struct CsrDF {
   const int32_t* colind = nullptr;
   const void* vals = nullptr;   // float2 pairs, or float when f32
   bool f32 = false;             // FP32 values and FP32 basis (mixed precision)
+  // The same matrix as ELLPACK interleaved by 32-row slices (optional): row i
+  // has its W slots at ((i / 32) * W + e) * 32 + i % 32, e < W, in CSR order,
+  // padded with column -1.  Used by the SpMV when set.
+  int W = 0;
+  const int32_t* ecol = nullptr;
+  const void* evals = nullptr;  // float2 pairs, or float when f32
 };
+
+// ELLPACK copy of a CSR matrix (see CsrDF): ecol and evals hold
+// ceil(n / 32) * 32 * W slots; vals are float2 pairs or float (f32).
+void launch_ell_fill(int64_t n, int W, const int32_t* rowptr, const int32_t* colind, const void* vals, bool f32,
+                     int32_t* ecol, void* evals, cudaStream_t st);
 
 cudaError_t configure_df_kernels();
 int df_small_smem(int d, int c);
