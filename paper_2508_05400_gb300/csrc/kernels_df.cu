@@ -431,7 +431,9 @@ __global__ void __launch_bounds__(512) k_df_spmv_sketch(
 // round need no row pointer first and each is one contiguous segment per warp.
 // Entries are taken in CSR order and padding (column -1) is skipped, so the
 // products and sums are those of the CSR kernel, bit for bit.
-template <class TA, class TU, bool SK>
+// WC > 0: rows of at most WC entries, all of a row's loads in one round
+// (5-point stencils: W = 5 fits WC = 6 without spilling at two CTAs per SM).
+template <class TA, class TU, bool SK, int WC>
 __global__ void __launch_bounds__(512) k_df_spmv_ell(
     const int32_t* __restrict__ ecol, const TA* __restrict__ evals, int W,
     const TU* __restrict__ x, TU* __restrict__ w, const SketchTiles tv, double* __restrict__ part) {
@@ -457,11 +459,32 @@ __global__ void __launch_bounds__(512) k_df_spmv_ell(
     const int64_t ia = r0 + la, ib = r0 + lb;
     const int64_t ba = (((ia >> 5) * W) << 5) + (ia & 31), bb = (((ib >> 5) * W) << 5) + (ib & 31);
     float sa = 0.f, ta = 0.f, sb = 0.f, tb = 0.f;
-    for (int q = 0; q < W; q += 4) {
-      int ca[4], cb[4];
-      float2 va[4], vbv[4], xa[4], xb[4];
+    if (WC > 0) {                                 // one round: every column and value, then x
+      constexpr int R1 = WC > 0 ? WC : 1;
+      int ca[R1], cb[R1];
+      float2 va[R1], vbv[R1];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int e = 0; e < R1; ++e) {
+        const int64_t oa = ba + ((int64_t)e << 5), ob = bb + ((int64_t)e << 5);
+        ca[e] = (oka && e < W) ? ecol[oa] : -1;
+        cb[e] = (okb && e < W) ? ecol[ob] : -1;
+        va[e] = (oka && e < W) ? ldv(evals + oa) : make_float2(0.f, 0.f);
+        vbv[e] = (okb && e < W) ? ldv(evals + ob) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int e = 0; e < R1; ++e) {
+        const float2 xa = ca[e] >= 0 ? ldv(x + ca[e]) : make_float2(0.f, 0.f);
+        const float2 xb = cb[e] >= 0 ? ldv(x + cb[e]) : make_float2(0.f, 0.f);
+        if (ca[e] >= 0) df_mac(va[e].x, va[e].y, xa.x, xa.y, sa, ta);
+        if (cb[e] >= 0) df_mac(vbv[e].x, vbv[e].y, xb.x, xb.y, sb, tb);
+      }
+    }
+    constexpr int RU = 4;                         // rounds of four entries
+    for (int q = 0; WC == 0 && q < W; q += RU) {
+      int ca[RU], cb[RU];
+      float2 va[RU], vbv[RU], xa[RU], xb[RU];
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
         const int e = q + u;
         const int64_t oa = ba + ((int64_t)e << 5), ob = bb + ((int64_t)e << 5);
         ca[u] = (oka && e < W) ? ecol[oa] : -1;
@@ -470,12 +493,12 @@ __global__ void __launch_bounds__(512) k_df_spmv_ell(
         vbv[u] = (okb && e < W) ? ldv(evals + ob) : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < RU; ++u) {
         xa[u] = ca[u] >= 0 ? ldv(x + ca[u]) : make_float2(0.f, 0.f);
         xb[u] = cb[u] >= 0 ? ldv(x + cb[u]) : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < RU; ++u) {
         if (ca[u] >= 0) df_mac(va[u].x, va[u].y, xa[u].x, xa[u].y, sa, ta);
         if (cb[u] >= 0) df_mac(vbv[u].x, vbv[u].y, xb[u].x, xb[u].y, sb, tb);
       }
@@ -1253,8 +1276,9 @@ cudaError_t configure_df_kernels() {
 #define RKS_SMEM(f) if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
   RKS_SMEM((k_df_spmv_sketch<float2, float2, true>)); RKS_SMEM((k_df_spmv_sketch<float, float, true>));
   RKS_SMEM((k_df_spmv_sketch<float2, float2, false>));
-  RKS_SMEM((k_df_spmv_ell<float2, float2, true>)); RKS_SMEM((k_df_spmv_ell<float, float, true>));
-  RKS_SMEM((k_df_spmv_ell<float2, float2, false>));
+  RKS_SMEM((k_df_spmv_ell<float2, float2, true, 0>)); RKS_SMEM((k_df_spmv_ell<float, float, true, 0>));
+  RKS_SMEM((k_df_spmv_ell<float2, float2, false, 0>)); RKS_SMEM((k_df_spmv_ell<float2, float2, true, 6>));
+  RKS_SMEM((k_df_spmv_ell<float, float, true, 6>)); RKS_SMEM((k_df_spmv_ell<float2, float2, false, 6>));
   constexpr int U8 = kDfUpdUnroll, MB = kDfUpdMinBlocks;
   RKS_SMEM((k_df_update_sketch<float2, U8, MB, 1>)); RKS_SMEM((k_df_update_sketch<float, U8, MB, 1>));
   RKS_SMEM((k_df_update_sketch<float2, U8, MB, 0>)); RKS_SMEM((k_df_update_sketch<float2, U8, MB, 2>));
@@ -1290,14 +1314,16 @@ void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, const SketchT
                            cudaStream_t st) {
   const size_t sm = tile_smem_bytes(t.d, t.L, 0, t.zeta);
   if (A.ecol) {
-    if (A.f32)
-      k_df_spmv_ell<float, float, true><<<t.G, 512, sm, st>>>(A.ecol, static_cast<const float*>(A.evals), A.W,
-                                                               static_cast<const float*>(x), static_cast<float*>(w),
-                                                               t, part);
-    else
-      k_df_spmv_ell<float2, float2, true><<<t.G, 512, sm, st>>>(A.ecol, static_cast<const float2*>(A.evals), A.W,
-                                                                 static_cast<const float2*>(x),
-                                                                 static_cast<float2*>(w), t, part);
+    const bool narrow = A.W <= 6;
+    if (A.f32) {
+      auto k = narrow ? k_df_spmv_ell<float, float, true, 6> : k_df_spmv_ell<float, float, true, 0>;
+      k<<<t.G, 512, sm, st>>>(A.ecol, static_cast<const float*>(A.evals), A.W, static_cast<const float*>(x),
+                              static_cast<float*>(w), t, part);
+    } else {
+      auto k = narrow ? k_df_spmv_ell<float2, float2, true, 6> : k_df_spmv_ell<float2, float2, true, 0>;
+      k<<<t.G, 512, sm, st>>>(A.ecol, static_cast<const float2*>(A.evals), A.W, static_cast<const float2*>(x),
+                              static_cast<float2*>(w), t, part);
+    }
     return;
   }
   if (A.f32)
@@ -1313,9 +1339,9 @@ void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, const SketchT
 void launch_df_spmv(const CsrDF& A, const void* x, void* w, const SketchTiles& t, cudaStream_t st) {
   const size_t sm = tile_smem_bytes(t.d, t.L, 0, t.zeta);
   if (A.ecol && !A.f32) {
-    k_df_spmv_ell<float2, float2, false><<<t.G, 512, sm, st>>>(A.ecol, static_cast<const float2*>(A.evals), A.W,
-                                                                static_cast<const float2*>(x),
-                                                                static_cast<float2*>(w), t, nullptr);
+    auto k = A.W <= 6 ? k_df_spmv_ell<float2, float2, false, 6> : k_df_spmv_ell<float2, float2, false, 0>;
+    k<<<t.G, 512, sm, st>>>(A.ecol, static_cast<const float2*>(A.evals), A.W, static_cast<const float2*>(x),
+                            static_cast<float2*>(w), t, nullptr);
     return;
   }
   k_df_spmv_sketch<float2, float2, false><<<t.G, 512, sm, st>>>(
