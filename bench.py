@@ -214,11 +214,20 @@ def run_ours(args) -> None:
     d_colind = torch.from_numpy(A.colind).to(dev)
     d_vals = torch.from_numpy(A.vals).to(dev)
     d_u1 = torch.from_numpy(u1).to(dev)
-    solver = rks.Solver(A.n, d_rowptr, d_colind, d_vals, P.k, P.p, P.d, which=P.which,
-                        seed=P.omega_seed, zeta=P.zeta, u1=d_u1, device=True,
-                        stream=stream.cuda_stream, profile=True, prec=args.prec, maxit=args.maxit,
-                        keep=keep, ortho=args.ortho, aggressive=args.aggressive, **P.solver_opts())
+    mk = lambda prof: rks.Solver(A.n, d_rowptr, d_colind, d_vals, P.k, P.p, P.d, which=P.which,
+                                 seed=P.omega_seed, zeta=P.zeta, u1=d_u1, device=True,
+                                 stream=stream.cuda_stream, profile=prof, prec=args.prec, maxit=args.maxit,
+                                 keep=keep, ortho=args.ortho, aggressive=args.aggressive, **P.solver_opts())
     X_dev = torch.empty((P.k + 1, A.n), dtype=torch.float64, device=dev)
+    # one untimed solve with every kernel timed (the first warm-up): the
+    # per-kernel breakdown and the dominant kernel; the timed solves then put
+    # events around that kernel only
+    with mk(True) as s_all:
+        s_all.solve(allow_noconv=False)
+        breakdown = s_all.stats()
+    dom = max((c for c in rks.KCLASSES if c != "other" and breakdown[c]["ms"] > 0),
+              key=lambda c: breakdown[c]["ms"])
+    solver = mk(rks.profile_mask(dom))
 
     def step():
         info = solver.solve(allow_noconv=False)
@@ -230,7 +239,7 @@ def run_ours(args) -> None:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    for _ in range(args.warmup):
+    for _ in range(max(args.warmup - 1, 1)):
         step()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -258,8 +267,6 @@ def run_ours(args) -> None:
 
     # roofline of the dominant kernel (live CUDA-event durations of the timed solves)
     peaks = _peaks()
-    classes = [c for c in rks.KCLASSES if agg[c]["ms"] > 0 and c != "other"]
-    dom = max(classes, key=lambda c: agg[c]["ms"])
     d = agg[dom]
     per_launch_ms = d["ms"] / d["launches"]
     bytes_per_launch = d["bytes"] / d["launches"]
@@ -269,8 +276,8 @@ def run_ours(args) -> None:
     if rec and rec.get("kernels_sha") == _kernel_hash() and args.prec == "df":
         traffic = rec["ratio"] * bytes_per_launch
     path = ("spmv_sketch", "ls", "update_sketch", "finish")
-    path_bytes = sum(agg[c]["bytes"] for c in path)
-    path_ms = sum(agg[c]["ms"] for c in path)
+    path_bytes = sum(breakdown[c]["bytes"] for c in path)
+    path_ms = sum(breakdown[c]["ms"] for c in path)
     fp64_gflops = d["flops"] / (d["ms"] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -322,7 +329,9 @@ def run_ours(args) -> None:
                       "nlocked": info["nlocked"], "max_resid": info["max_resid"],
                       "max_est": info["max_est"], "host_dense_ms_per_step": agg["host_ms"] / args.steps,
                       "whitenings_per_step": agg["whitenings"] / args.steps,
-                      "kernel_ms_per_step": {c: agg[c]["ms"] / args.steps for c in rks.KCLASSES}}}
+                      "kernel_ms_per_step": {c: breakdown[c]["ms"] for c in rks.KCLASSES},
+                      "kernel_ms_note": "one untimed solve with every kernel timed; the timed solves "
+                                        "time only " + dom}}
     solver.close()
     if rank == 0 and not args.no_cpu_baseline:
         s = cpu_sample(P, u1, restarts=1)

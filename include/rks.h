@@ -71,7 +71,12 @@ typedef struct {
                           estimates say (fixed-iteration runs, Sec. 5); 0: none;
                           -1: only the initial expansion of Algorithm 1 */
   int profile;         /* 1: time every kernel launch with CUDA events on the
-                          context's stream (see rks_get_stats); default 0 */
+                          context's stream (see rks_get_stats); default 0.
+                          profile > 1: time only the launches of the kernel
+                          classes whose bits are set in profile >> 1 (bit c
+                          for class c of RKS_K_*), e.g.
+                          1 | 2 << RKS_K_UPDATE for the update kernel alone:
+                          fewer events in the stream */
   int conv;            /* convergence scale, RKS_CONV_EIG (default) or
                           RKS_CONV_NORM1, see below */
   int prec;            /* arithmetic of the n-dimensional work:
@@ -165,7 +170,8 @@ enum {
 };
 
 /* Counters of the last rks_solve.  launches counts every kernel the library
- * launched.  ms (event time) is filled when opts.profile = 1, else 0.  bytes
+ * launched.  ms (event time) is filled for the timed classes when
+ * opts.profile is set, else 0.  bytes
  * and flops are the algorithmic traffic / work of the launches: SpMV
  * nnz*(P_A + 4) + 4(n+1) + 2 P_V n; update (c + 2) P_V n for c basis
  * columns; restart (m_a + k_a + 2) P_V n; P = bytes per value. */

@@ -162,6 +162,7 @@ inline double& M(std::vector<double>& a, int ld, int i, int j) { return a[i + (s
 // launches of a class are bracketed by CUDA events on the context's stream.
 int prof_begin(rks_ctx* c, int cls) {
   if (!c->opts.profile) return -1;
+  if (c->opts.profile > 1 && !((c->opts.profile >> (cls + 1)) & 1)) return -1;   // class not timed
   if ((size_t)(2 * c->evused + 2) > c->evpool.size()) {
     for (int t = 0; t < 64; ++t) {
       cudaEvent_t e;

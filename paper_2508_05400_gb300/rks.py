@@ -44,6 +44,14 @@ ORTHO = {"sketch": 0, "cgs2": 1}
 KCLASSES = ("spmv_sketch", "ls", "update_sketch", "finish", "restart", "other")
 
 
+def profile_mask(*classes: str) -> int:
+    """rks_opts.profile value that times only the given kernel classes."""
+    m = 1
+    for c in classes:
+        m |= 2 << KCLASSES.index(c)
+    return m
+
+
 class Stats(C.Structure):
     _fields_ = [("launches", C.c_int64 * 6), ("ms", C.c_double * 6), ("bytes", C.c_double * 6),
                 ("flops", C.c_double * 6), ("host_ms", C.c_double), ("whitenings", C.c_int64),
@@ -209,7 +217,7 @@ class Solver:
         o.u1 = _ptr(u1)
         o.eta_lock = float(eta_lock)
         o.max_restarts = int(max_restarts)
-        o.profile = int(bool(profile))
+        o.profile = int(profile)      # True/1: every kernel class; see rks_opts.profile for a class mask
         o.conv = CONV[conv]
         o.verify = float(verify)
         o.prec = PREC[prec]
