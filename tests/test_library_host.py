@@ -143,3 +143,24 @@ def test_sketch_qr_rejects_bad_arguments_before_any_device_call(lib, kw):
     rc = lib.rks_sketch_qr(a["n"], a["s"], None if nullK else fake, a["ldk"], a["d"], a["zeta"], 0, a["method"],
                            fake, a["ldq"], None if nullR else R.ctypes.data, None, None)
     assert rc == K.RKS_EINVAL
+
+
+def test_profile_mask_selects_kernel_classes():
+    # rks_opts.profile > 1: bit c + 1 times class c (RKS_K_* order = KCLASSES order)
+    assert K.profile_mask() == 1
+    assert K.profile_mask("update_sketch") == 1 | 2 << 2
+    assert K.profile_mask("spmv_sketch", "restart") == 1 | 2 << 0 | 2 << 4
+    hdr = open(os.path.join(ROOT, "include", "rks.h")).read()
+    for i, name in enumerate(["RKS_K_SPMV", "RKS_K_LS", "RKS_K_UPDATE", "RKS_K_FINISH", "RKS_K_RESTART",
+                              "RKS_K_OTHER"]):
+        assert re.search(r"\b%s = %d\b" % (name, i), hdr)
+
+
+def test_bench_kernel_hash_finds_the_update_kernel():
+    # the traffic figure is keyed to the update kernel's source; the markers
+    # that delimit it must exist
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    h = bench._kernel_hash()
+    assert h is not None and re.fullmatch(r"[0-9a-f]{16}", h)
