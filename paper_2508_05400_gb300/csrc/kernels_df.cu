@@ -1400,6 +1400,10 @@ int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_r
     const int nb = finish ? 2 * d : d;
     int g = (std::max(c, nb) + 7) / 8;
     g = std::min(g, 96);
+    // a small problem (less than one wave of sketch CTAs) shares the GPU with
+    // other solves: fewer CTAs are easier to co-schedule for the cooperative
+    // launch (the fold of a row is the same whichever warp does it)
+    if (G < 152) g = std::min((std::max(c, d) + 7) / 8, 48);
     void* args[] = {&j, &d, &zscale, &finish, &s_raw, &z_raw, &S64, &S2, &colscale, &rprev, &coef, &ldcoef,
                     &znorm_prev, &nrs, &sj, &r1, &M2, &ldm, &part_z, &part_s, &G, &bar, &flag};
     if (cudaLaunchCooperativeKernel((const void*)k_df_ls_coop, dim3(g), dim3(256), args, sm_coop, st) == cudaSuccess)
