@@ -406,12 +406,6 @@ __global__ void k_f32_to_f64(int64_t n, const float* __restrict__ a, double* __r
     b[i] = (double)a[i];
 }
 
-__global__ void k_fill(int64_t n, double v, double* __restrict__ a) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    a[i] = v;
-}
-
 __global__ void k_check_csr(int64_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
                             const int32_t* __restrict__ colind, int* bad) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -542,10 +536,6 @@ int launch_resid_sums(int64_t n, const double* X, const double* AX, int64_t ld, 
 
 void launch_f32_to_f64(int64_t n, const float* a, double* b, cudaStream_t st) {
   k_f32_to_f64<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, a, b);
-}
-
-void launch_fill(int64_t n, double v, double* a, cudaStream_t st) {
-  k_fill<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, v, a);
 }
 
 void launch_check_csr(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind, int* bad,

@@ -147,7 +147,6 @@ void launch_spmm(const Csr& A, const double* X, int64_t ldx, double* Y, int64_t 
 int launch_resid_sums(int64_t n, const double* X, const double* AX, int64_t ld, int npairs, const int* col,
                       const int* colim, const double* lre, const double* lim, double* out, cudaStream_t st);
 void launch_f32_to_f64(int64_t n, const float* a, double* b, cudaStream_t st);
-void launch_fill(int64_t n, double v, double* a, cudaStream_t st);
 void launch_check_csr(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind, int* bad,
                       cudaStream_t st);
 
