@@ -42,16 +42,22 @@ def test_strerror_and_defaults(lib):
 
 
 @pytest.mark.parametrize("kw", [dict(k=0), dict(p=1), dict(d=5), dict(tol=0.0), dict(which=7),
-                                dict(n_override=3), dict(zeta=40)])
+                                dict(n_override=3), dict(zeta=40),
+                                dict(opt=dict(aggressive=2)), dict(opt=dict(keep=-1)), dict(opt=dict(keep=5)),
+                                dict(opt=dict(ortho=5)), dict(opt=dict(ortho=1, prec=1)),
+                                dict(opt=dict(conv=3)), dict(opt=dict(prec=7))])
 def test_create_rejects_bad_arguments_before_any_device_call(lib, kw):
     from paper_2508_05400_gb300 import inputs as I
     A = I.toeplitz_tridiag(50)
     args = dict(k=4, p=8, d=40, tol=1e-8, which=0, zeta=4)
     n_override = kw.pop("n_override", None)
+    opt = kw.pop("opt", {})
     args.update(kw)
     o = K.Opts()
     lib.rks_opts_default(o)
     o.zeta = args["zeta"]
+    for f, v in opt.items():
+        setattr(o, f, v)
     h = K._P()
     rc = lib.rks_create(h, n_override or A.n, A.rowptr.ctypes.data, A.colind.ctypes.data,
                         A.vals.ctypes.data, 0, args["k"], args["p"], args["d"], args["which"],
