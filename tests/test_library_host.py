@@ -170,3 +170,30 @@ def test_bench_kernel_hash_finds_the_update_kernel():
     import bench
     h = bench._kernel_hash()
     assert h is not None and re.fullmatch(r"[0-9a-f]{16}", h)
+
+
+def test_create_batched_rejects_bad_arguments_before_any_device_call(lib):
+    # count, missing arrays and per-problem options (streams, start vectors)
+    # are checked before the first CUDA call
+    import ctypes as C
+    from paper_2508_05400_gb300 import inputs as I
+    A = I.toeplitz_tridiag(50)
+    ns = np.array([A.n], dtype=np.int64)
+    ptrs = [np.array([a.ctypes.data], dtype=np.uint64) for a in (A.rowptr, A.colind, A.vals)]
+    h = K._P()
+
+    def call(count=1, opts=None, null=None):
+        arrs = [None if null == j else ptrs[j].ctypes.data for j in range(3)]
+        return lib.rks_create_batched(C.byref(h), count, ns.ctypes.data, arrs[0], arrs[1], arrs[2], 0, 4, 8, 40, 0,
+                                      1e-8, 0, C.byref(opts) if opts is not None else None, 1)
+    assert call(count=0) == K.RKS_EINVAL
+    for j in range(3):
+        assert call(null=j) == K.RKS_EINVAL
+    o = K.Opts()
+    lib.rks_opts_default(o)
+    o.u1 = 0x1000
+    assert call(opts=o) == K.RKS_EINVAL
+    o.u1 = None
+    o.stream = 0x1000
+    assert call(opts=o) == K.RKS_EINVAL
+    assert not h.value
