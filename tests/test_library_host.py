@@ -197,3 +197,22 @@ def test_create_batched_rejects_bad_arguments_before_any_device_call(lib):
     o.stream = 0x1000
     assert call(opts=o) == K.RKS_EINVAL
     assert not h.value
+
+
+def test_binding_constants_match_the_header():
+    # the ctypes binding's names for statuses and options carry the header's values
+    hdr = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "rks.h")).read(), flags=re.S)
+    val = lambda name: int(re.search(r"\b%s\s*=\s*(-?\d+)" % name, hdr).group(1))
+    for code, name in K.STATUS.items():
+        assert val(name) == code, name
+    for name, v in K.WHICH.items():
+        assert val("RKS_" + name) == v
+    assert {n: val("RKS_CONV_" + n.upper()) for n in K.CONV} == K.CONV
+    assert {n: val("RKS_PREC_" + n.upper()) for n in K.PREC} == K.PREC
+    assert {n: val("RKS_ORTHO_" + n.upper()) for n in K.ORTHO} == K.ORTHO
+    assert {n: val("RKS_QR_" + n.upper()) for n in K.QR_METHODS} == K.QR_METHODS
+    # the options struct: same field order and count as the header's rks_opts
+    for cname, py in (("rks_opts", K.Opts), ("rks_info", K.Info), ("rks_stats", K.Stats)):
+        body = re.search(r"typedef struct \{([^{}]*)\} %s;" % cname, hdr).group(1)
+        fields = re.findall(r"(\w+)(?:\[\w+\])?;", body)
+        assert fields == [f for f, _ in py._fields_], cname
