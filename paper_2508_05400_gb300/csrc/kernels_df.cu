@@ -11,10 +11,14 @@
 //
 // One Arnoldi step of Algorithm 2 (Sec. 3.1), new column c = j + 1, is three
 // kernels:
-//   k_df_spmv_sketch  w' = A u~_j (unscaled, u_j = u~_j / beta_j), z' = Omega w'
-//   k_df_small        finish column j (beta_j = ||s~_j||, S, scale, coefficient
-//                     column), then b = S^+ z by CGS2 in the sketch against the
-//                     locked and active columns (Thm 4.3), z = z' / beta_j
+//   k_df_spmv_ell / k_df_spmv_sketch
+//                     w' = A u~_j (unscaled, u_j = u~_j / beta_j), z' = Omega w'
+//                     (A as interleaved ELLPACK when that is compact, else CSR)
+//   k_df_ls_coop      fold of the sketch partials, finish column j (beta_j =
+//                     ||s~_j||, S, scale, coefficient column), then b = S^+ z by
+//                     CGS2 in the sketch against the locked and active columns
+//                     (Thm 4.3), z = z' / beta_j (k_df_fold + k_df_ls1 +
+//                     k_df_ls_gram when a cooperative launch is unavailable)
 //   k_df_update_sketch u~_{j+1} = w'/beta_j - U b, s~_{j+1} = Omega u~_{j+1}
 //
 // Sketch accumulation is deterministic: no atomics.  Each CTA owns a fixed,
