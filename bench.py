@@ -33,7 +33,7 @@ WORKLOAD = ("convdiff2d_1000: 2D upwind convection-diffusion 1000x1000 (n=1e6), 
             "FP64 CSR; k=20 LR, p=60, d=320, zeta=8, tol=1e-8, locking")
 # Products with A that rKS needs on this workload (measured by this solver on a
 # GB300; the method's count, used to scale the bounded CPU samples).
-NMATVEC_WORKLOAD = 7535
+NMATVEC_WORKLOAD = 7621
 # DRAM traffic of the dominant kernel from one ncu capture, as a ratio to the
 # algorithmic bytes of the captured launch (applied to the mean launch), valid
 # only for the kernel source it was measured on (see _kernel_hash).
