@@ -1,14 +1,21 @@
 #!/usr/bin/env python
 """Benchmark: time to k eigenpairs of randomized Krylov-Schur on one GB300.
 
-Workload (default): the 2D convection-diffusion operator on a 1000 x 1000 grid
-(n = 1e6, 5-point upwind stencil, nu = 1, b = (20, 10), FP64 CSR,
-4,996,000 nonzeros); k = 20 eigenvalues of largest real part, p = 60, sketch
-d = 320 with zeta = 8 nonzeros per column, tolerance 1e-8 on the residual
-estimates, locking on.  A step is one complete solve (start vector, every
-Arnoldi step and restart, Ritz vectors and FP64 residuals).
+Workload (default): the 3D convection-diffusion operator on a 160^3 grid
+(n = 4 096 000, 7-point upwind stencil, log-normal diffusivity sigma = 1 from
+seed 2, convection (10, 5, 2), FP32 CSR values, 28 518 400 nonzeros); k = 50
+eigenvalues of largest real part, p = 100, sketch d = 600 with zeta = 8
+nonzeros per column, ||A x - l x|| / (||A||_1 ||x||) <= 1e-8 verified in FP64,
+locking on, thick restart keeping k active Schur vectors.  Mixed precision:
+FP32 basis, FP32 SpMV and basis updates with compensated arithmetic, the
+restart product as split-BF16 on the tensor cores with FP32 accumulation, the
+sketch sums, small least squares, Schur steps, residuals and Rayleigh
+quotients in FP64; a double-float phase finishes below the FP32 floor.  A step
+is one complete solve (start vector, every Arnoldi step and restart, Ritz
+vectors, FP64 residuals and Rayleigh quotients).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload convdiff3d_160|convdiff2d_1000] [--prec mixed|df|fp64]
 
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own
 replica of the problem (the solver does not shard: replicas only).
@@ -29,18 +36,24 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time to k eigpairs (resid≤1e-8) & SpMV+RGS HBM GB/s; mixed/batched vs FP64 rKS"
-WORKLOAD = ("convdiff2d_1000: 2D upwind convection-diffusion 1000x1000 (n=1e6), nu=1, b=(20,10), "
-            "FP64 CSR; k=20 LR, p=60, d=320, zeta=8, tol=1e-8, locking")
-# Products with A that rKS needs on this workload (measured by this solver on a
-# GB300; the method's count, used to scale the bounded CPU samples).
-NMATVEC_WORKLOAD = 7621
+WORKLOADS = {
+    "convdiff3d_160": ("convdiff3d_160: 3D upwind convection-diffusion 160^3 (n=4.096e6), log-normal nu "
+                       "(sigma=1, seed 2), b=(10,5,2), FP32 CSR; k=50 LR, p=100, d=600, zeta=8, "
+                       "resid<=1e-8 (FP64-verified), locking, thick restart keep=50"),
+    "convdiff2d_1000": ("convdiff2d_1000: 2D upwind convection-diffusion 1000x1000 (n=1e6), nu=1, b=(20,10), "
+                        "FP64 CSR; k=20 LR, p=60, d=320, zeta=8, resid<=1e-8 (FP64-verified), locking, "
+                        "thick restart keep=20"),
+}
+DEFAULT_PREC = {"convdiff3d_160": "mixed", "convdiff2d_1000": "fp64"}
 # DRAM traffic of the dominant kernel from one ncu capture, as a ratio to the
 # algorithmic bytes of the captured launch (applied to the mean launch), valid
 # only for the kernel source it was measured on (see _kernel_hash).
 NCU_TRAFFIC = {
-    # two launches of k_df_update_sketch at c = 64, 65 in the third restart (profiles/df_kernels_convdiff1000.md):
-    # DRAM 541.6 / 547.1 MB against 528 / 536 MB of algorithmic bytes (the bin lists of Omega are the rest)
-    "update_sketch": {"kernels_sha": "fdc1ba79cef500a9", "ratio": 1.023},
+    # (kernel class, precision, workload): DRAM bytes / algorithmic bytes of
+    # the captured launches of k_df_update_sketch (double-float, c = 64, 65,
+    # third restart of the 1000^2 workload: 541.6 / 547.1 MB against 528 /
+    # 536 MB; the bin lists of Omega are the rest)
+    ("update_sketch", "df", "convdiff2d_1000"): {"kernels_sha": "fdc1ba79cef500a9", "ratio": 1.023},
 }
 
 
@@ -127,25 +140,82 @@ class Clocks:
 
 DTYPES = {"fp64": "f64",
           "df": "df64 (fp32 pair, 48-bit significand; fp64 sketch/LS/Schur/residuals)",
-          "mixed": "f32 basis (split-bf16 tensor-core restart) then df64; fp64 sketch/LS/Schur/residuals"}
+          "mixed": ("f32 basis + f32 SpMV/updates (compensated), split-bf16 tensor-core restart with f32 "
+                    "accumulation, df64 finish below the f32 floor; f64 sketch/LS/Schur/residuals/Rayleigh")}
 
 
-def _problem():
+def _problem(workload: str):
     from paper_2508_05400_gb300 import inputs as I
-    P = I.convdiff2d_problem()
+    P = I.convdiff3d_problem() if workload == "convdiff3d_160" else I.convdiff2d_problem()
     u1 = I.start_vector(P.A.n, P.u1_seed)
     return P, u1
 
 
-def cpu_sample(P, u1, restarts: int = 1) -> dict:
-    """The FP64 oracle on the host cores: initial expansion + ``restarts`` cycles."""
-    from oracle import rks as R
-    t0 = time.perf_counter()
-    o = P.solver_opts()
-    res = R.rks(P.A.to_scipy(), P.k, P.p, P.d, u1, zeta=P.zeta, seed=P.omega_seed, which=P.which,
-                tol=o["tol"], eta_lock=o.get("eta_lock"), conv=o["conv"], max_restarts=restarts)
-    dt = time.perf_counter() - t0
-    return {"seconds": dt, "nmatvec": res.nmatvec, "restarts": res.restarts}
+class OracleSampler:
+    """Bounded samples of the FP64 oracle (numpy/scipy) on the host cores.
+
+    A sample times the oracle's Algorithm 2 (``extend``, as it stands) on the
+    full problem from a decomposition of jbar columns (the mean basis size of
+    the solve: the thick restart keeps k active vectors and expands to
+    m = k + p) by 1 and by 1 + s steps; the difference over s is the cost of
+    one product with A with its sketch, least squares and update at that
+    basis size, and a solve that needed N products is estimated as N times it.
+    The starting decomposition has the right sizes (its first column is the
+    start vector, the others random with orthonormal sketches): the cost of a
+    step does not depend on the values.  The dense Schur steps of the restarts
+    are not included."""
+
+    def __init__(self, P, u1, s: int = 3):
+        import numpy as np
+        import scipy.sparse as sp
+        from oracle import rks as R
+        from oracle import sketch as SK
+        self.P, self.s = P, s
+        self.A = sp.csr_matrix(P.A.to_scipy())
+        self.Om = SK.omega_matrix(P.A.n, P.d, P.zeta, P.omega_seed)
+        self.jbar = (P.k + P.k + P.p) // 2
+        j = self.jbar
+        st = R.start(self.A, self.Om, u1)
+        rng = np.random.default_rng(0)
+        U = np.asfortranarray(rng.standard_normal((P.A.n, j + 1)))
+        U[:, 0] = st.Ua[:, 0]
+        Q, _ = np.linalg.qr(rng.standard_normal((P.d, j + 1)))
+        self.base = dict(Ua=U, Sa=np.asfortranarray(Q), Ba=np.zeros((j + 1, j)), Tqa=np.zeros((0, j)))
+        self.st0 = st
+
+    def _run(self, steps: int) -> float:
+        import dataclasses
+        from oracle import rks as R
+        st = dataclasses.replace(self.st0, **self.base)
+        t0 = time.perf_counter()
+        R.extend(st, self.jbar + steps)
+        return time.perf_counter() - t0
+
+    def sample(self) -> dict:
+        t1, t2 = self._run(1), self._run(1 + self.s)
+        return {"seconds": t1 + t2, "per_product": max(t2 - t1, 0.0) / self.s}
+
+    @staticmethod
+    def cores() -> int:
+        try:
+            from threadpoolctl import threadpool_info
+            return max((int(x.get("num_threads", 1)) for x in threadpool_info()), default=1)
+        except Exception:
+            return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+    def estimate_ms(self, smp: dict, nmatvec: int) -> float:
+        return nmatvec * smp["per_product"] * 1e3
+
+    def describe(self, smp: dict, nmatvec: int) -> str:
+        return (f"FP64 oracle (numpy/scipy) on the full problem: its Algorithm 2 from a {self.jbar}-column "
+                f"decomposition by 1 and by {1 + self.s} steps ({smp['seconds']:.1f} s), "
+                f"{smp['per_product'] * 1e3:.0f} ms per product with A at that basis size, scaled to the "
+                f"{nmatvec} products of the solve (dense Schur steps not included)")
+
+
+# Products with A that the benchmarked solve needs (mixed precision, measured
+# with this solver on a GB300), used to scale the reference arm's samples.
+REFERENCE_NMATVEC = {"convdiff3d_160": 20698, "convdiff2d_1000": 7536}
 
 
 def reduce_max_over_ranks(values, device, dist, world: int):
@@ -163,29 +233,49 @@ def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    P, u1 = _problem()
-    times, nm = [], 0
+    P, u1 = _problem(args.workload)
+    sampler = OracleSampler(P, u1)
+    nm = REFERENCE_NMATVEC[args.workload]
+    vals, secs, last = [], [], None
     for i in range(args.warmup + args.steps):
-        s = cpu_sample(P, u1, restarts=1)
+        t0 = time.perf_counter()
+        smp = sampler.sample()
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
-            times.append(s["seconds"])
-            nm = s["nmatvec"]
-    per_matvec = statistics.mean(times) / nm
-    total = NMATVEC_WORKLOAD or nm
-    value_ms = per_matvec * total * 1e3
-    sample = (f"FP64 oracle (numpy/scipy) on the full problem: initial expansion + 1 restart "
-              f"({nm} products with A) per step, scaled to {total} products "
-              f"({'the count this solver needs to converge' if NMATVEC_WORKLOAD else 'unscaled'})")
+            vals.append(sampler.estimate_ms(smp, nm))
+            secs.append(dt)
+            last = smp
+    value_ms = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value_ms, "unit": "ms",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": False,
+            "ms_per_step": value_ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": P.A.n, "nnz": P.A.nnz},
-            "cpu_baseline": {"value": value_ms, "unit": "ms", "cores": os.cpu_count(),
-                             "kind": "oracle", "sample": sample},
-            "e2e": {"value": value_ms, "unit": "ms", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "config": {"workload": WORKLOADS[args.workload], "n": P.A.n, "nnz": P.A.nnz, "k": P.k, "p": P.p,
+                       "d": P.d, "zeta": P.zeta},
+            "cpu_baseline": {"value": value_ms, "unit": "ms", "cores": sampler.cores(), "kind": "oracle",
+                             "sample": sampler.describe(last, nm) + f"; {statistics.mean(secs):.1f} s of "
+                             f"host time per step"},
+            "e2e": {"value": value_ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _solve_once(rks, P, dev_arrays, stream, prec, keep, maxit, profile=False):
+    """One solve of P on resident device inputs; returns (info, lam, res, rq, stats, ms)."""
+    d_rowptr, d_colind, d_vals, d_u1 = dev_arrays
+    with rks.Solver(P.A.n, d_rowptr, d_colind, d_vals, P.k, P.p, P.d, which=P.which, seed=P.omega_seed,
+                    zeta=P.zeta, u1=d_u1, device=True, stream=stream, profile=profile, prec=prec, maxit=maxit,
+                    keep=keep, **P.solver_opts()) as s:
+        info = s.solve(allow_noconv=False)
+        lam, _, res = s.eigpairs(want_vectors=False)
+        rq = s.rayleigh()
+        return info, lam, res, rq, s.stats(), info["t_solve_ms"]
+
+
+def _pair_errors(lam, ref):
+    """|l_i - l_ref| / |l_ref| for each of lam's values against the nearest
+    reference value (both best first)."""
+    import numpy as np
+    return [float(np.min(np.abs(ref - l)) / abs(ref[int(np.argmin(np.abs(ref - l)))])) for l in lam]
 
 
 def run_ours(args) -> None:
@@ -205,20 +295,20 @@ def run_ours(args) -> None:
     __graft_entry__.build()
     from paper_2508_05400_gb300 import rks
 
-    P, u1 = _problem()
+    prec = args.prec or DEFAULT_PREC[args.workload]
+    P, u1 = _problem(args.workload)
     A = P.A
     keep = P.k if args.keep < 0 else args.keep
     stream = torch.cuda.current_stream(dev)
     # inputs resident in HBM before the timed region
-    d_rowptr = torch.from_numpy(A.rowptr).to(dev)
-    d_colind = torch.from_numpy(A.colind).to(dev)
-    d_vals = torch.from_numpy(A.vals).to(dev)
-    d_u1 = torch.from_numpy(u1).to(dev)
+    dev_arrays = (torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.colind).to(dev),
+                  torch.from_numpy(A.vals).to(dev), torch.from_numpy(u1).to(dev))
+    d_rowptr, d_colind, d_vals, d_u1 = dev_arrays
     mk = lambda prof: rks.Solver(A.n, d_rowptr, d_colind, d_vals, P.k, P.p, P.d, which=P.which,
                                  seed=P.omega_seed, zeta=P.zeta, u1=d_u1, device=True,
-                                 stream=stream.cuda_stream, profile=prof, prec=args.prec, maxit=args.maxit,
+                                 stream=stream.cuda_stream, profile=prof, prec=prec, maxit=args.maxit,
                                  keep=keep, ortho=args.ortho, aggressive=args.aggressive, **P.solver_opts())
-    X_dev = torch.empty((P.k + 1, A.n), dtype=torch.float64, device=dev)
+    X_dev = torch.empty((P.k + 2, A.n), dtype=torch.float64, device=dev)
     # one untimed solve with every kernel timed (the first warm-up): the
     # per-kernel breakdown and the dominant kernel; the timed solves then put
     # events around that kernel only
@@ -232,7 +322,8 @@ def run_ours(args) -> None:
     def step():
         info = solver.solve(allow_noconv=False)
         lam, _, res = solver.eigpairs(X_out=X_dev)
-        return info, lam, res
+        rq = solver.rayleigh()
+        return info, lam, res, rq
 
     def barrier():
         if world > 1:
@@ -243,12 +334,13 @@ def run_ours(args) -> None:
         step()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    infos, agg = [], None
+    infos, agg, last = [], None, None
     with Clocks(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            info, lam, res = step()
+            info, lam, res, rq = step()
             infos.append(info)
+            last = (lam, res, rq)
             st = solver.stats()
             if agg is None:
                 agg = st
@@ -272,55 +364,60 @@ def run_ours(args) -> None:
     bytes_per_launch = d["bytes"] / d["launches"]
     achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
     traffic = None
-    rec = NCU_TRAFFIC.get(dom)
-    if rec and rec.get("kernels_sha") == _kernel_hash() and args.prec == "df":
+    rec = NCU_TRAFFIC.get((dom, prec, args.workload))
+    if rec and rec.get("kernels_sha") == _kernel_hash():
         traffic = rec["ratio"] * bytes_per_launch
     path = ("spmv_sketch", "ls", "update_sketch", "finish")
     path_bytes = sum(breakdown[c]["bytes"] for c in path)
     path_ms = sum(breakdown[c]["ms"] for c in path)
-    fp64_gflops = d["flops"] / (d["ms"] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "peak_source": peaks["source"],
                 "bytes_per_launch": bytes_per_launch, "ms_per_launch": per_launch_ms,
-                "fp64_gflops": fp64_gflops}
+                "flop_rate_gflops": d["flops"] / (d["ms"] * 1e-3) / 1e9,
+                "flop_note": "algorithmic FLOP/s of the dominant kernel (multiply-adds counted as 2; "
+                             "double-float work runs on the FP32 pipes)"}
+    solver.close()
 
     # end to end through the C ABI with host (pinned) buffers, copies inside
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_rowptr, h_colind, h_vals, h_u1 = pin(A.rowptr), pin(A.colind), pin(A.vals), pin(u1)
-    h_X = torch.empty((P.k + 1, A.n), dtype=torch.float64).pin_memory()
+    h_X = torch.empty((P.k + 2, A.n), dtype=torch.float64).pin_memory()
     e2e_times = []
     barrier()
-    for _ in range(0 if args.no_e2e else args.steps):
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, args.e2e_steps))):
         t0 = time.perf_counter()
         with rks.Solver(A.n, h_rowptr, h_colind, h_vals, P.k, P.p, P.d, which=P.which,
                         seed=P.omega_seed, zeta=P.zeta, u1=h_u1, stream=stream.cuda_stream,
-                        prec=args.prec, maxit=args.maxit, keep=keep, ortho=args.ortho,
+                        prec=prec, maxit=args.maxit, keep=keep, ortho=args.ortho,
                         aggressive=args.aggressive, **P.solver_opts()) as s2:
             s2.solve(allow_noconv=False)
-            s2.eigpairs(X_out=h_X)
+            nwx = s2.nwanted
+            s2.eigpairs(X_out=h_X[:nwx])
         e2e_times.append((time.perf_counter() - t0) * 1e3)
     barrier()
     e2e_ms = statistics.mean(e2e_times) if e2e_times else None
-    kk = P.k
     if e2e_ms is not None:
         e2e_ms = reduce_max_over_ranks([e2e_ms], dev, dist, world)[0]
     h2d = A.rowptr.nbytes + A.colind.nbytes + A.vals.nbytes + u1.nbytes
-    d2h = 8 * A.n * kk + 3 * 8 * kk
+    nw = last[0].size
+    d2h = 8 * A.n * nw + 3 * 8 * nw
 
     info = infos[-1]
+    lam, res, rq = last
     line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPES[args.prec],
+            "dtype": DTYPES[prec],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "k": P.k, "p": P.p, "d": P.d,
-                       "zeta": P.zeta, "prec": args.prec, "keep": keep, "ortho": args.ortho,
+            "config": {"workload": WORKLOADS[args.workload], "n": A.n, "nnz": A.nnz, "k": P.k, "p": P.p,
+                       "d": P.d, "zeta": P.zeta, "prec": prec, "keep": keep, "ortho": args.ortho,
                        "aggressive": bool(args.aggressive),
                        "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (basis 648 MB, A 80 MB)"},
+                       "l2": "inputs larger than L2 (basis of m+1 columns and A are several GB)"},
             "roofline": roofline,
             "spmv_rgs_gbs": path_bytes / (path_ms * 1e-3) / 1e9 if path_ms else None,
+            "spmv_rgs_frac": (path_bytes / (path_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]) if path_ms else None,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(agg["launches_total"]),
@@ -329,24 +426,71 @@ def run_ours(args) -> None:
                       "nlocked": info["nlocked"], "max_resid": info["max_resid"],
                       "max_est": info["max_est"], "host_dense_ms_per_step": agg["host_ms"] / args.steps,
                       "whitenings_per_step": agg["whitenings"] / args.steps,
+                      "max_rayleigh_vs_ritz": float(np.max(np.abs(rq - lam) / np.abs(lam))),
                       "kernel_ms_per_step": {c: breakdown[c]["ms"] for c in rks.KCLASSES},
+                      "kernel_launches_per_step": {c: breakdown[c]["launches"] for c in rks.KCLASSES},
                       "kernel_ms_note": "one untimed solve with every kernel timed; the timed solves "
                                         "time only " + dom}}
-    solver.close()
+
+    # the same configuration on the other GPU paths (one solve each), and the
+    # per-eigenpair error of this run against the plain FP64 GPU path
+    if rank == 0 and not args.no_extras:
+        paths = {}
+        for other in ("fp64", "df", "mixed"):
+            if other == prec:
+                continue
+            oinfo, olam, ores, orq, _, oms = _solve_once(rks, P, dev_arrays, stream.cuda_stream, other, keep,
+                                                         args.maxit)
+            paths[other] = {"ms": oms, "restarts": oinfo["restarts"], "nmatvec": oinfo["nmatvec"],
+                            "max_resid": oinfo["max_resid"]}
+            if other == "fp64":
+                errs = _pair_errors(lam, olam)
+                rqerr = _pair_errors(rq, orq)
+                line["eig_error_vs_fp64_gpu"] = {
+                    "per_pair_rel": errs, "max": max(errs), "rayleigh_max": max(rqerr),
+                    "note": ("|l - l_fp64| / |l_fp64| per wanted pair against the plain FP64 GPU solve of the "
+                             "same problem; both have resid <= 1e-8 ||A||_1, which fixes l only to the "
+                             "eigenvalue condition number times that")}
+        line["paths"] = paths
+        if args.workload == "convdiff3d_160":
+            line["eig_error_vs_oracle_small"] = _small_oracle_errors(rks, prec)
+            P2, u2 = _problem("convdiff2d_1000")
+            arrs2 = (torch.from_numpy(P2.A.rowptr).to(dev), torch.from_numpy(P2.A.colind).to(dev),
+                     torch.from_numpy(P2.A.vals).to(dev), torch.from_numpy(u2).to(dev))
+            i2, _, _, _, _, ms2 = _solve_once(rks, P2, arrs2, stream.cuda_stream, "fp64", P2.k, args.maxit)
+            line["convdiff2d_1000_fp64"] = {"ms": ms2, "restarts": i2["restarts"], "nmatvec": i2["nmatvec"],
+                                            "max_resid": i2["max_resid"]}
+            del arrs2
     if rank == 0 and not args.no_cpu_baseline:
-        s = cpu_sample(P, u1, restarts=1)
-        per = s["seconds"] / s["nmatvec"]
+        sampler = OracleSampler(P, u1)
+        smp = sampler.sample()
         line["cpu_baseline"] = {
-            "value": per * info["nmatvec"] * 1e3, "unit": "ms", "cores": os.cpu_count(),
-            "kind": "oracle",
-            "sample": (f"FP64 oracle (numpy/scipy, host cores) on the full problem: initial "
-                       f"expansion + 1 restart ({s['nmatvec']} products with A, "
-                       f"{s['seconds']:.1f} s), scaled to the {info['nmatvec']} products this "
-                       f"solve needed")}
+            "value": sampler.estimate_ms(smp, info["nmatvec"]), "unit": "ms", "cores": sampler.cores(),
+            "kind": "oracle", "sample": sampler.describe(smp, info["nmatvec"])}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _small_oracle_errors(rks, prec: str) -> dict:
+    """Per-eigenpair error of this path against the FP64 oracle on the same
+    operator family at 20^3 (n = 8000), where the oracle finishes in seconds."""
+    import numpy as np
+    from oracle import rks as R
+    from paper_2508_05400_gb300 import inputs as I
+    P = I.convdiff3d_problem(N=20, k=8, p=24, d=96)
+    u1 = I.start_vector(P.A.n, 1)
+    o = P.solver_opts()
+    with rks.Solver.from_csr(P.A, P.k, P.p, P.d, which=P.which, zeta=P.zeta, u1=u1, prec=prec, keep=P.k, **o) as s:
+        s.solve(allow_noconv=False)
+        lam, _, res = s.eigpairs(want_vectors=False)
+    ores = R.rks(P.A.to_scipy(), P.k, P.p, P.d, u1, zeta=P.zeta, seed=0, which=P.which, tol=o["tol"],
+                 eta_lock=o["eta_lock"], conv="norm1", keep=P.k)
+    errs = _pair_errors(lam[:P.k], ores.eigvals)
+    return {"workload": "convdiff3d_20 (n=8000, k=8, p=24, d=96, same field/convection recipe)",
+            "per_pair_rel": errs, "max": max(errs), "gpu_max_resid": float(res.max()),
+            "oracle_max_resid": float(ores.resid.max())}
 
 
 def main():
@@ -355,8 +499,12 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="convdiff3d_160", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other precision paths and the per-eigenpair error records")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--e2e-steps", type=int, default=2, help="solves in the end-to-end leg (mean reported)")
     ap.add_argument("--maxit", type=int, default=4000, help="restart limit of each solve")
     ap.add_argument("--ortho", default="sketch", choices=["sketch", "cgs2"],
                     help="sketch: randomized Gram-Schmidt (rKS); cgs2: the Krylov-Schur baseline "
@@ -366,8 +514,9 @@ def main():
                          "-1: k; 0: k - q as in Algorithm 1")
     ap.add_argument("--aggressive", action="store_true",
                     help="aggressive deflation: converged Schur blocks move to the front and lock")
-    ap.add_argument("--prec", default="df", choices=["df", "fp64", "mixed"],
-                    help="arithmetic of the n-dimensional work (see include/rks.h)")
+    ap.add_argument("--prec", default=None, choices=["df", "fp64", "mixed"],
+                    help="arithmetic of the n-dimensional work (see include/rks.h); default: the "
+                         "workload's (mixed for the 3D workload)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

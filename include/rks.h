@@ -131,6 +131,14 @@ typedef struct {
                           then lock as usual.  Needs lock = 1.  Nothing moves
                           if a swap is refused.  0 (default): only a leading
                           prefix of converged Schur vectors locks. */
+  int debug_stall;     /* test hook for the failure path: 1 makes every grid
+                          barrier of the cooperative least-squares kernel wait
+                          for one CTA more than the grid holds, so each wait
+                          runs out its short limit (about a millisecond), the
+                          kernel records the timeout and finishes, and
+                          rks_solve returns RKS_ETIMEOUT; the context's
+                          barrier state is reset and the device stays usable.
+                          0 (default): off. */
 } rks_opts;
 
 enum { RKS_ORTHO_SKETCH = 0, RKS_ORTHO_CGS2 = 1 };
@@ -233,6 +241,17 @@ int rks_nwanted(const rks_ctx* c);
  * pointer may be NULL. */
 int rks_get_eigpairs(rks_ctx* c, double* lam_re, double* lam_im, double* X, double* resid);
 
+/* Rayleigh quotients lambda_RQ,i = x_i^H A x_i / x_i^H x_i of the Ritz
+ * vectors x_i = U Y e_i returned by rks_get_eigpairs (the refined eigenvalue
+ * estimate that goes with the residual of Sec. 4.1), in the same order, nw
+ * values each (host).  x^H A x and x^H x are summed in FP64 on the device
+ * from the FP64 Ritz vector and the FP64 product A x (the pass that gives the
+ * residuals), per-CTA partial sums added on the host in CTA order.  For a
+ * conjugate pair the member with Im > 0 gets x^H A x / x^H x of its complex
+ * eigenvector and its partner the conjugate.  Either pointer may be NULL.
+ * Returns RKS_OK, RKS_EINVAL or RKS_ESTATE (no completed solve). */
+int rks_get_rayleigh(rks_ctx* c, double* rq_re, double* rq_im);
+
 /* Residual estimates |b^T y_i| / |lambda_i| (Eq. 4.8) of the last solve, in
  * the order of rks_get_eigpairs (nw values, host). */
 int rks_get_estimates(rks_ctx* c, double* est);
@@ -331,12 +350,15 @@ int rks_sketch_apply(int64_t n, int d, int zeta, uint64_t seed, const double* x,
  * word) lives in one fixed device array of RKS_NOALLOC_MAX_D + 1 doubles that
  * every GPU loading the library holds until the process exits; d larger than
  * RKS_NOALLOC_MAX_D returns RKS_EINVAL.  The first call on a device (with that
- * device current) looks up the array's device address; make that first call
- * before any stream capture.  All calls share the array: the sums are cleared
- * at the start of each call, and calls that overlap on the GPU (different
- * streams or host threads) race on it.  x: n doubles, z: d doubles, device
- * pointers; the call synchronises `stream` to read the status.  Returns
- * RKS_OK, RKS_EINVAL (arguments, or the hash draw cap reached) or RKS_ECUDA. */
+ * device current) looks up the array's device address and caches it for the
+ * process; the cached address is not valid after cudaDeviceReset.  All calls
+ * share the array: the sums are cleared at the start of each call, and calls
+ * that overlap on the GPU (different streams or host threads) race on it.
+ * x: n doubles, z: d doubles, device pointers of the current device; z must
+ * hold at least d doubles.  Every call copies a status word to the host and
+ * synchronises `stream`, so it must not be called while `stream` is being
+ * captured into a CUDA graph.  Returns RKS_OK, RKS_EINVAL (arguments, or the
+ * hash draw cap reached) or RKS_ECUDA. */
 int rks_sketch_apply_noalloc(int64_t n, int d, int zeta, uint64_t seed, const double* x, double* z,
                              void* stream);
 

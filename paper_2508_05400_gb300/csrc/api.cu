@@ -122,6 +122,7 @@ struct rks_ctx {
   int kk = 0;               // columns of the kept decomposition (locked + active)
   int nw = 0;               // reported Ritz pairs: the best k (k + 1 for a pair at the cut)
   std::vector<double> Tfull, bfull, lre, lim, est, resid;
+  std::vector<double> rq_re, rq_im;   // Rayleigh quotients x^H A x / x^H x of the Ritz vectors
   std::vector<double> hist;
   std::vector<int> hist_lock;
   std::vector<cd> Y;
@@ -237,7 +238,7 @@ void expand_df_launches(rks_ctx* c, int c0) {
     s = prof_begin(c, RKS_K_LS);
     const int nls = rks::launch_df_small(j, c->d, c->zscale, j > c0 ? 1 : 0, 1, c->s_raw, c->z_raw, c->S, c->S2,
                                          c->colscale, c->rprev, c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1,
-                                         c->M2, c->m + 1, c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream);
+                                         c->M2, c->m + 1, c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream, c->opts.debug_stall);
     prof_end(c, s, RKS_K_LS, nls, 3.0 * P * c->d * col, 6.0 * c->d * col);
     s = prof_begin(c, RKS_K_UPDATE);
     rks::launch_df_update_sketch(c->Ub, c->ldu, col, c->nrs, c->sj, c->tiles, c->part_s, c->f32, c->stream);
@@ -247,7 +248,7 @@ void expand_df_launches(rks_ctx* c, int c0) {
   int s = prof_begin(c, RKS_K_FINISH);
   const int nf = rks::launch_df_small(c->m, c->d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale,
                                       c->rprev, c->coef, c->m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->M2, c->m + 1,
-                                      c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream);
+                                      c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream, c->opts.debug_stall);
   prof_end(c, s, RKS_K_FINISH, nf, 3.0 * P * c->d, 2.0 * c->d);
 }
 
@@ -328,6 +329,13 @@ int expand(rks_ctx* c) {
   rc = read_flag(c, &f);
   if (rc) return rc;
   prof_flush(c);
+  if ((f & rks::RKS_FLAG_TIMEOUT) && c->bar) {
+    // a grid barrier gave up: its arrival count no longer matches the grid,
+    // so start the next cooperative launch from a clean state
+    CK(cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), c->stream));
+    CK(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
   rc = flag_status(f);
   if (rc) return rc;
   absorb_columns(c, c0, c->m);
@@ -791,10 +799,21 @@ int finalize(rks_ctx* c) {
     for (int g = 0; g < rg; ++g) sums[q] += part[(size_t)q * rg + g];
   prof_flush(c);
   c->resid.assign(nw, 0.0);
+  c->rq_re.assign(nw, 0.0);
+  c->rq_im.assign(nw, 0.0);
   for (int t = 0; t < np; ++t) {
-    double res = std::sqrt(sums[4 * t]) / (c->norm1 * std::sqrt(std::max(sums[4 * t + 1], 1e-300)));
+    const double xx = std::max(sums[4 * t + 1], 1e-300);
+    double res = std::sqrt(sums[4 * t]) / (c->norm1 * std::sqrt(xx));
     c->resid[col[t]] = res;
-    if (colim[t] >= 0) c->resid[colim[t]] = res;
+    // x^H A x / x^H x for x = X[:, col] + i X[:, colim] (the member with
+    // Im lambda > 0); its conjugate partner gets the conjugate quotient
+    c->rq_re[col[t]] = sums[4 * t + 2] / xx;
+    c->rq_im[col[t]] = colim[t] >= 0 ? sums[4 * t + 3] / xx : 0.0;
+    if (colim[t] >= 0) {
+      c->resid[colim[t]] = res;
+      c->rq_re[colim[t]] = c->rq_re[col[t]];
+      c->rq_im[colim[t]] = -c->rq_im[col[t]];
+    }
   }
   return RKS_OK;
 }
@@ -859,6 +878,7 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
   if (o.zeta == 0) o.zeta = 8;
   if (o.conv != RKS_CONV_EIG && o.conv != RKS_CONV_NORM1) return RKS_EINVAL;
   if (o.prec != RKS_PREC_DF && o.prec != RKS_PREC_FP64 && o.prec != RKS_PREC_MIXED) return RKS_EINVAL;
+  if (o.debug_stall != 0 && o.debug_stall != 1) return RKS_EINVAL;
   if (o.maxit <= 0) o.maxit = 1000;
   if (o.keep < 0 || o.keep > k) return RKS_EINVAL;
   if (o.aggressive != 0 && o.aggressive != 1) return RKS_EINVAL;
@@ -930,6 +950,16 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
     if (e != cudaSuccess) return fail(RKS_ECUDA);
     std::vector<double> colsum(n, 0.0);
     for (int64_t p = 0; p < c->nnz; ++p) colsum[ci[p]] += std::fabs(cv[p]);
+    if (c->prec != RKS_PREC_FP64) {
+      // the double-float and FP32 copies need every value inside the FP32
+      // exponent range: above FLT_MAX a value becomes inf, below FLT_MIN it
+      // loses significand bits silently
+      for (int64_t p = 0; p < c->nnz; ++p) {
+        const double a = std::fabs(cv[p]);
+        if (!std::isfinite(a)) return fail(RKS_ENAN);
+        if (a > 3.4028234663852886e38 || (a != 0.0 && a < 1.1754943508222875e-38)) return fail(RKS_EINVAL);
+      }
+    }
     // widest row: an ELLPACK copy for the SpMV when the padding stays small
     std::vector<int32_t> rp(n + 1);
     if (cudaMemcpyAsync(rp.data(), c->rowptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream) !=
@@ -1060,7 +1090,7 @@ static int run_alg1(rks_ctx* c, const double* start, int limit, double verify, i
       CK(cudaMemsetAsync(c->znorm, 0, sizeof(double), c->stream));
       const int nf = rks::launch_df_small(0, d, c->zscale, 1, 0, c->s_raw, c->z_raw, c->S, c->S2, c->colscale,
                                           c->rprev, c->coef, m + 1, c->znorm, c->nrs, c->sj, c->lsr1, c->M2, c->m + 1,
-                                          c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream);
+                                          c->part_z, c->part_s, c->tiles.G, c->flag, c->bar, c->stream, c->opts.debug_stall);
       prof_end(c, ps, RKS_K_OTHER, (src == c->tmp64 && !start ? 3 : 2) + nf, 0.0, 0.0);
     }
   } else {
@@ -1125,6 +1155,8 @@ static int solve_impl(rks_ctx* c) {
   c->evused = 0;
   c->hist.clear();
   c->hist_lock.clear();
+  c->rq_re.clear();
+  c->rq_im.clear();
   const int limit = c->opts.max_restarts > 0 ? std::min(c->opts.maxit, c->opts.max_restarts) : c->opts.maxit;
   const double tol0 = c->tol, eta0 = c->eta_lock;
   bool converged = false;
@@ -1244,6 +1276,14 @@ int rks_get_schur(rks_ctx* c, double* T, double* U, double* b) {
                          c->opts.mem_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
+  return RKS_OK;
+}
+
+int rks_get_rayleigh(rks_ctx* c, double* rq_re, double* rq_im) {
+  if (!c) return RKS_EINVAL;
+  if (!c->solved || c->kk == 0 || c->rq_re.size() != (size_t)c->nw) return RKS_ESTATE;
+  if (rq_re) std::memcpy(rq_re, c->rq_re.data(), sizeof(double) * c->nw);
+  if (rq_im) std::memcpy(rq_im, c->rq_im.data(), sizeof(double) * c->nw);
   return RKS_OK;
 }
 

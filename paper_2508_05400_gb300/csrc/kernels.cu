@@ -24,6 +24,8 @@
 // into a global d-vector with one atomic add per bin; the 1/sqrt(zeta) scale
 // is applied by the consumers of the sums.
 
+#include <mutex>
+
 #include "rks_impl.h"
 
 namespace rks {
@@ -494,9 +496,22 @@ void launch_start_vector(int64_t n, uint64_t seed, double* x, cudaStream_t st) {
 
 // Opt every kernel with dynamic shared memory into the large carve-out
 // (sketch bins of up to d = 8192 doubles, restart product tiles).
-cudaError_t configure_kernels() {
-  static bool done = false;
-  if (done) return cudaSuccess;
+cudaError_t once_per_device(int slot, cudaError_t (*f)()) {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static bool done[kCfgSlots][kMaxDev] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (slot < 0 || slot >= kCfgSlots || dev < 0 || dev >= kMaxDev) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[slot][dev]) return cudaSuccess;
+  e = f();
+  if (e == cudaSuccess) done[slot][dev] = true;
+  return e;
+}
+
+static cudaError_t configure_kernels_once() {
   const int big = 200 * 1024;
   cudaError_t e = cudaSuccess;
 #define RKS_SMEM(f) if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
@@ -505,9 +520,10 @@ cudaError_t configure_kernels() {
   RKS_SMEM(k_update_sketch<4>); RKS_SMEM(k_update_sketch<8>); RKS_SMEM(k_update_sketch<16>);
   RKS_SMEM(k_rows_gemm);
 #undef RKS_SMEM
-  if (e == cudaSuccess) done = true;
   return e;
 }
+
+cudaError_t configure_kernels() { return once_per_device(kCfgBase, configure_kernels_once); }
 
 int rows_gemm_smem(int nin, int nout, int threads) {
   return (int)(((size_t)nin * nout + (size_t)threads * nout) * sizeof(double));

@@ -911,7 +911,7 @@ __global__ void __launch_bounds__(256) k_df_ls_gram(int j, const float2* __restr
 // and the host reports the failure instead of the device hanging.  The
 // cooperative launch guarantees that all CTAs are resident, so the bound is
 // never reached in a correct run.
-__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, int* flag) {
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, int* flag, long long limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vgen = bar + 1;
@@ -925,7 +925,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, in
     } else {
       const long long t0 = clock64();
       while (*vgen == gen) {
-        if (clock64() - t0 > 4000000000ll) { atomicOr(flag, RKS_FLAG_TIMEOUT); break; }
+        if (clock64() - t0 > limit) { atomicOr(flag, RKS_FLAG_TIMEOUT); break; }
         __nanosleep(32);
       }
     }
@@ -949,7 +949,8 @@ __global__ void __launch_bounds__(256) k_df_ls_coop(
     double* __restrict__ S64, float2* __restrict__ S2, double* __restrict__ colscale, double* __restrict__ rprev,
     double* __restrict__ coef, int ldcoef, double* __restrict__ znorm_prev, float2* __restrict__ nrs,
     float2* __restrict__ sj, float2* __restrict__ r1, float2* __restrict__ M2, int ldm,
-    const double* __restrict__ part_z, const double* __restrict__ part_s, int G, unsigned* bar, int* flag) {
+    const double* __restrict__ part_z, const double* __restrict__ part_s, int G, unsigned* bar, int* flag,
+    int stall) {
   extern __shared__ float2 zd[];   // d: z; d: s_j (when finishing); then 2d doubles: z_raw, s_raw
   float2* sjd = zd + d;
   double* zst = reinterpret_cast<double*>(sjd + d);
@@ -958,6 +959,10 @@ __global__ void __launch_bounds__(256) k_df_ls_coop(
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   const int gw = blockIdx.x * nw + warp, tw = gridDim.x * nw;   // global warp index, warps in grid
   const int c = j + 1;
+  // stall (a test hook) waits for one CTA more than the grid holds, so every
+  // barrier runs out its short limit and the solve reports RKS_ETIMEOUT
+  const unsigned expect = gridDim.x + (stall ? 1u : 0u);
+  const long long limit = stall ? 2000000ll : 4000000000ll;
   const bool stage = d <= kLsStageMax;
   // prefetch (independent of the fold): this warp's first column
   const int col0 = gw;
@@ -994,7 +999,7 @@ __global__ void __launch_bounds__(256) k_df_ls_coop(
         else s_raw[r - d] = v;
       }
     }
-    grid_barrier(bar, gridDim.x, flag);
+    grid_barrier(bar, expect, flag, limit);
   }
   // z_raw and s_raw in one round trip
   const double cs_j = finish ? 0.0 : colscale[j];
@@ -1077,7 +1082,7 @@ __global__ void __launch_bounds__(256) k_df_ls_coop(
       ls_phase_a(col, j, d, finish, 1, S2, zd, sjd, r1, M2, ldm, lane);
     }
   }
-  grid_barrier(bar, gridDim.x, flag);
+  grid_barrier(bar, expect, flag, limit);
   // phase B
   if (blockIdx.x == 0 && tid == 0) { sj[0] = df_from_double(scj); znorm_prev[0] = sqrt(zz); }
   for (int col = gw; col < c; col += tw) {
@@ -1272,9 +1277,7 @@ static int df_grid(int64_t n, int threads) {
   return (int)g;
 }
 
-cudaError_t configure_df_kernels() {
-  static bool done = false;
-  if (done) return cudaSuccess;
+static cudaError_t configure_df_kernels_once() {
   const int big = 200 * 1024;
   cudaError_t e = cudaSuccess;
 #define RKS_SMEM(f) if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
@@ -1296,9 +1299,10 @@ cudaError_t configure_df_kernels() {
   RKS_SMEM((k_df_restart<float2, 4>)); RKS_SMEM((k_df_restart<float2, 8>)); RKS_SMEM((k_df_restart<float2, 16>));
   RKS_SMEM((k_df_restart<float, 4>)); RKS_SMEM((k_df_restart<float, 8>)); RKS_SMEM((k_df_restart<float, 16>));
 #undef RKS_SMEM
-  if (e == cudaSuccess) done = true;
   return e;
 }
+
+cudaError_t configure_df_kernels() { return once_per_device(kCfgDf, configure_df_kernels_once); }
 
 int df_small_smem(int d, int c) { return (int)((size_t)2 * d * sizeof(float2)); }
 int df_gemm_smem(int nin, int nout) { return (int)(((size_t)nin * nout + (size_t)128 * nout) * sizeof(float2)); }
@@ -1393,7 +1397,7 @@ void launch_df_update_sketch(void* U, int64_t ldu, int c, const float2* nrs, con
 int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_raw, double* z_raw, double* S64,
                     float2* S2, double* colscale, double* rprev, double* coef, int ldcoef, double* znorm_prev,
                     float2* nrs, float2* sj, float2* r1, float2* M2, int ldm, const double* part_z,
-                    const double* part_s, int G, int* flag, unsigned* bar, cudaStream_t st) {
+                    const double* part_s, int G, int* flag, unsigned* bar, cudaStream_t st, int stall) {
   const size_t sm = (size_t)2 * d * sizeof(float2);
   const size_t sm_coop = sm + (d <= kLsStageMax ? (size_t)2 * d * sizeof(double) : 0);
   const int c = j + 1;
@@ -1409,7 +1413,7 @@ int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_r
     // launch (the fold of a row is the same whichever warp does it)
     if (G < 152) g = std::min((std::max(c, d) + 7) / 8, 48);
     void* args[] = {&j, &d, &zscale, &finish, &s_raw, &z_raw, &S64, &S2, &colscale, &rprev, &coef, &ldcoef,
-                    &znorm_prev, &nrs, &sj, &r1, &M2, &ldm, &part_z, &part_s, &G, &bar, &flag};
+                    &znorm_prev, &nrs, &sj, &r1, &M2, &ldm, &part_z, &part_s, &G, &bar, &flag, &stall};
     if (cudaLaunchCooperativeKernel((const void*)k_df_ls_coop, dim3(g), dim3(256), args, sm_coop, st) == cudaSuccess)
       return 1;
     (void)cudaGetLastError();   // not available: fall back to the kernels below

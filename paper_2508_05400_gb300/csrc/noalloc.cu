@@ -9,7 +9,8 @@
 //
 // The array is a host-side symbol: host code must not pass its name to a
 // kernel.  On the first call on each device (with that device current) the
-// device address is resolved once with cudaGetSymbolAddress and cached.
+// device address is resolved once with cudaGetSymbolAddress and cached for
+// the process (a cudaDeviceReset invalidates it).
 
 #include <cuda_runtime.h>
 

@@ -608,15 +608,14 @@ void launch_tc_restart_df(int64_t n, const float2* in, float2* out, int64_t ldu,
                                              fexp, pexp, rexp, mvsrc, mvdst, tcols, flag);
 }
 
-cudaError_t configure_tc_kernels() {
-  static bool done = false;
-  if (done) return cudaSuccess;
+static cudaError_t configure_tc_kernels_once() {
   cudaError_t e = cudaFuncSetAttribute(k_tc_restart_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tc_restart_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcDfSmemMax);
-  if (e == cudaSuccess) done = true;
   return e;
 }
+
+cudaError_t configure_tc_kernels() { return once_per_device(kCfgTc, configure_tc_kernels_once); }
 
 void launch_tc_restart_f32(int64_t n, const float* in, float* out, int64_t ldu, int nin, int nout, const void* bimg,
                            const float* mvsrc, float* mvdst, int* flag, cudaStream_t st) {

@@ -77,7 +77,7 @@ void launch_df_update_sketch(void* U, int64_t ldu, int c, const float2* nrs, con
 int launch_df_small(int j, int d, double zscale, int finish, int ls, double* s_raw, double* z_raw, double* S64,
                     float2* S2, double* colscale, double* rprev, double* coef, int ldcoef, double* znorm_prev,
                     float2* nrs, float2* sj, float2* r1, float2* M2, int ldm, const double* part_z,
-                    const double* part_s, int G, int* flag, unsigned* bar, cudaStream_t st);
+                    const double* part_s, int G, int* flag, unsigned* bar, cudaStream_t st, int stall = 0);
 // Krylov-Schur baseline with Euclidean CGS2 (no sketch), DF basis.
 void launch_df_spmv(const CsrDF& A, const void* x, void* w, const SketchTiles& t, cudaStream_t st);
 void launch_df_update_plain(void* U, int64_t ldu, int c, const float2* nrs, const float2* sj, const SketchTiles& t,
@@ -139,6 +139,12 @@ void launch_start_finish(int d, double zscale, double* s_raw, double* S, double*
                          cudaStream_t st);
 void launch_start_vector(int64_t n, uint64_t seed, double* x, cudaStream_t st);
 cudaError_t configure_kernels();
+// Run f() once per CUDA device (the device current at the call), safe to call
+// from several host threads: slot names the configuration; a failure is
+// returned and f() retried at the next call.  The record is per process and
+// is not reset by cudaDeviceReset.
+enum { kCfgBase = 0, kCfgDf = 1, kCfgTc = 2, kCfgSlots = 3 };
+cudaError_t once_per_device(int slot, cudaError_t (*f)());
 int rows_gemm_smem(int nin, int nout, int threads);
 void launch_rows_gemm(int64_t n, const double* A, int64_t lda, int a0, int nin, const double* B, int nout,
                       double* C, int64_t ldc, int c0, int move_src, cudaStream_t st);

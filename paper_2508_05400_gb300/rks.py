@@ -33,7 +33,8 @@ class Opts(C.Structure):
                 ("stream", C.c_void_p), ("u1", C.c_void_p), ("eta_lock", C.c_double),
                 ("max_restarts", C.c_int), ("profile", C.c_int), ("conv", C.c_int),
                 ("prec", C.c_int), ("mixed_tol", C.c_double), ("verify", C.c_double), ("keep", C.c_int), ("ortho", C.c_int),
-                ("tc_restart", C.c_int), ("aggressive", C.c_int)]
+                ("tc_restart", C.c_int), ("aggressive", C.c_int),
+                ("debug_stall", C.c_int)]
 
 
 CONV = {"eig": 0, "norm1": 1}
@@ -103,6 +104,8 @@ def lib() -> C.CDLL:
         L.rks_get_eigpairs.argtypes = [_P, _P, _P, _P, _P]
         L.rks_get_eigpairs.restype = C.c_int
         L.rks_get_estimates.argtypes = [_P, _P]
+        L.rks_get_rayleigh.argtypes = [_P, _P, _P]
+        L.rks_get_rayleigh.restype = C.c_int
         L.rks_get_estimates.restype = C.c_int
         L.rks_get_krylov.argtypes = [_P, C.POINTER(C.c_int), _P, _P, _P]
         L.rks_get_krylov.restype = C.c_int
@@ -193,7 +196,7 @@ class Solver:
                  zeta=8, maxit=1000, lock=True, u1=None, eta_lock=0.0, max_restarts=0,
                  device=False, stream=None, profile=False, conv="eig", verify=0.0, prec="df",
                  mixed_tol=0.0, keep=0, ortho="sketch", tc_restart=True,
-                 aggressive=False):
+                 aggressive=False, debug_stall=0):
         L = lib()
         self.n, self.k, self.p, self.d = int(n), int(k), int(p), int(d)
         self.device = bool(device)
@@ -226,6 +229,7 @@ class Solver:
         o.ortho = ORTHO[ortho]
         o.tc_restart = int(bool(tc_restart))
         o.aggressive = int(bool(aggressive))
+        o.debug_stall = int(debug_stall)
         h = _P()
         _check(L.rks_create(C.byref(h), self.n, _ptr(rowptr), _ptr(colind), _ptr(vals), vdt,
                             self.k, self.p, self.d, WHICH[which] if isinstance(which, str) else int(which),
@@ -289,6 +293,13 @@ class Solver:
         _check(lib().rks_get_eigpairs(self._h, lre.ctypes.data, lim.ctypes.data, _ptr(X),
                                       res.ctypes.data), "rks_get_eigpairs")
         return lre + 1j * lim, X, res
+
+    def rayleigh(self) -> np.ndarray:
+        """Rayleigh quotients x^H A x / x^H x of the returned Ritz vectors (complex[nw])."""
+        nw = self.nwanted
+        re, im = np.zeros(nw), np.zeros(nw)
+        _check(lib().rks_get_rayleigh(self._h, re.ctypes.data, im.ctypes.data), "rks_get_rayleigh")
+        return re + 1j * im
 
     def estimates(self) -> np.ndarray:
         e = np.zeros(self.nwanted)
@@ -370,10 +381,28 @@ def sketch_apply_noalloc(x, z, d: int, zeta: int, seed: int) -> int:
     """z = Omega x through the allocation-free entry point (x, z: CUDA float64 tensors).
 
     For callers that cannot allocate device memory; returns the status code.
+    x and z must be contiguous float64 tensors on the same CUDA device and z
+    must hold at least d values: the entry point writes d values into z
+    without knowing its size, so these are checked here (ValueError) before
+    anything runs.
     """
     import torch
-    stream = torch.cuda.current_stream().cuda_stream
-    return lib().rks_sketch_apply_noalloc(x.numel(), d, zeta, seed, x.data_ptr(), z.data_ptr(), stream)
+    for name, t in (("x", x), ("z", z)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if z.numel() < d:
+        raise ValueError(f"z holds {z.numel()} values, fewer than d = {d}")
+    if x.device != z.device:
+        raise ValueError(f"x and z are on different devices ({x.device}, {z.device})")
+    if not x.is_cuda:
+        raise ValueError("x and z must be CUDA tensors")
+    with torch.cuda.device(x.device):
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+        return lib().rks_sketch_apply_noalloc(x.numel(), d, zeta, seed, x.data_ptr(), z.data_ptr(), stream)
 
 
 def basis_product_f32(U, ldu: int, n: int, nin: int, Q: np.ndarray, out) -> None:

@@ -216,3 +216,24 @@ def test_binding_constants_match_the_header():
         body = re.search(r"typedef struct \{([^{}]*)\} %s;" % cname, hdr).group(1)
         fields = re.findall(r"(\w+)(?:\[\w+\])?;", body)
         assert fields == [f for f, _ in py._fields_], cname
+
+
+def test_noalloc_binding_rejects_bad_buffers_before_any_call(monkeypatch):
+    # the allocation-free sketch writes d values into z without knowing its
+    # size: the binding checks z's size, the dtypes, contiguity and devices
+    # before anything reaches the library (no GPU needed to see it)
+    torch = pytest.importorskip("torch")
+    from paper_2508_05400_gb300 import rks
+
+    def never(*a):
+        raise AssertionError("the library was called")
+    monkeypatch.setattr(rks, "lib", never)
+    x = torch.zeros(1000, dtype=torch.float64)
+    for z, msg in ((torch.zeros(79, dtype=torch.float64), "fewer than d"),
+                   (torch.zeros(80, dtype=torch.float32), "float64"),
+                   (torch.zeros(160, dtype=torch.float64)[::2], "contiguous"),
+                   (torch.zeros(80, dtype=torch.float64), "CUDA")):
+        with pytest.raises(ValueError, match=msg):
+            rks.sketch_apply_noalloc(x, z, 80, 4, 0)
+    with pytest.raises(ValueError, match="float64"):
+        rks.sketch_apply_noalloc(x.float(), torch.zeros(80, dtype=torch.float64), 80, 4, 0)
