@@ -404,19 +404,29 @@ int rks_basis_product_df(int64_t n, const double* U, int64_t ldu, int nin, const
  *                   Omega K = Q_s R, Q = K R^{-1}: Omega Q orthonormal.
  *   RKS_QR_RCHOLQR  randomized Cholesky QR: whiten, then Cholesky QR of the
  *                   whitened block: Q orthonormal in the Euclidean sense.
+ *   RKS_QR_RHQR     randomized Householder QR: Householder QR carried out in
+ *                   the sketched space of Theta = [[I_s, 0], [0, Omega']],
+ *                   where rows 0..s-1 are kept exactly and Omega' is the
+ *                   sparse-sign embedding of dimension n - s for (d, zeta,
+ *                   seed) on rows s..n-1; each reflector
+ *                   H_j = I - beta_j u_j (Theta u_j)^T Theta is applied to the
+ *                   columns, Q = H_0 ... H_{s-1} [I_s; 0]: Theta Q
+ *                   orthonormal, stable for ill-conditioned K.
  * RGS and WHITEN compute the same (unique) factorisation in exact
- * arithmetic, RCHOLQR the Euclidean QR of K.  Omega is the solver's
+ * arithmetic, RHQR the same with Theta in place of Omega, RCHOLQR the
+ * Euclidean QR of K.  Omega is the solver's
  * sparse-sign embedding for (n, d, zeta, seed).  The n-dimensional work runs
  * in double-float arithmetic on the device, the d x s and s x s work in FP64
  * on the host. */
-enum { RKS_QR_RGS = 0, RKS_QR_WHITEN = 1, RKS_QR_RCHOLQR = 2 };
+enum { RKS_QR_RGS = 0, RKS_QR_WHITEN = 1, RKS_QR_RCHOLQR = 2, RKS_QR_RHQR = 3 };
 #define RKS_SKETCH_QR_MAX_S 192
 
 /* K, Q: device FP64, column-major n x s with leading dimensions ldk, ldq >= n
  * (Q may be K, with ldq = ldk).  R: host s x s (column-major, ld s), written
  * with zeros below the diagonal.  S: host d x s or NULL; receives Omega Q
  * (measured by sketching the computed Q; for RGS the sketches the process
- * computed).  1 <= s <= min(RKS_SKETCH_QR_MAX_S, d, n), 1 <= zeta <= 16,
+ * computed; for RHQR Omega' Q[s:, :], the sketched rows of Theta Q, whose
+ * other rows are Q's first s rows).  RHQR needs n - s >= 2.  1 <= s <= min(RKS_SKETCH_QR_MAX_S, d, n), 1 <= zeta <= 16,
  * 2 zeta <= d <= 8192.  Work buffers (about 16 n s bytes) are allocated and
  * freed by the call; it runs on `stream` and synchronises it.  Returns
  * RKS_OK, RKS_EINVAL, RKS_ENOMEM, RKS_ECUDA, RKS_EBREAKDOWN (a zero or
@@ -424,6 +434,70 @@ enum { RKS_QR_RGS = 0, RKS_QR_WHITEN = 1, RKS_QR_RCHOLQR = 2 };
  * Gram matrix is not positive definite). */
 int rks_sketch_qr(int64_t n, int s, const double* K, int64_t ldk, int d, int zeta, uint64_t seed, int method,
                   double* Q, int64_t ldq, double* R, double* S, void* stream);
+
+/* ---- Learned start vector for a parametric operator family ----------- */
+
+/* The start vector u_1 of Algorithm 1 is drawn at random in the paper
+ * (Sec. 2.1: it only needs components along the wanted eigenvectors).  For a
+ * family of operators whose coefficient fields are known on an H x W grid
+ * (the 2D convection-diffusion family: log nu, bx / 50, by / 50 as three
+ * channels, channel-major, x fastest), a small network maps the fields to a
+ * start vector close to the wanted invariant subspace.  It is a 4-level
+ * U-Net: 15 3x3 convolutions (zero padding) of 32 channels (3 in, 1 out),
+ * ReLU, 2x2 average pooling, 2x nearest upsampling, additive skip
+ * connections; FP16 weights with FP32 masters, FP32 activations and
+ * accumulation.  It is trained with the subspace-capture loss
+ * L = 1 - ||Q^T u||^2 / ||u||^2, Q (n x q, n = H W) an orthonormal basis of
+ * the wanted Schur vectors a solve of that operator returned (rks_get_schur),
+ * by Adam.  A caller keeps a random component in the start vector and the
+ * random start as the fallback; the residual of the solve judges it.
+ * Parameters are one flat FP32 vector: for l = 1..15, W_l (cout x cin x 3 x 3,
+ * row-major) then b_l (cout).  All device pointers are of the current device;
+ * the calls run on the stream given at creation and synchronise it. */
+typedef struct rks_ws rks_ws;
+
+/* Number of parameters (121 409). */
+int64_t rks_ws_nparams(void);
+
+/* A network for H x W grids (H, W multiples of 8, H W <= 2^26) with He-normal
+ * weights from SplitMix64(seed) and zero biases.  stream: cudaStream_t or
+ * NULL (the network creates one).  Returns RKS_OK, RKS_EINVAL, RKS_ENOMEM or
+ * RKS_ECUDA; on error *out is NULL. */
+int rks_ws_create(rks_ws** out, int H, int W, uint64_t seed, void* stream);
+
+/* Copy the FP32 master parameters to / from a host array of rks_ws_nparams
+ * floats; set also clears the optimiser state and the accumulated gradient. */
+int rks_ws_get_params(const rks_ws* s, float* theta);
+int rks_ws_set_params(rks_ws* s, const float* theta);
+
+/* u (device, H W floats) = the network applied to x (device, 3 x H x W). */
+int rks_ws_forward(rks_ws* s, const float* x, float* u);
+
+/* Forward, loss and backward for one sample: x (device, 3 x H x W), Q
+ * (device FP32, n x q column-major, orthonormal columns, 1 <= q <= 64).  The
+ * gradient of L is added to the network's accumulator; *loss (may be NULL)
+ * receives L.  Returns RKS_ENAN if u = 0. */
+int rks_ws_accumulate(rks_ws* s, const float* x, const float* Q, int q, double* loss);
+
+/* The accumulated gradient (host, rks_ws_nparams floats); clear it. */
+int rks_ws_get_grad(const rks_ws* s, float* grad);
+int rks_ws_zero_grad(rks_ws* s);
+
+/* One Adam step (beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected)
+ * with the mean of the gradients accumulated since the last step, which are
+ * then cleared.  RKS_ESTATE if nothing was accumulated. */
+int rks_ws_adam_step(rks_ws* s, float lr);
+
+/* The start vector for rks_create's opts.u1: u1 (device, H W doubles) =
+ * u / ||u|| + eps g / ||g||, u the network's output for x (device,
+ * 3 x H x W) and g the solver's own random start (N(0,1) entries from
+ * SplitMix64(seed) and Box-Muller, as rks_create draws it from seed + 1):
+ * the random component (eps, e.g. 1e-3) keeps every wanted direction present
+ * whatever the network returns.  Norms in FP64.  RKS_ENAN if u = 0. */
+int rks_ws_start_vector(rks_ws* s, const float* x, double eps, uint64_t seed, double* u1);
+
+/* Free the network.  Safe on NULL. */
+void rks_ws_destroy(rks_ws* s);
 
 /* ---- Host-side small dense FP64 steps (Algorithm 1 contraction) ------ */
 

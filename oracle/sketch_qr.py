@@ -18,16 +18,29 @@ triangular:
   of the well-conditioned Q_1: Q_1^T Q_1 = R_2^T R_2, Q = Q_1 R_2^{-1},
   R = R_2 R_1.  Q is orthonormal (Euclidean).
 
+* RHQR, randomized Householder QR: Householder QR carried out in the
+  sketched space of Theta = [[I_s, 0], [0, Omega']] (the first s rows kept
+  exactly, the other n - s sketched by Omega').  For column j the reflector
+  of the sketched column y = Theta x (entries above j dropped) is
+  v = y - rho e_j, rho = -sign(y_j) ||y||, beta = 2 / v^T v; its n-dimensional
+  counterpart u (x with entries above j dropped and rho taken off entry j)
+  has Theta u = v, and H_j = I - beta u (Theta u)^T Theta satisfies
+  Theta H_j = (I - beta v v^T) Theta.  H_j is applied to the later columns,
+  R[:j, j] = y[:j], R[j, j] = rho, and Q = H_0 ... H_{s-1} [I_s; 0]
+  (accumulated backwards).  Theta Q is orthonormal.
+
 A sketch-orthonormal factorisation K = Q R with R upper triangular and a
 positive diagonal is unique (R is the R factor of Omega K), so RGS and sketch
-and whiten compute the same Q and R in exact arithmetic; randomized Cholesky
-QR computes the Euclidean QR factorisation of K.  The tests pin each function
-against the other and against LAPACK's QR.
+and whiten compute the same Q and R in exact arithmetic, and RHQR the same as
+both with Omega = Theta; randomized Cholesky QR computes the Euclidean QR
+factorisation of K.  With Omega' = I (Theta = I) RHQR is Householder QR.  The
+tests pin each function against the others and against LAPACK's QR.
 """
 from __future__ import annotations
 
 import numpy as np
 import scipy.linalg as sla
+import scipy.sparse as sp
 
 
 def _positive_qr(X: np.ndarray):
@@ -73,3 +86,53 @@ def rcholqr(K: np.ndarray, Omega) -> tuple[np.ndarray, np.ndarray]:
     R2 = np.linalg.cholesky(Q1.T @ Q1).T                 # upper, positive diagonal
     Q = sla.solve_triangular(R2, Q1.T, trans="T", lower=False).T
     return Q, R2 @ R1
+
+
+def theta_matrix(n: int, s: int, Omega_bottom):
+    """Theta = [[I_s, 0], [0, Omega']] ((s + d) x n) for RHQR."""
+    return sp.block_diag([sp.identity(s, format="csr"), sp.csr_matrix(Omega_bottom)], format="csr")
+
+
+def rhqr(K: np.ndarray, Omega_bottom) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Randomized Householder QR with Theta = [[I_s, 0], [0, Omega_bottom]].
+
+    Returns Q (n x s), R (s x s, positive diagonal) and Theta Q ((s + d) x s).
+    The reflectors are applied to the n-dimensional columns themselves; their
+    coefficients come from the sketched columns Theta x.
+    """
+    K = np.array(K, dtype=np.float64)
+    n, s = K.shape
+    Th = theta_matrix(n, s, Omega_bottom)
+    X = K.copy()
+    Us, Vs, betas = [], [], []
+    R = np.zeros((s, s))
+    for j in range(s):
+        x = X[:, j]
+        y = Th @ x                                   # sketched column
+        yv = y.copy()
+        yv[:j] = 0.0
+        nrm = np.linalg.norm(yv)
+        rho = -nrm if yv[j] >= 0 else nrm            # rho = -sign(y_j) ||y||
+        v = yv.copy()
+        v[j] -= rho                                  # v = y - rho e_j
+        u = x.copy()
+        u[:j] = 0.0
+        u[j] -= rho                                  # Theta u = v
+        beta = 2.0 / (v @ v)
+        R[:j, j] = y[:j]
+        R[j, j] = rho
+        for l in range(j + 1, s):                    # H_j applied to the later columns
+            X[:, l] -= beta * (v @ (Th @ X[:, l])) * u
+        Us.append(u)
+        Vs.append(v)
+        betas.append(beta)
+    Q = np.zeros((n, s))
+    Q[np.arange(s), np.arange(s)] = 1.0              # [I_s; 0]
+    for j in range(s - 1, -1, -1):                   # Q = H_0 ... H_{s-1} [I_s; 0]
+        c = betas[j] * (Vs[j] @ (Th @ Q))
+        Q -= np.outer(Us[j], c)
+    sgn = np.sign(np.diag(R))
+    sgn[sgn == 0] = 1.0
+    Q = Q * sgn
+    R = (R.T * sgn).T
+    return Q, R, Th @ Q

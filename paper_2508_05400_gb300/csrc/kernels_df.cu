@@ -1159,6 +1159,22 @@ __global__ void __launch_bounds__(512) k_df_sketch_vec(const TU* __restrict__ x,
   tile_write_part(acc, d, part);
 }
 
+// U[i, c0 + l] -= coef[l] * U[i, src] for l < ncols (double-float): one
+// reflector applied to a block of columns (randomized Householder QR).
+__global__ void __launch_bounds__(256) k_df_axpy_cols(int64_t n, float2* __restrict__ U, int64_t ldu, int src,
+                                                      int c0, int ncols, const float2* __restrict__ coef) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 u = U[i + (int64_t)src * ldu];
+    for (int l = 0; l < ncols; ++l) {
+      float2* y = U + i + (int64_t)(c0 + l) * ldu;
+      const float2 yv = *y, c = coef[l];
+      float sh = yv.x, sl = yv.y;
+      df_mac(-c.x, -c.y, u.x, u.y, sh, sl);
+      *y = df_norm(sh, sl);
+    }
+  }
+}
+
 // Row-blocked DF product, in place: U[i, c0 + o] = sum_l U[i, a0 + l] Q[l, o]
 // (Q DF, nin x nout column-major), then U[i, c0 + nout] = U[i, move_src].
 template <class TU>
@@ -1453,6 +1469,13 @@ void launch_df2d_cols(int64_t n, const void* x, int64_t ldx, double* y, int64_t 
   dim3 grid((unsigned)df_grid(n, 256), (unsigned)ncols);
   if (f32) k_df2d_cols<float><<<grid, 256, 0, st>>>(n, static_cast<const float*>(x), ldx, y, ldy, ncols);
   else k_df2d_cols<float2><<<grid, 256, 0, st>>>(n, static_cast<const float2*>(x), ldx, y, ldy, ncols);
+}
+
+void launch_df_axpy_cols(int64_t n, float2* U, int64_t ldu, int src, int c0, int ncols, const float2* coef,
+                         cudaStream_t st) {
+  if (ncols <= 0) return;
+  const int g = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  k_df_axpy_cols<<<g, 256, 0, st>>>(n, U, ldu, src, c0, ncols, coef);
 }
 
 void launch_df_sketch_vec(const void* x, const SketchTiles& t, double* part, bool f32, cudaStream_t st) {

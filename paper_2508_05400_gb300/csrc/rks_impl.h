@@ -85,6 +85,9 @@ void launch_df_update_plain(void* U, int64_t ldu, int c, const float2* nrs, cons
 void launch_df_dots(const void* U, int64_t ldu, int c, int cv, const SketchTiles& t, double* part, cudaStream_t st);
 // out[r] = sum over g < G of part[g * d + r] in a fixed order (r < d)
 void launch_df_fold(const double* part, int d, int G, double* out, cudaStream_t st);
+// U[:, c0 + l] -= coef[l] * U[:, src], l < ncols (double-float columns, coef device)
+void launch_df_axpy_cols(int64_t n, float2* U, int64_t ldu, int src, int c0, int ncols, const float2* coef,
+                         cudaStream_t st);
 void launch_ks_coef(int pass, int j, int c, int G, const double* part, const double* colscale, double* rprev,
                     float2* nrs, float2* sj, cudaStream_t st);
 void launch_ks_finish(int j, int G, const double* part, double thr, double* colscale,
@@ -143,7 +146,7 @@ cudaError_t configure_kernels();
 // from several host threads: slot names the configuration; a failure is
 // returned and f() retried at the next call.  The record is per process and
 // is not reset by cudaDeviceReset.
-enum { kCfgBase = 0, kCfgDf = 1, kCfgTc = 2, kCfgSlots = 3 };
+enum { kCfgBase = 0, kCfgDf = 1, kCfgTc = 2, kCfgWs = 3, kCfgSlots = 4 };
 cudaError_t once_per_device(int slot, cudaError_t (*f)());
 int rows_gemm_smem(int nin, int nout, int threads);
 void launch_rows_gemm(int64_t n, const double* A, int64_t lda, int a0, int nin, const double* B, int nout,

@@ -16,6 +16,11 @@
 //  * RKS_QR_RCHOLQR: randomized Cholesky QR: Q_1 = K R_1^{-1} as above, the
 //    Gram matrix Q_1^T Q_1 (double-float dot kernel), its Cholesky factor R_2,
 //    Q = Q_1 R_2^{-1}, R = R_2 R_1: a Euclidean-orthonormal Q.
+//  * RKS_QR_RHQR: randomized Householder QR: Householder QR of the sketched
+//    block Theta K, Theta = [[I_s, 0], [0, Omega']] (rows 0..s-1 kept,
+//    Omega' the embedding of dimension n - s on the others), on the host,
+//    with every reflector applied to the double-float columns on the device
+//    and Q accumulated from the reflectors: Theta Q orthonormal.
 //
 // Omega is the solver's sparse-sign embedding (SplitMix64 hash, zeta rows per
 // column, values +-1/sqrt(zeta)), applied through the deterministic per-tile
@@ -79,29 +84,30 @@ struct QrWork {
     if ((x) != cudaSuccess) return RKS_ECUDA;   \
   } while (0)
 
-int setup(QrWork& w, int64_t n, int s, int d, int zeta, uint64_t seed, cudaStream_t st) {
+// nsk: rows the sketch covers (n, or n - s for RHQR's Omega' on rows s..n-1)
+int setup(QrWork& w, int64_t n, int s, int d, int zeta, uint64_t seed, cudaStream_t st, int64_t nsk) {
   w.n = n; w.s = s; w.d = d; w.zeta = zeta; w.st = st;
   w.zscale = 1.0 / std::sqrt((double)zeta);
   w.ldu = (n + 31) / 32 * 32;
   const int wide = std::max(d, s);
   if (cudaMalloc(&w.U, (size_t)w.ldu * 2 * s * sizeof(float2)) != cudaSuccess ||
-      cudaMalloc(&w.otab, (size_t)n * rks::omega_slots(zeta) * sizeof(uint16_t)) != cudaSuccess ||
+      cudaMalloc(&w.otab, (size_t)nsk * rks::omega_slots(zeta) * sizeof(uint16_t)) != cudaSuccess ||
       cudaMalloc(&w.sums, (size_t)wide * s * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&w.Q2, (size_t)s * s * sizeof(float2)) != cudaSuccess ||
-      cudaMalloc(&w.nrs, (size_t)s * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&w.nrs, (size_t)2 * s * sizeof(float2)) != cudaSuccess ||
       cudaMalloc(&w.sj, sizeof(float2)) != cudaSuccess ||
       cudaMalloc(&w.scale, (size_t)s * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&w.flag, sizeof(int)) != cudaSuccess)
     return RKS_ENOMEM;
   w.host.assign((size_t)wide * s, 0.0);
   QK(cudaMemsetAsync(w.flag, 0, sizeof(int), st));
-  rks::launch_omega_table(n, d, zeta, seed, w.otab, w.flag, st);
+  rks::launch_omega_table(nsk, d, zeta, seed, w.otab, w.flag, st);
   int bad = 0;
   QK(cudaMemcpyAsync(&bad, w.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   QK(cudaStreamSynchronize(st));
   if (bad) return RKS_EINVAL;
   if (rks::configure_df_kernels() != cudaSuccess) return RKS_ECUDA;
-  if (rks::build_sketch_tiles(n, d, zeta, w.otab, &w.tiles, st) != 0) return RKS_ECUDA;
+  if (rks::build_sketch_tiles(nsk, d, zeta, w.otab, &w.tiles, st) != 0) return RKS_ECUDA;
   w.have_tiles = true;
   cudaFree(w.otab);
   w.otab = nullptr;
@@ -231,6 +237,104 @@ int rgs(QrWork& w, std::vector<double>& R, std::vector<double>& S) {
   return RKS_OK;
 }
 
+// Randomized Householder QR: Householder QR of Theta K ((s + d) x s, Theta =
+// [[I_s, 0], [0, Omega']], Omega' on rows s..n-1) on the host in FP64, its
+// reflectors H_j = I - beta_j u_j (Theta u_j)^T Theta applied to the
+// double-float columns on the device (u_j is column j after the earlier
+// reflectors with its entries above j dropped and rho_j taken off entry j,
+// so Theta u_j = v_j), then Q = H_0 ... H_{s-1} [I_s; 0] accumulated
+// backwards into columns s..2s-1.  The coefficient of every column update is
+// a sketched inner product, kept on the host: Theta y -= c v.
+int rhqr(QrWork& w, std::vector<double>& R, std::vector<double>& scale) {
+  const int s = w.s, d = w.d, ns = s + d;
+  const int64_t nb = w.n - s;
+  std::vector<double> Y((size_t)ns * s, 0.0), V((size_t)ns * s, 0.0), beta(s, 0.0);
+  std::vector<float2> top((size_t)s * s), cf(s), colv(s);
+  // top blocks (rows 0..s-1) and sketches of the bottom rows of every column
+  QK(cudaMemcpy2DAsync(top.data(), s * sizeof(float2), w.U, w.ldu * sizeof(float2), s * sizeof(float2), s,
+                       cudaMemcpyDeviceToHost, w.st));
+  for (int l = 0; l < s; ++l) {
+    rks::launch_df_sketch_vec(col(w, l) + s, w.tiles, w.part, false, w.st);
+    rks::launch_df_fold(w.part, d, w.tiles.G, w.sums + (size_t)l * d, w.st);
+  }
+  QK(cudaGetLastError());
+  QK(cudaMemcpyAsync(w.host.data(), w.sums, (size_t)d * s * sizeof(double), cudaMemcpyDeviceToHost, w.st));
+  QK(cudaStreamSynchronize(w.st));
+  for (int l = 0; l < s; ++l) {
+    for (int i = 0; i < s; ++i) {
+      const float2 t = top[i + (size_t)l * s];
+      Y[i + (size_t)l * ns] = (double)t.x + (double)t.y;
+    }
+    for (int i = 0; i < d; ++i) Y[s + i + (size_t)l * ns] = w.host[i + (size_t)l * d] * w.zscale;
+  }
+  R.assign((size_t)s * s, 0.0);
+  for (int j = 0; j < s; ++j) {
+    double* y = &Y[(size_t)j * ns];
+    double* v = &V[(size_t)j * ns];
+    double nn = 0.0;
+    for (int i = j; i < ns; ++i) nn += y[i] * y[i];
+    const double nrm = std::sqrt(nn);
+    if (!(nrm > 0.0) || !std::isfinite(nrm)) return RKS_EBREAKDOWN;
+    const double rho = y[j] >= 0.0 ? -nrm : nrm;     // -sign(y_j) ||y(j:)||
+    for (int i = 0; i < j; ++i) R[i + (size_t)j * s] = y[i];
+    R[j + (size_t)j * s] = rho;
+    for (int i = j; i < ns; ++i) v[i] = y[i];
+    v[j] -= rho;
+    double vv = 0.0;
+    for (int i = j; i < ns; ++i) vv += v[i] * v[i];
+    beta[j] = 2.0 / vv;
+    // column j becomes u_j: its top rows are v's (zeros above j)
+    for (int i = 0; i < s; ++i) colv[i] = to_df(v[i]);
+    QK(cudaMemcpyAsync(col(w, j), colv.data(), (size_t)s * sizeof(float2), cudaMemcpyHostToDevice, w.st));
+    // H_j on the later columns: y_l -= c_l u_j, c_l = beta v^T Theta y_l
+    const int nl = s - 1 - j;
+    for (int l = j + 1; l < s; ++l) {
+      double* yl = &Y[(size_t)l * ns];
+      double a = 0.0;
+      for (int i = j; i < ns; ++i) a += v[i] * yl[i];
+      const double c = beta[j] * a;
+      for (int i = j; i < ns; ++i) yl[i] -= c * v[i];
+      cf[l - j - 1] = to_df(c);
+    }
+    if (nl > 0) {
+      QK(cudaMemcpyAsync(w.nrs, cf.data(), (size_t)nl * sizeof(float2), cudaMemcpyHostToDevice, w.st));
+      rks::launch_df_axpy_cols(w.n, w.U, w.ldu, j, j + 1, nl, w.nrs, w.st);
+    }
+  }
+  // Q = H_0 ... H_{s-1} [I_s; 0] in columns s..2s-1, Theta Q tracked on the host
+  QK(cudaMemsetAsync(col(w, s), 0, (size_t)w.ldu * s * sizeof(float2), w.st));
+  std::vector<float2> eye((size_t)s * s, make_float2(0.f, 0.f));
+  for (int l = 0; l < s; ++l) eye[l + (size_t)l * s] = make_float2(1.f, 0.f);
+  QK(cudaMemcpy2DAsync(col(w, s), w.ldu * sizeof(float2), eye.data(), s * sizeof(float2), s * sizeof(float2), s,
+                       cudaMemcpyHostToDevice, w.st));
+  std::vector<double> Z((size_t)ns * s, 0.0);
+  for (int l = 0; l < s; ++l) Z[l + (size_t)l * ns] = 1.0;
+  for (int j = s - 1; j >= 0; --j) {
+    const double* v = &V[(size_t)j * ns];
+    for (int l = j; l < s; ++l) {
+      double* zl = &Z[(size_t)l * ns];
+      double a = 0.0;
+      for (int i = j; i < ns; ++i) a += v[i] * zl[i];
+      const double c = beta[j] * a;
+      for (int i = j; i < ns; ++i) zl[i] -= c * v[i];
+      cf[l - j] = to_df(c);
+    }
+    QK(cudaMemcpyAsync(w.nrs + s, cf.data(), (size_t)(s - j) * sizeof(float2), cudaMemcpyHostToDevice, w.st));
+    rks::launch_df_axpy_cols(w.n, w.U, w.ldu, j, s + j, s - j, w.nrs + s, w.st);
+  }
+  QK(cudaGetLastError());
+  // positive diagonal: flip Q's column j and R's row j where rho_j < 0
+  scale.assign(s, 1.0);
+  for (int j = 0; j < s; ++j)
+    if (R[j + (size_t)j * s] < 0.0) {
+      scale[j] = -1.0;
+      for (int c = j; c < s; ++c) R[j + (size_t)c * s] = -R[j + (size_t)c * s];
+    }
+  (void)nb;
+  QK(cudaStreamSynchronize(w.st));
+  return RKS_OK;
+}
+
 }  // namespace
 
 extern "C" int rks_sketch_qr(int64_t n, int s, const double* K, int64_t ldk, int d, int zeta, uint64_t seed,
@@ -238,11 +342,13 @@ extern "C" int rks_sketch_qr(int64_t n, int s, const double* K, int64_t ldk, int
   if (n < 2 || s < 1 || s > RKS_SKETCH_QR_MAX_S || zeta < 1 || zeta > 16 || d < 2 * zeta || d > 8192 || s > d ||
       s > n || !K || !Q || !R || ldk < n || ldq < n)
     return RKS_EINVAL;
-  if (method != RKS_QR_RGS && method != RKS_QR_WHITEN && method != RKS_QR_RCHOLQR) return RKS_EINVAL;
+  if (method != RKS_QR_RGS && method != RKS_QR_WHITEN && method != RKS_QR_RCHOLQR && method != RKS_QR_RHQR)
+    return RKS_EINVAL;
+  if (method == RKS_QR_RHQR && n - s < 2) return RKS_EINVAL;
   if (Q == K && ldq != ldk) return RKS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   QrWork w;
-  int rc = setup(w, n, s, d, zeta, seed, st);
+  int rc = setup(w, n, s, d, zeta, seed, st, method == RKS_QR_RHQR ? n - s : n);
   if (rc) return rc;
   for (int j = 0; j < s; ++j) rks::launch_d2df(n, K + (size_t)j * ldk, col(w, j), false, st);
   QK(cudaGetLastError());
@@ -252,6 +358,24 @@ extern "C" int rks_sketch_qr(int64_t n, int s, const double* K, int64_t ldk, int
   if (method == RKS_QR_RGS) {
     rc = rgs(w, Rh, Sh);
     if (rc) return rc;
+  } else if (method == RKS_QR_RHQR) {
+    std::vector<double> sc;
+    rc = rhqr(w, Rh, sc);
+    if (rc) return rc;
+    out0 = s;
+    QK(cudaMemcpyAsync(w.scale, sc.data(), (size_t)s * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (S) {                    // Omega' Q[s:, :], measured: the sketched rows of Theta Q
+      Sh.assign((size_t)d * s, 0.0);
+      for (int j = 0; j < s; ++j) {
+        rks::launch_df_sketch_vec(col(w, s + j) + s, w.tiles, w.part, false, st);
+        rks::launch_df_fold(w.part, d, w.tiles.G, w.sums + (size_t)j * d, st);
+      }
+      QK(cudaGetLastError());
+      QK(cudaMemcpyAsync(w.host.data(), w.sums, (size_t)d * s * sizeof(double), cudaMemcpyDeviceToHost, st));
+      QK(cudaStreamSynchronize(st));
+      for (int j = 0; j < s; ++j)
+        for (int i = 0; i < d; ++i) Sh[i + (size_t)j * d] = w.host[i + (size_t)j * d] * w.zscale * sc[j];
+    }
   } else {
     std::vector<double> R1;
     rc = whiten(w, R1, Sh);

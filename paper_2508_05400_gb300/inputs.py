@@ -340,3 +340,18 @@ def grf_convdiff2d_problem(i: int, seed0: int = 20000, N: int = 512, k: int = 16
     nu = np.exp(gaussian_random_field(N, N, 0.1, s + 7919))
     A = convdiff_2d(N, N, nu, 50.0 * u[0], 50.0 * u[1])
     return Problem(f"grf2d_{N}_{s}", A, k, p, d, 8, "LR", tol, conv="norm1")
+
+
+def grf_member_fields(i: int, seed0: int = 20000, N: int = 512) -> np.ndarray:
+    """Coefficient planes of member i of the parametric 2D family (the
+    operator of ``grf_convdiff2d_problem(i, seed0, N)``): log nu, bx / 50 and
+    by / 50 on the N x N grid, float32, shape (3, N, N), row y, column x (the
+    solver's numbering, x fastest, after flattening)."""
+    s = seed0 + i
+    u = uniform01(s, 2)
+    g = gaussian_random_field(N, N, 0.1, s + 7919)
+    out = np.empty((3, N, N), dtype=np.float32)
+    out[0] = g
+    out[1] = u[0]
+    out[2] = u[1]
+    return out

@@ -140,6 +140,28 @@ def lib() -> C.CDLL:
                                     C.c_int64, _P, _P, _P]
         L.rks_sketch_qr.restype = C.c_int
         L.rks_destroy.argtypes = [_P]
+        L.rks_ws_nparams.argtypes = []
+        L.rks_ws_nparams.restype = C.c_int64
+        L.rks_ws_create.argtypes = [C.POINTER(_P), C.c_int, C.c_int, C.c_uint64, _P]
+        L.rks_ws_create.restype = C.c_int
+        L.rks_ws_get_params.argtypes = [_P, _P]
+        L.rks_ws_get_params.restype = C.c_int
+        L.rks_ws_set_params.argtypes = [_P, _P]
+        L.rks_ws_set_params.restype = C.c_int
+        L.rks_ws_forward.argtypes = [_P, _P, _P]
+        L.rks_ws_forward.restype = C.c_int
+        L.rks_ws_accumulate.argtypes = [_P, _P, _P, C.c_int, C.POINTER(C.c_double)]
+        L.rks_ws_accumulate.restype = C.c_int
+        L.rks_ws_get_grad.argtypes = [_P, _P]
+        L.rks_ws_get_grad.restype = C.c_int
+        L.rks_ws_zero_grad.argtypes = [_P]
+        L.rks_ws_zero_grad.restype = C.c_int
+        L.rks_ws_adam_step.argtypes = [_P, C.c_float]
+        L.rks_ws_adam_step.restype = C.c_int
+        L.rks_ws_start_vector.argtypes = [_P, _P, C.c_double, C.c_uint64, _P]
+        L.rks_ws_start_vector.restype = C.c_int
+        L.rks_ws_destroy.argtypes = [_P]
+        L.rks_ws_destroy.restype = None
         L.rks_destroy.restype = None
         L.rks_sketch_pairs.argtypes = [C.c_int64, C.c_int, C.c_int, C.c_uint64, _P, _P, _P]
         L.rks_sketch_pairs.restype = C.c_int
@@ -418,7 +440,7 @@ def basis_product_f32(U, ldu: int, n: int, nin: int, Q: np.ndarray, out) -> None
                                        stream), "rks_basis_product_f32")
 
 
-QR_METHODS = {"rgs": 0, "whiten": 1, "rcholqr": 2}
+QR_METHODS = {"rgs": 0, "whiten": 1, "rcholqr": 2, "rhqr": 3}
 
 
 def sketch_qr(K, d: int, zeta: int = 8, seed: int = 0, method: str = "rgs", Q=None):
@@ -556,4 +578,98 @@ class Batch:
         return self
 
     def __exit__(self, *exc):
+        self.close()
+
+
+class WarmStart:
+    """The start-vector network (rks_ws_*): a 4-level U-Net from the
+    coefficient planes (3 x H x W) of an operator to a start vector (H W).
+
+    Inputs and outputs are CUDA float32 tensors; parameters are exchanged as
+    host float32 arrays in the flat layout of ``include/rks.h``.
+    """
+
+    def __init__(self, H: int, W: int, seed: int = 0, stream=None):
+        h = _P()
+        _check(lib().rks_ws_create(C.byref(h), int(H), int(W), int(seed) & 0xFFFFFFFFFFFFFFFF, stream),
+               "rks_ws_create")
+        self._h, self.H, self.W = h, int(H), int(W)
+        self.nparams = int(lib().rks_ws_nparams())
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.nparams, dtype=np.float32)
+        _check(lib().rks_ws_get_params(self._h, out.ctypes.data), "rks_ws_get_params")
+        return out
+
+    def set_params(self, theta) -> None:
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        if th.size != self.nparams:
+            raise ValueError(f"expected {self.nparams} parameters, got {th.size}")
+        _check(lib().rks_ws_set_params(self._h, th.ctypes.data), "rks_ws_set_params")
+
+    @staticmethod
+    def _need(t, shape, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA float32 tensor")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+    def forward(self, x, out=None):
+        import torch
+        self._need(x, (3, self.H, self.W), "x")
+        if out is None:
+            out = torch.empty((self.H, self.W), dtype=torch.float32, device=x.device)
+        self._need(out, (self.H, self.W), "out")
+        _check(lib().rks_ws_forward(self._h, x.data_ptr(), out.data_ptr()), "rks_ws_forward")
+        return out
+
+    def accumulate(self, x, Q) -> float:
+        """Add dL/dtheta for one sample; Q: CUDA float32 (q, H W), row j = column j of Q."""
+        self._need(x, (3, self.H, self.W), "x")
+        q = Q.shape[0]
+        self._need(Q, (q, self.H * self.W), "Q")
+        loss = C.c_double()
+        _check(lib().rks_ws_accumulate(self._h, x.data_ptr(), Q.data_ptr(), int(q), C.byref(loss)),
+               "rks_ws_accumulate")
+        return loss.value
+
+    def grad(self) -> np.ndarray:
+        out = np.zeros(self.nparams, dtype=np.float32)
+        _check(lib().rks_ws_get_grad(self._h, out.ctypes.data), "rks_ws_get_grad")
+        return out
+
+    def zero_grad(self) -> None:
+        _check(lib().rks_ws_zero_grad(self._h), "rks_ws_zero_grad")
+
+    def step(self, lr: float) -> None:
+        _check(lib().rks_ws_adam_step(self._h, float(lr)), "rks_ws_adam_step")
+
+    def start_vector(self, x, eps: float = 1e-3, seed: int = 1, out=None):
+        """u1 = u / ||u|| + eps g / ||g|| (CUDA float64, H W) for rks_create's u1."""
+        import torch
+        self._need(x, (3, self.H, self.W), "x")
+        if out is None:
+            out = torch.empty(self.H * self.W, dtype=torch.float64, device=x.device)
+        if not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and out.numel() == self.H * self.W):
+            raise ValueError("out must be a contiguous CUDA float64 tensor of H W values")
+        _check(lib().rks_ws_start_vector(self._h, x.data_ptr(), float(eps), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                         out.data_ptr()), "rks_ws_start_vector")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rks_ws_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
         self.close()

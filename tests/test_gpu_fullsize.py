@@ -12,7 +12,7 @@ forms whose accuracy the eigenvalue condition number bounds:
   (first-order perturbation bound; kappa from the closed-form left and right
   eigenvectors);
 * the non-symmetric Toeplitz workload (n = 2000, k = 10, p = 30, d = 80,
-  zeta = 4) run to convergence at 1e-8, against the oracle's residual and
+  zeta = 4) run to a residual of 1e-8, against the oracle's residual and
   decomposition invariants (its eigenvalues have condition numbers ~1e261
   and are not pinned);
 * the symmetric Toeplitz matrix with the same spectrum, n = 2000, to 1e-10.
@@ -160,22 +160,22 @@ def test_kronecker_closed_form_large(N, prec):
 
 def test_toeplitz_2000_to_convergence_against_oracle():
     # The non-symmetric Toeplitz workload (n = 2000, k = 10, p = 30, d = 80,
-    # zeta = 4), run to convergence with the thick restart (keep = k) at
-    # 1e-8 on the paper's estimate |b^T y| / |l| (here |l| ~ ||A||_1 = 4, so
-    # this is also the normwise residual target).  At the stated 1e-10 the
-    # estimate stalls near 1e-5..1e-3 for thousands of restarts, in the oracle
-    # as on the GPU (with keep <= k; the oracle converges with keep = 20):
-    # the Ritz values wander in a pseudospectrum of condition ~1e261.
+    # zeta = 4), run to ||A x - l x|| / (||A||_1 ||x||) <= 1e-8 with the thick
+    # restart (keep = k): the estimate |b^T y| / ||A||_1 at 1e-8 / 4, locking
+    # at 1e-8 / 8, FP64 verification at 1e-8 (about 2 200 restarts in the
+    # oracle).  At the stated 1e-10 on |b^T y| / |l| the estimate stalls near
+    # 1e-5..1e-3 for thousands of restarts, in the oracle as on the GPU (with
+    # keep <= k; the oracle converges with keep = 20): the Ritz values wander
+    # in a pseudospectrum of condition ~1e261.
     P = I.toeplitz_problem()
     u1 = I.start_vector(P.A.n, 1)
-    tol = 1e-8
-    with K().Solver.from_csr(P.A, P.k, P.p, P.d, which=P.which, tol=tol, zeta=P.zeta, u1=u1,
-                             keep=P.k, maxit=4000) as s:
+    kw = dict(tol=2.5e-9, eta_lock=1.25e-9, conv="norm1")
+    with K().Solver.from_csr(P.A, P.k, P.p, P.d, which=P.which, zeta=P.zeta, u1=u1, keep=P.k, maxit=6000,
+                             verify=1e-8, **kw) as s:
         info = s.solve(allow_noconv=False)
         lam, X, res = s.eigpairs()
         T, U, b = s.schur()
-        est = s.estimates()
-    assert info["converged"] == 1 and est.max() <= tol
+    assert info["converged"] == 1
     assert res.max() <= 1e-8
     Z = K().unpack_eigvecs(lam, X)
     hres, _ = R.true_residuals(P.A.to_scipy(), Z, lam)
@@ -185,7 +185,7 @@ def test_toeplitz_2000_to_convergence_against_oracle():
     r = AU - U @ T
     Pb = np.eye(b.size) - np.outer(b, b) / (b @ b)
     assert np.linalg.norm(r @ Pb) <= 1e-10 * np.linalg.norm(AU)
-    ores = R.rks(A, P.k, P.p, P.d, u1, zeta=P.zeta, seed=0, which="LM", tol=tol, keep=P.k, maxit=4000)
+    ores = R.rks(A, P.k, P.p, P.d, u1, zeta=P.zeta, seed=0, which="LM", keep=P.k, maxit=6000, **kw)
     assert ores.converged and ores.resid.max() <= 1e-8
     print(f"\ntoeplitz 2000: restarts GPU {info['restarts']} oracle {ores.restarts}; |l| GPU "
           f"{np.abs(lam).min():.4f}..{np.abs(lam).max():.4f} oracle {np.abs(ores.eigvals).min():.4f}.."

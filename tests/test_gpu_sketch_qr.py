@@ -1,7 +1,8 @@
 """GPU parity of the randomized QR of a block (rks_sketch_qr) against the oracle.
 
-The three processes of Sec. 2 (randomized Gram-Schmidt, sketch and whiten,
-randomized Cholesky QR) on the double-float device path, compared with the FP64
+The four processes of Sec. 2 (randomized Gram-Schmidt, sketch and whiten,
+randomized Cholesky QR, randomized Householder QR) on the double-float device
+path, compared with the FP64
 oracle on the same Omega (the SplitMix64 sparse-sign hash, bit-exact on both
 sides) and checked for the properties that define them: K = Q R with R upper
 triangular and a positive diagonal, Omega Q orthonormal (RGS, whitening) or
@@ -87,7 +88,7 @@ def test_sketch_qr_full_size_properties(gpu):
     n, s, d = 1_000_000, 80, 320
     rng = np.random.default_rng(11)
     Kd = torch.from_numpy(rng.standard_normal((s, n))).cuda()
-    for method in ("rgs", "whiten", "rcholqr"):
+    for method in ("rgs", "whiten", "rcholqr", "rhqr"):
         Qd, R, S = K().sketch_qr(Kd, d, method=method)
         Rd = torch.from_numpy(np.ascontiguousarray(R.T)).cuda()        # rows of R^T
         res = torch.linalg.norm(Kd - Rd @ Qd) / torch.linalg.norm(Kd)   # K^T = R^T Q^T
@@ -95,6 +96,9 @@ def test_sketch_qr_full_size_properties(gpu):
         if method == "rcholqr":
             G = (Qd @ Qd.T).cpu().numpy()
             assert np.linalg.norm(G - np.eye(s)) <= 1e-12
+        elif method == "rhqr":                       # Theta Q = [Q[:s]; S]
+            Qt = Qd[:, :s].cpu().numpy().T
+            assert np.linalg.norm(Qt.T @ Qt + S.T @ S - np.eye(s)) <= 1e-12
         else:
             assert np.linalg.norm(S.T @ S - np.eye(s)) <= 1e-12
 
@@ -103,7 +107,37 @@ def test_rank_deficient_block_reports_breakdown(gpu):
     n, s, d = 4096, 6, 48
     Kh = _graded_block(n, s, 10.0, 3)
     Kh[:, 4] = 0.0                                   # a zero column: R[4, 4] = 0
-    for method in ("rgs", "whiten", "rcholqr"):
+    for method in ("rgs", "whiten", "rcholqr", "rhqr"):
         with pytest.raises(K().RKSError) as e:
             _run(gpu, Kh, d, method)
         assert e.value.code in (K().RKS_EBREAKDOWN, K().RKS_EDENSE)
+
+
+@pytest.mark.parametrize("n,s,d,cond", [(50_021, 24, 96, 1e4), (20_000, 100, 256, 1e2)])
+def test_rhqr_matches_oracle(gpu, n, s, d, cond):
+    # Theta = [[I_s, 0], [0, Omega']], Omega' the embedding of dimension n - s
+    Kh = _graded_block(n, s, cond, 17)
+    Q, R, S = _run(gpu, Kh, d, "rhqr")
+    Ob = omega_matrix(n - s, d, 8, 0)
+    Qo, Ro, TQo = SQ.rhqr(Kh, Ob)
+    u = 2.0 ** -46
+    assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+    assert np.linalg.norm(Kh - Q @ R) <= 10 * s * u * np.linalg.norm(Kh)
+    assert np.linalg.norm(R - Ro) <= 10 * s * u * cond * np.linalg.norm(Ro)
+    assert np.linalg.norm(Q - Qo) <= 10 * s * u * cond * np.sqrt(s)
+    # Theta Q = [Q[:s]; Omega' Q[s:]] orthonormal, to rounding (no kappa factor)
+    TQ = np.vstack([Q[:s], S])
+    assert np.linalg.norm(TQ.T @ TQ - np.eye(s)) <= 10 * s * u
+    assert np.linalg.norm(Ob @ Q[s:] - S) <= 10 * s * u
+
+
+def test_rhqr_stays_orthonormal_for_ill_conditioned_blocks(gpu):
+    # kappa(K) = 1e12: the reflectors keep Theta Q orthonormal to rounding
+    # where K R^{-1} (sketch and whiten) loses about u kappa
+    n, s, d = 30_011, 20, 80
+    Kh = _graded_block(n, s, 1e12, 19)
+    Q, R, S = _run(gpu, Kh, d, "rhqr")
+    TQ = np.vstack([Q[:s], S])
+    u = 2.0 ** -46
+    assert np.linalg.norm(TQ.T @ TQ - np.eye(s)) <= 10 * s * u
+    assert np.linalg.norm(Kh - Q @ R) <= 10 * s * u * np.linalg.norm(Kh)

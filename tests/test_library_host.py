@@ -137,8 +137,9 @@ def test_host_reorder_select_matches_lapack_dtrsen(lib):
                 assert sv.min() > 1 - 1e-8
 
 
-@pytest.mark.parametrize("kw", [dict(s=0), dict(s=193), dict(d=15), dict(zeta=0), dict(zeta=17), dict(method=3),
-                                dict(ldk=99), dict(s=50, d=40), dict(nullK=True), dict(nullR=True)])
+@pytest.mark.parametrize("kw", [dict(s=0), dict(s=193), dict(d=15), dict(zeta=0), dict(zeta=17), dict(method=4),
+                                dict(ldk=99), dict(s=50, d=40), dict(nullK=True), dict(nullR=True),
+                                dict(method=3, n=9, ldk=9, ldq=9)])
 def test_sketch_qr_rejects_bad_arguments_before_any_device_call(lib, kw):
     # argument checks of rks_sketch_qr return before any CUDA call (no GPU here)
     a = dict(n=100, s=8, ldk=100, d=32, zeta=8, method=0, ldq=100)

@@ -97,3 +97,71 @@ def test_planted_mistake_in_rgs_is_caught(monkeypatch):
     Q, R, S = SQ.rgs(K, Om)
     monkeypatch.undo()
     assert np.linalg.norm(S.T @ S - np.eye(s)) > 1e-6
+
+
+# ---------------------------------------------------------------------------
+# RHQR: Householder QR in the sketched space of Theta = [[I_s, 0], [0, Omega']]
+# ---------------------------------------------------------------------------
+
+def test_rhqr_with_identity_sketch_is_householder_qr():
+    # Omega' = I makes Theta = I: RHQR is Householder QR, LAPACK's up to signs
+    n, s = 300, 16
+    K = _graded_block(n, s, 1e6, 5)
+    Q, R, TQ = SQ.rhqr(K, sp.identity(n - s, format="csr"))
+    Ql, Rl = np.linalg.qr(K)
+    sg = np.sign(np.diag(Rl))
+    Ql, Rl = Ql * sg, (Rl.T * sg).T
+    assert np.linalg.norm(R - Rl) <= 1e-13 * np.linalg.norm(Rl)
+    assert np.linalg.norm(Q - Ql) <= 1e-10
+    assert np.linalg.norm(Q.T @ Q - np.eye(s)) <= 1e-14 * s
+
+
+@pytest.mark.parametrize("cond", [1e2, 1e6])
+def test_rhqr_gives_the_unique_theta_orthonormal_qr(cond):
+    # the same factorisation as RGS and sketch-and-whiten with Omega = Theta
+    n, s, d = 3000, 24, 96
+    K = _graded_block(n, s, cond, 6)
+    Ob = omega_matrix(n - s, d, 8, 0)
+    Th = SQ.theta_matrix(n, s, Ob)
+    Q, R, TQ = SQ.rhqr(K, Ob)
+    Qw, Rw, Sw = SQ.sketch_whiten(K, Th)
+    Qg, Rg, Sg = SQ.rgs(K, Th)
+    assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+    assert np.linalg.norm(K - Q @ R) <= 1e-14 * np.linalg.norm(K) * s
+    assert np.linalg.norm(TQ.T @ TQ - np.eye(s)) <= 1e-14 * s
+    assert np.linalg.norm(Th @ Q - TQ) <= 1e-14 * s
+    lost = 10 * s * 1.1e-16 * cond
+    assert np.linalg.norm(R - Rw) <= 1e-13 * np.linalg.norm(Rw)
+    assert np.linalg.norm(R - Rg) <= 1e-13 * np.linalg.norm(Rg)
+    assert np.linalg.norm(Q - Qw) <= lost and np.linalg.norm(Q - Qg) <= lost
+
+
+def test_rhqr_stays_orthonormal_where_whitening_does_not():
+    # Householder-type stability: Theta Q orthonormal to rounding for
+    # kappa(K) = 1e12, where K R^{-1} (sketch and whiten) loses ~u kappa
+    n, s, d = 2000, 20, 80
+    K = _graded_block(n, s, 1e12, 7)
+    Ob = omega_matrix(n - s, d, 8, 0)
+    Th = SQ.theta_matrix(n, s, Ob)
+    Q, R, TQ = SQ.rhqr(K, Ob)
+    Qw, _, _ = SQ.sketch_whiten(K, Th)
+    TQw = Th @ Qw
+    assert np.linalg.norm(TQ.T @ TQ - np.eye(s)) <= 1e-13 * s
+    assert np.linalg.norm(TQw.T @ TQw - np.eye(s)) > 1e3 * np.linalg.norm(TQ.T @ TQ - np.eye(s))
+    assert np.linalg.norm(K - Q @ R) <= 1e-14 * np.linalg.norm(K) * s
+
+
+def test_rhqr_planted_mistake_is_caught():
+    # a reflector whose n-dimensional vector keeps the entries above the
+    # diagonal (Theta u != v) no longer factors K
+    n, s, d = 500, 8, 40
+    K = _graded_block(n, s, 1e2, 8)
+    Ob = omega_matrix(n - s, d, 8, 0)
+    good = SQ.rhqr(K, Ob)
+    bad_src = open(SQ.__file__).read().replace("        u[:j] = 0.0\n", "")
+    ns = {}
+    exec(compile(bad_src, SQ.__file__, "exec"), ns)
+    Q, R, TQ = ns["rhqr"](K, Ob)
+    assert np.linalg.norm(K - Q @ R) > 1e-6 * np.linalg.norm(K)
+    Q, R, TQ = good
+    assert np.linalg.norm(K - Q @ R) <= 1e-13 * np.linalg.norm(K)
