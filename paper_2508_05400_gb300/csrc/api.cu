@@ -66,6 +66,10 @@ struct rks_ctx {
   float2* U2 = nullptr;
   float* valsf = nullptr;  // mixed precision: FP32 values and basis
   int ell_w = 0;           // ELLPACK copy of A for the SpMV (0: not used)
+  int dia_d = 0;           // diagonal copy of A for the SpMV (0: not used), its offsets
+  int dia_off[16] = {};
+  float2* dia_val2 = nullptr;
+  float* dia_valf = nullptr;
   int32_t* ell_col = nullptr;
   float2* ell_val2 = nullptr;
   float* ell_valf = nullptr;
@@ -226,7 +230,10 @@ int flag_status(int f) {
 // Algorithm 2 in double-float: three kernels per step (see kernels_df.cu).
 void expand_df_launches(rks_ctx* c, int c0) {
   const double n = (double)c->n, P = 8.0, PV = c->f32 ? 4.0 : 8.0;
-  const double spmv_bytes = (double)c->nnz * (PV + 4) + 4.0 * (n + 1) + 2 * PV * n;
+  // algorithmic bytes of the storage the SpMV reads: CSR/ELLPACK values and
+  // columns (and row pointers), or the D diagonals; x read once, w written
+  const double spmv_bytes = c->A2.dvals ? (double)c->A2.D * PV * n + 2 * PV * n
+                                        : (double)c->nnz * (PV + 4) + 4.0 * (n + 1) + 2 * PV * n;
   for (int j = c0; j < c->m; ++j) {
     const int col = j + 1;
     int s = prof_begin(c, RKS_K_SPMV);
@@ -257,7 +264,8 @@ void expand_df_launches(rks_ctx* c, int c0) {
 // two passes of (dot products with every basis column, update), and the norm.
 void expand_ks_launches(rks_ctx* c, int c0) {
   const double n = (double)c->n, P = 8.0;
-  const double spmv_bytes = (double)c->nnz * (P + 4) + 4.0 * (n + 1) + 2 * P * n;
+  const double spmv_bytes = c->A2.dvals ? (double)c->A2.D * P * n + 2 * P * n
+                                        : (double)c->nnz * (P + 4) + 4.0 * (n + 1) + 2 * P * n;
   const int G = c->tiles.G;
   for (int j = c0; j < c->m; ++j) {
     const int col = j + 1;
@@ -825,7 +833,7 @@ void free_ctx(rks_ctx* c) {
   cudaFree(c->z_raw); cudaFree(c->s_raw); cudaFree(c->z1); cudaFree(c->r1); cudaFree(c->r); cudaFree(c->rs);
   cudaFree(c->coef); cudaFree(c->flag); cudaFree(c->Qd); cudaFree(c->u1);
   cudaFree(c->X); cudaFree(c->AX); cudaFree(c->rsum); cudaFree(c->pcol); cudaFree(c->plam);
-  cudaFree(c->ell_col); cudaFree(c->ell_val2); cudaFree(c->ell_valf);
+  cudaFree(c->ell_col); cudaFree(c->ell_val2); cudaFree(c->ell_valf); cudaFree(c->dia_val2); cudaFree(c->dia_valf);
   cudaFree(c->vals2); cudaFree(c->U2); cudaFree(c->S2); cudaFree(c->nrs); cudaFree(c->sj); cudaFree(c->Q2);
   cudaFree(c->rprev); cudaFree(c->znorm); cudaFree(c->tmp64); cudaFree(c->valsf); cudaFree(c->Uf);
   cudaFree(c->otab); cudaFree(c->lsr1); cudaFree(c->M2); cudaFree(c->bar); cudaFree(c->qimg);
@@ -970,6 +978,25 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
     for (int64_t i = 0; i < n; ++i) wmax = std::max(wmax, rp[i + 1] - rp[i]);
     const int64_t slots = (n + 31) / 32 * 32 * (int64_t)wmax;
     c->ell_w = (wmax >= 1 && wmax <= 16 && (double)slots <= 1.25 * (double)std::max<int64_t>(c->nnz, 1)) ? wmax : 0;
+    // at most 16 distinct diagonals with little padding (stencils): a
+    // diagonal copy for the SpMV instead
+    {
+      std::vector<int64_t> offs;
+      bool fits = c->nnz > 0;
+      for (int64_t i = 0; i < n && fits; ++i)
+        for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
+          const int64_t o = (int64_t)ci[q] - i;
+          if (std::find(offs.begin(), offs.end(), o) == offs.end()) {
+            offs.push_back(o);
+            if (offs.size() > 16) { fits = false; break; }
+          }
+        }
+      if (fits && (double)offs.size() * (double)n <= 1.3 * (double)c->nnz) {
+        std::sort(offs.begin(), offs.end());
+        c->dia_d = (int)offs.size();
+        for (int e = 0; e < c->dia_d; ++e) c->dia_off[e] = (int)offs[e];
+      }
+    }
     c->norm1 = n ? *std::max_element(colsum.begin(), colsum.end()) : 0.0;
     if (!std::isfinite(c->norm1)) return fail(RKS_ENAN);
     if (c->norm1 == 0.0) c->norm1 = 1.0;
@@ -1017,7 +1044,22 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
       return fail(rc);
     rks::launch_d2df(c->nnz, c->vals, c->vals2, false, c->stream);
     c->A2.n = n; c->A2.nnz = c->nnz; c->A2.rowptr = c->rowptr; c->A2.colind = c->colind; c->A2.vals = c->vals2;
-    if (c->ell_w) {
+    if (c->dia_d) {
+      const int64_t ldd = (n + 31) / 32 * 32;
+      if ((rc = dalloc(&c->dia_val2, (size_t)c->dia_d * ldd))) return fail(rc);
+      rks::launch_dia_fill(n, c->dia_d, c->dia_off, ldd, c->rowptr, c->colind, c->vals2, false, c->dia_val2,
+                           c->stream);
+      if (c->prec == RKS_PREC_MIXED) {
+        if ((rc = dalloc(&c->dia_valf, (size_t)c->dia_d * ldd))) return fail(rc);
+        rks::launch_dia_fill(n, c->dia_d, c->dia_off, ldd, c->rowptr, c->colind, c->valsf, true, c->dia_valf,
+                             c->stream);
+      }
+      if ((rc = launch_err())) return fail(rc);
+      c->A2.D = c->dia_d;
+      for (int e = 0; e < c->dia_d; ++e) c->A2.doff[e] = c->dia_off[e];
+      c->A2.ldd = ldd;
+      c->A2.dvals = c->dia_val2;
+    } else if (c->ell_w) {
       const size_t slots = (size_t)((n + 31) / 32 * 32) * c->ell_w;
       if ((rc = dalloc(&c->ell_col, slots)) || (rc = dalloc(&c->ell_val2, slots))) return fail(rc);
       rks::launch_ell_fill(n, c->ell_w, c->rowptr, c->colind, c->vals2, false, c->ell_col, c->ell_val2, c->stream);
@@ -1159,7 +1201,7 @@ static int solve_impl(rks_ctx* c) {
   c->rq_im.clear();
   const int limit = c->opts.max_restarts > 0 ? std::min(c->opts.maxit, c->opts.max_restarts) : c->opts.maxit;
   const double tol0 = c->tol, eta0 = c->eta_lock;
-  bool converged = false;
+  bool converged = false, fp32_done = false;
   int rc = RKS_OK;
   if (c->prec == RKS_PREC_MIXED) {
     // Phase 1: FP32 basis and values (compensated arithmetic), down to the
@@ -1168,6 +1210,7 @@ static int solve_impl(rks_ctx* c) {
     c->Ub = c->Uf;
     c->A2.vals = c->valsf;
     c->A2.evals = c->ell_valf;
+    if (c->dia_d) c->A2.dvals = c->dia_valf;
     c->A2.f32 = true;
     const double floor32 = c->opts.mixed_tol > 0 ? c->opts.mixed_tol : 64.0 * 5.9604644775390625e-08;
     c->tol = std::max(tol0, floor32);
@@ -1175,22 +1218,39 @@ static int solve_impl(rks_ctx* c) {
     bool conv1 = false;
     rc = run_alg1(c, nullptr, limit, 0.0, 20, &conv1);
     c->phase_restarts = c->restarts;
-    if (rc == RKS_OK && c->opts.max_restarts >= 0) {
+    // The FP32 result may already meet the target: its Ritz vectors checked
+    // in FP64 (finalize promotes the FP32 basis exactly); then no
+    // double-float phase is needed.
+    const bool near = c->opts.conv != RKS_CONV_NORM1 || c->hist.empty() || c->hist.back() <= c->opts.verify;
+    if (rc == RKS_OK && c->opts.max_restarts >= 0 && c->opts.verify > 0 && c->kk > 0 && near) {
+      rc = finalize(c);
+      if (rc == RKS_OK) {
+        double mr = 0.0;
+        for (double v : c->resid) mr = std::max(mr, v);
+        fp32_done = mr <= c->opts.verify;
+      }
+    }
+    if (rc == RKS_OK && !fp32_done && c->opts.max_restarts >= 0) {
       // Phase 2 start vector: the sum of the FP32 Schur vectors (all wanted
       // directions to FP32 accuracy), in FP64.
       rks::launch_sum_cols_f32(c->n, c->Uf, c->ldu, c->kk, c->tmp64, c->stream);
       rc = launch_err();
     }
-    c->f32 = false;
-    c->Ub = c->U2;
-    c->A2.vals = c->vals2;
-    c->A2.evals = c->ell_val2;
-    c->A2.f32 = false;
     c->tol = tol0;
     c->eta_lock = eta0;
-    if (rc == RKS_OK && c->opts.max_restarts >= 0) {
-      // Phase 2: double-float from that start vector, verified in FP64.
-      rc = run_alg1(c, c->tmp64, std::max(1, limit - c->restarts), c->opts.verify, 0, &converged);
+    if (fp32_done) {
+      converged = true;
+    } else {
+      c->f32 = false;
+      c->Ub = c->U2;
+      c->A2.vals = c->vals2;
+      c->A2.evals = c->ell_val2;
+      if (c->dia_d) c->A2.dvals = c->dia_val2;
+      c->A2.f32 = false;
+      if (rc == RKS_OK && c->opts.max_restarts >= 0) {
+        // Phase 2: double-float from that start vector, verified in FP64.
+        rc = run_alg1(c, c->tmp64, std::max(1, limit - c->restarts), c->opts.verify, 0, &converged);
+      }
     }
   } else {
     rc = run_alg1(c, nullptr, limit, c->opts.verify, 0, &converged);
@@ -1199,8 +1259,10 @@ static int solve_impl(rks_ctx* c) {
   c->eta_lock = eta0;
   if (rc) return rc;
   if (c->opts.max_restarts < 0) { c->solved = true; return RKS_OK; }
-  rc = finalize(c);
-  if (rc) return rc;
+  if (!fp32_done) {
+    rc = finalize(c);
+    if (rc) return rc;
+  }
   c->solved = true;
   if (converged && c->opts.verify > 0) {
     double mr = 0.0;

@@ -517,6 +517,82 @@ __global__ void __launch_bounds__(512) k_df_spmv_ell(
   if (SK) tile_write_part(acc, d, part);
 }
 
+// Offsets of the diagonal copy, passed by value.
+struct DiaOffs {
+  int o[16];
+};
+
+// w = A x (+ the per-CTA partial sketches of w when SK) on the diagonal copy
+// of A: every load independent of the others and coalesced (value of
+// diagonal e at row i, x at i + off_e), the products in increasing column
+// order (the CSR kernel's order, the same bits); two rows per thread, the
+// tiles and the sketch gather of k_df_spmv_ell.
+template <class TU, class TA, bool SK, int DMAX>
+__global__ void __launch_bounds__(512) k_df_spmv_dia(const DiaOffs offs, int D, const TA* __restrict__ dv,
+                                                     int64_t ldd, int64_t n, const TU* __restrict__ x,
+                                                     TU* __restrict__ w, const SketchTiles tv,
+                                                     double* __restrict__ part) {
+  static_assert(kTileRows == 1024, "two rows per thread of a 512-thread CTA");
+  extern __shared__ __align__(16) uint8_t smraw[];
+  const int d = tv.d, L1 = tv.L + 1;
+  const TileSmem lay = tile_smem_layout(d, tv.L, 0, tv.zeta);
+  float2* acc = reinterpret_cast<float2*>(smraw + lay.acc);
+  if (SK)
+    for (int r = threadIdx.x; r < d; r += blockDim.x) acc[r] = make_float2(0.f, 0.f);
+  const int t0 = tv.ctile[blockIdx.x], t1 = tv.ctile[blockIdx.x + 1];
+  for (int t = t0; t < t1; ++t) {
+    const int buf = (t - t0) & 1;
+    float2* v = reinterpret_cast<float2*>(smraw + lay.vb) + buf * kTileRows;
+    int* of = reinterpret_cast<int*>(smraw + lay.offs) + buf * L1;
+    uint32_t* ms = reinterpret_cast<uint32_t*>(smraw + lay.ms) + buf * d;
+    uint16_t* es = reinterpret_cast<uint16_t*>(smraw + lay.es) + (size_t)buf * kTileRows * tv.zeta;
+    const int64_t r0 = tv.row[t];
+    const int rows = (int)(tv.row[t + 1] - r0);
+    if (SK) tile_stage(tv, t, r0, rows, of, ms, es);
+    const int la = threadIdx.x, lb = threadIdx.x + 512;
+    const bool oka = la < rows, okb = lb < rows;
+    const int64_t ia = r0 + la, ib = r0 + lb;
+    float2 va[DMAX], vb[DMAX], xa[DMAX], xb[DMAX];
+#pragma unroll
+    for (int e = 0; e < DMAX; ++e) {
+      const bool on = e < D;
+      const int64_t ja = ia + offs.o[e], jb = ib + offs.o[e];
+      va[e] = (on && oka) ? ldv(dv + e * ldd + ia) : make_float2(0.f, 0.f);
+      vb[e] = (on && okb) ? ldv(dv + e * ldd + ib) : make_float2(0.f, 0.f);
+      xa[e] = (on && oka && ja >= 0 && ja < n) ? ldv(x + ja) : make_float2(0.f, 0.f);
+      xb[e] = (on && okb && jb >= 0 && jb < n) ? ldv(x + jb) : make_float2(0.f, 0.f);
+    }
+    float sa = 0.f, ta = 0.f, sb = 0.f, tb = 0.f;
+#pragma unroll
+    for (int e = 0; e < DMAX; ++e) {
+      if (e < D) {
+        df_mac(va[e].x, va[e].y, xa[e].x, xa[e].y, sa, ta);
+        df_mac(vb[e].x, vb[e].y, xb[e].x, xb[e].y, sb, tb);
+      }
+    }
+    if (oka) v[la] = stv(w + ia, df_norm(sa, ta));
+    if (okb) v[lb] = stv(w + ib, df_norm(sb, tb));
+    if (SK) {
+      __syncthreads();
+      tile_gather(d, tv.H, v, of, ms, es, acc);
+    }
+  }
+  if (SK) tile_write_part(acc, d, part);
+}
+
+// Row i's entries into the diagonal copy (dv cleared before)
+template <class TV>
+__global__ void k_dia_fill(int64_t n, const DiaOffs offs, int D, int64_t ldd, const int32_t* __restrict__ rowptr,
+                           const int32_t* __restrict__ colind, const TV* __restrict__ vals, TV* __restrict__ dv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      const int64_t off = (int64_t)colind[p] - i;
+      for (int e = 0; e < D; ++e)
+        if (offs.o[e] == off) { dv[e * ldd + i] = vals[p]; break; }
+    }
+  }
+}
+
 // ELLPACK slots of row i (and the padding rows of the last slice)
 template <class TV>
 __global__ void k_ell_fill(int64_t n, int W, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
@@ -1300,6 +1376,9 @@ static cudaError_t configure_df_kernels_once() {
   RKS_SMEM((k_df_spmv_sketch<float2, float2, true>)); RKS_SMEM((k_df_spmv_sketch<float, float, true>));
   RKS_SMEM((k_df_spmv_sketch<float2, float2, false>));
   RKS_SMEM((k_df_spmv_ell<float2, float2, true, 0>)); RKS_SMEM((k_df_spmv_ell<float, float, true, 0>));
+  RKS_SMEM((k_df_spmv_dia<float2, float2, true, 8>)); RKS_SMEM((k_df_spmv_dia<float, float, true, 8>));
+  RKS_SMEM((k_df_spmv_dia<float2, float2, true, 16>)); RKS_SMEM((k_df_spmv_dia<float, float, true, 16>));
+  RKS_SMEM((k_df_spmv_dia<float2, float2, false, 8>)); RKS_SMEM((k_df_spmv_dia<float2, float2, false, 16>));
   RKS_SMEM((k_df_spmv_ell<float2, float2, false, 0>)); RKS_SMEM((k_df_spmv_ell<float2, float2, true, 6>));
   RKS_SMEM((k_df_spmv_ell<float, float, true, 6>)); RKS_SMEM((k_df_spmv_ell<float2, float2, false, 6>));
   constexpr int U8 = kDfUpdUnroll, MB = kDfUpdMinBlocks;
@@ -1334,9 +1413,40 @@ void launch_ell_fill(int64_t n, int W, const int32_t* rowptr, const int32_t* col
                                           static_cast<float2*>(evals));
 }
 
+void launch_dia_fill(int64_t n, int D, const int* doff, int64_t ldd, const int32_t* rowptr, const int32_t* colind,
+                     const void* vals, bool f32, void* dvals, cudaStream_t st) {
+  DiaOffs o{};
+  for (int e = 0; e < D && e < 16; ++e) o.o[e] = doff[e];
+  const int g = df_grid(n, 256);
+  cudaMemsetAsync(dvals, 0, (size_t)D * ldd * (f32 ? sizeof(float) : sizeof(float2)), st);
+  if (f32)
+    k_dia_fill<float><<<g, 256, 0, st>>>(n, o, D, ldd, rowptr, colind, static_cast<const float*>(vals),
+                                         static_cast<float*>(dvals));
+  else
+    k_dia_fill<float2><<<g, 256, 0, st>>>(n, o, D, ldd, rowptr, colind, static_cast<const float2*>(vals),
+                                          static_cast<float2*>(dvals));
+}
+
+template <class TU, bool SK>
+static void launch_dia(const CsrDF& A, const void* x, void* w, const SketchTiles& t, double* part, size_t sm,
+                       cudaStream_t st) {
+  DiaOffs o{};
+  for (int e = 0; e < A.D; ++e) o.o[e] = A.doff[e];
+  const TU* xx = static_cast<const TU*>(x);
+  TU* ww = static_cast<TU*>(w);
+  const TU* dv = static_cast<const TU*>(A.dvals);
+  if (A.D <= 8) k_df_spmv_dia<TU, TU, SK, 8><<<t.G, 512, sm, st>>>(o, A.D, dv, A.ldd, A.n, xx, ww, t, part);
+  else k_df_spmv_dia<TU, TU, SK, 16><<<t.G, 512, sm, st>>>(o, A.D, dv, A.ldd, A.n, xx, ww, t, part);
+}
+
 void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, const SketchTiles& t, double* part,
                            cudaStream_t st) {
   const size_t sm = tile_smem_bytes(t.d, t.L, 0, t.zeta);
+  if (A.dvals) {
+    if (A.f32) launch_dia<float, true>(A, x, w, t, part, sm, st);
+    else launch_dia<float2, true>(A, x, w, t, part, sm, st);
+    return;
+  }
   if (A.ecol) {
     const bool narrow = A.W <= 6;
     if (A.f32) {
@@ -1362,6 +1472,10 @@ void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, const SketchT
 
 void launch_df_spmv(const CsrDF& A, const void* x, void* w, const SketchTiles& t, cudaStream_t st) {
   const size_t sm = tile_smem_bytes(t.d, t.L, 0, t.zeta);
+  if (A.dvals && !A.f32) {
+    launch_dia<float2, false>(A, x, w, t, nullptr, sm, st);
+    return;
+  }
   if (A.ecol && !A.f32) {
     auto k = A.W <= 6 ? k_df_spmv_ell<float2, float2, false, 6> : k_df_spmv_ell<float2, float2, false, 0>;
     k<<<t.G, 512, sm, st>>>(A.ecol, static_cast<const float2*>(A.evals), A.W, static_cast<const float2*>(x),

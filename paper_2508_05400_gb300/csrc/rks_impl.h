@@ -60,7 +60,20 @@ struct CsrDF {
   int W = 0;
   const int32_t* ecol = nullptr;
   const void* evals = nullptr;  // float2 pairs, or float when f32
+  // The same matrix by diagonals (optional; used first when set): D <= 16
+  // offsets doff[e] = column - row, increasing; row i's entry on diagonal e
+  // at dvals[e * ldd + i], zero where A has none.  In increasing column
+  // order, as a CSR row with sorted columns.
+  int D = 0;
+  int doff[16] = {};
+  int64_t ldd = 0;
+  const void* dvals = nullptr;  // float2 pairs, or float when f32
 };
+
+// Diagonal copy of a CSR matrix (see CsrDF); dvals (D * ldd values) is
+// cleared first.
+void launch_dia_fill(int64_t n, int D, const int* doff, int64_t ldd, const int32_t* rowptr, const int32_t* colind,
+                     const void* vals, bool f32, void* dvals, cudaStream_t st);
 
 // ELLPACK copy of a CSR matrix (see CsrDF): ecol and evals hold
 // ceil(n / 32) * 32 * W slots; vals are float2 pairs or float (f32).

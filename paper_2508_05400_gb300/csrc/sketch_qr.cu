@@ -244,7 +244,9 @@ int rgs(QrWork& w, std::vector<double>& R, std::vector<double>& S) {
 // reflectors with its entries above j dropped and rho_j taken off entry j,
 // so Theta u_j = v_j), then Q = H_0 ... H_{s-1} [I_s; 0] accumulated
 // backwards into columns s..2s-1.  The coefficient of every column update is
-// a sketched inner product, kept on the host: Theta y -= c v.
+// a sketched inner product: the sketches of the later columns are updated on
+// the host (Theta H_j = (I - beta v v^T) Theta), each pivot column is
+// re-read and re-sketched from the device before its reflector is formed.
 int rhqr(QrWork& w, std::vector<double>& R, std::vector<double>& scale) {
   const int s = w.s, d = w.d, ns = s + d;
   const int64_t nb = w.n - s;
@@ -271,6 +273,19 @@ int rhqr(QrWork& w, std::vector<double>& R, std::vector<double>& scale) {
   for (int j = 0; j < s; ++j) {
     double* y = &Y[(size_t)j * ns];
     double* v = &V[(size_t)j * ns];
+    if (j > 0) {
+      // the pivot column as the device holds it (its top rows and the sketch
+      // of the others), so that the reflector is consistent with the vector
+      // it is built from: Theta u_j = v_j to rounding
+      QK(cudaMemcpyAsync(colv.data(), col(w, j), (size_t)s * sizeof(float2), cudaMemcpyDeviceToHost, w.st));
+      rks::launch_df_sketch_vec(col(w, j) + s, w.tiles, w.part, false, w.st);
+      rks::launch_df_fold(w.part, d, w.tiles.G, w.sums, w.st);
+      QK(cudaGetLastError());
+      QK(cudaMemcpyAsync(w.host.data(), w.sums, (size_t)d * sizeof(double), cudaMemcpyDeviceToHost, w.st));
+      QK(cudaStreamSynchronize(w.st));
+      for (int i = 0; i < s; ++i) y[i] = (double)colv[i].x + (double)colv[i].y;
+      for (int i = 0; i < d; ++i) y[s + i] = w.host[i] * w.zscale;
+    }
     double nn = 0.0;
     for (int i = j; i < ns; ++i) nn += y[i] * y[i];
     const double nrm = std::sqrt(nn);
