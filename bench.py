@@ -452,6 +452,8 @@ def run_ours(args) -> None:
                              "same problem; both have resid <= 1e-8 ||A||_1, which fixes l only to the "
                              "eigenvalue condition number times that")}
         line["paths"] = paths
+        line["spmv_variants"] = _spmv_variants(rks)
+        line["exp1_tridiag_1e6"] = _exp1(rks)
         if args.workload == "convdiff3d_160":
             line["eig_error_vs_oracle_small"] = _small_oracle_errors(rks, prec)
             P2, u2 = _problem("convdiff2d_1000")
@@ -471,6 +473,41 @@ def run_ours(args) -> None:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _exp1(rks) -> dict:
+    """The paper's first experiment at n = 1e6 (Table 1 exponential diagonal,
+    N(0,1)/100 off-diagonals, LM, k = 40, m = 80, d = 160, zeta = 8,
+    |b^T y|/|l| <= 1e-10): rKS against Krylov-Schur with CGS2 on the same
+    kernels (double-float, keep = k), one solve each."""
+    from paper_2508_05400_gb300 import inputs as I
+    A = I.paper_tridiag(1_000_000, "exponential")
+    out = {}
+    for ortho in ("sketch", "cgs2"):
+        with rks.Solver.from_csr(A, 40, 40, 160, which="LM", tol=1e-10, zeta=8, u1=I.start_vector(A.n, 1),
+                                 keep=40, maxit=4000, ortho=ortho) as s:
+            info = s.solve(allow_noconv=True)
+        out["rks" if ortho == "sketch" else "ks_cgs2"] = {"ms": info["t_solve_ms"], "restarts": info["restarts"],
+                                                          "nmatvec": info["nmatvec"], "status": info["status"]}
+    out["speedup"] = out["ks_cgs2"]["ms"] / out["rks"]["ms"]
+    return out
+
+
+def _spmv_variants(rks) -> dict:
+    """Live GB/s of the SpMV+sketch on irregular matrices (algorithmic bytes:
+    nnz (8 + 4) + 4 (n + 1) + 16 n per product, CUDA events around every
+    launch of one restart of a double-float solve)."""
+    from paper_2508_05400_gb300 import inputs as I
+    out = {}
+    for name, A in (("powerlaw_2e6", I.powerlaw_matrix(2_000_003)), ("wide_rows_1e6", I.wide_rows_matrix(1_000_003))):
+        with rks.Solver.from_csr(A, 8, 24, 64, which="LM", tol=1e-12, zeta=8, profile=True, max_restarts=1) as s:
+            s.solve()
+            st = s.stats()["spmv_sketch"]
+            out[name] = {"format": s.spmv_format, "n": A.n, "nnz": A.nnz,
+                         "max_row": int((A.rowptr[1:] - A.rowptr[:-1]).max()),
+                         "launches": st["launches"], "us_per_launch": 1e3 * st["ms"] / max(st["launches"], 1),
+                         "gbs": st["bytes"] / max(st["ms"], 1e-9) / 1e6}
+    return out
 
 
 def _small_oracle_errors(rks, prec: str) -> dict:

@@ -225,6 +225,23 @@ int rks_solve(rks_ctx* c, rks_info* info);
  * ||Omega U e_i|| = 1; b: kk (host).  Any pointer may be NULL. */
 int rks_get_schur(rks_ctx* c, double* T, double* U, double* b);
 
+/* Storage the SpMV of a context reads, chosen at rks_create from the
+ * structure of A (double-float and mixed paths; the FP64 path reads CSR):
+ *   RKS_SPMV_CSR    CSR, two rows per thread (short, even rows);
+ *   RKS_SPMV_ELL    ELLPACK interleaved by 32-row slices (rows of at most 16
+ *                   entries with little padding);
+ *   RKS_SPMV_DIA    by diagonals (at most 16 distinct column - row offsets,
+ *                   little padding: stencils);
+ *   RKS_SPMV_WARP   CSR, one warp per row (mean row length >= 16);
+ *   RKS_SPMV_MERGE  CSR by merge path: rows + entries split evenly over the
+ *                   threads, partial rows folded in thread order, then the
+ *                   sketch (longest row > 128 and > 16 x the mean).
+ * The sum of a row is in column order for CSR, ELL and DIA (the same bits),
+ * lane-strided for WARP and split at thread boundaries for MERGE; every
+ * variant is deterministic.  Returns the format or RKS_EINVAL. */
+enum { RKS_SPMV_CSR = 0, RKS_SPMV_ELL = 1, RKS_SPMV_DIA = 2, RKS_SPMV_WARP = 3, RKS_SPMV_MERGE = 4 };
+int rks_spmv_format(const rks_ctx* c);
+
 /* Number of columns kk of the decomposition returned by rks_get_schur. */
 int rks_nkept(const rks_ctx* c);
 

@@ -66,6 +66,7 @@ struct rks_ctx {
   float2* U2 = nullptr;
   float* valsf = nullptr;  // mixed precision: FP32 values and basis
   int ell_w = 0;           // ELLPACK copy of A for the SpMV (0: not used)
+  bool spmv_merge = false, spmv_warp = false;   // CSR SpMV variants chosen by row lengths
   int dia_d = 0;           // diagonal copy of A for the SpMV (0: not used), its offsets
   int dia_off[16] = {};
   float2* dia_val2 = nullptr;
@@ -834,6 +835,7 @@ void free_ctx(rks_ctx* c) {
   cudaFree(c->coef); cudaFree(c->flag); cudaFree(c->Qd); cudaFree(c->u1);
   cudaFree(c->X); cudaFree(c->AX); cudaFree(c->rsum); cudaFree(c->pcol); cudaFree(c->plam);
   cudaFree(c->ell_col); cudaFree(c->ell_val2); cudaFree(c->ell_valf); cudaFree(c->dia_val2); cudaFree(c->dia_valf);
+  cudaFree(c->A2.mp_row); cudaFree(c->A2.mp_val); cudaFree(c->A2.mp_w); cudaFree(c->A2.mp_part);
   cudaFree(c->vals2); cudaFree(c->U2); cudaFree(c->S2); cudaFree(c->nrs); cudaFree(c->sj); cudaFree(c->Q2);
   cudaFree(c->rprev); cudaFree(c->znorm); cudaFree(c->tmp64); cudaFree(c->valsf); cudaFree(c->Uf);
   cudaFree(c->otab); cudaFree(c->lsr1); cudaFree(c->M2); cudaFree(c->bar); cudaFree(c->qimg);
@@ -978,6 +980,13 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
     for (int64_t i = 0; i < n; ++i) wmax = std::max(wmax, rp[i + 1] - rp[i]);
     const int64_t slots = (n + 31) / 32 * 32 * (int64_t)wmax;
     c->ell_w = (wmax >= 1 && wmax <= 16 && (double)slots <= 1.25 * (double)std::max<int64_t>(c->nnz, 1)) ? wmax : 0;
+    // row-length statistics for the CSR kernels: a warp per row for long
+    // rows, merge path when the longest row is far above the mean
+    {
+      const double mean = n ? (double)c->nnz / (double)n : 0.0;
+      c->spmv_merge = wmax > 128 && (double)wmax > 16.0 * mean;
+      c->spmv_warp = !c->spmv_merge && mean >= 16.0;
+    }
     // at most 16 distinct diagonals with little padding (stencils): a
     // diagonal copy for the SpMV instead
     {
@@ -1059,6 +1068,18 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
       for (int e = 0; e < c->dia_d; ++e) c->A2.doff[e] = c->dia_off[e];
       c->A2.ldd = ldd;
       c->A2.dvals = c->dia_val2;
+      c->A2.fmt = rks::kSpmvDia;
+    } else if (!c->ell_w && c->spmv_merge) {
+      // rows of very uneven length: merge path (rows + entries split evenly)
+      c->A2.fmt = rks::kSpmvMerge;
+      c->A2.mp_threads = (n + c->nnz + rks::kMergeItems - 1) / rks::kMergeItems;
+      const int64_t nbm = (c->A2.mp_threads + rks::kMergeCta - 1) / rks::kMergeCta;
+      if ((rc = dalloc(&c->A2.mp_row, (size_t)c->A2.mp_threads)) ||
+          (rc = dalloc(&c->A2.mp_val, (size_t)c->A2.mp_threads)) || (rc = dalloc(&c->A2.mp_part, (size_t)nbm + 1)))
+        return fail(rc);
+      if (c->prec == RKS_PREC_MIXED && (rc = dalloc(&c->A2.mp_w, (size_t)n))) return fail(rc);
+    } else if (!c->ell_w && c->spmv_warp) {
+      c->A2.fmt = rks::kSpmvWarp;          // long rows: a warp per row
     } else if (c->ell_w) {
       const size_t slots = (size_t)((n + 31) / 32 * 32) * c->ell_w;
       if ((rc = dalloc(&c->ell_col, slots)) || (rc = dalloc(&c->ell_val2, slots))) return fail(rc);
@@ -1071,6 +1092,7 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
       c->A2.W = c->ell_w;
       c->A2.ecol = c->ell_col;
       c->A2.evals = c->ell_val2;
+      c->A2.fmt = rks::kSpmvEll;
     }
     c->Ub = c->U2;
     if (rks::configure_df_kernels() != cudaSuccess) return fail(RKS_ECUDA);
@@ -1299,6 +1321,11 @@ int rks_solve(rks_ctx* c, rks_info* info) {
     info->t_solve_ms = ms;
   }
   return rc;
+}
+
+int rks_spmv_format(const rks_ctx* c) {
+  if (!c) return RKS_EINVAL;
+  return c->prec == RKS_PREC_FP64 ? RKS_SPMV_CSR : c->A2.fmt;
 }
 
 int rks_nkept(const rks_ctx* c) { return c ? c->kk : 0; }

@@ -517,6 +517,180 @@ __global__ void __launch_bounds__(512) k_df_spmv_ell(
   if (SK) tile_write_part(acc, d, part);
 }
 
+// w = A x (+ partial sketches) with one warp per row inside each sketch tile
+// (rows of many entries): lanes take the row's entries with a stride of 32,
+// then a fixed xor tree adds the lanes' double-float sums.
+template <class TA, class TU, bool SK, int LPR>
+__global__ void __launch_bounds__(512) k_df_spmv_warp(const int32_t* __restrict__ rowptr,
+                                                      const int32_t* __restrict__ colind, const TA* __restrict__ vals,
+                                                      const TU* __restrict__ x, TU* __restrict__ w,
+                                                      const SketchTiles tv, double* __restrict__ part) {
+  extern __shared__ __align__(16) uint8_t smraw[];
+  const int d = tv.d, L1 = tv.L + 1;
+  const TileSmem lay = tile_smem_layout(d, tv.L, 0, tv.zeta);
+  float2* acc = reinterpret_cast<float2*>(smraw + lay.acc);
+  if (SK)
+    for (int r = threadIdx.x; r < d; r += blockDim.x) acc[r] = make_float2(0.f, 0.f);
+  // groups of LPR lanes per row (LPR = 32: a warp per row)
+  const int grp = threadIdx.x / LPR, lane = threadIdx.x % LPR, ngrp = blockDim.x / LPR;
+  const int t0 = tv.ctile[blockIdx.x], t1 = tv.ctile[blockIdx.x + 1];
+  for (int t = t0; t < t1; ++t) {
+    const int buf = (t - t0) & 1;
+    float2* v = reinterpret_cast<float2*>(smraw + lay.vb) + buf * kTileRows;
+    int* of = reinterpret_cast<int*>(smraw + lay.offs) + buf * L1;
+    uint32_t* ms = reinterpret_cast<uint32_t*>(smraw + lay.ms) + buf * d;
+    uint16_t* es = reinterpret_cast<uint16_t*>(smraw + lay.es) + (size_t)buf * kTileRows * tv.zeta;
+    const int64_t r0 = tv.row[t];
+    const int rows = (int)(tv.row[t + 1] - r0);
+    if (SK) tile_stage(tv, t, r0, rows, of, ms, es);
+    const int nit = (rows + ngrp - 1) / ngrp;        // the same trip count for every lane
+    for (int it = 0; it < nit; ++it) {
+      const int l = it * ngrp + grp;
+      float sh = 0.f, sl = 0.f;
+      if (l < rows) {
+        const int p0 = rowptr[r0 + l], p1 = rowptr[r0 + l + 1];
+        for (int p = p0 + lane; p < p1; p += LPR) {
+          const float2 a = ldv(vals + p), xv = ldv(x + colind[p]);
+          df_mac(a.x, a.y, xv.x, xv.y, sh, sl);
+        }
+      }
+#pragma unroll
+      for (int o = LPR / 2; o; o >>= 1) {              // fixed xor tree inside the group
+        const float s2 = __shfl_xor_sync(0xffffffffu, sh, o);
+        const float t2 = __shfl_xor_sync(0xffffffffu, sl, o);
+        float ss, e;
+        two_sum(sh, s2, ss, e);
+        sh = ss;
+        sl = sl + t2 + e;
+      }
+      if (l < rows && lane == 0) v[l] = stv(w + r0 + l, df_norm(sh, sl));
+    }
+    if (SK) {
+      __syncthreads();
+      tile_gather(d, tv.H, v, of, ms, es, acc);
+    }
+  }
+  if (SK) tile_write_part(acc, d, part);
+}
+
+// Merge-path split: the number of rows i whose end marker lies before merge
+// position dd (marker of row i at rowptr[i + 1] + i); dd - i entries precede.
+__device__ __forceinline__ int64_t merge_split(int64_t dd, int64_t n, int64_t nnz, const int32_t* __restrict__ rowptr) {
+  int64_t lo = dd > nnz ? dd - nnz : 0, hi = dd < n ? dd : n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)rowptr[mid + 1] + mid < dd) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kMergeBlk = kMergeCta * kMergeItems;   // merge items per CTA
+
+// part_row[b] = rows whose end precedes merge position b * kMergeBlk, b <= nb
+__global__ void k_merge_partition(int64_t n, int64_t nnz, const int32_t* __restrict__ rowptr, int64_t nb,
+                                  int64_t* __restrict__ part_row) {
+  const int64_t total = n + nnz;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b <= nb; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t dd = b * kMergeBlk < total ? b * kMergeBlk : total;
+    part_row[b] = merge_split(dd, n, nnz, rowptr);
+  }
+}
+
+// w' = A x by merge path.  CTA b owns merge positions [b B, (b + 1) B)
+// (B = kMergeBlk rows + entries): first its entries' double-float products
+// a_p x[col_p] (coalesced, many loads in flight) and its rows' end offsets go
+// to shared memory, then thread t walks positions [t K, (t + 1) K) of them
+// (K = kMergeItems): a row ending in its range is written to wd (partial when
+// it began before), the row still open at its end goes to (mp_row, mp_val).
+// The products and their order within a row are those of the CSR kernel.
+template <class TA>
+__global__ void __launch_bounds__(kMergeCta) k_df_spmv_merge(
+    int64_t n, int64_t nnz, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+    const TA* __restrict__ vals, const float2* __restrict__ x2, const float* __restrict__ x1,
+    const int64_t* __restrict__ part_row, float2* __restrict__ wd, int* __restrict__ mp_row,
+    float2* __restrict__ mp_val, int64_t nthreads) {
+  __shared__ float2 prod[kMergeBlk];
+  __shared__ int32_t rend[kMergeBlk + 1];
+  const int64_t total = n + nnz;
+  const int64_t b = blockIdx.x;
+  const int64_t rlo = part_row[b], rhi = part_row[b + 1];
+  const int64_t dlo = b * kMergeBlk, dhi = dlo + kMergeBlk < total ? dlo + kMergeBlk : total;
+  const int64_t jlo = dlo - rlo, jhi = dhi - rhi;     // entries of the CTA's range
+  const int ne = (int)(jhi - jlo), nr = (int)(rhi - rlo);
+  for (int e = threadIdx.x; e < ne; e += kMergeCta) {
+    const int64_t p = jlo + e;
+    const float2 a = ldv(vals + p);
+    const int c = colind[p];
+    const float2 xv = x2 ? x2[c] : make_float2(x1[c], 0.f);
+    const float pr = a.x * xv.x;
+    float er = fmaf(a.x, xv.x, -pr);
+    er = fmaf(a.x, xv.y, er);
+    er = fmaf(a.y, xv.x, er);
+    prod[e] = make_float2(pr, er);
+  }
+  for (int r = threadIdx.x; r <= nr; r += kMergeCta) rend[r] = rowptr[rlo + r + 1 <= n ? rlo + r + 1 : n];
+  __syncthreads();
+  const int64_t t = b * kMergeCta + threadIdx.x;
+  if (t >= nthreads) return;
+  const int64_t d0 = t * kMergeItems;
+  if (d0 >= total) return;
+  const int64_t d1 = d0 + kMergeItems < total ? d0 + kMergeItems : total;
+  // split inside the CTA's rows: markers of rows rlo + q at rend[q] + rlo + q
+  auto split = [&](int64_t dd) {
+    int lo = 0, hi = nr;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((int64_t)rend[mid] + rlo + mid < dd) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo;
+  };
+  int q = split(d0);
+  const int qe = split(d1);
+  int64_t j = d0 - (rlo + q);
+  const int64_t je = d1 - (rlo + qe);
+  float sh = 0.f, sl = 0.f;
+  for (; q < qe; ++q) {
+    const int64_t pe = rend[q];
+    for (; j < pe; ++j) {
+      const float2 v = prod[j - jlo];
+      df_add(v.x, v.y, sh, sl);
+    }
+    wd[rlo + q] = df_norm(sh, sl);
+    sh = 0.f;
+    sl = 0.f;
+  }
+  for (; j < je; ++j) {
+    const float2 v = prod[j - jlo];
+    df_add(v.x, v.y, sh, sl);
+  }
+  mp_row[t] = rlo + qe < n ? (int)(rlo + qe) : -1;
+  mp_val[t] = df_norm(sh, sl);
+}
+
+// Fold of the merge-path carries: the first thread of each run of equal
+// carry rows adds the run's partial sums, in thread order, to that row.
+__global__ void k_df_merge_fix(const int* __restrict__ mp_row, const float2* __restrict__ mp_val, int64_t nthreads,
+                               float2* __restrict__ wd) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nthreads;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = mp_row[t];
+    if (r < 0 || (t > 0 && mp_row[t - 1] == r)) continue;
+    float sh = 0.f, sl = 0.f;
+    for (int64_t u = t; u < nthreads && mp_row[u] == r; ++u) df_add(mp_val[u].x, mp_val[u].y, sh, sl);
+    const float2 cur = wd[r];
+    df_add(cur.x, cur.y, sh, sl);
+    wd[r] = df_norm(sh, sl);
+  }
+}
+
+// FP32 copy of a double-float vector (the stored basis vector of the FP32 phase)
+__global__ void k_df_round_f32(int64_t n, const float2* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i].x + a[i].y;
+}
+
 // Offsets of the diagonal copy, passed by value.
 struct DiaOffs {
   int o[16];
@@ -528,7 +702,7 @@ struct DiaOffs {
 // order (the CSR kernel's order, the same bits); two rows per thread, the
 // tiles and the sketch gather of k_df_spmv_ell.
 template <class TU, class TA, bool SK, int DMAX>
-__global__ void __launch_bounds__(512) k_df_spmv_dia(const DiaOffs offs, int D, const TA* __restrict__ dv,
+__global__ void __launch_bounds__(512, 2) k_df_spmv_dia(const DiaOffs offs, int D, const TA* __restrict__ dv,
                                                      int64_t ldd, int64_t n, const TU* __restrict__ x,
                                                      TU* __restrict__ w, const SketchTiles tv,
                                                      double* __restrict__ part) {
@@ -552,22 +726,29 @@ __global__ void __launch_bounds__(512) k_df_spmv_dia(const DiaOffs offs, int D, 
     const int la = threadIdx.x, lb = threadIdx.x + 512;
     const bool oka = la < rows, okb = lb < rows;
     const int64_t ia = r0 + la, ib = r0 + lb;
-    float2 va[DMAX], vb[DMAX], xa[DMAX], xb[DMAX];
-#pragma unroll
-    for (int e = 0; e < DMAX; ++e) {
-      const bool on = e < D;
-      const int64_t ja = ia + offs.o[e], jb = ib + offs.o[e];
-      va[e] = (on && oka) ? ldv(dv + e * ldd + ia) : make_float2(0.f, 0.f);
-      vb[e] = (on && okb) ? ldv(dv + e * ldd + ib) : make_float2(0.f, 0.f);
-      xa[e] = (on && oka && ja >= 0 && ja < n) ? ldv(x + ja) : make_float2(0.f, 0.f);
-      xb[e] = (on && okb && jb >= 0 && jb < n) ? ldv(x + jb) : make_float2(0.f, 0.f);
-    }
+    // rounds of four diagonals: the loads of a round are all in flight at
+    // once, and the registers stay within two CTAs per SM
+    constexpr int RU = 4;
     float sa = 0.f, ta = 0.f, sb = 0.f, tb = 0.f;
 #pragma unroll
-    for (int e = 0; e < DMAX; ++e) {
-      if (e < D) {
-        df_mac(va[e].x, va[e].y, xa[e].x, xa[e].y, sa, ta);
-        df_mac(vb[e].x, vb[e].y, xb[e].x, xb[e].y, sb, tb);
+    for (int e0 = 0; e0 < DMAX; e0 += RU) {
+      float2 va[RU], vb[RU], xa[RU], xb[RU];
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
+        const int e = e0 + u;
+        const bool on = e < D;
+        const int64_t ja = ia + offs.o[e], jb = ib + offs.o[e];
+        va[u] = (on && oka) ? ldv(dv + e * ldd + ia) : make_float2(0.f, 0.f);
+        vb[u] = (on && okb) ? ldv(dv + e * ldd + ib) : make_float2(0.f, 0.f);
+        xa[u] = (on && oka && ja >= 0 && ja < n) ? ldv(x + ja) : make_float2(0.f, 0.f);
+        xb[u] = (on && okb && jb >= 0 && jb < n) ? ldv(x + jb) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
+        if (e0 + u < D) {
+          df_mac(va[u].x, va[u].y, xa[u].x, xa[u].y, sa, ta);
+          df_mac(vb[u].x, vb[u].y, xb[u].x, xb[u].y, sb, tb);
+        }
       }
     }
     if (oka) v[la] = stv(w + ia, df_norm(sa, ta));
@@ -1376,6 +1557,9 @@ static cudaError_t configure_df_kernels_once() {
   RKS_SMEM((k_df_spmv_sketch<float2, float2, true>)); RKS_SMEM((k_df_spmv_sketch<float, float, true>));
   RKS_SMEM((k_df_spmv_sketch<float2, float2, false>));
   RKS_SMEM((k_df_spmv_ell<float2, float2, true, 0>)); RKS_SMEM((k_df_spmv_ell<float, float, true, 0>));
+  RKS_SMEM((k_df_spmv_warp<float2, float2, true, 32>)); RKS_SMEM((k_df_spmv_warp<float, float, true, 32>));
+  RKS_SMEM((k_df_spmv_warp<float2, float2, false, 32>)); RKS_SMEM((k_df_spmv_warp<float2, float2, true, 8>));
+  RKS_SMEM((k_df_spmv_warp<float, float, true, 8>)); RKS_SMEM((k_df_spmv_warp<float2, float2, false, 8>));
   RKS_SMEM((k_df_spmv_dia<float2, float2, true, 8>)); RKS_SMEM((k_df_spmv_dia<float, float, true, 8>));
   RKS_SMEM((k_df_spmv_dia<float2, float2, true, 16>)); RKS_SMEM((k_df_spmv_dia<float, float, true, 16>));
   RKS_SMEM((k_df_spmv_dia<float2, float2, false, 8>)); RKS_SMEM((k_df_spmv_dia<float2, float2, false, 16>));
@@ -1439,9 +1623,46 @@ static void launch_dia(const CsrDF& A, const void* x, void* w, const SketchTiles
   else k_df_spmv_dia<TU, TU, SK, 16><<<t.G, 512, sm, st>>>(o, A.D, dv, A.ldd, A.n, xx, ww, t, part);
 }
 
+// merge path: w = A x (double-float partials folded), then rounded to FP32 (f32)
+static void launch_merge(const CsrDF& A, const void* x, void* w, cudaStream_t st) {
+  float2* wd = A.f32 ? A.mp_w : static_cast<float2*>(w);
+  const int64_t nb = (A.mp_threads + kMergeCta - 1) / kMergeCta;
+  const float2* x2 = A.f32 ? nullptr : static_cast<const float2*>(x);
+  const float* x1 = A.f32 ? static_cast<const float*>(x) : nullptr;
+  k_merge_partition<<<df_grid(nb + 1, 256), 256, 0, st>>>(A.n, A.nnz, A.rowptr, nb, A.mp_part);
+  if (A.f32)
+    k_df_spmv_merge<float><<<(unsigned)nb, kMergeCta, 0, st>>>(A.n, A.nnz, A.rowptr, A.colind,
+                                                              static_cast<const float*>(A.vals), x2, x1, A.mp_part,
+                                                              wd, A.mp_row, A.mp_val, A.mp_threads);
+  else
+    k_df_spmv_merge<float2><<<(unsigned)nb, kMergeCta, 0, st>>>(A.n, A.nnz, A.rowptr, A.colind,
+                                                               static_cast<const float2*>(A.vals), x2, x1, A.mp_part,
+                                                               wd, A.mp_row, A.mp_val, A.mp_threads);
+  k_df_merge_fix<<<df_grid(A.mp_threads, 256), 256, 0, st>>>(A.mp_row, A.mp_val, A.mp_threads, wd);
+  if (A.f32) k_df_round_f32<<<df_grid(A.n, 256), 256, 0, st>>>(A.n, wd, static_cast<float*>(w));
+}
+
 void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, const SketchTiles& t, double* part,
                            cudaStream_t st) {
   const size_t sm = tile_smem_bytes(t.d, t.L, 0, t.zeta);
+  if (A.fmt == kSpmvMerge) {
+    launch_merge(A, x, w, st);
+    launch_df_sketch_vec(w, t, part, A.f32, st);
+    return;
+  }
+  if (A.fmt == kSpmvWarp) {
+    const bool wide = A.nnz >= 64 * A.n;   // mean row length >= 64: a warp per row, else 8 lanes
+    if (A.f32) {
+      auto k = wide ? k_df_spmv_warp<float, float, true, 32> : k_df_spmv_warp<float, float, true, 8>;
+      k<<<t.G, 512, sm, st>>>(A.rowptr, A.colind, static_cast<const float*>(A.vals), static_cast<const float*>(x),
+                              static_cast<float*>(w), t, part);
+    } else {
+      auto k = wide ? k_df_spmv_warp<float2, float2, true, 32> : k_df_spmv_warp<float2, float2, true, 8>;
+      k<<<t.G, 512, sm, st>>>(A.rowptr, A.colind, static_cast<const float2*>(A.vals), static_cast<const float2*>(x),
+                              static_cast<float2*>(w), t, part);
+    }
+    return;
+  }
   if (A.dvals) {
     if (A.f32) launch_dia<float, true>(A, x, w, t, part, sm, st);
     else launch_dia<float2, true>(A, x, w, t, part, sm, st);
@@ -1472,6 +1693,16 @@ void launch_df_spmv_sketch(const CsrDF& A, const void* x, void* w, const SketchT
 
 void launch_df_spmv(const CsrDF& A, const void* x, void* w, const SketchTiles& t, cudaStream_t st) {
   const size_t sm = tile_smem_bytes(t.d, t.L, 0, t.zeta);
+  if (A.fmt == kSpmvMerge && !A.f32) {
+    launch_merge(A, x, w, st);
+    return;
+  }
+  if (A.fmt == kSpmvWarp && !A.f32) {
+    auto k = A.nnz >= 64 * A.n ? k_df_spmv_warp<float2, float2, false, 32> : k_df_spmv_warp<float2, float2, false, 8>;
+    k<<<t.G, 512, sm, st>>>(A.rowptr, A.colind, static_cast<const float2*>(A.vals), static_cast<const float2*>(x),
+                            static_cast<float2*>(w), t, nullptr);
+    return;
+  }
   if (A.dvals && !A.f32) {
     launch_dia<float2, false>(A, x, w, t, nullptr, sm, st);
     return;

@@ -68,7 +68,21 @@ struct CsrDF {
   int doff[16] = {};
   int64_t ldd = 0;
   const void* dvals = nullptr;  // float2 pairs, or float when f32
+  // Irregular rows (CSR only; see rks_spmv_format): kSpmvWarp takes a row
+  // per warp inside the sketch tiles; kSpmvMerge splits rows + entries evenly
+  // over threads (merge path), then folds the partial rows and sketches w.
+  int fmt = 0;
+  int64_t* mp_part = nullptr;   // merge path: first row of every CTA's range
+  int* mp_row = nullptr;        // merge path: carry row of every thread (-1: none)
+  float2* mp_val = nullptr;     // its partial sum (double-float)
+  float2* mp_w = nullptr;       // double-float result before rounding to FP32 (f32 only)
+  int64_t mp_threads = 0;
 };
+
+// SpMV formats (CsrDF::fmt, rks_spmv_format)
+enum { kSpmvCsr = 0, kSpmvEll = 1, kSpmvDia = 2, kSpmvWarp = 3, kSpmvMerge = 4 };
+constexpr int kMergeItems = 12;  // rows + entries per thread of the merge-path SpMV
+constexpr int kMergeCta = 256;   // threads per CTA of the merge path (a CTA stages 12 x 256 items)
 
 // Diagonal copy of a CSR matrix (see CsrDF); dvals (D * ldd values) is
 // cleared first.

@@ -355,3 +355,60 @@ def grf_member_fields(i: int, seed0: int = 20000, N: int = 512) -> np.ndarray:
     out[1] = u[0]
     out[2] = u[1]
     return out
+
+
+def powerlaw_matrix(n: int, seed: int = 0, max_len: int = 10000, alpha: float = 1.2,
+                    lead=(10.0, 9.0, 8.0, 7.0, 6.0, 5.5, 5.0, 4.5)) -> CSR:
+    """Sparse non-symmetric matrix whose row lengths follow a power law (rows
+    of 1 to ``max_len`` entries, P(L >= l) ~ l^-alpha), like the irregular
+    matrices of large sparse collections.  Row i: L_i = min(max_len,
+    floor(u^(-1/alpha))) entries at distinct random columns (SplitMix64
+    uniforms of ``seed``), values N(0,1) * 0.5 / sqrt(L_i), plus a diagonal:
+    ``lead`` for the first rows (well separated eigenvalues of largest
+    modulus), then values in [0, 2)."""
+    u = uniform01(seed, n)
+    L = np.minimum(max_len, np.floor(np.maximum(u, 1e-300) ** (-1.0 / alpha))).astype(np.int64)
+    L = np.maximum(L, 1)
+    tot = int(L.sum())
+    uc = uniform01(seed + 1, tot)
+    g = normal(seed + 2, tot)
+    rows = np.repeat(np.arange(n, dtype=np.int64), L)
+    cols = np.minimum((uc * n).astype(np.int64), n - 1)
+    vals = g * (0.5 / np.sqrt(L[rows]))
+    keep = cols != rows                      # the diagonal is set below
+    rows, cols, vals = rows[keep], cols[keep], vals[keep]
+    key = rows * n + cols                    # drop repeated (row, column) pairs
+    _, first = np.unique(key, return_index=True)
+    rows, cols, vals = rows[first], cols[first], vals[first]
+    diag = 2.0 * uniform01(seed + 3, n)
+    diag[:len(lead)] = lead
+    rows = np.concatenate([rows, np.arange(n)])
+    cols = np.concatenate([cols, np.arange(n)])
+    vals = np.concatenate([vals, diag])
+    return _from_triplets(n, rows, cols, vals, np.float64)
+
+
+def wide_rows_matrix(n: int, seed: int = 0, lo: int = 32, hi: int = 48,
+                     lead=(10.0, 9.0, 8.0, 7.0, 6.0, 5.5, 5.0, 4.5)) -> CSR:
+    """Sparse non-symmetric matrix with rows of lo..hi entries at random
+    columns (values N(0,1) * 0.5 / sqrt(L_i)) plus the diagonal of
+    ``powerlaw_matrix``."""
+    u = uniform01(seed, n)
+    L = (lo + np.floor(u * (hi - lo + 1))).astype(np.int64)
+    tot = int(L.sum())
+    uc = uniform01(seed + 1, tot)
+    g = normal(seed + 2, tot)
+    rows = np.repeat(np.arange(n, dtype=np.int64), L)
+    cols = np.minimum((uc * n).astype(np.int64), n - 1)
+    vals = g * (0.5 / np.sqrt(L[rows]))
+    keep = cols != rows
+    rows, cols, vals = rows[keep], cols[keep], vals[keep]
+    key = rows * n + cols
+    _, first = np.unique(key, return_index=True)
+    rows, cols, vals = rows[first], cols[first], vals[first]
+    diag = 2.0 * uniform01(seed + 3, n)
+    diag[:len(lead)] = lead
+    rows = np.concatenate([rows, np.arange(n)])
+    cols = np.concatenate([cols, np.arange(n)])
+    vals = np.concatenate([vals, diag])
+    return _from_triplets(n, rows, cols, vals, np.float64)

@@ -113,6 +113,8 @@ def lib() -> C.CDLL:
         L.rks_get_stats.restype = C.c_int
         L.rks_get_history.argtypes = [_P, _P, _P, C.c_int]
         L.rks_get_history.restype = C.c_int
+        L.rks_spmv_format.argtypes = [_P]
+        L.rks_spmv_format.restype = C.c_int
         L.rks_nkept.argtypes = [_P]
         L.rks_nkept.restype = C.c_int
         L.rks_nwanted.argtypes = [_P]
@@ -283,6 +285,13 @@ class Solver:
         st = Stats()
         _check(lib().rks_get_stats(self._h, C.byref(st)), "rks_get_stats")
         return st.as_dict()
+
+    SPMV_FORMATS = ("csr", "ell", "dia", "warp", "merge")
+
+    @property
+    def spmv_format(self) -> str:
+        """Storage the SpMV reads (rks_spmv_format)."""
+        return self.SPMV_FORMATS[_check(lib().rks_spmv_format(self._h), "rks_spmv_format", ok=(0, 1, 2, 3, 4))]
 
     @property
     def nkept(self) -> int:
