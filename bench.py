@@ -54,6 +54,11 @@ NCU_TRAFFIC = {
     # third restart of the 1000^2 workload: 541.6 / 547.1 MB against 528 /
     # 536 MB; the bin lists of Omega are the rest)
     ("update_sketch", "df", "convdiff2d_1000"): {"kernels_sha": "fdc1ba79cef500a9", "ratio": 1.023},
+    # k_df_update_sketch<float> of the 160^3 operator at 100^3 (FP32 phase, c ~ 41, first expansion;
+    # profiles/update_spmv_ls_convdiff3d_100_mixed.md): DRAM 189.1 MB against 172 MB of algorithmic
+    # bytes.  Applied to the mean launch of the 160^3 solve (c ~ 100, FP32 and double-float launches),
+    # where the bin lists' share of the traffic is smaller: an upper estimate by a few percent.
+    ("update_sketch", "mixed", "convdiff3d_160"): {"kernels_sha": "fdc1ba79cef500a9", "ratio": 1.10},
 }
 
 
@@ -144,9 +149,14 @@ DTYPES = {"fp64": "f64",
                     "accumulation, df64 finish below the f32 floor; f64 sketch/LS/Schur/residuals/Rayleigh")}
 
 
-def _problem(workload: str):
+def _problem(workload: str, grid: int = 0):
+    """The workload's problem; grid > 0 replaces the grid side (smaller cases
+    of the same operator for profiling)."""
     from paper_2508_05400_gb300 import inputs as I
-    P = I.convdiff3d_problem() if workload == "convdiff3d_160" else I.convdiff2d_problem()
+    if workload == "convdiff3d_160":
+        P = I.convdiff3d_problem(N=grid) if grid else I.convdiff3d_problem()
+    else:
+        P = I.convdiff2d_problem(N=grid) if grid else I.convdiff2d_problem()
     u1 = I.start_vector(P.A.n, P.u1_seed)
     return P, u1
 
@@ -233,7 +243,7 @@ def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    P, u1 = _problem(args.workload)
+    P, u1 = _problem(args.workload, args.grid)
     sampler = OracleSampler(P, u1)
     nm = REFERENCE_NMATVEC[args.workload]
     vals, secs, last = [], [], None
@@ -296,7 +306,7 @@ def run_ours(args) -> None:
     from paper_2508_05400_gb300 import rks
 
     prec = args.prec or DEFAULT_PREC[args.workload]
-    P, u1 = _problem(args.workload)
+    P, u1 = _problem(args.workload, args.grid)
     A = P.A
     keep = P.k if args.keep < 0 else args.keep
     stream = torch.cuda.current_stream(dev)
@@ -307,20 +317,22 @@ def run_ours(args) -> None:
     mk = lambda prof: rks.Solver(A.n, d_rowptr, d_colind, d_vals, P.k, P.p, P.d, which=P.which,
                                  seed=P.omega_seed, zeta=P.zeta, u1=d_u1, device=True,
                                  stream=stream.cuda_stream, profile=prof, prec=prec, maxit=args.maxit,
-                                 keep=keep, ortho=args.ortho, aggressive=args.aggressive, **P.solver_opts())
+                                 max_restarts=args.max_restarts, keep=keep, ortho=args.ortho,
+                                 aggressive=args.aggressive, **P.solver_opts())
+    noconv_ok = args.max_restarts > 0
     X_dev = torch.empty((P.k + 2, A.n), dtype=torch.float64, device=dev)
     # one untimed solve with every kernel timed (the first warm-up): the
     # per-kernel breakdown and the dominant kernel; the timed solves then put
     # events around that kernel only
     with mk(True) as s_all:
-        s_all.solve(allow_noconv=False)
+        s_all.solve(allow_noconv=noconv_ok)
         breakdown = s_all.stats()
     dom = max((c for c in rks.KCLASSES if c != "other" and breakdown[c]["ms"] > 0),
               key=lambda c: breakdown[c]["ms"])
     solver = mk(rks.profile_mask(dom))
 
     def step():
-        info = solver.solve(allow_noconv=False)
+        info = solver.solve(allow_noconv=noconv_ok)
         lam, _, res = solver.eigpairs(X_out=X_dev)
         rq = solver.rayleigh()
         return info, lam, res, rq
@@ -454,6 +466,7 @@ def run_ours(args) -> None:
         line["paths"] = paths
         line["spmv_variants"] = _spmv_variants(rks)
         line["exp1_tridiag_1e6"] = _exp1(rks)
+        line["batched_uneven256"] = _batched(rks)
         if args.workload == "convdiff3d_160":
             line["eig_error_vs_oracle_small"] = _small_oracle_errors(rks, prec)
             P2, u2 = _problem("convdiff2d_1000")
@@ -490,6 +503,27 @@ def _exp1(rks) -> dict:
         out["rks" if ortho == "sketch" else "ks_cgs2"] = {"ms": info["t_solve_ms"], "restarts": info["restarts"],
                                                           "nmatvec": info["nmatvec"], "status": info["status"]}
     out["speedup"] = out["ks_cgs2"]["ms"] / out["rks"]["ms"]
+    return out
+
+
+def _batched(rks) -> dict:
+    """The batch of 256 uneven 2D convection-diffusion problems (sides
+    U{70..450}, log-normal diffusivity, convection in [0, 30]^2, FP32 values;
+    k = 8, p = 24, d = 64, residual <= 1e-8, thick restart keep = 8), solved
+    concurrently (16 host threads, one stream per problem), mixed and
+    double-float; host wall time of rks_solve_batched."""
+    from paper_2508_05400_gb300 import inputs as I
+    probs = [I.uneven_convdiff2d_problem(i) for i in range(256)]
+    P0 = probs[0]
+    out = {"sum_n": int(sum(P.A.n for P in probs))}
+    for prec in ("mixed", "df"):
+        with rks.Batch([P.A for P in probs], P0.k, P0.p, P0.d, which=P0.which, zeta=P0.zeta, nthreads=16,
+                       prec=prec, keep=P0.k, maxit=4000, **P0.solver_opts()) as b:
+            t0 = time.perf_counter()
+            infos = b.solve(nthreads=16, allow_noconv=True)
+            wall = time.perf_counter() - t0
+        out[prec] = {"ms": wall * 1e3, "converged": int(sum(i["converged"] for i in infos)),
+                     "max_resid": float(max(i["max_resid"] for i in infos))}
     return out
 
 
@@ -543,6 +577,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--e2e-steps", type=int, default=2, help="solves in the end-to-end leg (mean reported)")
     ap.add_argument("--maxit", type=int, default=4000, help="restart limit of each solve")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="grid side in place of the workload's (smaller cases for profiling); 0: the workload's")
+    ap.add_argument("--max-restarts", type=int, default=0,
+                    help="stop every solve after this many restarts (profiling); 0: run to convergence")
     ap.add_argument("--ortho", default="sketch", choices=["sketch", "cgs2"],
                     help="sketch: randomized Gram-Schmidt (rKS); cgs2: the Krylov-Schur baseline "
                          "with Euclidean CGS2 (DF only)")

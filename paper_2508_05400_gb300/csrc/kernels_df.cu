@@ -612,6 +612,8 @@ __global__ void __launch_bounds__(kMergeCta) k_df_spmv_merge(
     float2* __restrict__ mp_val, int64_t nthreads) {
   __shared__ float2 prod[kMergeBlk];
   __shared__ int32_t rend[kMergeBlk + 1];
+  __shared__ int crow[kMergeCta];
+  __shared__ float2 cval[kMergeCta];
   const int64_t total = n + nnz;
   const int64_t b = blockIdx.x;
   const int64_t rlo = part_row[b], rhi = part_row[b + 1];
@@ -630,12 +632,13 @@ __global__ void __launch_bounds__(kMergeCta) k_df_spmv_merge(
     prod[e] = make_float2(pr, er);
   }
   for (int r = threadIdx.x; r <= nr; r += kMergeCta) rend[r] = rowptr[rlo + r + 1 <= n ? rlo + r + 1 : n];
+  crow[threadIdx.x] = -1;
+  cval[threadIdx.x] = make_float2(0.f, 0.f);
   __syncthreads();
   const int64_t t = b * kMergeCta + threadIdx.x;
-  if (t >= nthreads) return;
   const int64_t d0 = t * kMergeItems;
-  if (d0 >= total) return;
   const int64_t d1 = d0 + kMergeItems < total ? d0 + kMergeItems : total;
+  if (t < nthreads && d0 < total) {
   // split inside the CTA's rows: markers of rows rlo + q at rend[q] + rlo + q
   auto split = [&](int64_t dd) {
     int lo = 0, hi = nr;
@@ -665,12 +668,50 @@ __global__ void __launch_bounds__(kMergeCta) k_df_spmv_merge(
     const float2 v = prod[j - jlo];
     df_add(v.x, v.y, sh, sl);
   }
-  mp_row[t] = rlo + qe < n ? (int)(rlo + qe) : -1;
-  mp_val[t] = df_norm(sh, sl);
+  crow[threadIdx.x] = rlo + qe < n ? (int)(rlo + qe) : -1;
+  cval[threadIdx.x] = df_norm(sh, sl);
+  }
+  __syncthreads();
+  // Fold of the threads' open rows, in thread order: a row that ends inside
+  // the CTA (row < rhi) gets its partial sums added to the tail its last
+  // thread wrote; the row still open at the CTA's end becomes the CTA's carry
+  // (mp_row[b], mp_val[b]; -1: none).
+  if (threadIdx.x == 0) {
+    bool carried = false;
+    int cur = -1;
+    float ch = 0.f, cl = 0.f;
+    auto flush = [&]() {
+      if (cur < 0) return;
+      if (cur < rhi) {
+        const float2 tail = wd[cur];
+        df_add(tail.x, tail.y, ch, cl);
+        wd[cur] = df_norm(ch, cl);
+      } else {
+        mp_row[b] = cur;
+        mp_val[b] = df_norm(ch, cl);
+        carried = true;
+      }
+    };
+    for (int u = 0; u < kMergeCta; ++u) {
+      const int r = crow[u];
+      if (r != cur) {
+        flush();
+        cur = r;
+        ch = 0.f;
+        cl = 0.f;
+      }
+      if (r >= 0) {
+        const float2 v = cval[u];
+        df_add(v.x, v.y, ch, cl);
+      }
+    }
+    flush();
+    if (!carried) mp_row[b] = -1;
+  }
 }
 
-// Fold of the merge-path carries: the first thread of each run of equal
-// carry rows adds the run's partial sums, in thread order, to that row.
+// Fold of the merge-path carries of the CTAs: the first CTA of each run of
+// equal carry rows adds the run's partial sums, in CTA order, to that row.
 __global__ void k_df_merge_fix(const int* __restrict__ mp_row, const float2* __restrict__ mp_val, int64_t nthreads,
                                float2* __restrict__ wd) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nthreads;
@@ -1638,7 +1679,7 @@ static void launch_merge(const CsrDF& A, const void* x, void* w, cudaStream_t st
     k_df_spmv_merge<float2><<<(unsigned)nb, kMergeCta, 0, st>>>(A.n, A.nnz, A.rowptr, A.colind,
                                                                static_cast<const float2*>(A.vals), x2, x1, A.mp_part,
                                                                wd, A.mp_row, A.mp_val, A.mp_threads);
-  k_df_merge_fix<<<df_grid(A.mp_threads, 256), 256, 0, st>>>(A.mp_row, A.mp_val, A.mp_threads, wd);
+  k_df_merge_fix<<<df_grid(nb, 256), 256, 0, st>>>(A.mp_row, A.mp_val, nb, wd);
   if (A.f32) k_df_round_f32<<<df_grid(A.n, 256), 256, 0, st>>>(A.n, wd, static_cast<float*>(w));
 }
 
