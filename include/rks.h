@@ -336,6 +336,81 @@ int rks_batch_status(const rks_batch* b, int i);
 /* Free every context of the batch.  Safe on NULL. */
 void rks_destroy_batched(rks_batch* b);
 
+/* ---- Batched solve in one persistent launch -------------------------- */
+
+/* Many independent problems solved by one persistent kernel (Algorithm 1
+ * with Algorithm 2 for every problem, the small dense steps on the device):
+ * clusters of G CTAs (G = 1, 2, 4 or 8 on the same GPU) take problems from a
+ * device work queue, largest first (cost nnz + n m); the rows of a problem are
+ * split over the CTAs of its cluster.  Double-float basis and matrix values,
+ * FP64 sketch sums, least squares, dense steps and residuals; the restart
+ * keeps the max(k, min(opts.keep, m / 2)) best Schur vectors (a thick restart;
+ * the truncation of Algorithm 1 with a larger size) and locks nothing;
+ * convergence when the rks_nwanted best estimates (opts.conv scale) are <= tol,
+ * then, if opts.verify > 0, the FP64 residuals ||A x - l x|| / (||A||_1 ||x||)
+ * must be <= verify, else tol is divided by 4 and the restarts go on (bounded
+ * by opts.maxit).  Omega is the sparse-sign embedding of rks_create for every
+ * problem (rks_sketch_pairs with `seed`), the start vector the default of
+ * rks_create (SplitMix64(seed + 1)).  Every reduction has a fixed order that
+ * does not depend on G or on the other problems: a problem's results are the
+ * same bits in any batch and for any G. */
+typedef struct rks_dbatch rks_dbatch;
+
+/* Problems i < count from host CSR arrays (rowptr[i], colind[i], vals[i] of
+ * vals_dtype, n[i] rows; values finite and |v| <= 3e38); k, p (m = k + p <= 64,
+ * k + 1 <= 32, p >= 2), d (>= m + 1, >= 2 zeta), which, tol and seed as for
+ * rks_create; max(k, min(opts.keep, m / 2)) + 1 <= 32.  Of opts (may be
+ * NULL) zeta, maxit, conv, verify, keep and stream are used; mem_device and u1
+ * must be 0 / NULL; the other fields are ignored.
+ * ctas_per_problem: 1, 2, 4 or 8 CTAs per problem, or 0 to time one restart
+ * of the whole batch with each and keep the fastest (rks_dbatch_config).
+ * Copies everything to the device (the caller keeps its arrays) and captures
+ * the launch in a CUDA graph.  RKS_EINVAL for an invalid argument or a
+ * problem whose shared-memory layout exceeds the device's limit. */
+int rks_create_batched_dev(rks_dbatch** out, int count, const int64_t* n, const int32_t* const* rowptr,
+                           const int32_t* const* colind, const void* const* vals, int vals_dtype, int k, int p,
+                           int d, int which, double tol, uint64_t seed, const rks_opts* opts, int ctas_per_problem);
+
+/* One launch of the captured graph for all problems; infos (count entries,
+ * may be NULL) receive restarts, nmatvec, converged, nconv, max_est,
+ * max_resid (nlocked = 0) and t_solve_ms (the launch's event time, the same
+ * for every problem).  Returns the first status other than RKS_OK and
+ * RKS_ENOCONV in problem order, else RKS_ENOCONV if a problem did not
+ * converge, else RKS_OK. */
+int rks_solve_batched_dev(rks_dbatch* b, rks_info* infos);
+
+/* The launch configuration: CTAs per problem, grid size, dynamic shared
+ * memory per CTA, the timings of the tuning runs (4 floats, ms, for G = 1,
+ * 2, 4, 8; 0 where not run) and the event time of the last solve.  Any
+ * pointer may be NULL. */
+int rks_dbatch_config(const rks_dbatch* b, int* ctas_per_problem, int* grid, int64_t* smem_bytes, float* tune_ms,
+                      float* last_ms);
+
+/* Status of problem i in the last solve (RKS_ESTATE before one). */
+int rks_dbatch_status(const rks_dbatch* b, int i);
+
+/* Cycle counts of the last solve by phase, summed over CTAs and problems
+ * (clock64 deltas taken by thread 0 of every CTA at the barriers that end
+ * each phase): 0 start vector, 1 SpMV rows with the sketch sums of w, 2
+ * Hessenberg reduction, 3 exchanges of the sketch sums, 4 least squares, 5
+ * update rows with the sketch sums of u~, 6 Francis QR iteration, 7 beta and
+ * append, 8 reordering and truncation, 9 kept sketches and
+ * whitening, 10 restart product, 11 Ritz pairs and estimates, 12 Ritz
+ * vectors and residuals, 13 work queue.  Writes min(count, 14) entries and
+ * returns that number. */
+int rks_dbatch_phase_cycles(const rks_dbatch* b, int64_t* cycles, int count);
+
+/* Ritz pairs of problem i, best first: returns nw (k, or k + 1 when a
+ * complex pair straddles the cut) or a negative status; fills the first nw
+ * entries of each non-NULL host array: eigenvalues, FP64 residuals, Rayleigh
+ * quotients x^H A x / x^H x, estimates; X (n x nw host, LAPACK real packing
+ * as rks_get_eigpairs) the Ritz vectors U y with ||y|| = 1. */
+int rks_dbatch_eigpairs(rks_dbatch* b, int i, double* lam_re, double* lam_im, double* resid, double* rq_re,
+                        double* rq_im, double* est, double* X);
+
+/* Free the batch.  Safe on NULL. */
+void rks_destroy_batched_dev(rks_dbatch* b);
+
 /* ---- Sketch primitives (Sec. 5 setup; Def. 1.1) ---------------------- */
 
 /* The (row, sign) pairs of Omega: for column i and slot t < zeta,
@@ -538,6 +613,19 @@ int rks_host_reorder_select(int n, double* T, const int* select, double* Z);
  * host): a 2x2 block gives the pair (Im > 0 first).  Y_re, Y_im: n x n host
  * arrays (column j = eigenvector j).  Host only. */
 int rks_host_quasi_eig(int n, const double* T, double* lam_re, double* lam_im, double* Y_re, double* Y_im);
+
+/* The device dense step of the persistent batched solver on one matrix
+ * (test entry point): B (m x m, host, m <= 64) -> real Schur form T = Q^T B Q
+ * whose leading blocks are the best blocks for `which` covering nsort
+ * columns (pairs whole; in the order the Schur form had them): Algorithm 1's
+ * Schur, reordering and truncation choice; then eigenvalues and unit
+ * eigenvectors of T as rks_host_quasi_eig.  One warp on the current device,
+ * double-float arithmetic (as in the solver); T, Q, Y_re, Y_im (m x m) and
+ * lam_re, lam_im (m) host arrays (the last four may be NULL).  Returns RKS_OK,
+ * RKS_EINVAL, RKS_EDENSE (no convergence of the QR iteration, or a refused
+ * swap) or RKS_ECUDA. */
+int rks_dev_ordered_schur(int m, const double* B, int which, int nsort, double* T, double* Q, double* lam_re,
+                          double* lam_im, double* Y_re, double* Y_im);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,7 @@ NVCC = os.environ.get("NVCC", "nvcc")
 CXX = os.environ.get("CXX", "g++")
 
 SOURCES = ["kernels.cu", "kernels_df.cu", "restart_tc.cu", "api.cu", "batch.cu", "noalloc.cu", "sketch_qr.cu",
-           "warmstart.cu", "dense.cpp"]
+           "warmstart.cu", "batch_dev.cu", "dense.cpp"]
 
 
 def _cmd(src: str) -> list[str]:

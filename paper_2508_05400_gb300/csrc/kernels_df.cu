@@ -612,101 +612,119 @@ __global__ void __launch_bounds__(kMergeCta) k_df_spmv_merge(
     float2* __restrict__ mp_val, int64_t nthreads) {
   __shared__ float2 prod[kMergeBlk];
   __shared__ int32_t rend[kMergeBlk + 1];
-  __shared__ int crow[kMergeCta];
-  __shared__ float2 cval[kMergeCta];
+  __shared__ int crow[kMergeCta];       // row open at the end of each thread's range (-1: none)
+  __shared__ float2 cval[kMergeCta];    // its partial sum
+  __shared__ float2 fval[kMergeCta];    // partial sum of the first row the thread completes
+  __shared__ int fhas[kMergeCta];       // whether the thread completes a row
   const int64_t total = n + nnz;
   const int64_t b = blockIdx.x;
   const int64_t rlo = part_row[b], rhi = part_row[b + 1];
   const int64_t dlo = b * kMergeBlk, dhi = dlo + kMergeBlk < total ? dlo + kMergeBlk : total;
   const int64_t jlo = dlo - rlo, jhi = dhi - rhi;     // entries of the CTA's range
   const int ne = (int)(jhi - jlo), nr = (int)(rhi - rlo);
-  for (int e = threadIdx.x; e < ne; e += kMergeCta) {
-    const int64_t p = jlo + e;
-    const float2 a = ldv(vals + p);
-    const int c = colind[p];
-    const float2 xv = x2 ? x2[c] : make_float2(x1[c], 0.f);
-    const float pr = a.x * xv.x;
-    float er = fmaf(a.x, xv.x, -pr);
-    er = fmaf(a.x, xv.y, er);
-    er = fmaf(a.y, xv.x, er);
-    prod[e] = make_float2(pr, er);
+  // products a_p x[col_p], four entries per thread in flight at a time
+  for (int e0 = threadIdx.x; e0 < ne; e0 += 4 * kMergeCta) {
+    int c[4];
+    float2 a[4], xv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * kMergeCta;
+      c[u] = e < ne ? colind[jlo + e] : 0;
+      a[u] = e < ne ? ldv(vals + jlo + e) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * kMergeCta;
+      xv[u] = e < ne ? (x2 ? x2[c[u]] : make_float2(x1[c[u]], 0.f)) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * kMergeCta;
+      if (e < ne) {
+        const float pr = a[u].x * xv[u].x;
+        float er = fmaf(a[u].x, xv[u].x, -pr);
+        er = fmaf(a[u].x, xv[u].y, er);
+        er = fmaf(a[u].y, xv[u].x, er);
+        prod[e] = make_float2(pr, er);
+      }
+    }
   }
   for (int r = threadIdx.x; r <= nr; r += kMergeCta) rend[r] = rowptr[rlo + r + 1 <= n ? rlo + r + 1 : n];
   crow[threadIdx.x] = -1;
   cval[threadIdx.x] = make_float2(0.f, 0.f);
+  fval[threadIdx.x] = make_float2(0.f, 0.f);
+  fhas[threadIdx.x] = 0;
   __syncthreads();
   const int64_t t = b * kMergeCta + threadIdx.x;
   const int64_t d0 = t * kMergeItems;
   const int64_t d1 = d0 + kMergeItems < total ? d0 + kMergeItems : total;
   if (t < nthreads && d0 < total) {
-  // split inside the CTA's rows: markers of rows rlo + q at rend[q] + rlo + q
-  auto split = [&](int64_t dd) {
-    int lo = 0, hi = nr;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if ((int64_t)rend[mid] + rlo + mid < dd) lo = mid + 1;
-      else hi = mid;
+    // split inside the CTA's rows: marker of row rlo + q at rend[q] + rlo + q
+    auto split = [&](int64_t dd) {
+      int lo = 0, hi = nr;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int64_t)rend[mid] + rlo + mid < dd) lo = mid + 1;
+        else hi = mid;
+      }
+      return lo;
+    };
+    int q = split(d0);
+    const int qe = split(d1);
+    int64_t j = d0 - (rlo + q);
+    const int64_t je = d1 - (rlo + qe);
+    float sh = 0.f, sl = 0.f;
+    bool first = true;
+    for (; q < qe; ++q) {
+      const int64_t pe = rend[q];
+      for (; j < pe; ++j) {
+        const float2 v = prod[j - jlo];
+        df_add(v.x, v.y, sh, sl);
+      }
+      // the first row this thread completes is the one it started in, which
+      // may have begun in earlier ranges: its sum is finished by the fold
+      if (first) {
+        fval[threadIdx.x] = df_norm(sh, sl);
+        fhas[threadIdx.x] = 1;
+        first = false;
+      } else {
+        wd[rlo + q] = df_norm(sh, sl);
+      }
+      sh = 0.f;
+      sl = 0.f;
     }
-    return lo;
-  };
-  int q = split(d0);
-  const int qe = split(d1);
-  int64_t j = d0 - (rlo + q);
-  const int64_t je = d1 - (rlo + qe);
-  float sh = 0.f, sl = 0.f;
-  for (; q < qe; ++q) {
-    const int64_t pe = rend[q];
-    for (; j < pe; ++j) {
+    for (; j < je; ++j) {
       const float2 v = prod[j - jlo];
       df_add(v.x, v.y, sh, sl);
     }
-    wd[rlo + q] = df_norm(sh, sl);
-    sh = 0.f;
-    sl = 0.f;
-  }
-  for (; j < je; ++j) {
-    const float2 v = prod[j - jlo];
-    df_add(v.x, v.y, sh, sl);
-  }
-  crow[threadIdx.x] = rlo + qe < n ? (int)(rlo + qe) : -1;
-  cval[threadIdx.x] = df_norm(sh, sl);
+    crow[threadIdx.x] = rlo + qe < n ? (int)(rlo + qe) : -1;
+    cval[threadIdx.x] = df_norm(sh, sl);
   }
   __syncthreads();
-  // Fold of the threads' open rows, in thread order: a row that ends inside
-  // the CTA (row < rhi) gets its partial sums added to the tail its last
-  // thread wrote; the row still open at the CTA's end becomes the CTA's carry
-  // (mp_row[b], mp_val[b]; -1: none).
+  // Fold in thread order: the running row (open at the previous thread's
+  // end) collects the partial sums of the threads inside it and is written
+  // when a thread completes it; the row open at the CTA's end becomes the
+  // CTA's carry (mp_row[b], mp_val[b]; -1: none), added by k_df_merge_fix.
   if (threadIdx.x == 0) {
-    bool carried = false;
-    int cur = -1;
+    int rc = (int)rlo;
     float ch = 0.f, cl = 0.f;
-    auto flush = [&]() {
-      if (cur < 0) return;
-      if (cur < rhi) {
-        const float2 tail = wd[cur];
-        df_add(tail.x, tail.y, ch, cl);
-        wd[cur] = df_norm(ch, cl);
-      } else {
-        mp_row[b] = cur;
-        mp_val[b] = df_norm(ch, cl);
-        carried = true;
-      }
-    };
     for (int u = 0; u < kMergeCta; ++u) {
-      const int r = crow[u];
-      if (r != cur) {
-        flush();
-        cur = r;
+      if (fhas[u]) {
+        const float2 f = fval[u];
+        df_add(f.x, f.y, ch, cl);
+        if (rc >= 0) wd[rc] = df_norm(ch, cl);
+        rc = crow[u];
+        const float2 v = cval[u];
         ch = 0.f;
         cl = 0.f;
-      }
-      if (r >= 0) {
+        df_add(v.x, v.y, ch, cl);
+      } else if (crow[u] >= 0) {
         const float2 v = cval[u];
         df_add(v.x, v.y, ch, cl);
       }
     }
-    flush();
-    if (!carried) mp_row[b] = -1;
+    mp_row[b] = rc >= 0 && rc < n ? rc : -1;
+    mp_val[b] = df_norm(ch, cl);
   }
 }
 

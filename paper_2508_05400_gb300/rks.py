@@ -136,6 +136,23 @@ def lib() -> C.CDLL:
         L.rks_batch_status.restype = C.c_int
         L.rks_destroy_batched.argtypes = [_P]
         L.rks_destroy_batched.restype = None
+        L.rks_create_batched_dev.argtypes = [C.POINTER(_P), C.c_int, _P, _P, _P, _P, C.c_int, C.c_int, C.c_int,
+                                             C.c_int, C.c_int, C.c_double, C.c_uint64, _P, C.c_int]
+        L.rks_create_batched_dev.restype = C.c_int
+        L.rks_solve_batched_dev.argtypes = [_P, _P]
+        L.rks_solve_batched_dev.restype = C.c_int
+        L.rks_dbatch_config.argtypes = [_P, _P, _P, _P, _P, _P]
+        L.rks_dbatch_config.restype = C.c_int
+        L.rks_dbatch_status.argtypes = [_P, C.c_int]
+        L.rks_dbatch_status.restype = C.c_int
+        L.rks_dbatch_phase_cycles.argtypes = [_P, _P, C.c_int]
+        L.rks_dbatch_phase_cycles.restype = C.c_int
+        L.rks_dbatch_eigpairs.argtypes = [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P]
+        L.rks_dbatch_eigpairs.restype = C.c_int
+        L.rks_destroy_batched_dev.argtypes = [_P]
+        L.rks_destroy_batched_dev.restype = None
+        L.rks_dev_ordered_schur.argtypes = [C.c_int, _P, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P]
+        L.rks_dev_ordered_schur.restype = C.c_int
         L.rks_basis_product_df.argtypes = [C.c_int64, _P, C.c_int64, C.c_int, _P, C.c_int, _P, _P]
         L.rks_basis_product_df.restype = C.c_int
         L.rks_sketch_qr.argtypes = [C.c_int64, C.c_int, _P, C.c_int64, C.c_int, C.c_int, C.c_uint64, C.c_int, _P,
@@ -588,6 +605,133 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class DevBatch:
+    """Independent problems solved by one persistent launch
+    (rks_create_batched_dev): clusters of CTAs take problems from a device
+    work queue and run the whole of Algorithm 1 for each on the device.
+
+    ``problems``: list of ``inputs.CSR`` (host arrays, one value type).
+    ``ctas``: CTAs per problem (1, 2, 4, 8) or 0 to pick the fastest by
+    timing one restart of the batch.  Restarts keep max(k, min(keep, m // 2))
+    Schur vectors and lock nothing; ``tol``, ``conv``, ``verify``, ``maxit``,
+    ``zeta`` and ``seed`` mean what they mean for ``Solver``.
+    """
+
+    def __init__(self, problems, k, p, d, which="LM", tol=1e-10, seed=0, *, zeta=8, maxit=1000, conv="eig",
+                 verify=0.0, keep=0, ctas=0, **ignored):
+        L = lib()
+        self.count = len(problems)
+        self._keep = [(_host(A.rowptr, np.int32), _host(A.colind, np.int32), np.ascontiguousarray(A.vals))
+                      for A in problems]
+        vdt = 0 if self._keep[0][2].dtype == np.float64 else 1
+        if any((0 if a[2].dtype == np.float64 else 1) != vdt for a in self._keep):
+            raise ValueError("all problems must share one value type")
+        ns = np.array([A.n for A in problems], dtype=np.int64)
+        ptrs = [np.array([a[j].ctypes.data for a in self._keep], dtype=np.uint64) for j in range(3)]
+        o = Opts()
+        L.rks_opts_default(C.byref(o))
+        o.zeta, o.maxit, o.conv, o.verify, o.keep = int(zeta), int(maxit), CONV[conv], float(verify), int(keep)
+        self.n = ns
+        self.k, self.p, self.d = int(k), int(p), int(d)
+        h = _P()
+        _check(L.rks_create_batched_dev(C.byref(h), self.count, ns.ctypes.data, ptrs[0].ctypes.data,
+                                        ptrs[1].ctypes.data, ptrs[2].ctypes.data, vdt, self.k, self.p, self.d,
+                                        WHICH[which] if isinstance(which, str) else int(which), float(tol),
+                                        int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(o), int(ctas)),
+               "rks_create_batched_dev")
+        self._h = h
+        self._keep = None
+
+    def config(self) -> dict:
+        """CTAs per problem, grid, shared memory per CTA, the tuning times (ms
+        for 1, 2, 4, 8 CTAs per problem) and the last solve's event time."""
+        g, grid, sm = C.c_int(), C.c_int(), C.c_int64()
+        tune = (C.c_float * 4)()
+        last = C.c_float()
+        _check(lib().rks_dbatch_config(self._h, C.byref(g), C.byref(grid), C.byref(sm), C.cast(tune, _P),
+                                       C.byref(last)), "rks_dbatch_config")
+        return {"ctas_per_problem": g.value, "grid": grid.value, "smem_bytes": sm.value,
+                "tune_ms": {c: float(t) for c, t in zip((1, 2, 4, 8), tune)}, "last_ms": float(last.value)}
+
+    PHASES = ("start", "spmv_sketch", "hessenberg", "exchange", "ls", "update_sketch", "francis", "beta",
+              "reorder", "kept_whiten", "restart", "ritz", "final", "queue")
+
+    def phase_cycles(self) -> dict:
+        """Cycle counts of the last solve by phase (summed over CTAs)."""
+        buf = (C.c_int64 * len(self.PHASES))()
+        nc = lib().rks_dbatch_phase_cycles(self._h, C.cast(buf, _P), len(self.PHASES))
+        _check(min(nc, 0), "rks_dbatch_phase_cycles")
+        return {name: int(buf[q]) for q, name in enumerate(self.PHASES[:nc])}
+
+    def solve(self, allow_noconv=True):
+        infos = (Info * self.count)()
+        rc = lib().rks_solve_batched_dev(self._h, C.cast(infos, _P))
+        _check(rc, "rks_solve_batched_dev", ok=(RKS_OK, RKS_ENOCONV) if allow_noconv else (RKS_OK,))
+        out = []
+        for i in range(self.count):
+            d = infos[i].as_dict()
+            d["status"] = STATUS.get(lib().rks_dbatch_status(self._h, i), None)
+            out.append(d)
+        return out
+
+    def eigpairs(self, i, want_vectors=True):
+        """(lam, X, resid, rq, est) of problem i: nw Ritz values (complex),
+        X (n x nw complex, or None), FP64 residuals, Rayleigh quotients and
+        estimates."""
+        kk = self.k + 1
+        a = [np.zeros(kk) for _ in range(6)]
+        n = int(self.n[i])
+        Xp = _fortran((n, kk)) if want_vectors else None
+        nw = lib().rks_dbatch_eigpairs(self._h, int(i), *(x.ctypes.data for x in a),
+                                       Xp.ctypes.data if Xp is not None else None)
+        _check(min(nw, 0), "rks_dbatch_eigpairs")
+        lre, lim, res, rqr, rqi, est = (x[:nw] for x in a)
+        lam = lre + 1j * lim
+        X = None
+        if Xp is not None:
+            X = np.zeros((n, nw), dtype=np.complex128)
+            t = 0
+            while t < nw:
+                if lim[t] > 0 and t + 1 < nw:
+                    X[:, t] = Xp[:, t] + 1j * Xp[:, t + 1]
+                    X[:, t + 1] = Xp[:, t] - 1j * Xp[:, t + 1]
+                    t += 2
+                else:
+                    X[:, t] = Xp[:, t]
+                    t += 1
+        return lam, X, res, rqr + 1j * rqi, est
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rks_destroy_batched_dev(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def dev_ordered_schur(B: np.ndarray, which: str, nsort: int):
+    """The device dense step (rks_dev_ordered_schur): T, Q with B = Q T Q^T,
+    the best nsort blocks leading, and the eigenvalues / unit eigenvectors of T."""
+    m = B.shape[0]
+    Bf = np.asfortranarray(B, dtype=np.float64)
+    T, Q, Yr, Yi = (_fortran((m, m)) for _ in range(4))
+    lre, lim = np.zeros(m), np.zeros(m)
+    _check(lib().rks_dev_ordered_schur(m, Bf.ctypes.data, WHICH[which], int(nsort), T.ctypes.data, Q.ctypes.data,
+                                       lre.ctypes.data, lim.ctypes.data, Yr.ctypes.data, Yi.ctypes.data),
+           "rks_dev_ordered_schur")
+    return T, Q, lre + 1j * lim, Yr + 1j * Yi
 
 
 class WarmStart:
