@@ -195,7 +195,7 @@ struct BdArgs {
 };
 
 struct BdLayout {
-  int S, B, T, Q, Td, Qd, W, G, Ri, QC, z, sv, r, sig, coef, bk, lre, lim, est, scr, total;
+  int S, B, T, Q, Td, Qd, W, G, Ri, QC, z, sv, r, sig, coef, bk, lre, lim, est, scr, xs, total;
 };
 
 __host__ __device__ inline int bd_take(int& o, int cnt) {
@@ -205,19 +205,13 @@ __host__ __device__ inline int bd_take(int& o, int cnt) {
 }
 
 // Offsets (in 8-byte words) of the per-CTA arrays in dynamic shared memory.
+// The arrays of the contraction share their space with the two tile buffers
+// of the expansions (never live at the same time).
 __host__ __device__ inline BdLayout bd_layout(int m, int d) {
   BdLayout L;
   int o = 0;
   L.S = bd_take(o, d * (m + 1));         // sketches of the basis (orthonormal), FP64
   L.B = bd_take(o, (m + 1) * m);         // [B; b^T] of the decomposition, FP64
-  L.T = bd_take(o, m * m);               // Hessenberg / Schur form, double-float
-  L.Q = bd_take(o, m * m);               // Schur vectors, double-float
-  L.Td = bd_take(o, m * m);              // kept block of the Schur form, FP64
-  L.Qd = bd_take(o, m * m);              // kept Schur vectors, FP64
-  L.W = bd_take(o, d * m > 2 * m * m ? d * m : 2 * m * m);   // kept sketches; Ritz vectors of T
-  L.G = bd_take(o, m * m);               // Gram matrix, then R
-  L.Ri = bd_take(o, m * m);              // R^{-1}
-  L.QC = bd_take(o, m * m);              // restart coefficients (double-float); packed Y
   L.z = bd_take(o, d);
   L.sv = bd_take(o, d);
   L.r = bd_take(o, m + 1);
@@ -228,6 +222,17 @@ __host__ __device__ inline BdLayout bd_layout(int m, int d) {
   L.lim = bd_take(o, m);
   L.est = bd_take(o, m);
   L.scr = bd_take(o, 4 * m + 64);
+  const int u0 = o;                      // contraction / finalisation only:
+  L.T = bd_take(o, m * m);               // Hessenberg / Schur form, double-float
+  L.Q = bd_take(o, m * m);               // Schur vectors, double-float
+  L.Td = bd_take(o, m * m);              // kept block of the Schur form, FP64
+  L.Qd = bd_take(o, m * m);              // kept Schur vectors, FP64
+  L.W = bd_take(o, d * m > 2 * m * m ? d * m : 2 * m * m);   // kept sketches; Ritz vectors of T
+  L.G = bd_take(o, m * m);               // Gram matrix, then R
+  L.Ri = bd_take(o, m * m);              // R^{-1}
+  L.QC = bd_take(o, m * m);              // restart coefficients (double-float); packed Y
+  L.xs = u0;                             // expansions only: two tiles of one column (double-float)
+  if (o < u0 + 2 * kBR) o = u0 + 2 * kBR;
   L.total = o;
   return L;
 }
@@ -315,7 +320,7 @@ __device__ __forceinline__ int64_t bd_uix(int64_t i, int c, int m1) {
 // of the tiled basis; kBRowsPerThread rows per thread at a time.  L2: read x
 // through L2 only (rows written by other CTAs).
 template <bool L2>
-__device__ __forceinline__ void bd_spmv_csr(const BdProb& P, int t, int m1, int j, float2 sg) {
+__device__ __forceinline__ void bd_spmv_csr(const BdProb& P, int t, int m1, int j, float2 sg, float2* xs) {
   const int64_t r0 = (int64_t)t * kBR;
   const int rows = (int)min((int64_t)kBR, P.n - r0);
   float2* w = P.U + ((int64_t)t * m1 + j + 1) * kBR;
@@ -356,7 +361,9 @@ __device__ __forceinline__ void bd_spmv_csr(const BdProb& P, int t, int m1, int 
       const float2 y = bd_norm(s[q], e[q]);
       float s2 = 0.f, e2 = 0.f;
       bd_mac(y.x, y.y, sg.x, sg.y, s2, e2);
-      w[rr] = bd_norm(s2, e2);
+      const float2 o = bd_norm(s2, e2);
+      w[rr] = o;
+      xs[rr] = o;
     }
   }
 }
@@ -364,7 +371,7 @@ __device__ __forceinline__ void bd_spmv_csr(const BdProb& P, int t, int m1, int 
 // The same product from the diagonal storage (columns i + doff[e] in
 // increasing order, as the CSR rows).
 template <bool L2>
-__device__ __forceinline__ void bd_spmv_dia(const BdProb& P, int t, int m1, int j, float2 sg) {
+__device__ __forceinline__ void bd_spmv_dia(const BdProb& P, int t, int m1, int j, float2 sg, float2* xs) {
   const int64_t r0 = (int64_t)t * kBR, n = P.n, ld = P.ldu;
   const int rows = (int)min((int64_t)kBR, n - r0);
   float2* w = P.U + ((int64_t)t * m1 + j + 1) * kBR;
@@ -392,7 +399,9 @@ __device__ __forceinline__ void bd_spmv_dia(const BdProb& P, int t, int m1, int 
       const float2 y = bd_norm(s[q], e[q]);
       float s2 = 0.f, e2 = 0.f;
       bd_mac(y.x, y.y, sg.x, sg.y, s2, e2);
-      w[rr] = bd_norm(s2, e2);
+      const float2 o = bd_norm(s2, e2);
+      w[rr] = o;
+      xs[rr] = o;
     }
   }
 }
@@ -400,7 +409,7 @@ __device__ __forceinline__ void bd_spmv_dia(const BdProb& P, int t, int m1, int 
 // u~ = w + sum_c U[:, c] coef[c] (c <= j) for the rows of tile t, in place on
 // column j + 1 (which holds w).  Thread p takes the row pairs (2 p, 2 p + 1),
 // p = threadIdx.x, threadIdx.x + kBT (16-byte loads).
-__device__ __forceinline__ void bd_update_full(float2* __restrict__ Ut, int j, const float2* coef) {
+__device__ __forceinline__ void bd_update_full(float2* __restrict__ Ut, int j, const float2* coef, float2* xs) {
   constexpr int kPairs = kBR / (2 * kBT);
   float2* wcol = Ut + (size_t)(j + 1) * kBR;
   float s[2 * kPairs], e[2 * kPairs];
@@ -425,15 +434,18 @@ __device__ __forceinline__ void bd_update_full(float2* __restrict__ Ut, int j, c
 #pragma unroll
   for (int q = 0; q < kPairs; ++q) {
     const float2 a = bd_norm(s[2 * q], e[2 * q]), b = bd_norm(s[2 * q + 1], e[2 * q + 1]);
-    *reinterpret_cast<float4*>(wcol + 2 * (threadIdx.x + q * kBT)) = make_float4(a.x, a.y, b.x, b.y);
+    const float4 o = make_float4(a.x, a.y, b.x, b.y);
+    *reinterpret_cast<float4*>(wcol + 2 * (threadIdx.x + q * kBT)) = o;
+    *reinterpret_cast<float4*>(xs + 2 * (threadIdx.x + q * kBT)) = o;
   }
 }
 
-__device__ __forceinline__ void bd_update_tile(const BdProb& P, int t, int m1, int j, const float2* coef) {
+__device__ __forceinline__ void bd_update_tile(const BdProb& P, int t, int m1, int j, const float2* coef,
+                                              float2* xs) {
   constexpr int kPairs = kBR / (2 * kBT);
   const int rows = (int)min((int64_t)kBR, P.n - (int64_t)t * kBR);
   if (rows == kBR) {   // a full tile: no bounds tests between the loads
-    bd_update_full(P.U + (int64_t)t * m1 * kBR, j, coef);
+    bd_update_full(P.U + (int64_t)t * m1 * kBR, j, coef, xs);
     return;
   }
   const float2* Ut = P.U + (int64_t)t * m1 * kBR;
@@ -468,8 +480,13 @@ __device__ __forceinline__ void bd_update_tile(const BdProb& P, int t, int m1, i
   for (int q = 0; q < kPairs; ++q) {
     const int r = 2 * (threadIdx.x + q * kBT);
     const float2 a = bd_norm(s[2 * q], e[2 * q]), b = bd_norm(s[2 * q + 1], e[2 * q + 1]);
-    if (r + 1 < rows) *reinterpret_cast<float4*>(wcol + r) = make_float4(a.x, a.y, b.x, b.y);
-    else if (r < rows) wcol[r] = a;
+    if (r + 1 < rows) {
+      *reinterpret_cast<float4*>(wcol + r) = make_float4(a.x, a.y, b.x, b.y);
+      *reinterpret_cast<float4*>(xs + r) = make_float4(a.x, a.y, b.x, b.y);
+    } else if (r < rows) {
+      wcol[r] = a;
+      xs[r] = a;
+    }
   }
 }
 
@@ -505,35 +522,44 @@ __device__ __noinline__ void bd_restart_tile(const BdProb& P, int t, int m, int 
 // The passes over the tiles t0..t1-1 of this CTA, each a function of its own
 // (own register allocation, one call per pass).  The sketch sums of tile t - 1
 // are formed while the rows of tile t are computed; one barrier per tile.
+// xs: two tile buffers in shared memory (tile t in buffer t % 2).
 template <bool L2>
 __device__ __noinline__ void bd_pass_spmv(const BdProb& P, int t0, int t1, int m1, int j, float2 sg, int d,
-                                          float2* ts) {
+                                          float2* ts, float2* xs) {
   for (int t = t0; t <= t1; ++t) {
     if (t < t1) {
-      if (P.D > 0) bd_spmv_dia<L2>(P, t, m1, j, sg);
-      else bd_spmv_csr<L2>(P, t, m1, j, sg);
+      if (P.D > 0) bd_spmv_dia<L2>(P, t, m1, j, sg, xs + (t & 1) * kBR);
+      else bd_spmv_csr<L2>(P, t, m1, j, sg, xs + (t & 1) * kBR);
     }
-    if (t > t0) bd_bins_tile(P, d, t - 1, P.U + ((int64_t)(t - 1) * m1 + j + 1) * kBR, ts);
+    if (t > t0) bd_bins_tile(P, d, t - 1, xs + ((t - 1) & 1) * kBR, ts);
     __syncthreads();
   }
 }
 __device__ __noinline__ void bd_pass_update(const BdProb& P, int t0, int t1, int m1, int j, const float2* coef, int d,
-                                            float2* ts) {
+                                            float2* ts, float2* xs) {
   for (int t = t0; t <= t1; ++t) {
-    if (t < t1) bd_update_tile(P, t, m1, j, coef);
-    if (t > t0) bd_bins_tile(P, d, t - 1, P.U + ((int64_t)(t - 1) * m1 + j + 1) * kBR, ts);
+    if (t < t1) bd_update_tile(P, t, m1, j, coef, xs + (t & 1) * kBR);
+    if (t > t0) bd_bins_tile(P, d, t - 1, xs + ((t - 1) & 1) * kBR, ts);
     __syncthreads();
   }
 }
-__device__ __noinline__ void bd_pass_start(const BdProb& P, int t0, int t1, int m1, uint64_t seed, int d, float2* ts) {
-  for (int t = t0; t < t1; ++t) {
-    const int64_t r0 = (int64_t)t * kBR;
-    const int rows = (int)min((int64_t)kBR, P.n - r0);
-    float2* col = P.U + (int64_t)t * m1 * kBR;
-    for (int r = threadIdx.x; r < rows; r += kBT) col[r] = bd_from(bd_normal(seed, r0 + r));
+__device__ __noinline__ void bd_pass_start(const BdProb& P, int t0, int t1, int m1, uint64_t seed, int d, float2* ts,
+                                           float2* xs) {
+  for (int t = t0; t <= t1; ++t) {
+    if (t < t1) {
+      const int64_t r0 = (int64_t)t * kBR;
+      const int rows = (int)min((int64_t)kBR, P.n - r0);
+      float2* col = P.U + (int64_t)t * m1 * kBR;
+      float2* x = xs + (t & 1) * kBR;
+      for (int r = threadIdx.x; r < rows; r += kBT) {
+        const float2 v = bd_from(bd_normal(seed, r0 + r));
+        col[r] = v;
+        x[r] = v;
+      }
+    }
+    if (t > t0) bd_bins_tile(P, d, t - 1, xs + ((t - 1) & 1) * kBR, ts);
+    __syncthreads();
   }
-  __syncthreads();
-  for (int t = t0; t < t1; ++t) bd_bins_tile(P, d, t, P.U + (int64_t)t * m1 * kBR, ts);
 }
 
 // cluster-wide barrier; the fence orders this thread's global writes before it
@@ -596,8 +622,9 @@ __device__ __noinline__ void bd_hess(int m, rks_dd::df* T, rks_dd::df* Q, rks_dd
 __device__ __noinline__ int bd_francis(int m, rks_dd::df* T, rks_dd::df* Q, int lane) {
   return rks_dd::schur(m, T, m, Q, m, m, lane);
 }
-__device__ __noinline__ int bd_reorder_truncate(int m, rks_dd::df* T, rks_dd::df* Q, int which, int want, int lane) {
-  return min(rks_dd::reorder_select(m, T, m, Q, m, m, which, want, lane), m - 1);
+__device__ __noinline__ int bd_reorder_truncate(int m, rks_dd::df* T, rks_dd::df* Q, int which, int want,
+                                                rks_dd::df* keys, int lane) {
+  return min(rks_dd::reorder_select(m, T, m, Q, m, m, which, want, keys, lane), m - 1);
 }
 __device__ __noinline__ void bd_quasi_eig(int ka, int m, const rks_dd::df* T, rks_dd::df* lre, rks_dd::df* lim,
                                           rks_dd::df* Yr, rks_dd::df* Yi, int lane) {
@@ -643,6 +670,7 @@ __device__ void bd_solve(const BdArgs& A, const BdProb& P, double* sm, BdShared&
   double* est = sm + L.est;
   double* scr = sm + L.scr;
   df* scr_df = reinterpret_cast<df*>(scr);
+  float2* xs = reinterpret_cast<float2*>(sm + L.xs);
   df* Yr = reinterpret_cast<df*>(W);
   df* Yi = reinterpret_cast<df*>(W) + m * m;
   const int ldb = m + 1;
@@ -663,7 +691,7 @@ __device__ void bd_solve(const BdArgs& A, const BdProb& P, double* sm, BdShared&
   // ---- start (Sec. 3.1 with k = 0): U[:, 0] = u~_1, S[:, 0] = Omega u~_1 / beta
   {
     float2* ts = P.tsum + (size_t)(ex & 1) * P.ntile * d;
-    bd_pass_start(P, t0, t1, m1, A.seed + 1, d, ts);
+    bd_pass_start(P, t0, t1, m1, A.seed + 1, d, ts, xs);
     bd_cluster_sync(cl);
     bd_tiles_reduce(ts, P.ntile, d, zscale, sv);
     ++ex;
@@ -689,8 +717,8 @@ __device__ void bd_solve(const BdArgs& A, const BdProb& P, double* sm, BdShared&
     for (int j = ja; j < m; ++j) {
       float2* ts = P.tsum + (size_t)(ex & 1) * P.ntile * d;
       const float2 sg = bd_from(sig[j]);
-      if (G > 1) bd_pass_spmv<true>(P, t0, t1, m1, j, sg, d, ts);   // w = A u_j, partial z = Omega w
-      else bd_pass_spmv<false>(P, t0, t1, m1, j, sg, d, ts);
+      if (G > 1) bd_pass_spmv<true>(P, t0, t1, m1, j, sg, d, ts, xs);   // w = A u_j, partial z = Omega w
+      else bd_pass_spmv<false>(P, t0, t1, m1, j, sg, d, ts, xs);
       BD_MARK(kPhSpmvRows);
       bd_cluster_sync(cl);
       bd_tiles_reduce(ts, P.ntile, d, zscale, z);
@@ -723,7 +751,7 @@ __device__ void bd_solve(const BdArgs& A, const BdProb& P, double* sm, BdShared&
       __syncthreads();
       BD_MARK(kPhLs);
       ts = P.tsum + (size_t)(ex & 1) * P.ntile * d;
-      bd_pass_update(P, t0, t1, m1, j, coef, d, ts);   // u~ = w - U b, partial s~ = Omega u~
+      bd_pass_update(P, t0, t1, m1, j, coef, d, ts, xs);   // u~ = w - U b, partial s~ = Omega u~
       BD_MARK(kPhUpdRows);
       bd_cluster_sync(cl);
       bd_tiles_reduce(ts, P.ntile, d, zscale, sv);
@@ -763,7 +791,7 @@ __device__ void bd_solve(const BdArgs& A, const BdProb& P, double* sm, BdShared&
       BD_MARK(kPhHess);
       const int rc = bd_francis(m, T, Q, lane);
       BD_MARK(kPhSchur);
-      const int kt = rc == 0 ? bd_reorder_truncate(m, T, Q, A.which, A.want, lane) : 0;
+      const int kt = rc == 0 ? bd_reorder_truncate(m, T, Q, A.which, A.want, reinterpret_cast<df*>(W), lane) : 0;
       if (lane == 0) {
         sh.flag[0] = rc ? RKS_EDENSE : RKS_OK;
         sh.flag[1] = kt;
@@ -1092,7 +1120,7 @@ __global__ void k_dense_test(int m, const double* B, rks_dd::df* T, rks_dd::df* 
   const int rc = rks_dd::schur(m, T, m, Q, m, m, lane);
   int fails = 0;
   if (rc == 0) {
-    const int top = rks_dd::reorder_select(m, T, m, Q, m, m, which, nsort, lane);
+    const int top = rks_dd::reorder_select(m, T, m, Q, m, m, which, nsort, scratch + m, lane);
     fails = top < min(nsort, m) ? 1 : 0;
     rks_dd::quasi_eig(m, T, m, lre, lim, Yr, Yi, m, lane);
   }
@@ -1647,7 +1675,7 @@ extern "C" int rks_dev_ordered_schur(int m, const double* Bh, int which, int nso
   df* dv = nullptr;
   double* dout = nullptr;
   int* ds = nullptr;
-  if (cudaMalloc(&dB, sizeof(double) * mm) != cudaSuccess || cudaMalloc(&dv, sizeof(df) * (nout + m)) != cudaSuccess ||
+  if (cudaMalloc(&dB, sizeof(double) * mm) != cudaSuccess || cudaMalloc(&dv, sizeof(df) * (nout + 2 * m)) != cudaSuccess ||
       cudaMalloc(&dout, sizeof(double) * nout) != cudaSuccess || cudaMalloc(&ds, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(dB);
@@ -1659,7 +1687,7 @@ extern "C" int rks_dev_ordered_schur(int m, const double* Bh, int which, int nso
   df *dT = dv, *dQ = dv + mm, *dYr = dv + 2 * mm, *dYi = dv + 3 * mm, *dl = dv + 4 * mm;
   int rc = RKS_OK, st = 0;
   if (cudaMemcpy(dB, Bh, sizeof(double) * mm, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(dv, 0, sizeof(df) * (nout + m)) != cudaSuccess)
+      cudaMemset(dv, 0, sizeof(df) * (nout + 2 * m)) != cudaSuccess)
     rc = RKS_ECUDA;
   if (!rc) {
     k_dense_test<<<1, 32>>>(m, dB, dT, dQ, which, std::min(nsort, m), dl, dl + m, dYr, dYi, dl + 2 * m, ds);

@@ -23,6 +23,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace rks_dd {
 
@@ -138,28 +139,98 @@ __device__ __forceinline__ R& at(R* A, int ld, int i, int j) { return A[i + j * 
 template <class R>
 __device__ __forceinline__ R at(const R* A, int ld, int i, int j) { return A[i + j * ld]; }
 
+// Butterfly sum / max over the 32 lanes (the same value in every lane: each
+// step adds two partials in either order, and + and max commute exactly).
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ df warp_allsum(df v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = v + df(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+  return v;
+}
+__device__ __forceinline__ double warp_allmax(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ df warp_allmax(df v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = rmax(v, df(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)));
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // reflectors and rotations
 // ---------------------------------------------------------------------------
 
-// Householder vector for x (len <= 4): P = I - beta v v^T, v[0] = 1.
-template <class R>
-__device__ inline void house(const R* x, int len, R* v, R* beta) {
+// Householder vector for x (LEN <= 4, in registers): P = I - beta v v^T, v[0] = 1.
+template <int LEN, class R>
+__device__ __forceinline__ void house(const R (&x)[LEN], R (&v)[LEN], R& beta) {
   R s = R(0);
-  for (int i = 1; i < len; ++i) s += x[i] * x[i];
+#pragma unroll
+  for (int i = 1; i < LEN; ++i) s += x[i] * x[i];
   v[0] = R(1);
-  for (int i = 1; i < len; ++i) v[i] = x[i];
-  if (s == R(0)) { *beta = R(0); return; }
+#pragma unroll
+  for (int i = 1; i < LEN; ++i) v[i] = x[i];
+  beta = R(0);
+  if (s == R(0)) return;
   const R nrm = rsqrt_(x[0] * x[0] + s);
   const R v0 = x[0] >= R(0) ? x[0] + nrm : x[0] - nrm;
   const R iv0 = R(1) / v0;
-  for (int i = 1; i < len; ++i) v[i] *= iv0;
+#pragma unroll
+  for (int i = 1; i < LEN; ++i) v[i] *= iv0;
   R vtv = R(1);
-  for (int i = 1; i < len; ++i) vtv += v[i] * v[i];
-  *beta = R(2) / vtv;
+#pragma unroll
+  for (int i = 1; i < LEN; ++i) vtv += v[i] * v[i];
+  beta = R(2) / vtv;
 }
 
-// rows r0..r0+len-1, columns c0..c1: A <- (I - beta v v^T) A (lanes over columns)
+// rows r0..r0+LEN-1, columns c0..c1: A <- (I - beta v v^T) A (lanes over columns)
+template <int LEN, class R>
+__device__ __forceinline__ void apply_left_n(R* A, int ld, int r0, int c0, int c1, const R (&v)[LEN], R beta,
+                                             int lane) {
+  if (beta != R(0)) {
+    for (int j = c0 + lane; j <= c1; j += 32) {
+      R a[LEN];
+      R s = R(0);
+#pragma unroll
+      for (int i = 0; i < LEN; ++i) {
+        a[i] = at(A, ld, r0 + i, j);
+        s += v[i] * a[i];
+      }
+      s *= beta;
+#pragma unroll
+      for (int i = 0; i < LEN; ++i) at(A, ld, r0 + i, j) = a[i] - s * v[i];
+    }
+  }
+  __syncwarp();
+}
+
+// columns c0..c0+LEN-1, rows r0..r1: A <- A (I - beta v v^T) (lanes over rows)
+template <int LEN, class R>
+__device__ __forceinline__ void apply_right_n(R* A, int ld, int c0, int r0, int r1, const R (&v)[LEN], R beta,
+                                              int lane) {
+  if (beta != R(0)) {
+    for (int i = r0 + lane; i <= r1; i += 32) {
+      R a[LEN];
+      R s = R(0);
+#pragma unroll
+      for (int j = 0; j < LEN; ++j) {
+        a[j] = at(A, ld, i, c0 + j);
+        s += a[j] * v[j];
+      }
+      s *= beta;
+#pragma unroll
+      for (int j = 0; j < LEN; ++j) at(A, ld, i, c0 + j) = a[j] - s * v[j];
+    }
+  }
+  __syncwarp();
+}
+
+// The same with a vector of any length in shared memory (Hessenberg reduction).
 template <class R>
 __device__ inline void apply_left(R* A, int ld, int r0, int len, int c0, int c1, const R* v, R beta, int lane) {
   if (beta != R(0)) {
@@ -172,8 +243,6 @@ __device__ inline void apply_left(R* A, int ld, int r0, int len, int c0, int c1,
   }
   __syncwarp();
 }
-
-// columns c0..c0+len-1, rows r0..r1: A <- A (I - beta v v^T) (lanes over rows)
 template <class R>
 __device__ inline void apply_right(R* A, int ld, int c0, int len, int r0, int r1, const R* v, R beta, int lane) {
   if (beta != R(0)) {
@@ -211,16 +280,17 @@ __device__ inline void rotate_pair(int n, R* T, int ldt, R* Z, int ldz, int nz, 
 }
 
 // A (n x n) <- Q^T A Q upper Hessenberg, Q = the reflectors (Q set to I first).
-// v: scratch of n values (shared by the warp).
+// v: scratch of n values in shared memory.  The norm of each column is a
+// butterfly over the lanes (the same value in every lane).
 template <class R>
 __device__ inline void hessenberg(int n, R* A, int lda, R* Q, int ldq, R* v, int lane) {
   for (int t = lane; t < n * n; t += 32) at(Q, ldq, t % n, t / n) = (t % n == t / n) ? R(1) : R(0);
   __syncwarp();
   for (int k = 0; k + 2 < n; ++k) {
     const int len = n - k - 1;
-    // the reflector, by every lane (the same values)
     R s = R(0);
-    for (int i = 1; i < len; ++i) s += at(A, lda, k + 1 + i, k) * at(A, lda, k + 1 + i, k);
+    for (int i = 1 + lane; i < len; i += 32) s += at(A, lda, k + 1 + i, k) * at(A, lda, k + 1 + i, k);
+    s = warp_allsum(s);
     const R x0 = at(A, lda, k + 1, k);
     R beta = R(0), iv0 = R(1);
     if (s != R(0)) {
@@ -228,13 +298,15 @@ __device__ inline void hessenberg(int n, R* A, int lda, R* Q, int ldq, R* v, int
       iv0 = R(1) / (x0 >= R(0) ? x0 + nrm : x0 - nrm);
     }
     __syncwarp();
-    for (int i = lane; i < len; i += 32) v[i] = i == 0 ? R(1) : (s != R(0) ? at(A, lda, k + 1 + i, k) * iv0 : R(0));
-    __syncwarp();
-    if (s != R(0)) {
-      R vtv = R(1);
-      for (int i = 1; i < len; ++i) vtv += v[i] * v[i];
-      beta = R(2) / vtv;
+    R vv = R(0);
+    for (int i = lane; i < len; i += 32) {
+      const R vi = i == 0 ? R(1) : (s != R(0) ? at(A, lda, k + 1 + i, k) * iv0 : R(0));
+      v[i] = vi;
+      if (i > 0) vv += vi * vi;
     }
+    vv = warp_allsum(vv);
+    __syncwarp();
+    if (s != R(0)) beta = R(2) / (R(1) + vv);
     apply_left(A, lda, k + 1, len, k, n - 1, v, beta, lane);
     apply_right(A, lda, k + 1, len, 0, n - 1, v, beta, lane);
     apply_right(Q, ldq, k + 1, len, 0, n - 1, v, beta, lane);
@@ -311,12 +383,12 @@ __device__ inline int schur(int n, R* H, int ldh, R* Z, int ldz, int nz, int lan
   if (n <= 0) return 0;
   const R eps = reps<R>();
   R anorm = R(0);
-  for (int j = 0; j < n; ++j)
+  for (int j = lane; j < n; j += 32)
     for (int i = 0; i <= min(j + 1, n - 1); ++i) anorm = rmax(anorm, rabs(at(H, ldh, i, j)));
+  anorm = warp_allmax(anorm);
   if (anorm == R(0)) return 0;
   int hi = n - 1, its = 0, total = 0;
   const int max_total = 60 * n + 100;
-  R v[3];
   while (hi >= 0) {
     int l = hi;
     while (l > 0) {
@@ -350,14 +422,13 @@ __device__ inline int schur(int n, R* H, int ldh, R* Z, int ldz, int nz, int lan
     R y = at(H, ldh, l + 1, l) * (at(H, ldh, l, l) + at(H, ldh, l + 1, l + 1) - s);
     R z = at(H, ldh, l + 1, l) * at(H, ldh, l + 2, l + 1);
     for (int k = l; k <= hi - 2; ++k) {
-      R xv[3] = {x, y, z}, beta;
-      house(xv, 3, v, &beta);
+      const R xv[3] = {x, y, z};
+      R v[3], beta;
+      house<3>(xv, v, beta);
       __syncwarp();
-      const int c0 = max(l, k - 1);
-      apply_left(H, ldh, k, 3, c0, n - 1, v, beta, lane);
-      const int r1 = min(k + 3, hi);
-      apply_right(H, ldh, k, 3, 0, r1, v, beta, lane);
-      apply_right(Z, ldz, k, 3, 0, nz - 1, v, beta, lane);
+      apply_left_n<3>(H, ldh, k, max(l, k - 1), n - 1, v, beta, lane);
+      apply_right_n<3>(H, ldh, k, 0, min(k + 3, hi), v, beta, lane);
+      apply_right_n<3>(Z, ldz, k, 0, nz - 1, v, beta, lane);
       if (k > l && lane == 0) { at(H, ldh, k + 1, k - 1) = R(0); at(H, ldh, k + 2, k - 1) = R(0); }
       __syncwarp();
       x = at(H, ldh, k + 1, k);
@@ -365,12 +436,13 @@ __device__ inline int schur(int n, R* H, int ldh, R* Z, int ldz, int nz, int lan
       if (k < hi - 2) z = at(H, ldh, k + 3, k);
       __syncwarp();
     }
-    R xv[2] = {x, y}, beta;
-    house(xv, 2, v, &beta);
+    const R xv[2] = {x, y};
+    R v[2], beta;
+    house<2>(xv, v, beta);
     __syncwarp();
-    apply_left(H, ldh, hi - 1, 2, hi - 2, n - 1, v, beta, lane);
-    apply_right(H, ldh, hi - 1, 2, 0, hi, v, beta, lane);
-    apply_right(Z, ldz, hi - 1, 2, 0, nz - 1, v, beta, lane);
+    apply_left_n<2>(H, ldh, hi - 1, hi - 2, n - 1, v, beta, lane);
+    apply_right_n<2>(H, ldh, hi - 1, 0, hi, v, beta, lane);
+    apply_right_n<2>(Z, ldz, hi - 1, 0, nz - 1, v, beta, lane);
     if (hi - 2 > l && lane == 0) at(H, ldh, hi, hi - 2) = R(0);
     __syncwarp();
   }
@@ -399,18 +471,6 @@ __device__ inline Block<R> block_at(const R* T, int ldt, int i, int n) {
   return {i, 1, at(T, ldt, i, i), R(0)};
 }
 
-// Diagonal blocks starting in [i0, i1) into out (at most cap); returns the count.
-template <class R>
-__device__ inline int scan_blocks(const R* T, int ldt, int i0, int i1, int n, Block<R>* out, int cap) {
-  int i = i0, cnt = 0;
-  while (i < i1 && cnt < cap) {
-    out[cnt] = block_at(T, ldt, i, n);
-    i += out[cnt].size;
-    ++cnt;
-  }
-  return cnt;
-}
-
 // Ordering key of an eigenvalue (smaller is wanted first).
 template <class R>
 __device__ inline R key(R re, R im, int which) {
@@ -422,25 +482,47 @@ __device__ inline R key(R re, R im, int which) {
   }
 }
 
-template <class R>
-__device__ inline bool small_solve(int s, R M[4][4], R r[4]) {
-  for (int k = 0; k < s; ++k) {
+// S x S linear system M x = r by Gaussian elimination with partial pivoting,
+// in registers (the row exchanges are selects); false if singular.
+template <int S, class R>
+__device__ __forceinline__ bool small_solve(R (&M)[S][S], R (&r)[S]) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
     int p = k;
-    for (int i = k + 1; i < s; ++i) if (rabs(M[i][k]) > rabs(M[p][k])) p = i;
-    if (M[p][k] == R(0)) return false;
-    if (p != k) {
-      for (int j = 0; j < s; ++j) { const R tt = M[k][j]; M[k][j] = M[p][j]; M[p][j] = tt; }
-      const R tr = r[k]; r[k] = r[p]; r[p] = tr;
+    R pv = rabs(M[k][k]);
+#pragma unroll
+    for (int i = k + 1; i < S; ++i)
+      if (rabs(M[i][k]) > pv) { p = i; pv = rabs(M[i][k]); }
+#pragma unroll
+    for (int i = k + 1; i < S; ++i) {
+      const bool sw = i == p;
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const R a = M[k][j], b = M[i][j];
+        M[k][j] = sw ? b : a;
+        M[i][j] = sw ? a : b;
+      }
+      const R a = r[k], b = r[i];
+      r[k] = sw ? b : a;
+      r[i] = sw ? a : b;
     }
-    for (int i = k + 1; i < s; ++i) {
-      const R f = M[i][k] / M[k][k];
-      for (int j = k; j < s; ++j) M[i][j] -= f * M[k][j];
+    if (M[k][k] == R(0)) ok = false;
+    const R inv = M[k][k] == R(0) ? R(0) : R(1) / M[k][k];
+#pragma unroll
+    for (int i = k + 1; i < S; ++i) {
+      const R f = M[i][k] * inv;
+#pragma unroll
+      for (int j = k; j < S; ++j) M[i][j] -= f * M[k][j];
       r[i] -= f * r[k];
     }
   }
-  for (int k = s - 1; k >= 0; --k) {
+  if (!ok) return false;
+#pragma unroll
+  for (int k = S - 1; k >= 0; --k) {
     R acc = r[k];
-    for (int j = k + 1; j < s; ++j) acc -= M[k][j] * r[j];
+#pragma unroll
+    for (int j = k + 1; j < S; ++j) acc -= M[k][j] * r[j];
     r[k] = acc / M[k][k];
   }
   return true;
@@ -454,7 +536,8 @@ __device__ inline void swap_singles(int n, R* T, int ldt, R* Z, int ldz, int nz,
   const R r = rhypot(x, y);
   __syncwarp();
   if (r == R(0)) return;
-  const R cs = x / r, sn = y / r;
+  const R ir = R(1) / r;
+  const R cs = x * ir, sn = y * ir;
   for (int col = j + lane; col < n; col += 32) {
     const R t0 = at(T, ldt, j, col), t1 = at(T, ldt, j + 1, col);
     at(T, ldt, j, col) = cs * t0 + sn * t1;
@@ -481,176 +564,204 @@ __device__ inline void swap_singles(int n, R* T, int ldt, R* Z, int ldz, int nz,
   __syncwarp();
 }
 
-// Swap the adjacent diagonal blocks at j (sizes p then q); 0 on success, -1 / -2
-// when refused (T and Z unchanged).
+// Reflector L of the Householder QR of W (S x Q), accumulated into Qs.
+template <int S, int Q, int L, class R>
+__device__ __forceinline__ void qr_step(R (&W)[S][Q], R (&Qs)[S][S]) {
+  constexpr int LEN = S - L;
+  R x[LEN], v[LEN], beta;
+#pragma unroll
+  for (int i = 0; i < LEN; ++i) x[i] = W[L + i][L];
+  house<LEN>(x, v, beta);
+  if (beta == R(0)) return;
+#pragma unroll
+  for (int c = L; c < Q; ++c) {
+    R acc = R(0);
+#pragma unroll
+    for (int i = 0; i < LEN; ++i) acc += v[i] * W[L + i][c];
+    acc *= beta;
+#pragma unroll
+    for (int i = 0; i < LEN; ++i) W[L + i][c] -= acc * v[i];
+  }
+#pragma unroll
+  for (int a = 0; a < S; ++a) {
+    R acc = R(0);
+#pragma unroll
+    for (int i = 0; i < LEN; ++i) acc += Qs[a][L + i] * v[i];
+    acc *= beta;
+#pragma unroll
+    for (int i = 0; i < LEN; ++i) Qs[a][L + i] -= acc * v[i];
+  }
+}
+
+// T (rows / columns j..j+S-1) <- G^T T G and Z <- Z G for an orthogonal S x S G
+// (transpose: G^T in place of G), lanes over columns, then rows.
+template <int S, bool TR, class R>
+__device__ __forceinline__ void apply_similarity(int n, R* T, int ldt, R* Z, int ldz, int nz, int j, const R (&G)[S][S],
+                                                 int lane) {
+  for (int c = j + lane; c < n; c += 32) {
+    R tmp[S];
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+      R acc = R(0);
+#pragma unroll
+      for (int b = 0; b < S; ++b) acc += (TR ? G[a][b] : G[b][a]) * at(T, ldt, j + b, c);
+      tmp[a] = acc;
+    }
+#pragma unroll
+    for (int a = 0; a < S; ++a) at(T, ldt, j + a, c) = tmp[a];
+  }
+  __syncwarp();
+  for (int rr = lane; rr < j + S; rr += 32) {
+    R tmp[S];
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+      R acc = R(0);
+#pragma unroll
+      for (int b = 0; b < S; ++b) acc += at(T, ldt, rr, j + b) * (TR ? G[a][b] : G[b][a]);
+      tmp[a] = acc;
+    }
+#pragma unroll
+    for (int a = 0; a < S; ++a) at(T, ldt, rr, j + a) = tmp[a];
+  }
+  if (Z)
+    for (int rr = lane; rr < nz; rr += 32) {
+      R tmp[S];
+#pragma unroll
+      for (int a = 0; a < S; ++a) {
+        R acc = R(0);
+#pragma unroll
+        for (int b = 0; b < S; ++b) acc += at(Z, ldz, rr, j + b) * (TR ? G[a][b] : G[b][a]);
+        tmp[a] = acc;
+      }
+#pragma unroll
+      for (int a = 0; a < S; ++a) at(Z, ldz, rr, j + a) = tmp[a];
+    }
+  __syncwarp();
+}
+
+// Swap the adjacent diagonal blocks at j (sizes P then Q, not both 1): the
+// Sylvester equation T11 X - X T22 = -T12, then the orthogonal factor of the
+// QR of [X; I] moves T22's block to the top (Bai & Demmel).  0 on success,
+// -1 / -2 when refused (T and Z unchanged).
+template <int P, int Q, class R>
+__device__ inline int swap_pq(int n, R* T, int ldt, R* Z, int ldz, int nz, int j, int lane) {
+  constexpr int S = P + Q, PQ = P * Q;
+  R M[PQ][PQ], r[PQ];
+#pragma unroll
+  for (int a = 0; a < PQ; ++a) {
+    r[a] = R(0);
+#pragma unroll
+    for (int b = 0; b < PQ; ++b) M[a][b] = R(0);
+  }
+#pragma unroll
+  for (int l = 0; l < Q; ++l)
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      const int row = i + P * l;
+#pragma unroll
+      for (int ii = 0; ii < P; ++ii) M[row][ii + P * l] += at(T, ldt, j + i, j + ii);
+#pragma unroll
+      for (int ll = 0; ll < Q; ++ll) M[row][i + P * ll] -= at(T, ldt, j + P + ll, j + P + l);
+      r[row] = -at(T, ldt, j + i, j + P + l);
+    }
+  if (!small_solve<PQ>(M, r)) { __syncwarp(); return -1; }
+  R W[S][Q];
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+#pragma unroll
+    for (int i = 0; i < P; ++i) W[i][l] = r[i + P * l];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) W[P + i][l] = (i == l) ? R(1) : R(0);
+  }
+  R Qs[S][S];
+#pragma unroll
+  for (int a = 0; a < S; ++a)
+#pragma unroll
+    for (int b = 0; b < S; ++b) Qs[a][b] = (a == b) ? R(1) : R(0);
+  qr_step<S, Q, 0>(W, Qs);
+  if (Q == 2) qr_step<S, Q, (Q == 2 ? 1 : 0)>(W, Qs);
+  R wnorm = R(0);
+#pragma unroll
+  for (int a = 0; a < S; ++a)
+#pragma unroll
+    for (int b = 0; b < S; ++b) wnorm = rmax(wnorm, rabs(at(T, ldt, j + a, j + b)));
+  __syncwarp();
+  apply_similarity<S, false>(n, T, ldt, Z, ldz, nz, j, Qs, lane);
+  R lower = R(0);
+#pragma unroll
+  for (int a = Q; a < S; ++a)
+#pragma unroll
+    for (int b = 0; b < Q; ++b) lower = rmax(lower, rabs(at(T, ldt, j + a, j + b)));
+  __syncwarp();
+  if (lower > R(1000) * reps<R>() * rmax(wnorm, R(1e-30f))) {   // refused: undo
+    apply_similarity<S, true>(n, T, ldt, Z, ldz, nz, j, Qs, lane);
+    return -2;
+  }
+  if (lane == 0) {
+    for (int a = Q; a < S; ++a) for (int b = 0; b < Q; ++b) at(T, ldt, j + a, j + b) = R(0);
+    for (int c = 0; c < j; ++c) for (int a = 0; a < S; ++a) at(T, ldt, j + a, c) = R(0);
+  }
+  __syncwarp();
+  if (Q == 2) standardize_2x2(n, T, ldt, Z, ldz, nz, j, lane);
+  if (P == 2) standardize_2x2(n, T, ldt, Z, ldz, nz, j + Q, lane);
+  if (lane == 0)
+    for (int a = 0; a < S; ++a)
+      for (int b = 0; b < S; ++b)
+        if (a > b + 1) at(T, ldt, j + a, j + b) = R(0);
+  __syncwarp();
+  return 0;
+}
+
+// Swap the adjacent diagonal blocks at j (sizes p then q); 0 on success,
+// -1 / -2 when refused (T and Z unchanged).
 template <class R>
 __device__ inline int swap_blocks(int n, R* T, int ldt, R* Z, int ldz, int nz, int j, int p, int q, int lane) {
   if (p == 1 && q == 1) {
     swap_singles(n, T, ldt, Z, ldz, nz, j, lane);
     return 0;
   }
-  const int s = p + q;
-  R M[4][4], r[4];
-  for (int a = 0; a < 4; ++a) {
-    r[a] = R(0);
-    for (int b = 0; b < 4; ++b) M[a][b] = R(0);
-  }
-  // Sylvester equation T11 X - X T22 = -T12 for the p x q block X, by rows of vec(X)
-  for (int l = 0; l < q; ++l)
-    for (int i = 0; i < p; ++i) {
-      const int row = i + p * l;
-      for (int ii = 0; ii < p; ++ii) M[row][ii + p * l] += at(T, ldt, j + i, j + ii);
-      for (int ll = 0; ll < q; ++ll) M[row][i + p * ll] -= at(T, ldt, j + p + ll, j + p + l);
-      r[row] = -at(T, ldt, j + i, j + p + l);
-    }
-  if (!small_solve(p * q, M, r)) { __syncwarp(); return -1; }
-  R W[4][2];
-  for (int l = 0; l < q; ++l) {
-    for (int i = 0; i < p; ++i) W[i][l] = r[i + p * l];
-    for (int i = 0; i < q; ++i) W[p + i][l] = (i == l) ? R(1) : R(0);
-  }
-  R Qs[4][4];
-  for (int a = 0; a < s; ++a) for (int b = 0; b < s; ++b) Qs[a][b] = (a == b) ? R(1) : R(0);
-  for (int l = 0; l < q; ++l) {   // Householder QR of [X; I]: Qs's leading q columns span it
-    R xx[4], v[4], beta;
-    const int len = s - l;
-    for (int i = 0; i < len; ++i) xx[i] = W[l + i][l];
-    house(xx, len, v, &beta);
-    if (beta == R(0)) continue;
-    for (int c = l; c < q; ++c) {
-      R acc = R(0);
-      for (int i = 0; i < len; ++i) acc += v[i] * W[l + i][c];
-      acc *= beta;
-      for (int i = 0; i < len; ++i) W[l + i][c] -= acc * v[i];
-    }
-    for (int a = 0; a < s; ++a) {
-      R acc = R(0);
-      for (int i = 0; i < len; ++i) acc += Qs[a][l + i] * v[i];
-      acc *= beta;
-      for (int i = 0; i < len; ++i) Qs[a][l + i] -= acc * v[i];
-    }
-  }
-  R wnorm = R(0);
-  for (int a = 0; a < s; ++a) for (int b = 0; b < s; ++b) wnorm = rmax(wnorm, rabs(at(T, ldt, j + a, j + b)));
-  __syncwarp();
-  // T <- Qs^T T Qs on rows / columns j..j+s-1, Z <- Z Qs (lanes over columns, then rows)
-  for (int c = j + lane; c < n; c += 32) {
-    R tmp[4];
-    for (int a = 0; a < s; ++a) {
-      R acc = R(0);
-      for (int b = 0; b < s; ++b) acc += Qs[b][a] * at(T, ldt, j + b, c);
-      tmp[a] = acc;
-    }
-    for (int a = 0; a < s; ++a) at(T, ldt, j + a, c) = tmp[a];
-  }
-  __syncwarp();
-  for (int rr = lane; rr < j + s; rr += 32) {
-    R tmp[4];
-    for (int a = 0; a < s; ++a) {
-      R acc = R(0);
-      for (int b = 0; b < s; ++b) acc += at(T, ldt, rr, j + b) * Qs[b][a];
-      tmp[a] = acc;
-    }
-    for (int a = 0; a < s; ++a) at(T, ldt, rr, j + a) = tmp[a];
-  }
-  if (Z)
-    for (int rr = lane; rr < nz; rr += 32) {
-      R tmp[4];
-      for (int a = 0; a < s; ++a) {
-        R acc = R(0);
-        for (int b = 0; b < s; ++b) acc += at(Z, ldz, rr, j + b) * Qs[b][a];
-        tmp[a] = acc;
-      }
-      for (int a = 0; a < s; ++a) at(Z, ldz, rr, j + a) = tmp[a];
-    }
-  __syncwarp();
-  R lower = R(0);
-  for (int a = q; a < s; ++a) for (int b = 0; b < q; ++b) lower = rmax(lower, rabs(at(T, ldt, j + a, j + b)));
-  __syncwarp();
-  if (lower > R(1000) * reps<R>() * rmax(wnorm, R(1e-30f))) {
-    // refused: undo the similarity (Qs orthogonal)
-    for (int c = j + lane; c < n; c += 32) {
-      R tmp[4];
-      for (int a = 0; a < s; ++a) {
-        R acc = R(0);
-        for (int b = 0; b < s; ++b) acc += Qs[a][b] * at(T, ldt, j + b, c);
-        tmp[a] = acc;
-      }
-      for (int a = 0; a < s; ++a) at(T, ldt, j + a, c) = tmp[a];
-    }
-    __syncwarp();
-    for (int rr = lane; rr < j + s; rr += 32) {
-      R tmp[4];
-      for (int a = 0; a < s; ++a) {
-        R acc = R(0);
-        for (int b = 0; b < s; ++b) acc += at(T, ldt, rr, j + b) * Qs[a][b];
-        tmp[a] = acc;
-      }
-      for (int a = 0; a < s; ++a) at(T, ldt, rr, j + a) = tmp[a];
-    }
-    if (Z)
-      for (int rr = lane; rr < nz; rr += 32) {
-        R tmp[4];
-        for (int a = 0; a < s; ++a) {
-          R acc = R(0);
-          for (int b = 0; b < s; ++b) acc += at(Z, ldz, rr, j + b) * Qs[a][b];
-          tmp[a] = acc;
-        }
-        for (int a = 0; a < s; ++a) at(Z, ldz, rr, j + a) = tmp[a];
-      }
-    __syncwarp();
-    return -2;
-  }
-  if (lane == 0) {
-    for (int a = q; a < s; ++a) for (int b = 0; b < q; ++b) at(T, ldt, j + a, j + b) = R(0);
-    for (int c = 0; c < j; ++c) for (int a = 0; a < s; ++a) at(T, ldt, j + a, c) = R(0);
-  }
-  __syncwarp();
-  if (q == 2) standardize_2x2(n, T, ldt, Z, ldz, nz, j, lane);
-  if (p == 2) standardize_2x2(n, T, ldt, Z, ldz, nz, j + q, lane);
-  if (lane == 0)
-    for (int a = 0; a < s; ++a)
-      for (int b = 0; b < s; ++b)
-        if (a > b + 1) at(T, ldt, j + a, j + b) = R(0);
-  __syncwarp();
-  return 0;
+  if (p == 1) return swap_pq<1, 2>(n, T, ldt, Z, ldz, nz, j, lane);
+  if (q == 1) return swap_pq<2, 1>(n, T, ldt, Z, ldz, nz, j, lane);
+  return swap_pq<2, 2>(n, T, ldt, Z, ldz, nz, j, lane);
 }
 
 // Move the best diagonal blocks (by key; ties by position) covering `want`
 // columns, pairs whole, to the top, keeping their relative order (the
 // selection of Algorithm 1's truncation): each selected block, top to bottom,
-// is swapped up past the unselected blocks above it.  Returns the number of
-// leading columns that hold selected blocks (want or want + 1, fewer only if
-// a swap was refused).  n <= kMaxM.
+// is swapped up past the unselected blocks above it.  keys: scratch of n
+// values (shared memory).  Returns the number of leading columns that hold
+// selected blocks (want or want + 1, fewer only if a swap was refused).
+// n <= kMaxM; the selection is a bit mask of rows.
 template <class R>
-__device__ inline int reorder_select(int n, R* T, int ldt, R* Z, int ldz, int nz, int which, int want, int lane) {
-  unsigned char selr[kMaxM];
-  for (int i = 0; i < n; ++i) selr[i] = 0;
-  {
-    Block<R> bl[kMaxM];
-    bool taken[kMaxM];
-    const int nb = scan_blocks(T, ldt, 0, n, n, bl, n);
-    for (int t = 0; t < nb; ++t) taken[t] = false;
-    int cols = 0;
-    while (cols < want) {
-      int best = -1;
-      R bk = R(0);
-      for (int t = 0; t < nb; ++t) {
-        if (taken[t]) continue;
-        const R kk = key(bl[t].re, bl[t].im, which);
-        if (best < 0 || kk < bk) { best = t; bk = kk; }
-      }
-      if (best < 0) break;
-      taken[best] = true;
-      cols += bl[best].size;
-      for (int i = bl[best].start; i < bl[best].start + bl[best].size; ++i) selr[i] = 1;
+__device__ inline int reorder_select(int n, R* T, int ldt, R* Z, int ldz, int nz, int which, int want, R* keys,
+                                     int lane) {
+  for (int i = lane; i < n; i += 32) {   // key of the block starting at i (rows that start none: unused)
+    const bool second = i > 0 && at(T, ldt, i, i - 1) != R(0);
+    if (!second) {
+      const Block<R> b = block_at(T, ldt, i, n);
+      keys[i] = key(b.re, b.im, which);
     }
+  }
+  __syncwarp();
+  uint64_t sel = 0;
+  int cols = 0;
+  while (cols < want) {
+    int best = -1, bsz = 0;
+    R bk = R(0);
+    for (int i = 0; i < n;) {
+      const int sz = (i + 1 < n && at(T, ldt, i + 1, i) != R(0)) ? 2 : 1;
+      if (!((sel >> i) & 1ull) && (best < 0 || keys[i] < bk)) { best = i; bk = keys[i]; bsz = sz; }
+      i += sz;
+    }
+    if (best < 0) break;
+    sel |= (bsz == 2 ? 3ull : 1ull) << best;
+    cols += bsz;
   }
   __syncwarp();
   int top = 0;
   for (int placed = 0; placed < n && top < n; ++placed) {
     int i = top;   // the first selected block at or below top (the blocks between are unselected)
-    while (i < n && !selr[i]) i += (i + 1 < n && at(T, ldt, i + 1, i) != R(0)) ? 2 : 1;
+    while (i < n && !((sel >> i) & 1ull)) i += (i + 1 < n && at(T, ldt, i + 1, i) != R(0)) ? 2 : 1;
     if (i >= n) break;
     int size = (i + 1 < n && at(T, ldt, i + 1, i) != R(0)) ? 2 : 1;
     int cur = i;
@@ -660,8 +771,8 @@ __device__ inline int reorder_select(int n, R* T, int ldt, R* Z, int ldz, int nz
       const int up_size = cur - up_start;
       const int rc = swap_blocks(n, T, ldt, Z, ldz, nz, up_start, up_size, size, lane);
       if (rc != 0) { refused = true; break; }
-      for (int r = up_start; r < up_start + size; ++r) selr[r] = 1;
-      for (int r = up_start + size; r < cur + size; ++r) selr[r] = 0;
+      sel |= ((1ull << size) - 1ull) << up_start;
+      sel &= ~(((1ull << up_size) - 1ull) << (up_start + size));
       cur = up_start;
       size = (cur + 1 < n && at(T, ldt, cur + 1, cur) != R(0)) ? 2 : 1;   // a standardised pair may be real
     }
@@ -672,23 +783,26 @@ __device__ inline int reorder_select(int n, R* T, int ldt, R* Z, int ldz, int nz
   return top;
 }
 
-// Eigenvalues and unit eigenvectors of a quasi-triangular T (n x n,
-// n <= kMaxM): column c of (Yre, Yim) (ld ldy) for eigenvalue c in block
-// order (a pair: Im > 0 first).  Lanes take one eigenvector each.
+// Eigenvalues and unit eigenvectors of a quasi-triangular T (n x n): column c
+// of (Yre, Yim) (ld ldy) for eigenvalue c in block order (a pair: Im > 0
+// first).  Lanes take one eigenvector each: back substitution through the
+// blocks above the eigenvalue's own, read from T's subdiagonal.
 template <class R>
-__device__ inline int quasi_eig(int n, const R* T, int ldt, R* lre, R* lim, R* Yre, R* Yim, int ldy, int lane) {
-  Block<R> bl[kMaxM];
-  const int nb = scan_blocks(T, ldt, 0, n, n, bl, n);
+__device__ inline void quasi_eig(int n, const R* T, int ldt, R* lre, R* lim, R* Yre, R* Yim, int ldy, int lane) {
   R tnorm = R(0);
-  for (int j = 0; j < n; ++j) for (int i = 0; i <= min(j + 1, n - 1); ++i) tnorm = rmax(tnorm, rabs(at(T, ldt, i, j)));
+  for (int j = lane; j < n; j += 32)
+    for (int i = 0; i <= min(j + 1, n - 1); ++i) tnorm = rmax(tnorm, rabs(at(T, ldt, i, j)));
+  tnorm = warp_allmax(tnorm);
   const R small = rmax(tnorm * reps<R>(), R(1e-30f));
   for (int c = lane; c < n; c += 32) {
-    int bidx = 0, col = 0, e = 0;
-    for (int b2 = 0; b2 < nb; ++b2) {
-      if (c < col + bl[b2].size) { bidx = b2; e = c - col; break; }
-      col += bl[b2].size;
+    int start = 0;   // the block holding column c
+    while (true) {
+      const int sz = (start + 1 < n && at(T, ldt, start + 1, start) != R(0)) ? 2 : 1;
+      if (c < start + sz) break;
+      start += sz;
     }
-    const Block<R> B = bl[bidx];
+    const Block<R> B = block_at(T, ldt, start, n);
+    const int e = c - start;
     const R lr = B.re, li = B.size == 2 ? (e == 0 ? B.im : -B.im) : R(0);
     R* yr = Yre + c * ldy;
     R* yi = Yim + c * ldy;
@@ -700,57 +814,59 @@ __device__ inline int quasi_eig(int n, const R* T, int ldt, R* lre, R* lim, R* Y
       yr[B.start + 1] = lr - at(T, ldt, B.start, B.start);
       yi[B.start + 1] = li;
     }
-    const int top = B.start;
-    for (int ci = bidx - 1; ci >= 0; --ci) {   // back substitution, block by block
-      const Block<R> C = bl[ci];
-      R rr[2] = {R(0), R(0)}, ri[2] = {R(0), R(0)};
-      for (int a = 0; a < C.size; ++a) {
-        R ar = R(0), ai = R(0);
-        for (int l = C.start + C.size; l <= top + B.size - 1; ++l) {
-          const R tv = at(T, ldt, C.start + a, l);
-          ar += tv * yr[l];
-          ai += tv * yi[l];
+    const int last = B.start + B.size - 1;
+    int bot = B.start - 1;   // bottom row of the next block above
+    while (bot >= 0) {
+      const int csz = (bot >= 1 && at(T, ldt, bot, bot - 1) != R(0)) ? 2 : 1;
+      const int cs0 = bot - csz + 1;
+      R rr0 = R(0), ri0 = R(0), rr1 = R(0), ri1 = R(0);
+      for (int l = cs0 + csz; l <= last; ++l) {
+        const R t0 = at(T, ldt, cs0, l);
+        rr0 -= t0 * yr[l];
+        ri0 -= t0 * yi[l];
+        if (csz == 2) {
+          const R t1 = at(T, ldt, cs0 + 1, l);
+          rr1 -= t1 * yr[l];
+          ri1 -= t1 * yi[l];
         }
-        rr[a] = -ar;
-        ri[a] = -ai;
       }
-      if (C.size == 1) {
-        R dr = at(T, ldt, C.start, C.start) - lr, di = -li;
+      if (csz == 1) {
+        R dr = at(T, ldt, cs0, cs0) - lr, di = -li;
         if (rhypot(dr, di) < small) { dr = small; di = R(0); }
-        const R den = dr * dr + di * di;
-        yr[C.start] = (rr[0] * dr + ri[0] * di) / den;
-        yi[C.start] = (ri[0] * dr - rr[0] * di) / den;
+        const R den = R(1) / (dr * dr + di * di);
+        yr[cs0] = (rr0 * dr + ri0 * di) * den;
+        yi[cs0] = (ri0 * dr - rr0 * di) * den;
       } else {
-        const R m00r = at(T, ldt, C.start, C.start) - lr, m00i = -li;
-        const R m01 = at(T, ldt, C.start, C.start + 1), m10 = at(T, ldt, C.start + 1, C.start);
-        const R m11r = at(T, ldt, C.start + 1, C.start + 1) - lr, m11i = -li;
+        const R m00r = at(T, ldt, cs0, cs0) - lr, m00i = -li;
+        const R m01 = at(T, ldt, cs0, cs0 + 1), m10 = at(T, ldt, cs0 + 1, cs0);
+        const R m11r = at(T, ldt, cs0 + 1, cs0 + 1) - lr, m11i = -li;
         R detr = m00r * m11r - m00i * m11i - m01 * m10, deti = m00r * m11i + m00i * m11r;
         if (rhypot(detr, deti) < small * small) { detr = small * small; deti = R(0); }
-        const R dd = detr * detr + deti * deti;
-        const R n0r = rr[0] * m11r - ri[0] * m11i - m01 * rr[1], n0i = rr[0] * m11i + ri[0] * m11r - m01 * ri[1];
-        const R n1r = m00r * rr[1] - m00i * ri[1] - m10 * rr[0], n1i = m00r * ri[1] + m00i * rr[1] - m10 * ri[0];
-        yr[C.start] = (n0r * detr + n0i * deti) / dd;
-        yi[C.start] = (n0i * detr - n0r * deti) / dd;
-        yr[C.start + 1] = (n1r * detr + n1i * deti) / dd;
-        yi[C.start + 1] = (n1i * detr - n1r * deti) / dd;
+        const R dd = R(1) / (detr * detr + deti * deti);
+        const R n0r = rr0 * m11r - ri0 * m11i - m01 * rr1, n0i = rr0 * m11i + ri0 * m11r - m01 * ri1;
+        const R n1r = m00r * rr1 - m00i * ri1 - m10 * rr0, n1i = m00r * ri1 + m00i * rr1 - m10 * ri0;
+        yr[cs0] = (n0r * detr + n0i * deti) * dd;
+        yi[cs0] = (n0i * detr - n0r * deti) * dd;
+        yr[cs0 + 1] = (n1r * detr + n1i * deti) * dd;
+        yi[cs0 + 1] = (n1i * detr - n1r * deti) * dd;
       }
+      bot = cs0 - 1;
     }
     // unit norm (scaled, so that the squares neither overflow nor underflow)
     R mx = R(0);
-    for (int i = 0; i < n; ++i) mx = rmax(mx, rmax(rabs(yr[i]), rabs(yi[i])));
+    for (int i = 0; i <= last; ++i) mx = rmax(mx, rmax(rabs(yr[i]), rabs(yi[i])));
     const R imx = R(1) / mx;
     R nrm = R(0);
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i <= last; ++i) {
       const R a = yr[i] * imx, b = yi[i] * imx;
       nrm += a * a + b * b;
     }
     const R inv = imx / rsqrt_(nrm);
-    for (int i = 0; i < n; ++i) { yr[i] *= inv; yi[i] *= inv; }
+    for (int i = 0; i <= last; ++i) { yr[i] *= inv; yi[i] *= inv; }
     lre[c] = lr;
     lim[c] = li;
   }
   __syncwarp();
-  return nb;
 }
 
 }  // namespace rks_dd
