@@ -509,21 +509,41 @@ def _exp1(rks) -> dict:
 def _batched(rks) -> dict:
     """The batch of 256 uneven 2D convection-diffusion problems (sides
     U{70..450}, log-normal diffusivity, convection in [0, 30]^2, FP32 values;
-    k = 8, p = 24, d = 64, residual <= 1e-8, thick restart keep = 8), solved
-    concurrently (16 host threads, one stream per problem), mixed and
-    double-float; host wall time of rks_solve_batched."""
+    k = 8, p = 24, d = 64, residual <= 1e-8 verified in FP64):
+      - persistent: one CUDA graph of persistent kernels (rks_solve_batched_dev:
+        the whole of Algorithm 1 on the device, thick restart keep = 12, no
+        locking, launch configuration autotuned at creation); CUDA-event time
+        of the graph launch and host wall time of the call;
+      - streams: one context per problem on its own stream, 16 host threads
+        (rks_solve_batched, double-float, locking, keep = 8); host wall time."""
     from paper_2508_05400_gb300 import inputs as I
     probs = [I.uneven_convdiff2d_problem(i) for i in range(256)]
     P0 = probs[0]
+    o = P0.solver_opts()
     out = {"sum_n": int(sum(P.A.n for P in probs))}
-    for prec in ("mixed", "df"):
-        with rks.Batch([P.A for P in probs], P0.k, P0.p, P0.d, which=P0.which, zeta=P0.zeta, nthreads=16,
-                       prec=prec, keep=P0.k, maxit=4000, **P0.solver_opts()) as b:
-            t0 = time.perf_counter()
-            infos = b.solve(nthreads=16, allow_noconv=True)
-            wall = time.perf_counter() - t0
-        out[prec] = {"ms": wall * 1e3, "converged": int(sum(i["converged"] for i in infos)),
-                     "max_resid": float(max(i["max_resid"] for i in infos))}
+    t0 = time.perf_counter()
+    with rks.DevBatch([P.A for P in probs], P0.k, P0.p, P0.d, which=P0.which, zeta=P0.zeta, tol=o["tol"],
+                      conv="norm1", verify=o["verify"], maxit=4000, keep=12) as b:
+        t_create = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        infos = b.solve(allow_noconv=True)
+        wall = time.perf_counter() - t0
+        cfg = b.config()
+        ph = b.phase_cycles()
+    tot = sum(ph.values())
+    out["persistent"] = {"ms": cfg["last_ms"], "wall_ms": wall * 1e3, "create_s": t_create,
+                         "config": {k: cfg[k] for k in ("GL", "nL", "GS", "nS")}, "tune_ms": cfg["tune_ms"],
+                         "converged": int(sum(i["converged"] for i in infos)),
+                         "max_resid": float(max(i["max_resid"] for i in infos)),
+                         "restarts_median": float(statistics.median([i["restarts"] for i in infos])),
+                         "phase_share": {k: round(v / max(tot, 1), 4) for k, v in ph.items()}}
+    with rks.Batch([P.A for P in probs], P0.k, P0.p, P0.d, which=P0.which, zeta=P0.zeta, nthreads=16,
+                   prec="df", keep=P0.k, maxit=4000, **o) as b:
+        t0 = time.perf_counter()
+        infos = b.solve(nthreads=16, allow_noconv=True)
+        wall = time.perf_counter() - t0
+    out["streams_df"] = {"ms": wall * 1e3, "converged": int(sum(i["converged"] for i in infos)),
+                         "max_resid": float(max(i["max_resid"] for i in infos))}
     return out
 
 

@@ -338,11 +338,14 @@ void rks_destroy_batched(rks_batch* b);
 
 /* ---- Batched solve in one persistent launch -------------------------- */
 
-/* Many independent problems solved by one persistent kernel (Algorithm 1
- * with Algorithm 2 for every problem, the small dense steps on the device):
- * clusters of G CTAs (G = 1, 2, 4 or 8 on the same GPU) take problems from a
- * device work queue, largest first (cost nnz + n m); the rows of a problem are
- * split over the CTAs of its cluster.  Double-float basis and matrix values,
+/* Many independent problems solved by persistent kernels (Algorithm 1 with
+ * Algorithm 2 for every problem, the small dense steps on the device) in one
+ * CUDA graph: clusters of G CTAs (G = 1, 2, 4 or 8) take problems from a
+ * device work queue sorted by cost (nnz + n m), largest first; the rows of a
+ * problem are split over the CTAs of its cluster.  A configuration is one
+ * kernel, or two running at once: clusters of GL CTAs taking problems from the
+ * front of the queue and clusters of GS < GL CTAs taking them from the back
+ * (one atomic counter pair, so the two ends never take the same problem).  Double-float basis and matrix values,
  * FP64 sketch sums, least squares, dense steps and residuals; the restart
  * keeps the max(k, min(opts.keep, m / 2)) best Schur vectors (a thick restart;
  * the truncation of Algorithm 1 with a larger size) and locks nothing;
@@ -362,8 +365,10 @@ typedef struct rks_dbatch rks_dbatch;
  * rks_create; max(k, min(opts.keep, m / 2)) + 1 <= 32.  Of opts (may be
  * NULL) zeta, maxit, conv, verify, keep and stream are used; mem_device and u1
  * must be 0 / NULL; the other fields are ignored.
- * ctas_per_problem: 1, 2, 4 or 8 CTAs per problem, or 0 to time one restart
- * of the whole batch with each and keep the fastest (rks_dbatch_config).
+ * ctas_per_problem: 1, 2, 4 or 8 CTAs per problem (one kernel), or 0 to time
+ * candidate configurations (one kernel with G = 2, 4, 8; two kernels with
+ * (GL, GS) = (8, 2), (8, 4), (4, 2) sharing the CTA slots) on a tuning run of
+ * two restarts of every problem, and keep the fastest (rks_dbatch_config).
  * Copies everything to the device (the caller keeps its arrays) and captures
  * the launch in a CUDA graph.  RKS_EINVAL for an invalid argument or a
  * problem whose shared-memory layout exceeds the device's limit. */
@@ -379,12 +384,12 @@ int rks_create_batched_dev(rks_dbatch** out, int count, const int64_t* n, const 
  * converge, else RKS_OK. */
 int rks_solve_batched_dev(rks_dbatch* b, rks_info* infos);
 
-/* The launch configuration: CTAs per problem, grid size, dynamic shared
- * memory per CTA, the timings of the tuning runs (4 floats, ms, for G = 1,
- * 2, 4, 8; 0 where not run) and the event time of the last solve.  Any
- * pointer may be NULL. */
-int rks_dbatch_config(const rks_dbatch* b, int* ctas_per_problem, int* grid, int64_t* smem_bytes, float* tune_ms,
-                      float* last_ms);
+/* The launch configuration: cfg4 = {GL, nL, GS, nS} (nL clusters of GL CTAs
+ * from the front of the queue, nS clusters of GS CTAs from the back; nS = 0
+ * for one kernel), the times (ms) of the first ntune tuning runs in candidate
+ * order, and the event time of the last solve; returns the number of tuning
+ * runs (1 when the configuration was given).  Any pointer may be NULL. */
+int rks_dbatch_config(const rks_dbatch* b, int* cfg4, float* tune_ms, int ntune, float* last_ms);
 
 /* Status of problem i in the last solve (RKS_ESTATE before one). */
 int rks_dbatch_status(const rks_dbatch* b, int i);

@@ -1,8 +1,10 @@
 // Batched rKS in one persistent launch.
 //
-// Each thread-block cluster (G CTAs, G = 1, 2, 4 or 8, picked by timing at
-// creation) takes problems from a device work queue, largest first, and runs
-// the whole of Algorithm 1 for each on the device, with no host round trip:
+// Each thread-block cluster (G CTAs, G = 1, 2, 4 or 8) takes problems from a
+// device work queue sorted by cost, largest first, and runs the whole of
+// Algorithm 1 for each on the device, with no host round trip (the launch
+// configuration, one kernel or two taking problems from the two ends of the
+// queue with different G, is picked by timing at creation):
 //   - the expansions of Algorithm 2: SpMV, sketch, randomized Gram-Schmidt in
 //     the sketch (CGS2 on the d-dimensional sketches), update, sketch of the
 //     update; the rows of the problem are split over the G CTAs by tiles of
@@ -73,6 +75,13 @@ constexpr int kBInfo = 8;                // ints of every problem's record
 constexpr int kBSlot = 6;                // doubles per reported pair: lre, lim, resid, rq_re, rq_im, est
 
 enum { kIStatus = 0, kIRestarts, kIMatvec, kINw, kIConv, kIWhiten, kINconv };
+
+// Scalar type of the warp-level dense step (Hessenberg, Francis QR,
+// reordering, Ritz pairs).  The step is latency-bound on one warp: FP64 and
+// the double-float type of dense_dev.cuh take the same time here, and FP64 is
+// the more accurate.
+using DenseR = double;
+__device__ __forceinline__ DenseR dense_from(double x) { return DenseR(x); }
 
 // Phases of the per-CTA cycle counters (clock64 deltas taken by thread 0 at
 // the CTA barriers that end each phase, summed over CTAs and problems).
@@ -186,7 +195,10 @@ struct BdProb {
 struct BdArgs {
   const BdProb* probs;
   const int* order;       // problems, largest first
-  int* queue;             // next position in order (0 before the launch)
+  unsigned long long* queue;   // positions taken from the front (low 32 bits) and the back (high 32 bits)
+  int dir;                // 0: this kernel takes problems from the front of order, 1: from the back
+  int tune;               // > 0: a tuning run, every problem stops after `tune` restarts
+  int64_t nmax;
   int count, k, m, d, zeta, which, maxit, conv;
   int want;               // Schur vectors kept by a restart (thick restart, >= k)
   double tol, verify;
@@ -616,18 +628,18 @@ __device__ __noinline__ void bd_resid_tile(const BdProb& P, int64_t r0, int rows
 // The warp-0 stages of the contraction, each with its own register
 // allocation: Hessenberg reduction, Francis QR, reordering with the kept size
 // (blocks covering `want` columns, pairs whole, at most m - 1), Ritz pairs.
-__device__ __noinline__ void bd_hess(int m, rks_dd::df* T, rks_dd::df* Q, rks_dd::df* v, int lane) {
+__device__ __noinline__ void bd_hess(int m, DenseR* T, DenseR* Q, DenseR* v, int lane) {
   rks_dd::hessenberg(m, T, m, Q, m, v, lane);
 }
-__device__ __noinline__ int bd_francis(int m, rks_dd::df* T, rks_dd::df* Q, int lane) {
+__device__ __noinline__ int bd_francis(int m, DenseR* T, DenseR* Q, int lane) {
   return rks_dd::schur(m, T, m, Q, m, m, lane);
 }
-__device__ __noinline__ int bd_reorder_truncate(int m, rks_dd::df* T, rks_dd::df* Q, int which, int want,
-                                                rks_dd::df* keys, int lane) {
+__device__ __noinline__ int bd_reorder_truncate(int m, DenseR* T, DenseR* Q, int which, int want,
+                                                DenseR* keys, int lane) {
   return min(rks_dd::reorder_select(m, T, m, Q, m, m, which, want, keys, lane), m - 1);
 }
-__device__ __noinline__ void bd_quasi_eig(int ka, int m, const rks_dd::df* T, rks_dd::df* lre, rks_dd::df* lim,
-                                          rks_dd::df* Yr, rks_dd::df* Yi, int lane) {
+__device__ __noinline__ void bd_quasi_eig(int ka, int m, const DenseR* T, DenseR* lre, DenseR* lim,
+                                          DenseR* Yr, DenseR* Yi, int lane) {
   rks_dd::quasi_eig(ka, T, m, lre, lim, Yr, Yi, m, lane);
 }
 
@@ -637,7 +649,7 @@ __device__ __noinline__ void bd_quasi_eig(int ka, int m, const rks_dd::df* T, rk
 
 __device__ void bd_solve(const BdArgs& A, const BdProb& P, double* sm, BdShared& sh, cg::cluster_group& cl,
                          long long* pacc, long long& tlast) {
-  using rks_dd::df;
+  using df = DenseR;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #define BD_MARK(ph)                     \
   if (tid == 0) {                       \
@@ -683,6 +695,7 @@ __device__ void bd_solve(const BdArgs& A, const BdProb& P, double* sm, BdShared&
   const double tiny = 2.2250738585072014e-308;
   int ex = 0;
   double tol = A.tol;
+  const int maxit = A.tune > 0 ? A.tune : A.maxit;
   int restarts = 0, status = RKS_OK, nw = 0, converged = 0, whit = 0, ka = 0, nconv = 0;
   int64_t nmatvec = 0;
   double max_est = 0.0, max_res = 0.0;
@@ -988,7 +1001,7 @@ __device__ void bd_solve(const BdArgs& A, const BdProb& P, double* sm, BdShared&
     const bool conv_now = max_est <= tol;
     bd_cluster_sync(cl);   // restarted rows visible to the cluster
     BD_MARK(kPhRitz);
-    if (!conv_now && restarts < A.maxit) {
+    if (!conv_now && restarts < maxit) {
       ja = ka;
       continue;
     }
@@ -1037,7 +1050,7 @@ __device__ void bd_solve(const BdArgs& A, const BdProb& P, double* sm, BdShared&
       max_res = fmax(max_res, isfinite(res) ? res : INFINITY);
     }
     const bool verified = !(A.verify > 0.0) || max_res <= A.verify;
-    if (conv_now && !verified && restarts < A.maxit) {
+    if (conv_now && !verified && restarts < maxit) {
       tol *= 0.25;
       bd_cluster_sync(cl);   // every CTA has read rsum before it is written again
       BD_MARK(kPhFinal);
@@ -1089,8 +1102,11 @@ __global__ void __launch_bounds__(kBT, 2) k_batch_rks(BdArgs A) {
   long long tlast = clock64();
   for (int guard = 0; guard <= A.count; ++guard) {
     if (cl.block_rank() == 0 && threadIdx.x == 0) {
-      const int pos = atomicAdd(A.queue, 1);
-      const int p = pos < A.count ? A.order[pos] : -1;
+      // one atomic add on both counters: the old value tells how many
+      // positions either end had taken, so the two ends never overlap
+      const unsigned long long old = atomicAdd(A.queue, A.dir ? (1ull << 32) : 1ull);
+      const int head = (int)(old & 0xffffffffull), tail = (int)(old >> 32);
+      const int p = head + tail < A.count ? A.order[A.dir ? A.count - 1 - tail : head] : -1;
       for (unsigned r = 0; r < G; ++r) *cl.map_shared_rank(&sh.prob, r) = p;
     }
     cl.sync();
@@ -1110,11 +1126,11 @@ __global__ void __launch_bounds__(kBT, 2) k_batch_rks(BdArgs A) {
 
 // The device dense step on one matrix (test entry point): one warp, the
 // matrices in global memory, double-float arithmetic (as in the solver).
-__global__ void k_dense_test(int m, const double* B, rks_dd::df* T, rks_dd::df* Q, int which, int nsort,
-                             rks_dd::df* lre, rks_dd::df* lim, rks_dd::df* Yr, rks_dd::df* Yi, rks_dd::df* scratch,
+__global__ void k_dense_test(int m, const double* B, DenseR* T, DenseR* Q, int which, int nsort,
+                             DenseR* lre, DenseR* lim, DenseR* Yr, DenseR* Yi, DenseR* scratch,
                              int* status) {
   const int lane = threadIdx.x;
-  for (int t = lane; t < m * m; t += 32) T[t] = rks_dd::df(B[t]);
+  for (int t = lane; t < m * m; t += 32) T[t] = dense_from(B[t]);
   __syncwarp();
   rks_dd::hessenberg(m, T, m, Q, m, scratch, lane);
   const int rc = rks_dd::schur(m, T, m, Q, m, m, lane);
@@ -1127,7 +1143,7 @@ __global__ void k_dense_test(int m, const double* B, rks_dd::df* T, rks_dd::df* 
   if (lane == 0) status[0] = rc ? RKS_EDENSE : fails;
 }
 
-__global__ void k_df_to_double(int64_t count, const rks_dd::df* in, double* out) {
+__global__ void k_df_to_double(int64_t count, const DenseR* in, double* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (double)in[i];
 }
@@ -1244,23 +1260,26 @@ struct rks_dbatch {
   int device = 0, count = 0, k = 0, p = 0, m = 0, d = 0, zeta = 8, which = 0, maxit = 1000, conv = 0, want = 0;
   double tol = 0.0, verify = 0.0;
   uint64_t seed = 0;
-  int G = 1, grid = 0;
+  // launch configuration: nL clusters of GL CTAs take problems from the
+  // front (largest first), nS clusters of GS CTAs from the back (nS = 0: one kernel)
+  int GL = 1, nL = 0, GS = 0, nS = 0;
   size_t smem = 0;
+  int64_t nmax = 0;
   std::vector<int64_t> n;
   std::vector<BdProb> probs;
-  float tune_ms[4] = {0.f, 0.f, 0.f, 0.f};   // one restart of the batch with G = 1, 2, 4, 8 (0: not run)
+  std::vector<float> tune_ms;   // tuning runs, one per candidate configuration
   char* pool = nullptr;
   BdProb* d_probs = nullptr;
   int* d_order = nullptr;
-  int* d_queue = nullptr;
+  unsigned long long* d_queue = nullptr;
   int* d_info = nullptr;
   double* d_out = nullptr;
   unsigned long long* d_phase = nullptr;
   unsigned long long phase[kPhases] = {};
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr, stream2 = nullptr;
   bool own_stream = false;
   cudaGraphExec_t graph = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, fork = nullptr, join = nullptr;
   std::vector<int> info;
   std::vector<double> out;
   bool solved = false;
@@ -1285,18 +1304,21 @@ void cluster_cfg(const rks_dbatch* b, int G, int grid, cudaLaunchConfig_t& cfg, 
   cfg.numAttrs = 1;
 }
 
-cudaError_t launch_batch(rks_dbatch* b, int G, int grid, int maxit) {
+cudaError_t launch_kernel(rks_dbatch* b, cudaStream_t st, int G, int nclusters, int dir, int tune) {
   BdArgs a;
   a.probs = b->d_probs;
   a.order = b->d_order;
   a.queue = b->d_queue;
+  a.dir = dir;
+  a.tune = tune;
+  a.nmax = b->nmax;
   a.count = b->count;
   a.k = b->k;
   a.m = b->m;
   a.d = b->d;
   a.zeta = b->zeta;
   a.which = b->which;
-  a.maxit = maxit;
+  a.maxit = b->maxit;
   a.want = b->want;
   a.conv = b->conv;
   a.tol = b->tol;
@@ -1305,11 +1327,26 @@ cudaError_t launch_batch(rks_dbatch* b, int G, int grid, int maxit) {
   a.phase = b->d_phase;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  cluster_cfg(b, G, grid, cfg, attr);
-  cudaError_t e = cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->stream);
+  cluster_cfg(b, G, nclusters * G, cfg, attr);
+  cfg.stream = st;
+  return cudaLaunchKernelEx(&cfg, k_batch_rks, a);
+}
+
+// The whole launch on b->stream: queue and counters reset, the front kernel,
+// and the back kernel (if any) on a second stream forked and joined by events.
+cudaError_t launch_batch(rks_dbatch* b, int GL, int nL, int GS, int nS, int tune) {
+  cudaError_t e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_phase, 0, sizeof(unsigned long long) * kPhases, b->stream);
   if (e != cudaSuccess) return e;
-  return cudaLaunchKernelEx(&cfg, k_batch_rks, a);
+  if (nS > 0) {
+    if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(b->stream2, b->fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_kernel(b, b->stream2, GS, nS, 1, tune)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(b->join, b->stream2)) != cudaSuccess) return e;
+  }
+  if ((e = launch_kernel(b, b->stream, GL, nL, 0, tune)) != cudaSuccess) return e;
+  if (nS > 0) e = cudaStreamWaitEvent(b->stream, b->join, 0);
+  return e;
 }
 
 // Clusters of G CTAs resident on the device at once (0: G not possible).
@@ -1470,7 +1507,7 @@ extern "C" int rks_create_batched_dev(rks_dbatch** out, int count, const int64_t
   }
   b->d_probs = (BdProb*)(b->pool + off_probs);
   b->d_order = (int*)(b->pool + off_order);
-  b->d_queue = (int*)(b->pool + off_queue);
+  b->d_queue = (unsigned long long*)(b->pool + off_queue);
   b->d_phase = (unsigned long long*)(b->pool + off_phase);
   b->d_info = (int*)(b->pool + off_info);
   b->d_out = (double*)(b->pool + off_out);
@@ -1519,41 +1556,63 @@ extern "C" int rks_create_batched_dev(rks_dbatch** out, int count, const int64_t
     b->own_stream = true;
   }
   if (cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess) return fail(RKS_ECUDA);
-  // cluster size: the one asked for, else the fastest of 1, 2, 4, 8 on one
-  // restart of the whole batch
-  const int cands[4] = {1, 2, 4, 8};
-  int bestG = 0;
-  float best = 0.f;
-  for (int c = 0; c < 4; ++c) {
-    const int G = cands[c];
-    if (ctas_per_problem && G != ctas_per_problem) continue;
-    const int nc = resident_clusters(b, G);
-    if (nc <= 0) continue;
-    const int grid = std::min(nc, count) * G;
+  if (cudaStreamCreateWithFlags(&b->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess)
+    return fail(RKS_ECUDA);
+  b->nmax = *std::max_element(n, n + count);
+  // launch configuration: the one asked for (one kernel, ctas_per_problem
+  // CTAs a problem), else the fastest candidate on a tuning run of two
+  // restarts of every problem (the throughput of the configuration)
+  {
+    struct Cand { int GL, nL, GS, nS; };
+    std::vector<Cand> cands;
+    const int slots1 = resident_clusters(b, 1);   // CTAs resident at once
+    auto single = [&](int G) {
+      const int nc = resident_clusters(b, G);
+      if (nc > 0) cands.push_back({G, std::min(nc, count), 0, 0});
+    };
+    auto dual = [&](int GL, int GS, int num, int den) {   // num / den of the CTA slots for the front kernel
+      if (resident_clusters(b, GL) <= 0 || resident_clusters(b, GS) <= 0 || count < 2) return;
+      const int nL = std::max(1, slots1 * num / den / GL);
+      const int nS = std::max(1, (slots1 - nL * GL) / GS);
+      cands.push_back({GL, std::min(nL, count), GS, std::min(nS, count)});
+    };
     if (ctas_per_problem) {
-      bestG = G;
-      b->grid = grid;
-      break;
+      single(ctas_per_problem);
+    } else {
+      single(2);
+      single(4);
+      single(8);
+      dual(8, 2, 1, 4);
+      dual(8, 2, 1, 2);
+      dual(8, 4, 1, 2);
+      dual(4, 2, 1, 2);
     }
-    if (cudaEventRecord(b->e0, b->stream) != cudaSuccess || launch_batch(b, G, grid, 1) != cudaSuccess ||
-        cudaEventRecord(b->e1, b->stream) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess)
-      return fail(RKS_ECUDA);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, b->e0, b->e1);
-    b->tune_ms[c] = ms;
-    if (!bestG || ms < best) {
-      bestG = G;
-      best = ms;
-      b->grid = grid;
+    if (cands.empty()) return fail(RKS_EINVAL);
+    b->tune_ms.assign(cands.size(), 0.f);
+    int best = 0;
+    if (cands.size() > 1) {
+      for (size_t c = 0; c < cands.size(); ++c) {
+        const Cand& cd = cands[c];
+        if (cudaEventRecord(b->e0, b->stream) != cudaSuccess ||
+            launch_batch(b, cd.GL, cd.nL, cd.GS, cd.nS, 2) != cudaSuccess ||
+            cudaEventRecord(b->e1, b->stream) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess)
+          return fail(RKS_ECUDA);
+        cudaEventElapsedTime(&b->tune_ms[c], b->e0, b->e1);
+        if (b->tune_ms[c] < b->tune_ms[best]) best = (int)c;
+      }
     }
+    b->GL = cands[best].GL;
+    b->nL = cands[best].nL;
+    b->GS = cands[best].GS;
+    b->nS = cands[best].nS;
   }
-  if (!bestG) return fail(RKS_EINVAL);
-  b->G = bestG;
   // the launch (queue reset + kernel) as a CUDA graph
   {
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(RKS_ECUDA);
-    const cudaError_t le = launch_batch(b, b->G, b->grid, b->maxit);
+    const cudaError_t le = launch_batch(b, b->GL, b->nL, b->GS, b->nS, 0);
     const cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
     if (le != cudaSuccess || ce != cudaSuccess || !g) {
       if (g) cudaGraphDestroy(g);
@@ -1605,16 +1664,18 @@ extern "C" int rks_solve_batched_dev(rks_dbatch* b, rks_info* infos) {
   return noconv ? RKS_ENOCONV : RKS_OK;
 }
 
-extern "C" int rks_dbatch_config(const rks_dbatch* b, int* ctas_per_problem, int* grid, int64_t* smem_bytes,
-                                 float* tune_ms, float* last_ms) {
+extern "C" int rks_dbatch_config(const rks_dbatch* b, int* cfg4, float* tune_ms, int ntune, float* last_ms) {
   if (!b) return RKS_EINVAL;
-  if (ctas_per_problem) *ctas_per_problem = b->G;
-  if (grid) *grid = b->grid;
-  if (smem_bytes) *smem_bytes = (int64_t)b->smem;
+  if (cfg4) {
+    cfg4[0] = b->GL;
+    cfg4[1] = b->nL;
+    cfg4[2] = b->GS;
+    cfg4[3] = b->nS;
+  }
   if (tune_ms)
-    for (int c = 0; c < 4; ++c) tune_ms[c] = b->tune_ms[c];
+    for (int c = 0; c < ntune && c < (int)b->tune_ms.size(); ++c) tune_ms[c] = b->tune_ms[c];
   if (last_ms) *last_ms = b->last_ms;
-  return RKS_OK;
+  return (int)b->tune_ms.size();
 }
 
 extern "C" int rks_dbatch_phase_cycles(const rks_dbatch* b, int64_t* cycles, int count) {
@@ -1661,13 +1722,16 @@ extern "C" void rks_destroy_batched_dev(rks_dbatch* b) {
   if (b->e0) cudaEventDestroy(b->e0);
   if (b->e1) cudaEventDestroy(b->e1);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  if (b->stream2) cudaStreamDestroy(b->stream2);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
   if (b->pool) cudaFree(b->pool);
   delete b;
 }
 
 extern "C" int rks_dev_ordered_schur(int m, const double* Bh, int which, int nsort, double* T, double* Q,
                                      double* lam_re, double* lam_im, double* Y_re, double* Y_im) {
-  using rks_dd::df;
+  using df = DenseR;
   if (m < 1 || m > kBMaxM || !Bh || !T || !Q || which < 0 || which > 3 || nsort < 0) return RKS_EINVAL;
   const size_t mm = (size_t)m * m;
   const size_t nout = 4 * mm + 2 * (size_t)m;   // T, Q, Yr, Yi, lre, lim

@@ -76,12 +76,16 @@ __device__ __forceinline__ df operator*(df a, df b) {
   df_quick_two_sum(p, e, s, e);
   return df(s, e);
 }
+// quotient by two correction steps on a fast float quotient: each step
+// divides the exact-ish remainder, so the float quotients need only be
+// accurate to a few units in the last place
 __device__ __forceinline__ df operator/(df a, df b) {
-  const float q1 = a.hi / b.hi;
+  const float rb = __frcp_rn(b.hi);
+  const float q1 = a.hi * rb;
   const df r = a - b * df(q1);
-  const float q2 = r.hi / b.hi;
+  const float q2 = r.hi * rb;
   const df r2 = r - b * df(q2);
-  const float q3 = r2.hi / b.hi;
+  const float q3 = r2.hi * rb;
   float s, e;
   df_quick_two_sum(q1, q2, s, e);
   return df(s, e) + df(q3);
@@ -124,7 +128,8 @@ __device__ __forceinline__ R rhypot(R a, R b) {
   b = rabs(b);
   const R s = rmax(a, b);
   if (s == R(0)) return R(0);
-  const R x = a / s, y = b / s;
+  const R is = R(1) / s;
+  const R x = a * is, y = b * is;
   return s * rsqrt_(x * x + y * y);
 }
 template <class R>
@@ -225,6 +230,40 @@ __device__ __forceinline__ void apply_right_n(R* A, int ld, int c0, int r0, int 
       s *= beta;
 #pragma unroll
       for (int j = 0; j < LEN; ++j) at(A, ld, i, c0 + j) = a[j] - s * v[j];
+    }
+  }
+  __syncwarp();
+}
+
+// apply_left_n on rows r0.. of A and, in the same phase, apply_right_n on
+// columns r0.. of Z (nz rows): different arrays, one barrier.
+template <int LEN, class R>
+__device__ __forceinline__ void apply_left_right_n(R* A, int ld, int r0, int c0, int c1, R* Z, int ldz, int nz,
+                                                   const R (&v)[LEN], R beta, int lane) {
+  if (beta != R(0)) {
+    for (int j = c0 + lane; j <= c1; j += 32) {
+      R a[LEN];
+      R s = R(0);
+#pragma unroll
+      for (int i = 0; i < LEN; ++i) {
+        a[i] = at(A, ld, r0 + i, j);
+        s += v[i] * a[i];
+      }
+      s *= beta;
+#pragma unroll
+      for (int i = 0; i < LEN; ++i) at(A, ld, r0 + i, j) = a[i] - s * v[i];
+    }
+    for (int i = lane; i < nz; i += 32) {
+      R a[LEN];
+      R s = R(0);
+#pragma unroll
+      for (int j = 0; j < LEN; ++j) {
+        a[j] = at(Z, ldz, i, r0 + j);
+        s += a[j] * v[j];
+      }
+      s *= beta;
+#pragma unroll
+      for (int j = 0; j < LEN; ++j) at(Z, ldz, i, r0 + j) = a[j] - s * v[j];
     }
   }
   __syncwarp();
@@ -426,9 +465,8 @@ __device__ inline int schur(int n, R* H, int ldh, R* Z, int ldz, int nz, int lan
       R v[3], beta;
       house<3>(xv, v, beta);
       __syncwarp();
-      apply_left_n<3>(H, ldh, k, max(l, k - 1), n - 1, v, beta, lane);
+      apply_left_right_n<3>(H, ldh, k, max(l, k - 1), n - 1, Z, ldz, nz, v, beta, lane);
       apply_right_n<3>(H, ldh, k, 0, min(k + 3, hi), v, beta, lane);
-      apply_right_n<3>(Z, ldz, k, 0, nz - 1, v, beta, lane);
       if (k > l && lane == 0) { at(H, ldh, k + 1, k - 1) = R(0); at(H, ldh, k + 2, k - 1) = R(0); }
       __syncwarp();
       x = at(H, ldh, k + 1, k);
@@ -440,9 +478,8 @@ __device__ inline int schur(int n, R* H, int ldh, R* Z, int ldz, int nz, int lan
     R v[2], beta;
     house<2>(xv, v, beta);
     __syncwarp();
-    apply_left_n<2>(H, ldh, hi - 1, hi - 2, n - 1, v, beta, lane);
+    apply_left_right_n<2>(H, ldh, hi - 1, hi - 2, n - 1, Z, ldz, nz, v, beta, lane);
     apply_right_n<2>(H, ldh, hi - 1, 0, hi, v, beta, lane);
-    apply_right_n<2>(Z, ldz, hi - 1, 0, nz - 1, v, beta, lane);
     if (hi - 2 > l && lane == 0) at(H, ldh, hi, hi - 2) = R(0);
     __syncwarp();
   }

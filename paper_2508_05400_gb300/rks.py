@@ -141,7 +141,7 @@ def lib() -> C.CDLL:
         L.rks_create_batched_dev.restype = C.c_int
         L.rks_solve_batched_dev.argtypes = [_P, _P]
         L.rks_solve_batched_dev.restype = C.c_int
-        L.rks_dbatch_config.argtypes = [_P, _P, _P, _P, _P, _P]
+        L.rks_dbatch_config.argtypes = [_P, _P, _P, C.c_int, _P]
         L.rks_dbatch_config.restype = C.c_int
         L.rks_dbatch_status.argtypes = [_P, C.c_int]
         L.rks_dbatch_status.restype = C.c_int
@@ -645,15 +645,16 @@ class DevBatch:
         self._keep = None
 
     def config(self) -> dict:
-        """CTAs per problem, grid, shared memory per CTA, the tuning times (ms
-        for 1, 2, 4, 8 CTAs per problem) and the last solve's event time."""
-        g, grid, sm = C.c_int(), C.c_int(), C.c_int64()
-        tune = (C.c_float * 4)()
+        """The launch configuration (front kernel: nL clusters of GL CTAs; back
+        kernel: nS clusters of GS CTAs), the tuning times (ms, candidate order)
+        and the last solve's event time."""
+        cfg = (C.c_int * 4)()
+        tune = (C.c_float * 16)()
         last = C.c_float()
-        _check(lib().rks_dbatch_config(self._h, C.byref(g), C.byref(grid), C.byref(sm), C.cast(tune, _P),
-                                       C.byref(last)), "rks_dbatch_config")
-        return {"ctas_per_problem": g.value, "grid": grid.value, "smem_bytes": sm.value,
-                "tune_ms": {c: float(t) for c, t in zip((1, 2, 4, 8), tune)}, "last_ms": float(last.value)}
+        nt = lib().rks_dbatch_config(self._h, C.cast(cfg, _P), C.cast(tune, _P), 16, C.byref(last))
+        _check(min(nt, 0), "rks_dbatch_config")
+        return {"GL": cfg[0], "nL": cfg[1], "GS": cfg[2], "nS": cfg[3],
+                "tune_ms": [float(tune[i]) for i in range(min(nt, 16))], "last_ms": float(last.value)}
 
     PHASES = ("start", "spmv_sketch", "hessenberg", "exchange", "ls", "update_sketch", "francis", "beta",
               "reorder", "kept_whiten", "restart", "ritz", "final", "queue")

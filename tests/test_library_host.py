@@ -238,3 +238,48 @@ def test_noalloc_binding_rejects_bad_buffers_before_any_call(monkeypatch):
             rks.sketch_apply_noalloc(x, z, 80, 4, 0)
     with pytest.raises(ValueError, match="float64"):
         rks.sketch_apply_noalloc(x.float(), torch.zeros(80, dtype=torch.float64), 80, 4, 0)
+
+
+def test_create_batched_dev_rejects_bad_arguments_before_any_device_call(lib):
+    # sizes, keep, cluster size, CSR structure, values and the unsupported
+    # options are all checked before the first CUDA call
+    import ctypes as C
+    from paper_2508_05400_gb300 import inputs as I
+    A = I.toeplitz_tridiag(200)
+    bad_col = A.colind.copy()
+    bad_col[5] = A.n
+    bad_val = np.ascontiguousarray(A.vals, dtype=np.float64).copy()
+    bad_val[3] = np.nan
+    h = K._P()
+
+    def call(k=8, p=24, d=64, count=1, ctas=0, opts=None, colind=None, vals=None, n=None, which=2, tol=1e-8):
+        ci = A.colind if colind is None else colind
+        vv = np.ascontiguousarray(A.vals, dtype=np.float64) if vals is None else vals
+        ns = np.array([A.n if n is None else n], dtype=np.int64)
+        ptrs = [np.array([a.ctypes.data], dtype=np.uint64) for a in (A.rowptr, ci, vv)]
+        return lib.rks_create_batched_dev(C.byref(h), count, ns.ctypes.data, ptrs[0].ctypes.data, ptrs[1].ctypes.data,
+                                          ptrs[2].ctypes.data, 0, k, p, d, which, tol, 0,
+                                          C.byref(opts) if opts is not None else None, ctas)
+    assert call(count=0) == K.RKS_EINVAL
+    assert call(k=0) == K.RKS_EINVAL
+    assert call(p=1) == K.RKS_EINVAL
+    assert call(k=40, p=30) == K.RKS_EINVAL            # m > 64
+    assert call(k=32, p=8, d=64) == K.RKS_EINVAL        # k + 1 > 32
+    assert call(d=32) == K.RKS_EINVAL                   # d < m + 1
+    assert call(ctas=3) == K.RKS_EINVAL
+    assert call(which=4) == K.RKS_EINVAL
+    assert call(tol=0.0) == K.RKS_EINVAL
+    assert call(n=20) == K.RKS_EINVAL                   # n < m + 1
+    assert call(colind=bad_col) == K.RKS_EINVAL
+    assert call(vals=bad_val) == K.RKS_EINVAL
+    o = K.Opts()
+    lib.rks_opts_default(o)
+    o.keep = 40                                         # keep >= m
+    assert call(opts=o) == K.RKS_EINVAL
+    o.keep = 0
+    o.mem_device = 1
+    assert call(opts=o) == K.RKS_EINVAL
+    o.mem_device = 0
+    o.u1 = 0x1000
+    assert call(opts=o) == K.RKS_EINVAL
+    assert not h.value
