@@ -531,6 +531,16 @@ def _batched(rks) -> dict:
         cfg = b.config()
         ph = b.phase_cycles()
     tot = sum(ph.values())
+    # algorithmic bytes: per row and expansion step j the diagonal SpMV (D
+    # values, x, w), the update ((j + 2) columns read, one written) and two
+    # sketch-list reads (1.25 zeta uint16 entries each); per restart the
+    # restart product (m + 1 columns read, ka + 1 written), ka = keep + 1
+    m, zeta, D, ka = P0.k + P0.p, P0.zeta, 5, 13
+    step = lambda j: 8 * (D + 2) + 8 * (j + 3) + 2 * 1.25 * zeta * 2
+    first = sum(step(j) for j in range(m))
+    per_restart = sum(step(j) for j in range(ka, m)) + 8 * (m + 1 + ka + 1)
+    alg_bytes = sum(P.A.n * (first + i["restarts"] * per_restart) for P, i in zip(probs, infos))
+    out["persistent_gbs"] = alg_bytes / (cfg["last_ms"] * 1e-3) / 1e9
     out["persistent"] = {"ms": cfg["last_ms"], "wall_ms": wall * 1e3, "create_s": t_create,
                          "config": {k: cfg[k] for k in ("GL", "nL", "GS", "nS")}, "tune_ms": cfg["tune_ms"],
                          "converged": int(sum(i["converged"] for i in infos)),
@@ -584,6 +594,28 @@ def _small_oracle_errors(rks, prec: str) -> dict:
             "oracle_max_resid": float(ores.resid.max())}
 
 
+def run_batch_only(args) -> None:
+    """The persistent batched solve alone on the first COUNT members of the
+    batch of uneven 2D operators; one JSON line with its event time."""
+    from paper_2508_05400_gb300 import build as B
+    B.build()
+    from paper_2508_05400_gb300 import inputs as I
+    from paper_2508_05400_gb300 import rks
+    probs = [I.uneven_convdiff2d_problem(i) for i in range(args.batch_only)]
+    P0 = probs[0]
+    o = P0.solver_opts()
+    with rks.DevBatch([P.A for P in probs], P0.k, P0.p, P0.d, which=P0.which, zeta=P0.zeta, tol=o["tol"],
+                      conv="norm1", verify=o["verify"], maxit=args.max_restarts or args.maxit, keep=12,
+                      ctas=args.batch_ctas) as b:
+        infos = b.solve(allow_noconv=True)
+        cfg = b.config()
+    print(json.dumps({"workload": "batch of uneven 2D convection-diffusion operators", "count": args.batch_only,
+                      "sum_n": int(sum(P.A.n for P in probs)), "ms": cfg["last_ms"],
+                      "config": {k: cfg[k] for k in ("GL", "nL", "GS", "nS")},
+                      "converged": int(sum(i["converged"] for i in infos)),
+                      "restarts": int(sum(i["restarts"] for i in infos))}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -612,8 +644,14 @@ def main():
     ap.add_argument("--prec", default=None, choices=["df", "fp64", "mixed"],
                     help="arithmetic of the n-dimensional work (see include/rks.h); default: the "
                          "workload's (mixed for the 3D workload)")
+    ap.add_argument("--batch-only", type=int, default=0, metavar="COUNT",
+                    help="only the persistent batched solve of the first COUNT uneven 2D operators "
+                         "(profiling; --max-restarts caps the restarts, --batch-ctas fixes the cluster size)")
+    ap.add_argument("--batch-ctas", type=int, default=0, help="CTAs per problem of --batch-only; 0: autotuned")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.batch_only:
+        run_batch_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

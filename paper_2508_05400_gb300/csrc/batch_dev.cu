@@ -381,40 +381,49 @@ __device__ __forceinline__ void bd_spmv_csr(const BdProb& P, int t, int m1, int 
 }
 
 // The same product from the diagonal storage (columns i + doff[e] in
-// increasing order, as the CSR rows).
-template <bool L2>
-__device__ __forceinline__ void bd_spmv_dia(const BdProb& P, int t, int m1, int j, float2 sg, float2* xs) {
+// increasing order, as the CSR rows), ND diagonals.
+template <bool L2, int ND>
+__device__ __forceinline__ void bd_spmv_dia_n(const BdProb& P, int t, int m1, int j, float2 sg, float2* xs) {
   const int64_t r0 = (int64_t)t * kBR, n = P.n, ld = P.ldu;
   const int rows = (int)min((int64_t)kBR, n - r0);
   float2* w = P.U + ((int64_t)t * m1 + j + 1) * kBR;
-  float s[kBRowsPerThread], e[kBRowsPerThread];
-#pragma unroll
-  for (int q = 0; q < kBRowsPerThread; ++q) { s[q] = 0.f; e[q] = 0.f; }
-  for (int dg = 0; dg < P.D; ++dg) {
-    const int off = P.doff[dg];
-    const float2* dv = P.dvals + (size_t)dg * ld + r0;
-    float2 a[kBRowsPerThread], v[kBRowsPerThread];
-#pragma unroll
-    for (int q = 0; q < kBRowsPerThread; ++q) {   // rows past n read row n - 1 (never stored)
-      const int rr = min(threadIdx.x + q * kBT, rows - 1);
-      const int64_t c = min(max(r0 + rr + off, (int64_t)0), n - 1);   // value 0 outside A
-      a[q] = dv[rr];
-      v[q] = bd_ld<L2>(P.U + bd_uix(c, j, m1));
-    }
-#pragma unroll
-    for (int q = 0; q < kBRowsPerThread; ++q) bd_mac(a[q].x, a[q].y, v[q].x, v[q].y, s[q], e[q]);
-  }
 #pragma unroll
   for (int q = 0; q < kBRowsPerThread; ++q) {
-    const int rr = threadIdx.x + q * kBT;
-    if (rr < rows) {
-      const float2 y = bd_norm(s[q], e[q]);
+    const int rq = threadIdx.x + q * kBT;
+    const int rr = min(rq, rows - 1);   // rows past n read row n - 1 (never stored)
+    float2 a[ND], v[ND];
+#pragma unroll
+    for (int dg = 0; dg < ND; ++dg) {
+      const int64_t c = min(max(r0 + rr + P.doff[dg], (int64_t)0), n - 1);   // value 0 outside A
+      a[dg] = P.dvals[(size_t)dg * ld + r0 + rr];
+      v[dg] = bd_ld<L2>(P.U + bd_uix(c, j, m1));
+    }
+    float s = 0.f, e = 0.f;
+#pragma unroll
+    for (int dg = 0; dg < ND; ++dg) bd_mac(a[dg].x, a[dg].y, v[dg].x, v[dg].y, s, e);
+    if (rq < rows) {
+      const float2 y = bd_norm(s, e);
       float s2 = 0.f, e2 = 0.f;
       bd_mac(y.x, y.y, sg.x, sg.y, s2, e2);
       const float2 o = bd_norm(s2, e2);
-      w[rr] = o;
-      xs[rr] = o;
+      w[rq] = o;
+      xs[rq] = o;
     }
+  }
+}
+
+// Dispatch on the number of diagonals.
+template <bool L2>
+__device__ __forceinline__ void bd_spmv_dia(const BdProb& P, int t, int m1, int j, float2 sg, float2* xs) {
+  switch (P.D) {   // a compile-time number of diagonals: all loads of a row issued together
+    case 1: bd_spmv_dia_n<L2, 1>(P, t, m1, j, sg, xs); return;
+    case 2: bd_spmv_dia_n<L2, 2>(P, t, m1, j, sg, xs); return;
+    case 3: bd_spmv_dia_n<L2, 3>(P, t, m1, j, sg, xs); return;
+    case 4: bd_spmv_dia_n<L2, 4>(P, t, m1, j, sg, xs); return;
+    case 5: bd_spmv_dia_n<L2, 5>(P, t, m1, j, sg, xs); return;
+    case 6: bd_spmv_dia_n<L2, 6>(P, t, m1, j, sg, xs); return;
+    case 7: bd_spmv_dia_n<L2, 7>(P, t, m1, j, sg, xs); return;
+    default: bd_spmv_dia_n<L2, 8>(P, t, m1, j, sg, xs); return;
   }
 }
 
