@@ -173,14 +173,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_tc_restart_f32(int64_t n, const
       v[u] = (tile < ntiles && i < n && l < nin) ? in[i + (int64_t)l * ldu] : 0.f;
     }
   };
-  float v[16], vn[16];
-  load16(blockIdx.x, 0, v);
+  // loads run two stages ahead of the split (three register stages): one
+  // stage of work is shorter than the DRAM latency
+  auto next_step = [&](int64_t& t, int& k) {
+    if (++k == nk) { k = 0; t += gridDim.x; }
+  };
+  float v[16], vn[16], vnn[16];
+  int64_t pt = blockIdx.x;
+  int pk = 0;
+  load16(pt, pk, v);
+  next_step(pt, pk);
+  load16(pt, pk, vn);
   for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     for (int kc = 0; kc < nk && ok; ++kc, ++g) {
       const int s = g & 1;
-      // the next stage's loads go out before this stage is split and consumed
-      if (kc + 1 < nk) load16(tile, kc + 1, vn);
-      else load16(tile + gridDim.x, 0, vn);
+      next_step(pt, pk);
+      load16(pt, pk, vnn);
       if (g >= 2) ok = mbar_wait(smem_u32(mbar + s), (uint32_t)(((g - 2) >> 1) & 1), flag);
       ok = __syncthreads_and(ok);
       if (!ok) break;
@@ -228,7 +236,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_tc_restart_f32(int64_t n, const
         if (kc == nk - 1) mma_commit(smem_u32(mbar + 2));
       }
 #pragma unroll
-      for (int u = 0; u < 16; ++u) v[u] = vn[u];
+      for (int u = 0; u < 16; ++u) {
+        v[u] = vn[u];
+        vn[u] = vnn[u];
+      }
     }
     if (!ok) break;
     // epilogue
@@ -335,35 +346,62 @@ __device__ __forceinline__ int64_t fixed48(float x, int emax) {
 
 // out[i, o] = sum_l in[i, l] 2^pexp[l] Q'[l, o] (DF) for i < n, o < nout;
 // then, when mvsrc is given, mvdst[i] = mvsrc[i].  bimg: the digit slices of
-// Q' (Kp x N,
-// canonical layout, slice t at byte t * Kp * N * 2); fexp[o] = f_o; rexp[i]
-// from k_row_exp.  Every read of a tile's rows precedes its writes (in place).
-__global__ void __launch_bounds__(kDfThreads, 1) k_tc_restart_df(int64_t n, const float2* in, float2* out,
-                                                                 int64_t ldu, int nin, int Kp, int N, int nout,
-                                                                 const uint4* __restrict__ bimg,
-                                                                 const int* __restrict__ fexp,
-                                                                 const int* __restrict__ pexp,
-                                                                 const int* __restrict__ rexp,
-                                                                 const float2* mvsrc, float2* mvdst, int tcols,
-                                                                 int* flag) {
+// Q' (Kp x N, canonical layout, slice t at byte t * Kp * N * 2); fexp[o] =
+// f_o; rexp[i] from k_row_exp.  Every read of a tile's rows precedes its
+// writes (in place).
+//
+// Warp roles: warps 0..15 (kDfThreads threads) load and split the digits of
+// one K-step into a shared-memory stage and run the epilogue; warp 16 issues
+// the MMAs.  Per stage s: full[s] (the splitters arrive once the digits are
+// stored) and empty[s] (the MMA commit arrives once they are consumed); per
+// tile: done (accumulators complete) and tfree (the epilogue has read them).
+// The split of step g + 1 thus overlaps the MMA issue of step g.  Every wait
+// is bounded (mbar_wait); the splitters agree on the outcome at their named
+// barrier, so a timeout ends every role's loop.
+__device__ __forceinline__ bool splitters_and(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred P, Q;\n\tsetp.ne.u32 P, %1, 0;\n\tbar.red.and.pred Q, 1, %2, P;\n\t"
+      "selp.u32 %0, 1, 0, Q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)p), "n"(kDfThreads)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+constexpr int kDfAllThreads = kDfThreads + 32;
+
+__global__ void __launch_bounds__(kDfAllThreads, 1) k_tc_restart_df(int64_t n, const float2* in, float2* out,
+                                                                    int64_t ldu, int nin, int Kp, int N, int nout,
+                                                                    const uint4* __restrict__ bimg,
+                                                                    const int* __restrict__ fexp,
+                                                                    const int* __restrict__ pexp,
+                                                                    const int* __restrict__ rexp,
+                                                                    const float2* mvsrc, float2* mvdst, int tcols,
+                                                                    int* flag) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int bbytes = kDfDigits * Kp * N * 2;
   uint8_t* sB = smem;
   uint8_t* sA = smem + ((bbytes + 1023) & ~1023);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sA + 2 * kDfStage);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
-  int* sp = reinterpret_cast<int*>(mbar + 4);            // column power-of-two scales (Kp)
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sA + 2 * kDfStage);   // full[2], empty[2], done, tfree
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 6);
+  int* sp = reinterpret_cast<int*>(mbar + 7);            // column power-of-two scales (Kp)
+  const uint32_t full0 = smem_u32(mbar + 0), empty0 = smem_u32(mbar + 2);
+  const uint32_t done_b = smem_u32(mbar + 4), tfree_b = smem_u32(mbar + 5);
 
-  for (int t = tid; t < bbytes / 16; t += kDfThreads) reinterpret_cast<uint4*>(sB)[t] = bimg[t];
-  for (int t = tid; t < Kp; t += kDfThreads) sp[t] = t < nin ? pexp[t] : 0;
+  for (int t = tid; t < bbytes / 16; t += kDfAllThreads) reinterpret_cast<uint4*>(sB)[t] = bimg[t];
+  for (int t = tid; t < Kp; t += kDfAllThreads) sp[t] = t < nin ? pexp[t] : 0;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(tcols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int s = 0; s < 3; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + s)));
+    for (int s = 0; s < 6; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + s)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_async_smem();
@@ -371,140 +409,164 @@ __global__ void __launch_bounds__(kDfThreads, 1) k_tc_restart_df(int64_t n, cons
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = idesc_bf16(N);
-  const uint32_t sA32 = smem_u32(sA), sB32 = smem_u32(sB);
   const int nk = Kp / 16;
   const int64_t ntiles = (n + kM - 1) / kM;
-  int g = 0;                 // stages filled so far (all tiles)
-  uint32_t dpar = 0;         // parity of the accumulator-done barrier
   bool ok = true;
-  const int r = tid & (kM - 1), kq = tid >> 7;   // loader: row, quarter of the K-step's 16 columns
 
-  auto load4 = [&](int64_t tile, int kc, float2* v) {
-    const int64_t i = tile * kM + r;
-    const int l0 = kc * 16 + kq * 4;
+  if (warp == kDfThreads / 32) {
+    // ---- MMA issuer (lane 0 of warp 16)
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(N);
+      const uint32_t sA32 = smem_u32(sA), sB32 = smem_u32(sB);
+      int g = 0, tcount = 0;
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tcount) {
+        if (tcount > 0) {   // the epilogue of the previous tile has read the accumulators
+          ok = mbar_wait(tfree_b, (uint32_t)((tcount - 1) & 1), flag);
+          if (!ok) break;
+          fence_after();
+        }
+        for (int kc = 0; kc < nk; ++kc, ++g) {
+          const int s = g & 1;
+          ok = mbar_wait(full0 + 8u * s, (uint32_t)((g >> 1) & 1), flag);
+          if (!ok) break;
+          fence_after();
+          const bool first = kc == 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int l = l0 + u;
-      v[u] = (tile < ntiles && i < n && l < nin) ? in[i + (int64_t)l * ldu] : make_float2(0.f, 0.f);
+          for (int gg = 0; gg < kDfGroups; ++gg)
+#pragma unroll
+            for (int sa = gg < kDfDigits ? 0 : gg - kDfDigits + 1; sa <= gg && sa < kDfDigits; ++sa) {
+              const int tb = gg - sa;
+              const int sa0 = gg < kDfDigits ? 0 : gg - kDfDigits + 1;   // first pair of the group
+              const uint64_t a = sdesc(sA32 + s * kDfStage + sa * kDfStepSplit);
+              const uint64_t b = sdesc(sB32 + tb * Kp * N * 2 + kc * N * 32);
+              mma_bf16(tmem + (uint32_t)(gg * N), a, b, idesc, (first && sa == sa0) ? 0u : 1u);
+            }
+          mma_commit(empty0 + 8u * s);
+          if (kc == nk - 1) mma_commit(done_b);
+        }
+      }
+      // every issued MMA has completed before the accumulators are freed
+      if (g > 0) (void)mbar_wait(empty0 + 8u * ((g - 1) & 1), (uint32_t)(((g - 1) >> 1) & 1), flag);
+      if (g > 1) (void)mbar_wait(empty0 + 8u * ((g - 2) & 1), (uint32_t)(((g - 2) >> 1) & 1), flag);
     }
-  };
-  float2 v[4], vn[4];
-  load4(blockIdx.x, 0, v);
-  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const int64_t irow = tile * kM + r;
-    const int emax = irow < n ? rexp[irow] : 0;
-    for (int kc = 0; kc < nk && ok; ++kc, ++g) {
-      const int s = g & 1;
-      if (kc + 1 < nk) load4(tile, kc + 1, vn);
-      else load4(tile + gridDim.x, 0, vn);
-      if (g >= 2) ok = mbar_wait(smem_u32(mbar + s), (uint32_t)(((g - 2) >> 1) & 1), flag);
-      ok = __syncthreads_and(ok);
+    __syncwarp();
+  } else {
+    // ---- splitters (warps 0..15) and the epilogue
+    int g = 0;                 // stages filled so far (all tiles)
+    uint32_t dpar = 0;         // parity of the accumulator-done barrier
+    const int r = tid & (kM - 1), kq = tid >> 7;   // loader: row, quarter of the K-step's 16 columns
+    auto load4 = [&](int64_t tile, int kc, float2* v) {
+      const int64_t i = tile * kM + r;
+      const int l0 = kc * 16 + kq * 4;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int l = l0 + u;
+        v[u] = (tile < ntiles && i < n && l < nin) ? in[i + (int64_t)l * ldu] : make_float2(0.f, 0.f);
+      }
+    };
+    auto next_step = [&](int64_t& t, int& k) {
+      if (++k == nk) { k = 0; t += gridDim.x; }
+    };
+    float2 v[4], vn[4];   // the next K-step's values are loaded during this one's split
+    int64_t pt = blockIdx.x;
+    int pk = 0;
+    load4(pt, pk, v);
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      const int64_t irow = tile * kM + r;
+      const int emax = irow < n ? rexp[irow] : 0;
+      for (int kc = 0; kc < nk && ok; ++kc, ++g) {
+        const int s = g & 1;
+        next_step(pt, pk);
+        load4(pt, pk, vn);
+        if (g >= 2) ok = mbar_wait(empty0 + 8u * s, (uint32_t)(((g - 2) >> 1) & 1), flag);
+        ok = splitters_and(ok);
+        if (!ok) break;
+        // digits of 4 values of one row
+        uint32_t w[kDfDigits][2];
+#pragma unroll
+        for (int u = 0; u < 4; u += 2) {
+          uint32_t pk2[kDfDigits][2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float2 x = v[u + e];
+            const int ep = emax - sp[kc * 16 + kq * 4 + u + e];
+            const int64_t V = fixed48(x.x, ep) + fixed48(x.y, ep);
+            // digits from two 32-bit halves: bits 21..47 (signed) and 0..20
+            const int vh = (int)(V >> 21);
+            const int vl = (int)(V & 0x1FFFFF);
+            const int d0 = vh >> 21;                                   // -32 .. 32
+            pk2[0][e] = __float_as_uint(__int_as_float(0x4B000000 | (d0 + 128)) - 8388736.0f) >> 16;
+            pk2[1][e] = small_bf16((vh >> 14) & 127);
+            pk2[2][e] = small_bf16((vh >> 7) & 127);
+            pk2[3][e] = small_bf16(vh & 127);
+            pk2[4][e] = small_bf16(vl >> 14);
+            pk2[5][e] = small_bf16((vl >> 7) & 127);
+            pk2[6][e] = small_bf16(vl & 127);
+          }
+#pragma unroll
+          for (int q = 0; q < kDfDigits; ++q) w[q][u >> 1] = pk2[q][0] | (pk2[q][1] << 16);
+        }
+        uint8_t* st = sA + s * kDfStage;
+        const uint32_t off = canon_off(r, kq * 4, kM);
+#pragma unroll
+        for (int q = 0; q < kDfDigits; ++q)
+          *reinterpret_cast<uint2*>(st + q * kDfStepSplit + off) = make_uint2(w[q][0], w[q][1]);
+        fence_async_smem();
+        asm volatile("bar.sync 1, %0;" ::"n"(kDfThreads) : "memory");
+        if (tid == 0) mbar_arrive(full0 + 8u * s);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = vn[u];
+      }
       if (!ok) break;
-      // digits of 4 values of one row
-      uint32_t w[kDfDigits][2];
+      // epilogue: sum_g 2^(-7g) G_g in DF, times 2^(e_i + f_o - 12)
+      ok = mbar_wait(done_b, dpar, flag);
+      dpar ^= 1u;
+      ok = splitters_and(ok);
+      if (!ok) break;
+      fence_after();
+      const int q4 = warp & 3;
+      const int64_t ir = tile * kM + q4 * 32 + lane;
+      const int er = ir < n ? rexp[ir] - 125 : 0;
+      float2 mv = make_float2(0.f, 0.f);
+      if (mvsrc && warp < 4 && ir < n) mv = mvsrc[ir];
+      for (int cg = warp >> 2; cg < N / 16; cg += kDfThreads / 128) {
+        float hs[16], ls[16];
+        {
+          float gv[16];
+          tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((kDfGroups - 1) * N + cg * 16), gv);
 #pragma unroll
-      for (int u = 0; u < 4; u += 2) {
-        uint32_t pk[kDfDigits][2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const float2 x = v[u + e];
-          const int ep = emax - sp[kc * 16 + kq * 4 + u + e];
-          const int64_t V = fixed48(x.x, ep) + fixed48(x.y, ep);
-          // digits from two 32-bit halves: bits 21..47 (signed) and 0..20
-          const int vh = (int)(V >> 21);
-          const int vl = (int)(V & 0x1FFFFF);
-          const int d0 = vh >> 21;                                   // -32 .. 32
-          pk[0][e] = __float_as_uint(__int_as_float(0x4B000000 | (d0 + 128)) - 8388736.0f) >> 16;
-          pk[1][e] = small_bf16((vh >> 14) & 127);
-          pk[2][e] = small_bf16((vh >> 7) & 127);
-          pk[3][e] = small_bf16(vh & 127);
-          pk[4][e] = small_bf16(vl >> 14);
-          pk[5][e] = small_bf16((vl >> 7) & 127);
-          pk[6][e] = small_bf16(vl & 127);
+          for (int jj = 0; jj < 16; ++jj) { hs[jj] = gv[jj]; ls[jj] = 0.f; }
         }
+        for (int gg = kDfGroups - 2; gg >= 0; --gg) {
+          float gv[16];
+          tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(gg * N + cg * 16), gv);
 #pragma unroll
-        for (int q = 0; q < kDfDigits; ++q) w[q][u >> 1] = pk[q][0] | (pk[q][1] << 16);
-      }
-      uint8_t* st = sA + s * kDfStage;
-      const uint32_t off = canon_off(r, kq * 4, kM);
-#pragma unroll
-      for (int q = 0; q < kDfDigits; ++q)
-        *reinterpret_cast<uint2*>(st + q * kDfStepSplit + off) = make_uint2(w[q][0], w[q][1]);
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        fence_after();
-        const bool first = kc == 0;
-#pragma unroll
-        for (int gg = 0; gg < kDfGroups; ++gg)
-#pragma unroll
-          for (int sa = gg < kDfDigits ? 0 : gg - kDfDigits + 1; sa <= gg && sa < kDfDigits; ++sa) {
-            const int tb = gg - sa;
-            const int sa0 = gg < kDfDigits ? 0 : gg - kDfDigits + 1;   // first pair of the group
-            const uint64_t a = sdesc(sA32 + s * kDfStage + sa * kDfStepSplit);
-            const uint64_t b = sdesc(sB32 + tb * Kp * N * 2 + kc * N * 32);
-            mma_bf16(tmem + (uint32_t)(gg * N), a, b, idesc, (first && sa == sa0) ? 0u : 1u);
+          for (int jj = 0; jj < 16; ++jj) {
+            const float sh = hs[jj] * 0.0078125f, sl = ls[jj] * 0.0078125f;   // exact scaling by 2^-7
+            float s2, e2;
+            two_sum_f(gv[jj], sh, s2, e2);
+            hs[jj] = s2;
+            ls[jj] = e2 + sl;
           }
-        mma_commit(smem_u32(mbar + s));
-        if (kc == nk - 1) mma_commit(smem_u32(mbar + 2));
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = vn[u];
-    }
-    if (!ok) break;
-    // epilogue: sum_g 2^(-7g) G_g in DF, times 2^(e_i + f_o - 12)
-    ok = mbar_wait(smem_u32(mbar + 2), dpar, flag);
-    dpar ^= 1u;
-    ok = __syncthreads_and(ok);
-    if (!ok) break;
-    fence_after();
-    const int q4 = warp & 3;
-    const int64_t ir = tile * kM + q4 * 32 + lane;
-    const int er = ir < n ? rexp[ir] - 125 : 0;
-    float2 mv = make_float2(0.f, 0.f);
-    if (mvsrc && warp < 4 && ir < n) mv = mvsrc[ir];
-    for (int cg = warp >> 2; cg < N / 16; cg += kDfThreads / 128) {
-      float hs[16], ls[16];
-      {
-        float gv[16];
-        tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((kDfGroups - 1) * N + cg * 16), gv);
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) { hs[jj] = gv[jj]; ls[jj] = 0.f; }
-      }
-      for (int gg = kDfGroups - 2; gg >= 0; --gg) {
-        float gv[16];
-        tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(gg * N + cg * 16), gv);
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const float sh = hs[jj] * 0.0078125f, sl = ls[jj] * 0.0078125f;   // exact scaling by 2^-7
-          float s2, e2;
-          two_sum_f(gv[jj], sh, s2, e2);
-          hs[jj] = s2;
-          ls[jj] = e2 + sl;
         }
-      }
-      if (ir < n) {
+        if (ir < n) {
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int o = cg * 16 + jj;
-          if (o < nout) {
-            const int sc = er + fexp[o] - 12;
-            float h, l;
-            two_sum_f(hs[jj], ls[jj], h, l);
-            out[ir + (int64_t)o * ldu] = make_float2(ldexpf(h, sc), ldexpf(l, sc));
+          for (int jj = 0; jj < 16; ++jj) {
+            const int o = cg * 16 + jj;
+            if (o < nout) {
+              const int sc = er + fexp[o] - 12;
+              float h, l;
+              two_sum_f(hs[jj], ls[jj], h, l);
+              out[ir + (int64_t)o * ldu] = make_float2(ldexpf(h, sc), ldexpf(l, sc));
+            }
           }
         }
       }
+      if (mvsrc && warp < 4 && ir < n) mvdst[ir] = mv;
+      fence_before();
+      asm volatile("bar.sync 1, %0;" ::"n"(kDfThreads) : "memory");
+      if (tid == 0) mbar_arrive(tfree_b);
     }
-    if (mvsrc && warp < 4 && ir < n) mvdst[ir] = mv;
-    fence_before();
-    __syncthreads();
-  }
-  if (!ok && tid == 0) {
-    const int c0 = (g + 1) / 2, c1 = g / 2;
-    if (c0 > 0) (void)mbar_wait(smem_u32(mbar + 0), (uint32_t)((c0 - 1) & 1), flag);
-    if (c1 > 0) (void)mbar_wait(smem_u32(mbar + 1), (uint32_t)((c1 - 1) & 1), flag);
   }
   fence_before();
   __syncthreads();
@@ -597,14 +659,14 @@ void launch_tc_restart_df(int64_t n, const float2* in, float2* out, int64_t ldu,
   const size_t sm = tc_restart_df_smem(nin, nout);
   int sms = 152, dev = 0, per_sm = 1;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_restart_df, kDfThreads, sm) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_restart_df, kDfAllThreads, sm) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   per_sm = std::min(per_sm, 512 / tcols);          // tensor memory columns per SM
   const int ge = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
   k_row_exp<<<std::max(ge, 1), 256, 0, st>>>(n, in, ldu, nin, pexp, rexp);
   const int g = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
-  k_tc_restart_df<<<g, kDfThreads, sm, st>>>(n, in, out, ldu, nin, Kp, N, nout, static_cast<const uint4*>(bimg),
+  k_tc_restart_df<<<g, kDfAllThreads, sm, st>>>(n, in, out, ldu, nin, Kp, N, nout, static_cast<const uint4*>(bimg),
                                              fexp, pexp, rexp, mvsrc, mvdst, tcols, flag);
 }
 
