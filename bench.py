@@ -648,8 +648,15 @@ def main():
                     help="only the persistent batched solve of the first COUNT uneven 2D operators "
                          "(profiling; --max-restarts caps the restarts, --batch-ctas fixes the cluster size)")
     ap.add_argument("--batch-ctas", type=int, default=0, help="CTAs per problem of --batch-only; 0: autotuned")
+    ap.add_argument("--spmv-variants-only", action="store_true",
+                    help="only the live GB/s of the irregular-row SpMV variants (profiling)")
     args = ap.parse_args()
-    if args.batch_only:
+    if args.spmv_variants_only:
+        from paper_2508_05400_gb300 import build as B
+        B.build()
+        from paper_2508_05400_gb300 import rks
+        print(json.dumps(_spmv_variants(rks)))
+    elif args.batch_only:
         run_batch_only(args)
     elif args.impl == "reference":
         run_reference(args)

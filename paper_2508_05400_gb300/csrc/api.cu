@@ -1078,6 +1078,8 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
           (rc = dalloc(&c->A2.mp_val, (size_t)c->A2.mp_threads)) || (rc = dalloc(&c->A2.mp_part, (size_t)nbm + 1)))
         return fail(rc);
       if (c->prec == RKS_PREC_MIXED && (rc = dalloc(&c->A2.mp_w, (size_t)n))) return fail(rc);
+      rks::launch_merge_partition(c->A2, c->stream);
+      if ((rc = launch_err())) return fail(rc);
     } else if (!c->ell_w && c->spmv_warp) {
       c->A2.fmt = rks::kSpmvWarp;          // long rows: a warp per row
     } else if (c->ell_w) {

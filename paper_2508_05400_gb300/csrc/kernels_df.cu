@@ -622,23 +622,20 @@ __global__ void __launch_bounds__(kMergeCta) k_df_spmv_merge(
   const int64_t dlo = b * kMergeBlk, dhi = dlo + kMergeBlk < total ? dlo + kMergeBlk : total;
   const int64_t jlo = dlo - rlo, jhi = dhi - rhi;     // entries of the CTA's range
   const int ne = (int)(jhi - jlo), nr = (int)(rhi - rlo);
-  // products a_p x[col_p], four entries per thread in flight at a time
-  for (int e0 = threadIdx.x; e0 < ne; e0 += 4 * kMergeCta) {
-    int c[4];
-    float2 a[4], xv[4];
+  // products a_p x[col_p], eight entries per thread in flight at a time
+  for (int e0 = threadIdx.x; e0 < ne; e0 += 8 * kMergeCta) {
+    int c[8];
+    float2 a[8], xv[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       const int e = e0 + u * kMergeCta;
       c[u] = e < ne ? colind[jlo + e] : 0;
       a[u] = e < ne ? ldv(vals + jlo + e) : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int e = e0 + u * kMergeCta;
-      xv[u] = e < ne ? (x2 ? x2[c[u]] : make_float2(x1[c[u]], 0.f)) : make_float2(0.f, 0.f);
-    }
+    for (int u = 0; u < 8; ++u) xv[u] = x2 ? x2[c[u]] : make_float2(x1[c[u]], 0.f);   // c = 0 past the end
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       const int e = e0 + u * kMergeCta;
       if (e < ne) {
         const float pr = a[u].x * xv[u].x;
@@ -701,30 +698,68 @@ __global__ void __launch_bounds__(kMergeCta) k_df_spmv_merge(
     cval[threadIdx.x] = df_norm(sh, sl);
   }
   __syncthreads();
-  // Fold in thread order: the running row (open at the previous thread's
-  // end) collects the partial sums of the threads inside it and is written
-  // when a thread completes it; the row open at the CTA's end becomes the
-  // CTA's carry (mp_row[b], mp_val[b]; -1: none), added by k_df_merge_fix.
-  if (threadIdx.x == 0) {
-    int rc = (int)rlo;
-    float ch = 0.f, cl = 0.f;
-    for (int u = 0; u < kMergeCta; ++u) {
+  // Fold in thread order, by warp 0: lane L folds the records of threads
+  // 8L .. 8L+7 (the partial sums of the row it enters with, up to and with
+  // its first completion, and the rows it completes after that, written
+  // here), then lane 0 chains the 32 lanes: the running row collects each
+  // lane's leading partial and is written at the lane's first completion.
+  // The row open at the CTA's end becomes the CTA's carry (mp_row[b],
+  // mp_val[b]; -1: none), added by k_df_merge_fix.  A fixed order: the sums
+  // are the same bits on every run.
+  if (threadIdx.x < 32) {
+    constexpr int kSeg = kMergeCta / 32;
+    const int lane = threadIdx.x;
+    float ph = 0.f, pl = 0.f;          // contribution to the row the lane enters with
+    float oh = 0.f, ol = 0.f;          // partial of the row open at the lane's end (after a completion)
+    int has = 0, orow = -1;
+    for (int q = 0; q < kSeg; ++q) {
+      const int u = lane * kSeg + q;
       if (fhas[u]) {
         const float2 f = fval[u];
-        df_add(f.x, f.y, ch, cl);
-        if (rc >= 0) wd[rc] = df_norm(ch, cl);
-        rc = crow[u];
+        if (!has) {
+          df_add(f.x, f.y, ph, pl);
+          has = 1;
+        } else {
+          df_add(f.x, f.y, oh, ol);
+          if (orow >= 0) wd[orow] = df_norm(oh, ol);
+        }
+        orow = crow[u];
         const float2 v = cval[u];
-        ch = 0.f;
-        cl = 0.f;
-        df_add(v.x, v.y, ch, cl);
+        oh = 0.f;
+        ol = 0.f;
+        df_add(v.x, v.y, oh, ol);
       } else if (crow[u] >= 0) {
         const float2 v = cval[u];
-        df_add(v.x, v.y, ch, cl);
+        if (has) df_add(v.x, v.y, oh, ol);
+        else df_add(v.x, v.y, ph, pl);
       }
     }
-    mp_row[b] = rc >= 0 && rc < n ? rc : -1;
-    mp_val[b] = df_norm(ch, cl);
+    const float2 pre = df_norm(ph, pl), post = df_norm(oh, ol);
+    __shared__ float2 s_pre[32], s_post[32];
+    __shared__ int s_has[32], s_orow[32];
+    s_pre[lane] = pre;
+    s_post[lane] = post;
+    s_has[lane] = has;
+    s_orow[lane] = orow;
+    __syncwarp();
+    if (lane == 0) {
+      int rc = (int)rlo;
+      float ch = 0.f, cl = 0.f;
+      for (int L = 0; L < 32; ++L) {
+        const float2 v = s_pre[L];
+        df_add(v.x, v.y, ch, cl);
+        if (s_has[L]) {
+          if (rc >= 0) wd[rc] = df_norm(ch, cl);
+          rc = s_orow[L];
+          const float2 w2 = s_post[L];
+          ch = 0.f;
+          cl = 0.f;
+          df_add(w2.x, w2.y, ch, cl);
+        }
+      }
+      mp_row[b] = rc >= 0 && rc < n ? rc : -1;
+      mp_val[b] = df_norm(ch, cl);
+    }
   }
 }
 
@@ -1682,13 +1717,19 @@ static void launch_dia(const CsrDF& A, const void* x, void* w, const SketchTiles
   else k_df_spmv_dia<TU, TU, SK, 16><<<t.G, 512, sm, st>>>(o, A.D, dv, A.ldd, A.n, xx, ww, t, part);
 }
 
+// The merge-path partition of A (the first row of every CTA's range), once per
+// matrix: it depends on the row pointers only.
+void launch_merge_partition(const CsrDF& A, cudaStream_t st) {
+  const int64_t nb = (A.mp_threads + kMergeCta - 1) / kMergeCta;
+  k_merge_partition<<<df_grid(nb + 1, 256), 256, 0, st>>>(A.n, A.nnz, A.rowptr, nb, A.mp_part);
+}
+
 // merge path: w = A x (double-float partials folded), then rounded to FP32 (f32)
 static void launch_merge(const CsrDF& A, const void* x, void* w, cudaStream_t st) {
   float2* wd = A.f32 ? A.mp_w : static_cast<float2*>(w);
   const int64_t nb = (A.mp_threads + kMergeCta - 1) / kMergeCta;
   const float2* x2 = A.f32 ? nullptr : static_cast<const float2*>(x);
   const float* x1 = A.f32 ? static_cast<const float*>(x) : nullptr;
-  k_merge_partition<<<df_grid(nb + 1, 256), 256, 0, st>>>(A.n, A.nnz, A.rowptr, nb, A.mp_part);
   if (A.f32)
     k_df_spmv_merge<float><<<(unsigned)nb, kMergeCta, 0, st>>>(A.n, A.nnz, A.rowptr, A.colind,
                                                               static_cast<const float*>(A.vals), x2, x1, A.mp_part,

@@ -86,6 +86,7 @@ constexpr int kMergeCta = 256;   // threads per CTA of the merge path (a CTA sta
 
 // Diagonal copy of a CSR matrix (see CsrDF); dvals (D * ldd values) is
 // cleared first.
+void launch_merge_partition(const CsrDF& A, cudaStream_t st);
 void launch_dia_fill(int64_t n, int D, const int* doff, int64_t ldd, const int32_t* rowptr, const int32_t* colind,
                      const void* vals, bool f32, void* dvals, cudaStream_t st);
 
