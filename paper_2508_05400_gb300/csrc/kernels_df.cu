@@ -360,6 +360,59 @@ __device__ __forceinline__ void tile_stage(const SketchTiles& tv, int64_t t, int
   for (int q = q0 + threadIdx.x; q < cnt; q += blockDim.x) es[q] = src[q];
 }
 
+// The bin lists of one tile held in registers between their load and their
+// store into shared memory, so that the loads of the next tile's lists are in
+// flight while this tile's rows are computed.  Valid when every per-thread
+// count fits (tile_regs_fit); the stored bytes are those of tile_stage.
+constexpr int kStageRegs = 2;   // uint4 of entries per thread (zeta <= 8)
+struct TileRegs {
+  uint4 e[kStageRegs];
+  int of[2];
+  uint32_t ms[2];
+};
+__host__ __device__ inline bool tile_regs_fit(const SketchTiles& tv) {
+  return tv.L + 1 <= 2 * 512 && tv.d <= 2 * 512 && kTileRows * tv.zeta / 8 <= kStageRegs * 512;
+}
+__device__ __forceinline__ void tile_regs_load(const SketchTiles& tv, int64_t t, TileRegs& R) {
+  const int L1 = tv.L + 1, d = tv.d;
+  const int64_t r0 = tv.row[t];
+  const int cnt = (int)(tv.row[t + 1] - r0) * tv.zeta;
+  const uint4* src = reinterpret_cast<const uint4*>(tv.ent + r0 * tv.zeta);   // r0 is a multiple of kTileRows
+#pragma unroll
+  for (int u = 0; u < kStageRegs; ++u) {
+    const int q = threadIdx.x + u * 512;
+    R.e[u] = q * 8 < cnt ? __ldg(src + q) : make_uint4(0u, 0u, 0u, 0u);
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int q = threadIdx.x + u * 512;
+    R.of[u] = q < L1 ? tv.off[t * L1 + q] : 0;
+    R.ms[u] = q < d ? __ldg(tv.meta + t * d + q) : 0u;
+  }
+}
+__device__ __forceinline__ void tile_regs_store(const SketchTiles& tv, int64_t t, const TileRegs& R, int* of,
+                                                uint32_t* ms, uint16_t* es) {
+  const int L1 = tv.L + 1, d = tv.d;
+  const int cnt = (int)(tv.row[t + 1] - tv.row[t]) * tv.zeta;
+#pragma unroll
+  for (int u = 0; u < kStageRegs; ++u) {
+    const int q = threadIdx.x + u * 512;
+    if (q * 8 + 8 <= cnt) reinterpret_cast<uint4*>(es)[q] = R.e[u];
+    else if (q * 8 < cnt) {   // the ragged end of the last tile
+      const uint32_t wd[4] = {R.e[u].x, R.e[u].y, R.e[u].z, R.e[u].w};
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (q * 8 + k < cnt) es[q * 8 + k] = (uint16_t)((wd[k >> 1] >> (16 * (k & 1))) & 0xFFFFu);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int q = threadIdx.x + u * 512;
+    if (q < L1) of[q] = R.of[u];
+    if (q < d) ms[q] = R.ms[u];
+  }
+}
+
 __device__ __forceinline__ void tile_write_part(const float2* acc, int d, double* part) {
   __syncthreads();
   for (int r = threadIdx.x; r < d; r += blockDim.x) part[(size_t)blockIdx.x * d + r] = df_to_double(acc[r]);
@@ -808,6 +861,9 @@ __global__ void __launch_bounds__(512, 2) k_df_spmv_dia(const DiaOffs offs, int 
   if (SK)
     for (int r = threadIdx.x; r < d; r += blockDim.x) acc[r] = make_float2(0.f, 0.f);
   const int t0 = tv.ctile[blockIdx.x], t1 = tv.ctile[blockIdx.x + 1];
+  const bool regs = SK && tile_regs_fit(tv);
+  TileRegs R;
+  if (regs && t0 < t1) tile_regs_load(tv, t0, R);
   for (int t = t0; t < t1; ++t) {
     const int buf = (t - t0) & 1;
     float2* v = reinterpret_cast<float2*>(smraw + lay.vb) + buf * kTileRows;
@@ -816,7 +872,12 @@ __global__ void __launch_bounds__(512, 2) k_df_spmv_dia(const DiaOffs offs, int 
     uint16_t* es = reinterpret_cast<uint16_t*>(smraw + lay.es) + (size_t)buf * kTileRows * tv.zeta;
     const int64_t r0 = tv.row[t];
     const int rows = (int)(tv.row[t + 1] - r0);
-    if (SK) tile_stage(tv, t, r0, rows, of, ms, es);
+    if (regs) {            // this tile's lists were loaded during the previous tile
+      tile_regs_store(tv, t, R, of, ms, es);
+      if (t + 1 < t1) tile_regs_load(tv, t + 1, R);
+    } else if (SK) {
+      tile_stage(tv, t, r0, rows, of, ms, es);
+    }
     const int la = threadIdx.x, lb = threadIdx.x + 512;
     const bool oka = la < rows, okb = lb < rows;
     const int64_t ia = r0 + la, ib = r0 + lb;
