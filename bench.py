@@ -438,6 +438,9 @@ def run_ours(args) -> None:
                       "nlocked": info["nlocked"], "max_resid": info["max_resid"],
                       "max_est": info["max_est"], "host_dense_ms_per_step": agg["host_ms"] / args.steps,
                       "whitenings_per_step": agg["whitenings"] / args.steps,
+                      "fp32_restarts": st["fp32_restarts"],
+                      "mixed_phase2": ("none", "handover", "restart")[st["mixed_phase2"]],
+                      "handover_rel": st["handover_rel"],
                       "max_rayleigh_vs_ritz": float(np.max(np.abs(rq - lam) / np.abs(lam))),
                       "kernel_ms_per_step": {c: breakdown[c]["ms"] for c in rks.KCLASSES},
                       "kernel_launches_per_step": {c: breakdown[c]["launches"] for c in rks.KCLASSES},

@@ -85,13 +85,22 @@ typedef struct {
                           products and sums by error-free transformations on the
                           FP32 pipes; RKS_PREC_FP64: native FP64;
                           RKS_PREC_MIXED: FP32 basis and FP32 matrix values with
-                          compensated (error-free) products and sums until the
-                          estimates reach mixed_tol or stagnate, then a
-                          double-float solve started from the sum of the FP32
-                          Schur vectors (all wanted directions to FP32
-                          accuracy) finishes to tol.  The sketch sums, the
-                          small dense work and the final residuals are FP64 in
-                          all three. */
+                          compensated (error-free) products and sums until
+                          the estimates reach mixed_tol or stagnate.  With
+                          keep > 0 this phase does not lock and the
+                          double-float restarts continue from its
+                          Krylov-Schur decomposition A U = U T + u b^T: U
+                          promoted exactly,
+                          its relation error (the FP32 rounding of the stored
+                          vectors) reduced by damped Jacobi sweeps on
+                          A X - X T = -(A U - U T - u b^T) with U <- U + X,
+                          [U u] re-orthonormalised in the sketch.  With
+                          keep = 0, or if the relation error left is above
+                          what tol asks (see rks_stats.handover_rel) or that
+                          phase stagnates, a double-float solve started from
+                          the sum of the FP32 Schur vectors finishes to tol.
+                          The sketch sums, the small dense work and the final
+                          residuals are FP64 in all three. */
   double mixed_tol;    /* RKS_PREC_MIXED: tolerance of the FP32 phase on the
                           opts.conv scale; 0: 64 * 2^-24 */
   double verify;       /* > 0: after convergence, check the FP64 residuals
@@ -191,6 +200,18 @@ typedef struct {
   double host_ms;      /* host time in the small dense step (Schur ... locking) */
   int64_t whitenings;  /* restarts that whitened the kept sketches (Sec. 3.3) */
   int64_t reorders;    /* restarts whose aggressive deflation moved a block */
+  int fp32_restarts;   /* RKS_PREC_MIXED: restarts of the FP32 phase */
+  int mixed_phase2;    /* RKS_PREC_MIXED: how the double-float phase began:
+                          0 none (the FP32 result met the target), 1 from the
+                          FP32 decomposition made exact (see opts.prec),
+                          2 from the sum of the FP32 Schur vectors */
+  double handover_rel; /* RKS_PREC_MIXED: largest column norm of the relation
+                          error A U - U T - u b^T left by the correction, over
+                          ||A||_1 (phase 2 continues from it only when it is
+                          below what the target asks: tol on the ||A||_1
+                          scale, verify - tol with the FP64 check, tol times
+                          the smallest wanted |lambda| / ||A||_1 on the
+                          |lambda| scale; otherwise mixed_phase2 = 2) */
 } rks_stats;
 
 /* Counters of the last rks_solve (see rks_stats). */

@@ -67,6 +67,7 @@ struct rks_ctx {
   float* valsf = nullptr;  // mixed precision: FP32 values and basis
   int ell_w = 0;           // ELLPACK copy of A for the SpMV (0: not used)
   bool spmv_merge = false, spmv_warp = false;   // CSR SpMV variants chosen by row lengths
+  bool vals_f32 = false;   // every value of A is an FP32 number (the double-float copies' low words are 0)
   int dia_d = 0;           // diagonal copy of A for the SpMV (0: not used), its offsets
   int dia_off[16] = {};
   float2* dia_val2 = nullptr;
@@ -964,11 +965,14 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
       // the double-float and FP32 copies need every value inside the FP32
       // exponent range: above FLT_MAX a value becomes inf, below FLT_MIN it
       // loses significand bits silently
+      bool exact = true;
       for (int64_t p = 0; p < c->nnz; ++p) {
         const double a = std::fabs(cv[p]);
         if (!std::isfinite(a)) return fail(RKS_ENAN);
         if (a > 3.4028234663852886e38 || (a != 0.0 && a < 1.1754943508222875e-38)) return fail(RKS_EINVAL);
+        exact = exact && (double)(float)cv[p] == cv[p];
       }
+      c->vals_f32 = exact;
     }
     // widest row: an ELLPACK copy for the SpMV when the padding stays small
     std::vector<int32_t> rp(n + 1);
@@ -1062,7 +1066,17 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
         if ((rc = dalloc(&c->dia_valf, (size_t)c->dia_d * ldd))) return fail(rc);
         rks::launch_dia_fill(n, c->dia_d, c->dia_off, ldd, c->rowptr, c->colind, c->valsf, true, c->dia_valf,
                              c->stream);
+      } else if (c->vals_f32 && c->dia_d <= 8) {
+        // FP32 values: the double-float SpMV reads them from an FP32 copy
+        float* vf = nullptr;
+        if ((rc = dalloc(&vf, c->nnz))) return fail(rc);
+        rks::launch_d2df(c->nnz, c->vals, vf, true, c->stream);
+        if ((rc = dalloc(&c->dia_valf, (size_t)c->dia_d * ldd))) { cudaFree(vf); return fail(rc); }
+        rks::launch_dia_fill(n, c->dia_d, c->dia_off, ldd, c->rowptr, c->colind, vf, true, c->dia_valf, c->stream);
+        cudaStreamSynchronize(c->stream);
+        cudaFree(vf);
       }
+      if (c->vals_f32 && c->dia_d <= 8) c->A2.dvals_f32 = c->dia_valf;
       if ((rc = launch_err())) return fail(rc);
       c->A2.D = c->dia_d;
       for (int e = 0; e < c->dia_d; ++e) c->A2.doff[e] = c->dia_off[e];
@@ -1122,14 +1136,217 @@ int rks_create(rks_ctx** out, int64_t n, const int32_t* rowptr, const int32_t* c
   return RKS_OK;
 }
 
-// Algorithm 1 from the start vector `start` (NULL: the user's u1 or the
-// library's generator) until the estimates reach c->tol (with the FP64
-// verification when verify > 0), `limit` restarts, or stagnation (if
-// stall > 0: no decrease of the largest estimate over `stall` restarts).
-// Sets *converged; leaves the Ritz pairs of the last contraction in c.
-static int run_alg1(rks_ctx* c, const double* start, int limit, double verify, int stall, bool* converged) {
+// Mixed path: carry the FP32 phase's Krylov-Schur decomposition
+// A U = U T + u b^T (q = 0, ka = ja kept columns, u at column ka) over to
+// double-float, so that the double-float restarts continue from it instead of
+// from one start vector.  The FP32 columns are promoted exactly; their
+// relation error E = A U - U T - u b^T (the FP32 rounding of the stored basis
+// vectors, of the order of 2^-24 ||A|| per column) is formed in double-float
+// and reduced by damped Jacobi sweeps on the correction equation
+// A X - X T = -E, U <- U + X; the corrected columns are sketched again and
+// [U u] is made sketch-orthonormal once more (the R of the QR of
+// [Omega U, Omega u], Sec. 3.3), T and b following the change of basis
+// exactly: with [U u] = [V v] R, A V = V (R11 T + r12 b^T) R11^-1 +
+// v r22 b^T R11^-1.  The sweeps stop once the largest column norm of the
+// relation error, over ||A||_1 (*rel, measured every kHandoverCheck sweeps
+// at the sweep's input), is at most thr / 2, stops falling, or after
+// kHandoverSweeps; above thr the decomposition is not accurate enough for the
+// target: RKS_EDENSE, the basis is left promoted but not rotated.
+// RKS_EINVAL: the state does not allow it (nothing in the basis has changed).
+constexpr int kHandoverSweeps = 48;
+constexpr int kHandoverCheck = 8;
+constexpr float kJacobiOmega = 0.67f;
+
+static int handover_df(rks_ctx* c, double thr, double* rel) {
+  const int ka = c->ja, m = c->m, d = c->d, ldb = m + 1;
+  const int64_t n = c->n, ldu = c->ldu;
+  if (c->prec != RKS_PREC_MIXED || c->q != 0 || ka < 1 || ka + 1 > m + 1 || !c->valsf ||
+      c->opts.ortho != RKS_ORTHO_SKETCH)
+    return RKS_EINVAL;
+  std::vector<double> T((size_t)ka * ka), b(ka);
+  for (int j = 0; j < ka; ++j) {
+    for (int i = 0; i < ka; ++i) T[i + (size_t)j * ka] = M(c->Ba, ldb, i, j);
+    b[j] = M(c->Ba, ldb, ka, j);
+  }
+  const double cs_u = c->cs_h[ka];
+  for (int j = 0; j < ka; ++j)
+    if (c->cs_h[j] != 1.0) return RKS_EINVAL;
+  // the double-float basis and storage of A from here on
+  c->f32 = false;
+  c->Ub = c->U2;
+  c->A2.vals = c->vals2;
+  c->A2.evals = c->ell_val2;
+  if (c->dia_d) c->A2.dvals = c->dia_val2;
+  c->A2.f32 = false;
+  float *work = nullptr, *dinv = nullptr;
+  float2* dfw = nullptr;
+  double* part = nullptr;
+  const int gj = rks::jacobi_sweep_ctas(n);
+  int rc = dalloc(&work, (size_t)4 * ka * ldu);
+  if (!rc) rc = dalloc(&dinv, (size_t)n);
+  if (!rc) rc = dalloc(&part, (size_t)gj * ka);
+  if (!rc) rc = dalloc(&dfw, (size_t)(2 * ka + 1) * ldu);
+  auto release = [&]() { cudaFree(work); cudaFree(dinv); cudaFree(part); cudaFree(dfw); };
+  if (rc) { release(); return rc; }
+  const int ps = prof_begin(c, RKS_K_OTHER);
+  rks::launch_f32_to_df_cols(n, c->Uf, ldu, ka + 1, c->U2, c->stream);
+  // double-float scratch: U in columns 0 .. ka-1, V = U T in ka .. 2ka-1,
+  // w = A u_j in 2ka
+  std::vector<float2> T2((size_t)ka * ka);
+  for (size_t t = 0; t < T.size(); ++t) {
+    const float h = (float)T[t];
+    T2[t] = make_float2(h, (float)(T[t] - (double)h));
+  }
+  CK(cudaMemcpyAsync(c->Q2, T2.data(), T2.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(dfw, c->U2, (size_t)ka * ldu * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+  rks::launch_df_rows_gemm(n, dfw, ldu, 0, ka, c->Q2, ka, ka, -1, false, c->stream);
+  float* Xa = work;
+  float* Xb = work + (size_t)ka * ldu;
+  float* Y = work + (size_t)2 * ka * ldu;
+  float* E = work + (size_t)3 * ka * ldu;
+  float2* wcol = dfw + (size_t)(2 * ka) * ldu;
+  for (int j = 0; j < ka; ++j) {
+    rks::launch_df_spmv(c->A2, c->U2 + (size_t)j * ldu, wcol, c->tiles, c->stream);
+    rks::launch_relation_resid(n, wcol, dfw + (size_t)(ka + j) * ldu, c->U2 + (size_t)ka * ldu, b[j] * cs_u,
+                               E + (size_t)j * ldu, c->stream);
+  }
+  // Jacobi sweeps in FP32 (E is formed in double-float; X is a correction of
+  // relative size 2^-24, so FP32 carries it far below the target)
+  rks::launch_diag_inv(n, c->rowptr, c->colind, c->valsf, dinv, c->stream);
+  CK(cudaMemsetAsync(Xa, 0, (size_t)ka * ldu * sizeof(float), c->stream));
+  int cur = 0;   // the iterate is in columns cur .. cur + ka - 1 of the work array, the next in the other half
+  std::vector<double> ph((size_t)gj * ka);
+  double prev = 1e300;
+  *rel = 1e300;
+  int sweeps = 0;
+  for (int it = 0; it < kHandoverSweeps; ++it) {
+    rks::launch_df_rows_gemm(n, work, ldu, cur, ka, c->Q2, ka, 2 * ka, -1, true, c->stream);   // Y = X T
+    const bool check = (it + 1) % kHandoverCheck == 0;
+    rks::launch_jacobi_sweep(n, c->rowptr, c->colind, c->valsf, dinv, ka, ldu, cur ? Xb : Xa, E, Y, kJacobiOmega,
+                             cur ? Xa : Xb, check ? part : nullptr, c->stream);
+    cur = ka - cur;
+    ++sweeps;
+    if (!check) continue;
+    rc = launch_err();
+    if (rc) { release(); return rc; }
+    CK(cudaMemcpyAsync(ph.data(), part, ph.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double worst = 0.0;
+    for (int j = 0; j < ka; ++j) {
+      double acc = 0.0;
+      for (int g = 0; g < gj; ++g) acc += ph[(size_t)g * ka + j];
+      worst = std::max(worst, std::sqrt(acc));
+    }
+    *rel = worst / c->norm1;
+    if (*rel <= 0.5 * thr || *rel > 0.9 * prev) break;
+    prev = *rel;
+  }
+  rks::launch_df_add_f32_cols(n, c->U2, ldu, ka, cur ? Xb : Xa, ldu, c->stream);
+  rc = launch_err();
+  if (rc) { release(); return rc; }
+  if (!(*rel <= thr)) {
+    prof_end(c, ps, RKS_K_OTHER, 4 + 2 * ka + 2 * sweeps, 0.0, 0.0);
+    release();
+    return RKS_EDENSE;
+  }
+  // sketches of the corrected columns and of u (the per-CTA partials summed in
+  // CTA order); u's must agree with the one the FP32 phase kept
+  std::vector<double> Sall((size_t)d * (ka + 1)), pz((size_t)c->tiles.G * d);
+  for (int j = 0; j <= ka; ++j) {
+    rks::launch_df_sketch_vec(c->U2 + (size_t)j * ldu, c->tiles, c->part_s, false, c->stream);
+    CK(cudaMemcpyAsync(pz.data(), c->part_s, pz.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double sc = c->zscale * (j == ka ? cs_u : 1.0);
+    for (int r = 0; r < d; ++r) {
+      double acc = 0.0;
+      for (int g = 0; g < c->tiles.G; ++g) acc += pz[(size_t)g * d + r];
+      Sall[r + (size_t)j * d] = sc * acc;
+    }
+  }
+  prof_end(c, ps, RKS_K_OTHER, 5 + 2 * ka + 2 * sweeps + ka + 1, 0.0, 0.0);
+  release();
+  {
+    double du = 0.0, nu = 0.0;
+    for (int r = 0; r < d; ++r) {
+      const double a = Sall[r + (size_t)ka * d], e = c->S_h[r + (size_t)ka * d];
+      du += (a - e) * (a - e);
+      nu += e * e;
+    }
+    if (!(du <= 1e-6 * nu)) return RKS_EINVAL;   // not the decomposition the FP32 phase left
+  }
+  const int kb = ka + 1;
+  std::vector<double> R((size_t)kb * kb), Rinv((size_t)kb * kb, 0.0);
+  rks_dense::house_qr(d, kb, Sall.data(), R.data());
+  for (int j = 0; j < kb; ++j) {
+    if (R[j + (size_t)j * kb] == 0.0) return RKS_EINVAL;
+    Rinv[j + (size_t)j * kb] = 1.0 / R[j + (size_t)j * kb];
+    for (int i = j - 1; i >= 0; --i) {
+      double acc = 0.0;
+      for (int l = i + 1; l <= j; ++l) acc += R[i + (size_t)l * kb] * Rinv[l + (size_t)j * kb];
+      Rinv[i + (size_t)j * kb] = -acc / R[i + (size_t)i * kb];
+    }
+  }
+  // T' = (R11 T + r12 b^T) R11^-1, b'^T = r22 b^T R11^-1
+  std::vector<double> P((size_t)ka * ka, 0.0), Tn((size_t)ka * ka, 0.0), bn(ka, 0.0);
+  for (int j = 0; j < ka; ++j)
+    for (int i = 0; i < ka; ++i) {
+      double acc = R[i + (size_t)ka * kb] * b[j];
+      for (int l = i; l < ka; ++l) acc += R[i + (size_t)l * kb] * T[l + (size_t)j * ka];
+      P[i + (size_t)j * ka] = acc;
+    }
+  for (int j = 0; j < ka; ++j) {
+    for (int i = 0; i < ka; ++i) {
+      double acc = 0.0;
+      for (int l = 0; l <= j; ++l) acc += P[i + (size_t)l * ka] * Rinv[l + (size_t)j * kb];
+      Tn[i + (size_t)j * ka] = acc;
+    }
+    double acc = 0.0;
+    for (int l = 0; l <= j; ++l) acc += b[l] * Rinv[l + (size_t)j * kb];
+    bn[j] = R[ka + (size_t)ka * kb] * acc;
+  }
+  // [V v] = [U u] diag(cs) R^-1 in place
+  rc = restart_launch(c, 0, kb, Rinv, c->cs_h.data(), kb, -1);
+  if (rc) return rc;
+  for (int j = 0; j <= m; ++j) c->cs_h[j] = j < kb ? 1.0 : 0.0;
+  std::fill(c->S_h.begin(), c->S_h.end(), 0.0);
+  std::copy(Sall.begin(), Sall.end(), c->S_h.begin());
+  std::fill(c->Ba.begin(), c->Ba.end(), 0.0);
+  for (int j = 0; j < ka; ++j) {
+    for (int i = 0; i < ka; ++i) M(c->Ba, ldb, i, j) = Tn[i + (size_t)j * ka];
+    M(c->Ba, ldb, ka, j) = bn[j];
+  }
+  c->Tqq.assign((size_t)(c->k + 2) * (c->k + 2), 0.0);
+  c->Tqa.assign((size_t)(c->k + 2) * (m + 1), 0.0);
+  c->corr.clear();
+  c->up_M2 = c->M2 != nullptr;
+  if (c->up_M2) {
+    const int ldm = m + 1;
+    c->M2_h.assign((size_t)ldm * ldm, make_float2(0.f, 0.f));
+    for (int b2 = 0; b2 < kb; ++b2)
+      for (int a2 = 0; a2 <= b2; ++a2) {
+        double acc = 0.0;
+        for (int i = 0; i < d; ++i) acc += c->S_h[i + (size_t)a2 * d] * c->S_h[i + (size_t)b2 * d];
+        const float h = (float)acc;
+        const float2 v = make_float2(h, (float)(acc - (double)h));
+        c->M2_h[a2 + (size_t)b2 * ldm] = v;
+        c->M2_h[b2 + (size_t)a2 * ldm] = v;
+      }
+  }
+  c->S2_h.resize(c->S_h.size());
+  for (size_t t = 0; t < c->S_h.size(); ++t) {
+    const float h = (float)c->S_h[t];
+    c->S2_h[t] = make_float2(h, (float)(c->S_h[t] - (double)h));
+  }
+  rc = upload_restart(c);
+  if (rc) return rc;
+  ritz(c);
+  return RKS_OK;
+}
+
+// Algorithm 1's initial state: the start vector u_1 = u~_1 / ||Omega u~_1||
+// (Sec. 3.1, k = 0) in column 0, nothing kept.
+static int start_alg1(rks_ctx* c, const double* start) {
   const int m = c->m, d = c->d;
-  *converged = false;
   c->q = 0; c->ja = 0; c->kk = 0; c->nw = 0;
   c->Ba.assign((size_t)(m + 1) * m, 0.0);
   c->Tqq.assign((size_t)(c->k + 2) * (c->k + 2), 0.0);
@@ -1166,14 +1383,33 @@ static int run_alg1(rks_ctx* c, const double* start, int limit, double verify, i
     rks::launch_start_finish(d, c->zscale, c->s_raw, c->S, c->colscale, c->flag, c->stream);
     prof_end(c, ps, RKS_K_OTHER, c->u1 ? 2 : 3, 0.0, 0.0);
   }
-  int rc = launch_err();
-  if (rc) return rc;
+  return launch_err();
+}
+
+// Algorithm 1 from the start vector `start` (NULL: the user's u1 or the
+// library's generator) until the estimates reach c->tol (with the FP64
+// verification when verify > 0), `limit` restarts, or stagnation (if
+// stall > 0: no decrease of the largest estimate over `stall` restarts).
+// Sets *converged; leaves the Ritz pairs of the last contraction in c.
+static int run_alg1(rks_ctx* c, const double* start, int limit, double verify, int stall, bool* converged,
+                    bool resume = false) {
+  const int m = c->m, d = c->d;
+  *converged = false;
+  int rc = RKS_OK;
+  if (resume) {                        // from the decomposition in c (the mixed path's hand-over)
+    CK(cudaMemsetAsync(c->flag, 0, 4 * sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->z_raw, 0, d * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(c->s_raw, 0, d * sizeof(double), c->stream));
+  } else {
+    rc = start_alg1(c, start);
+    if (rc) return rc;
+  }
   rc = expand(c);                      // Algorithm 1, initial expansion to m
   if (rc) return rc;
   if (c->opts.max_restarts < 0) { c->solved = true; return RKS_OK; }
   int done = 0;
   double best = 1e300;
-  int since_best = 0;
+  int since_best = 0, q_seen = c->q;
   while (true) {
     auto h0 = std::chrono::steady_clock::now();
     rc = contract(c);                  // Schur, reorder, truncate, whiten, lock, restart
@@ -1207,7 +1443,11 @@ static int run_alg1(rks_ctx* c, const double* start, int limit, double verify, i
       }
       return RKS_OK;
     }
-    if (mx < 0.5 * best) { best = mx; since_best = 0; } else if (++since_best >= stall && stall > 0) return RKS_OK;
+    // stagnation: no halving of the largest estimate over `stall` restarts,
+    // counted afresh when vectors lock (the next wanted pair enters the set)
+    if (c->q > q_seen) { q_seen = c->q; best = mx; since_best = 0; }
+    else if (mx < 0.5 * best) { best = mx; since_best = 0; }
+    else if (++since_best >= stall && stall > 0) return RKS_OK;
     if (done >= limit) return RKS_OK;
     rc = expand(c);                    // Algorithm 2 from k to m
     if (rc) return rc;
@@ -1229,7 +1469,11 @@ static int solve_impl(rks_ctx* c) {
   int rc = RKS_OK;
   if (c->prec == RKS_PREC_MIXED) {
     // Phase 1: FP32 basis and values (compensated arithmetic), down to the
-    // FP32 floor or until the estimates stagnate.
+    // FP32 floor or until the estimates stagnate.  With a thick restart
+    // (keep > 0) phase 2 continues from this phase's decomposition, so there
+    // is no locking here: a locked vector's dropped residual would stay in
+    // the decomposition that phase 2 continues from.  With keep = 0 (the
+    // truncation of Algorithm 1) this phase locks and phase 2 starts afresh.
     c->f32 = true;
     c->Ub = c->Uf;
     c->A2.vals = c->valsf;
@@ -1239,9 +1483,19 @@ static int solve_impl(rks_ctx* c) {
     const double floor32 = c->opts.mixed_tol > 0 ? c->opts.mixed_tol : 64.0 * 5.9604644775390625e-08;
     c->tol = std::max(tol0, floor32);
     c->eta_lock = std::max(eta0, 0.5 * floor32);
+    const int lock0 = c->opts.lock, aggr0 = c->opts.aggressive;
+    const bool carry = c->opts.keep > 0 && c->opts.ortho == RKS_ORTHO_SKETCH;
+    if (carry) {
+      c->opts.lock = 0;
+      c->opts.aggressive = 0;
+    }
     bool conv1 = false;
     rc = run_alg1(c, nullptr, limit, 0.0, 20, &conv1);
+    c->opts.lock = lock0;
+    c->opts.aggressive = aggr0;
     c->phase_restarts = c->restarts;
+    c->stats.fp32_restarts = c->restarts;
+    const int kk32 = c->kk;
     // The FP32 result may already meet the target: its Ritz vectors checked
     // in FP64 (finalize promotes the FP32 basis exactly); then no
     // double-float phase is needed.
@@ -1254,26 +1508,50 @@ static int solve_impl(rks_ctx* c) {
         fp32_done = mr <= c->opts.verify;
       }
     }
-    if (rc == RKS_OK && !fp32_done && c->opts.max_restarts >= 0) {
-      // Phase 2 start vector: the sum of the FP32 Schur vectors (all wanted
-      // directions to FP32 accuracy), in FP64.
-      rks::launch_sum_cols_f32(c->n, c->Uf, c->ldu, c->kk, c->tmp64, c->stream);
-      rc = launch_err();
-    }
     c->tol = tol0;
     c->eta_lock = eta0;
     if (fp32_done) {
       converged = true;
-    } else {
-      c->f32 = false;
-      c->Ub = c->U2;
-      c->A2.vals = c->vals2;
-      c->A2.evals = c->ell_val2;
-      if (c->dia_d) c->A2.dvals = c->dia_val2;
-      c->A2.f32 = false;
-      if (rc == RKS_OK && c->opts.max_restarts >= 0) {
-        // Phase 2: double-float from that start vector, verified in FP64.
-        rc = run_alg1(c, c->tmp64, std::max(1, limit - c->restarts), c->opts.verify, 0, &converged);
+    } else if (rc == RKS_OK && c->opts.max_restarts >= 0) {
+      // Phase 2: double-float, continuing from the FP32 decomposition made
+      // exact (handover_df); if that is not possible or does not converge,
+      // from the sum of the FP32 Schur vectors (all wanted directions to
+      // FP32 accuracy), verified in FP64 either way.
+      // The relation error left must be below what the target asks of the
+      // residuals (on the ||A||_1 scale): the estimate tolerance, or with
+      // the FP64 check what the verified bound leaves above it; on the
+      // |lambda| scale, tol times the smallest wanted |lambda|.
+      double thr = tol0;
+      if (c->opts.conv == RKS_CONV_NORM1) {
+        if (c->opts.verify > 0) thr = std::max(tol0, c->opts.verify - tol0);
+      } else {
+        double lmin = 1e300;
+        for (int t = 0; t < c->nw; ++t) lmin = std::min(lmin, std::hypot(c->lre[t], c->lim[t]));
+        thr = c->nw > 0 ? tol0 * lmin / c->norm1 : 0.0;
+      }
+      double rel = 0.0;
+      const int h = carry ? handover_df(c, thr, &rel) : RKS_EINVAL;
+      c->stats.handover_rel = carry ? rel : 0.0;
+      if (h == RKS_OK) {
+        c->stats.mixed_phase2 = 1;
+        rc = run_alg1(c, nullptr, std::max(1, limit - c->restarts), c->opts.verify, 60, &converged, true);
+      } else if (h != RKS_EINVAL && h != RKS_EDENSE) {
+        rc = h;
+      }
+      if (rc == RKS_OK && !converged && c->restarts < limit) {
+        c->stats.mixed_phase2 = 2;
+        c->tol = tol0;
+        c->eta_lock = eta0;
+        rks::launch_sum_cols_f32(c->n, c->Uf, c->ldu, kk32, c->tmp64, c->stream);
+        rc = launch_err();
+        c->f32 = false;
+        c->Ub = c->U2;
+        c->A2.vals = c->vals2;
+        c->A2.evals = c->ell_val2;
+        if (c->dia_d) c->A2.dvals = c->dia_val2;
+        c->A2.f32 = false;
+        if (rc == RKS_OK)
+          rc = run_alg1(c, c->tmp64, std::max(1, limit - c->restarts), c->opts.verify, 0, &converged);
       }
     }
   } else {

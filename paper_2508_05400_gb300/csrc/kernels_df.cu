@@ -32,6 +32,7 @@
 // order (fold_row).  The result is the same bits on every run.
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "rks_impl.h"
@@ -1694,6 +1695,122 @@ __global__ void __launch_bounds__(256) k_df_restart(int64_t n, TU* U, int64_t ld
 }
 
 // ---------------------------------------------------------------------------
+// Hand-over of the mixed path's FP32 Krylov-Schur decomposition
+// A U = U T + u b^T to double-float: the FP32 basis promoted exactly, the
+// relation error E = A U - U T - u b^T of the promoted columns, and damped
+// Jacobi sweeps on A X - X T = -E for the correction U <- U + X.
+// ---------------------------------------------------------------------------
+
+// U2[:, j] = Uf[:, j], j < ncols (exact: the pairs' low words are zero)
+__global__ void k_f32_to_df_cols(int64_t n, const float* __restrict__ Uf, int64_t ldu, int ncols,
+                                 float2* __restrict__ U2) {
+  const int64_t total = (int64_t)ncols * ldu;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = q % ldu;
+    if (i < n) U2[q] = make_float2(Uf[q], 0.f);
+  }
+}
+
+// e = w - v - beta u in double-float, rounded to FP32 (column j of E:
+// w = A u_j, v = (U T)_j, beta = b_j times the column scale of u)
+__global__ void k_relation_resid(int64_t n, const float2* __restrict__ w, const float2* __restrict__ v,
+                                 const float2* __restrict__ u, double beta, float* __restrict__ e) {
+  const float2 nb = df_from_double(-beta);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 a = w[i], b = v[i], c = u[i];
+    float s = a.x, t = a.y;
+    df_add(-b.x, -b.y, s, t);
+    df_mac(nb.x, nb.y, c.x, c.y, s, t);
+    e[i] = s + t;
+  }
+}
+
+// 1 / a_ii (0 where row i has no diagonal entry or a zero one)
+__global__ void k_diag_inv(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                           const float* __restrict__ vals, float* __restrict__ dinv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float a = 0.f;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p)
+      if (colind[p] == i) a += vals[p];
+    dinv[i] = a != 0.f ? 1.0f / a : 0.f;
+  }
+}
+
+// One damped Jacobi sweep on A X - X T = -E for all kk columns:
+//   R = E + A X - Y (Y = X T, given),  Xn = X - omega D^{-1} R,
+// a thread per row (the row's entries loaded once, up to 16 kept in
+// registers), FP32 with FMA.  With part: the per-CTA sums of R^2 per column
+// (warp sums by a fixed butterfly, then the warps in order) in
+// part[blockIdx.x * kk + j].
+constexpr int kJacobiCta = 256;
+__global__ void __launch_bounds__(kJacobiCta) k_jacobi_sweep(int64_t n, const int32_t* __restrict__ rowptr,
+                                                             const int32_t* __restrict__ colind,
+                                                             const float* __restrict__ vals,
+                                                             const float* __restrict__ dinv, int kk, int64_t ld,
+                                                             const float* __restrict__ X,
+                                                             const float* __restrict__ E,
+                                                             const float* __restrict__ Y, float omega,
+                                                             float* __restrict__ Xn, double* __restrict__ part) {
+  constexpr int RM = 16;
+  __shared__ double wsum[kJacobiCta / 32];
+  const int64_t i = blockIdx.x * (int64_t)kJacobiCta + threadIdx.x;
+  const bool on = i < n;
+  int p0 = 0, len = 0;
+  float di = 0.f;
+  int cj[RM];
+  float aj[RM];
+  if (on) {
+    p0 = rowptr[i];
+    len = rowptr[i + 1] - p0;
+    di = dinv[i];
+  }
+#pragma unroll
+  for (int e = 0; e < RM; ++e) {
+    const bool h = e < len;
+    cj[e] = h ? colind[p0 + e] : 0;
+    aj[e] = h ? vals[p0 + e] : 0.f;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = 0; j < kk; ++j) {
+    const int64_t o = (int64_t)j * ld;
+    double r2 = 0.0;
+    if (on) {
+      float acc = E[o + i] - Y[o + i];
+#pragma unroll
+      for (int e = 0; e < RM; ++e)
+        if (e < len) acc = fmaf(aj[e], X[o + cj[e]], acc);
+      for (int e = RM; e < len; ++e) acc = fmaf(vals[p0 + e], X[o + colind[p0 + e]], acc);
+      Xn[o + i] = fmaf(-omega * di, acc, X[o + i]);
+      r2 = (double)acc * (double)acc;
+    }
+    if (part) {
+      for (int s = 16; s; s >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, s);
+      if (lane == 0) wsum[wid] = r2;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kJacobiCta / 32; ++w) t += wsum[w];
+        part[(int64_t)blockIdx.x * kk + j] = t;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// U2[:, j] += X[:, j] (double-float + FP32), j < kk
+__global__ void k_df_add_f32_cols(int64_t n, float2* __restrict__ U2, int64_t ldu, int kk,
+                                  const float* __restrict__ X, int64_t ldx) {
+  const int64_t total = (int64_t)kk * n;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = q / n, i = q - j * n;
+    const float2 u = U2[j * ldu + i];
+    float s = u.x, t = u.y;
+    df_add(X[j * ldx + i], 0.f, s, t);
+    U2[j * ldu + i] = df_norm(s, t);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 
@@ -1718,6 +1835,7 @@ static cudaError_t configure_df_kernels_once() {
   RKS_SMEM((k_df_spmv_dia<float2, float2, true, 8>)); RKS_SMEM((k_df_spmv_dia<float, float, true, 8>));
   RKS_SMEM((k_df_spmv_dia<float2, float2, true, 16>)); RKS_SMEM((k_df_spmv_dia<float, float, true, 16>));
   RKS_SMEM((k_df_spmv_dia<float2, float2, false, 8>)); RKS_SMEM((k_df_spmv_dia<float2, float2, false, 16>));
+  RKS_SMEM((k_df_spmv_dia<float2, float, true, 8>)); RKS_SMEM((k_df_spmv_dia<float2, float, false, 8>));
   RKS_SMEM((k_df_spmv_ell<float2, float2, false, 0>)); RKS_SMEM((k_df_spmv_ell<float2, float2, true, 6>));
   RKS_SMEM((k_df_spmv_ell<float, float, true, 6>)); RKS_SMEM((k_df_spmv_ell<float2, float2, false, 6>));
   constexpr int U8 = kDfUpdUnroll, MB = kDfUpdMinBlocks;
@@ -1774,8 +1892,19 @@ static void launch_dia(const CsrDF& A, const void* x, void* w, const SketchTiles
   const TU* xx = static_cast<const TU*>(x);
   TU* ww = static_cast<TU*>(w);
   const TU* dv = static_cast<const TU*>(A.dvals);
-  if (A.D <= 8) k_df_spmv_dia<TU, TU, SK, 8><<<t.G, 512, sm, st>>>(o, A.D, dv, A.ldd, A.n, xx, ww, t, part);
-  else k_df_spmv_dia<TU, TU, SK, 16><<<t.G, 512, sm, st>>>(o, A.D, dv, A.ldd, A.n, xx, ww, t, part);
+  if (A.D > 8) {
+    k_df_spmv_dia<TU, TU, SK, 16><<<t.G, 512, sm, st>>>(o, A.D, dv, A.ldd, A.n, xx, ww, t, part);
+  } else if constexpr (std::is_same<TU, float2>::value) {
+    // double-float vectors: the FP32 copy of the diagonals when every value
+    // of A is an FP32 number (the pairs' low words are zero: the same bits)
+    if (A.dvals_f32)
+      k_df_spmv_dia<float2, float, SK, 8><<<t.G, 512, sm, st>>>(o, A.D, static_cast<const float*>(A.dvals_f32),
+                                                                A.ldd, A.n, xx, ww, t, part);
+    else
+      k_df_spmv_dia<float2, float2, SK, 8><<<t.G, 512, sm, st>>>(o, A.D, dv, A.ldd, A.n, xx, ww, t, part);
+  } else {
+    k_df_spmv_dia<TU, TU, SK, 8><<<t.G, 512, sm, st>>>(o, A.D, dv, A.ldd, A.n, xx, ww, t, part);
+  }
 }
 
 // The merge-path partition of A (the first row of every CTA's range), once per
@@ -2076,6 +2205,35 @@ void launch_df_rows_gemm(int64_t n, void* U, int64_t ldu, int a0, int nin, const
   const int g = (int)((n + 127) / 128);
   if (f32) k_df_rows_gemm<float><<<g, 128, sm, st>>>(n, static_cast<float*>(U), ldu, a0, nin, Q, nout, c0, move_src);
   else k_df_rows_gemm<float2><<<g, 128, sm, st>>>(n, static_cast<float2*>(U), ldu, a0, nin, Q, nout, c0, move_src);
+}
+
+
+void launch_f32_to_df_cols(int64_t n, const float* Uf, int64_t ldu, int ncols, float2* U2, cudaStream_t st) {
+  k_f32_to_df_cols<<<df_grid((int64_t)ncols * ldu, 256), 256, 0, st>>>(n, Uf, ldu, ncols, U2);
+}
+
+void launch_relation_resid(int64_t n, const float2* w, const float2* v, const float2* u, double beta, float* e,
+                           cudaStream_t st) {
+  k_relation_resid<<<df_grid(n, 256), 256, 0, st>>>(n, w, v, u, beta, e);
+}
+
+void launch_diag_inv(int64_t n, const int32_t* rowptr, const int32_t* colind, const float* vals, float* dinv,
+                     cudaStream_t st) {
+  k_diag_inv<<<df_grid(n, 256), 256, 0, st>>>(n, rowptr, colind, vals, dinv);
+}
+
+int jacobi_sweep_ctas(int64_t n) { return (int)((n + kJacobiCta - 1) / kJacobiCta); }
+
+void launch_jacobi_sweep(int64_t n, const int32_t* rowptr, const int32_t* colind, const float* vals,
+                         const float* dinv, int kk, int64_t ld, const float* X, const float* E, const float* Y,
+                         float omega, float* Xn, double* part, cudaStream_t st) {
+  k_jacobi_sweep<<<jacobi_sweep_ctas(n), kJacobiCta, 0, st>>>(n, rowptr, colind, vals, dinv, kk, ld, X, E, Y, omega,
+                                                              Xn, part);
+}
+
+void launch_df_add_f32_cols(int64_t n, float2* U2, int64_t ldu, int kk, const float* X, int64_t ldx,
+                            cudaStream_t st) {
+  k_df_add_f32_cols<<<df_grid((int64_t)kk * n, 256), 256, 0, st>>>(n, U2, ldu, kk, X, ldx);
 }
 
 }  // namespace rks

@@ -68,6 +68,10 @@ struct CsrDF {
   int doff[16] = {};
   int64_t ldd = 0;
   const void* dvals = nullptr;  // float2 pairs, or float when f32
+  // FP32 copy of the diagonals for double-float vectors (optional, D <= 8):
+  // set when every value of A is an FP32 number, so that the pairs' low
+  // words are zero and the products are the same bits
+  const void* dvals_f32 = nullptr;
   // Irregular rows (CSR only; see rks_spmv_format): kSpmvWarp takes a row
   // per warp inside the sketch tiles; kSpmvMerge splits rows + entries evenly
   // over threads (merge path), then folds the partial rows and sketches w.
@@ -132,6 +136,22 @@ void launch_df2d_cols(int64_t n, const void* x, int64_t ldx, double* y, int64_t 
 void launch_df_sketch_vec(const void* x, const SketchTiles& t, double* part, bool f32, cudaStream_t st);
 void launch_df_rows_gemm(int64_t n, void* U, int64_t ldu, int a0, int nin, const float2* Q, int nout, int c0,
                          int move_src, bool f32, cudaStream_t st);
+// Hand-over of the mixed path's FP32 decomposition to double-float
+// (kernels_df.cu): exact promotion of FP32 columns, the relation error
+// e = w - v - beta u rounded to FP32, 1 / a_ii, damped Jacobi sweeps on
+// A X - X T = -E (Y = X T given; with part, the per-CTA sums of the squared
+// residual per column, jacobi_sweep_ctas(n) x kk), and U2 += X.
+void launch_f32_to_df_cols(int64_t n, const float* Uf, int64_t ldu, int ncols, float2* U2, cudaStream_t st);
+void launch_relation_resid(int64_t n, const float2* w, const float2* v, const float2* u, double beta, float* e,
+                           cudaStream_t st);
+void launch_diag_inv(int64_t n, const int32_t* rowptr, const int32_t* colind, const float* vals, float* dinv,
+                     cudaStream_t st);
+int jacobi_sweep_ctas(int64_t n);
+void launch_jacobi_sweep(int64_t n, const int32_t* rowptr, const int32_t* colind, const float* vals,
+                         const float* dinv, int kk, int64_t ld, const float* X, const float* E, const float* Y,
+                         float omega, float* Xn, double* part, cudaStream_t st);
+void launch_df_add_f32_cols(int64_t n, float2* U2, int64_t ldu, int kk, const float* X, int64_t ldx,
+                            cudaStream_t st);
 
 // Tensor-core restart product for an FP32 basis (restart_tc.cu):
 // out[:, o] = sum_l in[:, l] Q[l, o], in place allowed, then mvdst = mvsrc.

@@ -56,7 +56,8 @@ def profile_mask(*classes: str) -> int:
 class Stats(C.Structure):
     _fields_ = [("launches", C.c_int64 * 6), ("ms", C.c_double * 6), ("bytes", C.c_double * 6),
                 ("flops", C.c_double * 6), ("host_ms", C.c_double), ("whitenings", C.c_int64),
-                ("reorders", C.c_int64)]
+                ("reorders", C.c_int64), ("fp32_restarts", C.c_int), ("mixed_phase2", C.c_int),
+                ("handover_rel", C.c_double)]
 
     def as_dict(self) -> dict:
         out = {name: {"launches": self.launches[i], "ms": self.ms[i], "bytes": self.bytes[i],
@@ -64,6 +65,9 @@ class Stats(C.Structure):
         out["host_ms"] = self.host_ms
         out["whitenings"] = self.whitenings
         out["reorders"] = self.reorders
+        out["fp32_restarts"] = self.fp32_restarts
+        out["mixed_phase2"] = self.mixed_phase2     # 0 none, 1 from the hand-over, 2 from the sum of Schur vectors
+        out["handover_rel"] = self.handover_rel
         out["launches_total"] = int(sum(self.launches))
         return out
 
