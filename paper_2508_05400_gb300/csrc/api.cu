@@ -1490,7 +1490,9 @@ static int solve_impl(rks_ctx* c) {
       c->opts.aggressive = 0;
     }
     bool conv1 = false;
-    rc = run_alg1(c, nullptr, limit, 0.0, 20, &conv1);
+    // (with the hand-over every FP32 restart counts toward the double-float
+    // phase, so a long stagnation window: 40 restarts)
+    rc = run_alg1(c, nullptr, limit, 0.0, carry ? 40 : 20, &conv1);
     c->opts.lock = lock0;
     c->opts.aggressive = aggr0;
     c->phase_restarts = c->restarts;
