@@ -1534,13 +1534,17 @@ static int solve_impl(rks_ctx* c) {
       double rel = 0.0;
       const int h = carry ? handover_df(c, thr, &rel) : RKS_EINVAL;
       c->stats.handover_rel = carry ? rel : 0.0;
-      if (h == RKS_OK) {
+      const bool cont = h == RKS_OK;
+      if (cont) {
         c->stats.mixed_phase2 = 1;
         rc = run_alg1(c, nullptr, std::max(1, limit - c->restarts), c->opts.verify, 60, &converged, true);
       } else if (h != RKS_EINVAL && h != RKS_EDENSE) {
         rc = h;
       }
-      if (rc == RKS_OK && !converged && c->restarts < limit) {
+      // a fresh double-float phase: without the hand-over (at least one
+      // restart, as a partial result must be a double-float decomposition),
+      // or after a continuation that stagnated before the limit
+      if (rc == RKS_OK && !converged && (!cont || c->restarts < limit)) {
         c->stats.mixed_phase2 = 2;
         c->tol = tol0;
         c->eta_lock = eta0;

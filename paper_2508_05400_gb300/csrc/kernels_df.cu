@@ -882,9 +882,10 @@ __global__ void __launch_bounds__(512, 2) k_df_spmv_dia(const DiaOffs offs, int 
     const int la = threadIdx.x, lb = threadIdx.x + 512;
     const bool oka = la < rows, okb = lb < rows;
     const int64_t ia = r0 + la, ib = r0 + lb;
-    // rounds of four diagonals: the loads of a round are all in flight at
-    // once, and the registers stay within two CTAs per SM
-    constexpr int RU = 4;
+    // rounds of four diagonals (eight for FP32 vectors and values): the loads
+    // of a round are all in flight at once, and the registers stay within
+    // two CTAs per SM
+    constexpr int RU = sizeof(TU) == 4 && sizeof(TA) == 4 ? 8 : 4;
     float sa = 0.f, ta = 0.f, sb = 0.f, tb = 0.f;
 #pragma unroll
     for (int e0 = 0; e0 < DMAX; e0 += RU) {
@@ -1839,7 +1840,7 @@ static cudaError_t configure_df_kernels_once() {
   RKS_SMEM((k_df_spmv_ell<float2, float2, false, 0>)); RKS_SMEM((k_df_spmv_ell<float2, float2, true, 6>));
   RKS_SMEM((k_df_spmv_ell<float, float, true, 6>)); RKS_SMEM((k_df_spmv_ell<float2, float2, false, 6>));
   constexpr int U8 = kDfUpdUnroll, MB = kDfUpdMinBlocks;
-  RKS_SMEM((k_df_update_sketch<float2, U8, MB, 1>)); RKS_SMEM((k_df_update_sketch<float, U8, MB, 1>));
+  RKS_SMEM((k_df_update_sketch<float2, U8, MB, 1>)); RKS_SMEM((k_df_update_sketch<float, 2 * U8, MB, 1>));
   RKS_SMEM((k_df_update_sketch<float2, U8, MB, 0>)); RKS_SMEM((k_df_update_sketch<float2, U8, MB, 2>));
   RKS_SMEM(k_df_sketch_vec<float2>); RKS_SMEM(k_df_sketch_vec<float>);
   RKS_SMEM(k_tiles_count<4>); RKS_SMEM(k_tiles_count<8>); RKS_SMEM(k_tiles_count<16>);
@@ -2039,8 +2040,11 @@ void launch_df_update_sketch(void* U, int64_t ldu, int c, const float2* nrs, con
                              double* part, bool f32, cudaStream_t st) {
   constexpr int U8 = kDfUpdUnroll, MB = kDfUpdMinBlocks;
   const size_t sm = tile_smem_bytes(t.d, t.L, c, t.zeta);
+  // FP32 basis: twice the columns per batch, so that a thread has as many
+  // bytes of loads in flight as with pairs (same order of the sums)
   if (f32)
-    k_df_update_sketch<float, U8, MB, 1><<<t.G, 512, sm, st>>>(static_cast<float*>(U), ldu, c, nrs, sj, t, part);
+    k_df_update_sketch<float, 2 * U8, MB, 1><<<t.G, 512, sm, st>>>(static_cast<float*>(U), ldu, c, nrs, sj, t,
+                                                                   part);
   else
     k_df_update_sketch<float2, U8, MB, 1><<<t.G, 512, sm, st>>>(static_cast<float2*>(U), ldu, c, nrs, sj, t, part);
 }
