@@ -146,7 +146,8 @@ class Clocks:
 DTYPES = {"fp64": "f64",
           "df": "df64 (fp32 pair, 48-bit significand; fp64 sketch/LS/Schur/residuals)",
           "mixed": ("f32 basis + f32 SpMV/updates (compensated), split-bf16 tensor-core restart with f32 "
-                    "accumulation, df64 finish below the f32 floor; f64 sketch/LS/Schur/residuals/Rayleigh")}
+                    "accumulation; below the f32 floor df64 restarts continuing from the f32 Krylov-Schur "
+                    "decomposition (relation error corrected in df64/f32); f64 sketch/LS/Schur/residuals/Rayleigh")}
 
 
 def _problem(workload: str, grid: int = 0):
