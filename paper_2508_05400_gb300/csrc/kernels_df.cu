@@ -842,6 +842,7 @@ __global__ void k_df_round_f32(int64_t n, const float2* __restrict__ a, float* _
 // Offsets of the diagonal copy, passed by value.
 struct DiaOffs {
   int o[16];
+  int lo = 0, hi = 0;   // smallest and largest offset (the SpMV's interior-tile test)
 };
 
 // w = A x (+ the per-CTA partial sketches of w when SK) on the diagonal copy
@@ -885,26 +886,58 @@ __global__ void __launch_bounds__(512, 2) k_df_spmv_dia(const DiaOffs offs, int 
     // rounds of four diagonals (eight for FP32 vectors and values): the loads
     // of a round are all in flight at once, and the registers stay within
     // two CTAs per SM
-    constexpr int RU = sizeof(TU) == 4 && sizeof(TA) == 4 ? 8 : 4;
+    constexpr int RU = sizeof(TU) == 4 && sizeof(TA) == 4 && DMAX == 8 ? 8 : 4;
     float sa = 0.f, ta = 0.f, sb = 0.f, tb = 0.f;
+    // an interior tile (every x[i + off] of its rows inside 0 .. n-1, the
+    // usual case) needs no bounds test: 32-bit offsets from the row pointers
+    // (D <= 8 and FP32 values; the other kernels keep one path within their
+    // registers)
+    const bool interior = DMAX == 8 && sizeof(TA) == 4 && r0 + offs.lo >= 0 && r0 + kTileRows + offs.hi <= n;
+    if (interior) {
+      const TA* dva = dv + ia;
+      const TU* xpa = x + ia;
 #pragma unroll
-    for (int e0 = 0; e0 < DMAX; e0 += RU) {
-      float2 va[RU], vb[RU], xa[RU], xb[RU];
+      for (int e0 = 0; e0 < DMAX; e0 += RU) {
+        float2 va[RU], vb[RU], xa[RU], xb[RU];
 #pragma unroll
-      for (int u = 0; u < RU; ++u) {
-        const int e = e0 + u;
-        const bool on = e < D;
-        const int64_t ja = ia + offs.o[e], jb = ib + offs.o[e];
-        va[u] = (on && oka) ? ldv(dv + e * ldd + ia) : make_float2(0.f, 0.f);
-        vb[u] = (on && okb) ? ldv(dv + e * ldd + ib) : make_float2(0.f, 0.f);
-        xa[u] = (on && oka && ja >= 0 && ja < n) ? ldv(x + ja) : make_float2(0.f, 0.f);
-        xb[u] = (on && okb && jb >= 0 && jb < n) ? ldv(x + jb) : make_float2(0.f, 0.f);
+        for (int u = 0; u < RU; ++u) {
+          const int e = e0 + u;
+          const bool on = e < D;
+          const TA* pv = dva + e * ldd;
+          const TU* px = xpa + offs.o[e];
+          va[u] = (on && oka) ? ldv(pv) : make_float2(0.f, 0.f);
+          vb[u] = (on && okb) ? ldv(pv + 512) : make_float2(0.f, 0.f);
+          xa[u] = (on && oka) ? ldv(px) : make_float2(0.f, 0.f);
+          xb[u] = (on && okb) ? ldv(px + 512) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+          if (e0 + u < D) {
+            df_mac(va[u].x, va[u].y, xa[u].x, xa[u].y, sa, ta);
+            df_mac(vb[u].x, vb[u].y, xb[u].x, xb[u].y, sb, tb);
+          }
+        }
       }
+    } else {
 #pragma unroll
-      for (int u = 0; u < RU; ++u) {
-        if (e0 + u < D) {
-          df_mac(va[u].x, va[u].y, xa[u].x, xa[u].y, sa, ta);
-          df_mac(vb[u].x, vb[u].y, xb[u].x, xb[u].y, sb, tb);
+      for (int e0 = 0; e0 < DMAX; e0 += RU) {
+        float2 va[RU], vb[RU], xa[RU], xb[RU];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+          const int e = e0 + u;
+          const bool on = e < D;
+          const int64_t ja = ia + offs.o[e], jb = ib + offs.o[e];
+          va[u] = (on && oka) ? ldv(dv + e * ldd + ia) : make_float2(0.f, 0.f);
+          vb[u] = (on && okb) ? ldv(dv + e * ldd + ib) : make_float2(0.f, 0.f);
+          xa[u] = (on && oka && ja >= 0 && ja < n) ? ldv(x + ja) : make_float2(0.f, 0.f);
+          xb[u] = (on && okb && jb >= 0 && jb < n) ? ldv(x + jb) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+          if (e0 + u < D) {
+            df_mac(va[u].x, va[u].y, xa[u].x, xa[u].y, sa, ta);
+            df_mac(vb[u].x, vb[u].y, xb[u].x, xb[u].y, sb, tb);
+          }
         }
       }
     }
@@ -1890,6 +1923,8 @@ static void launch_dia(const CsrDF& A, const void* x, void* w, const SketchTiles
                        cudaStream_t st) {
   DiaOffs o{};
   for (int e = 0; e < A.D; ++e) o.o[e] = A.doff[e];
+  o.lo = A.D ? A.doff[0] : 0;
+  o.hi = A.D ? A.doff[A.D - 1] : 0;
   const TU* xx = static_cast<const TU*>(x);
   TU* ww = static_cast<TU*>(w);
   const TU* dv = static_cast<const TU*>(A.dvals);
