@@ -178,6 +178,8 @@ struct BdProb {
   int D;                  // > 0: A also by diagonals, offsets doff[e] increasing,
   int doff[kBMaxDiag];    //   row i's entry on diagonal e at dvals[e * ldu + i] (0 where A has none)
   const float2* dvals;
+  int dv32;               // 1: every value of A is an FP32 number and dvals holds FP32 values
+                          //   (const float*, the pairs' low words being zero)
   const int32_t* tbin;    // ntile x (d + 1): start of every (tile, sketch row) entry block
   const uint16_t* ent;    // entry blocks: 8 lane chunks of equal padded length,
                           //   entry = row in tile | 0x8000 if negative, 0xFFFF = none
@@ -382,7 +384,7 @@ __device__ __forceinline__ void bd_spmv_csr(const BdProb& P, int t, int m1, int 
 
 // The same product from the diagonal storage (columns i + doff[e] in
 // increasing order, as the CSR rows), ND diagonals.
-template <bool L2, int ND>
+template <bool L2, int ND, bool V32>
 __device__ __forceinline__ void bd_spmv_dia_n(const BdProb& P, int t, int m1, int j, float2 sg, float2* xs) {
   const int64_t r0 = (int64_t)t * kBR, n = P.n, ld = P.ldu;
   const int rows = (int)min((int64_t)kBR, n - r0);
@@ -395,7 +397,8 @@ __device__ __forceinline__ void bd_spmv_dia_n(const BdProb& P, int t, int m1, in
 #pragma unroll
     for (int dg = 0; dg < ND; ++dg) {
       const int64_t c = min(max(r0 + rr + P.doff[dg], (int64_t)0), n - 1);   // value 0 outside A
-      a[dg] = P.dvals[(size_t)dg * ld + r0 + rr];
+      const size_t ia = (size_t)dg * ld + r0 + rr;
+      a[dg] = V32 ? make_float2(reinterpret_cast<const float*>(P.dvals)[ia], 0.f) : P.dvals[ia];
       v[dg] = bd_ld<L2>(P.U + bd_uix(c, j, m1));
     }
     float s = 0.f, e = 0.f;
@@ -413,17 +416,17 @@ __device__ __forceinline__ void bd_spmv_dia_n(const BdProb& P, int t, int m1, in
 }
 
 // Dispatch on the number of diagonals.
-template <bool L2>
+template <bool L2, bool V32>
 __device__ __forceinline__ void bd_spmv_dia(const BdProb& P, int t, int m1, int j, float2 sg, float2* xs) {
   switch (P.D) {   // a compile-time number of diagonals: all loads of a row issued together
-    case 1: bd_spmv_dia_n<L2, 1>(P, t, m1, j, sg, xs); return;
-    case 2: bd_spmv_dia_n<L2, 2>(P, t, m1, j, sg, xs); return;
-    case 3: bd_spmv_dia_n<L2, 3>(P, t, m1, j, sg, xs); return;
-    case 4: bd_spmv_dia_n<L2, 4>(P, t, m1, j, sg, xs); return;
-    case 5: bd_spmv_dia_n<L2, 5>(P, t, m1, j, sg, xs); return;
-    case 6: bd_spmv_dia_n<L2, 6>(P, t, m1, j, sg, xs); return;
-    case 7: bd_spmv_dia_n<L2, 7>(P, t, m1, j, sg, xs); return;
-    default: bd_spmv_dia_n<L2, 8>(P, t, m1, j, sg, xs); return;
+    case 1: bd_spmv_dia_n<L2, 1, V32>(P, t, m1, j, sg, xs); return;
+    case 2: bd_spmv_dia_n<L2, 2, V32>(P, t, m1, j, sg, xs); return;
+    case 3: bd_spmv_dia_n<L2, 3, V32>(P, t, m1, j, sg, xs); return;
+    case 4: bd_spmv_dia_n<L2, 4, V32>(P, t, m1, j, sg, xs); return;
+    case 5: bd_spmv_dia_n<L2, 5, V32>(P, t, m1, j, sg, xs); return;
+    case 6: bd_spmv_dia_n<L2, 6, V32>(P, t, m1, j, sg, xs); return;
+    case 7: bd_spmv_dia_n<L2, 7, V32>(P, t, m1, j, sg, xs); return;
+    default: bd_spmv_dia_n<L2, 8, V32>(P, t, m1, j, sg, xs); return;
   }
 }
 
@@ -544,12 +547,13 @@ __device__ __noinline__ void bd_restart_tile(const BdProb& P, int t, int m, int 
 // (own register allocation, one call per pass).  The sketch sums of tile t - 1
 // are formed while the rows of tile t are computed; one barrier per tile.
 // xs: two tile buffers in shared memory (tile t in buffer t % 2).
-template <bool L2>
+template <bool L2, bool V32>
 __device__ __noinline__ void bd_pass_spmv(const BdProb& P, int t0, int t1, int m1, int j, float2 sg, int d,
                                           float2* ts, float2* xs) {
   for (int t = t0; t <= t1; ++t) {
     if (t < t1) {
-      if (P.D > 0) bd_spmv_dia<L2>(P, t, m1, j, sg, xs + (t & 1) * kBR);
+      if (V32) bd_spmv_dia<L2, true>(P, t, m1, j, sg, xs + (t & 1) * kBR);
+      else if (P.D > 0) bd_spmv_dia<L2, false>(P, t, m1, j, sg, xs + (t & 1) * kBR);
       else bd_spmv_csr<L2>(P, t, m1, j, sg, xs + (t & 1) * kBR);
     }
     if (t > t0) bd_bins_tile(P, d, t - 1, xs + ((t - 1) & 1) * kBR, ts);
@@ -739,8 +743,14 @@ __device__ void bd_solve(const BdArgs& A, const BdProb& P, double* sm, BdShared&
     for (int j = ja; j < m; ++j) {
       float2* ts = P.tsum + (size_t)(ex & 1) * P.ntile * d;
       const float2 sg = bd_from(sig[j]);
-      if (G > 1) bd_pass_spmv<true>(P, t0, t1, m1, j, sg, d, ts, xs);   // w = A u_j, partial z = Omega w
-      else bd_pass_spmv<false>(P, t0, t1, m1, j, sg, d, ts, xs);
+      // w = A u_j, partial z = Omega w (FP32 diagonals when A's values are FP32 numbers)
+      if (P.dv32) {
+        if (G > 1) bd_pass_spmv<true, true>(P, t0, t1, m1, j, sg, d, ts, xs);
+        else bd_pass_spmv<false, true>(P, t0, t1, m1, j, sg, d, ts, xs);
+      } else {
+        if (G > 1) bd_pass_spmv<true, false>(P, t0, t1, m1, j, sg, d, ts, xs);
+        else bd_pass_spmv<false, false>(P, t0, t1, m1, j, sg, d, ts, xs);
+      }
       BD_MARK(kPhSpmvRows);
       bd_cluster_sync(cl);
       bd_tiles_reduce(ts, P.ntile, d, zscale, z);
@@ -1445,6 +1455,7 @@ extern "C" int rks_create_batched_dev(rks_dbatch** out, int count, const int64_t
   std::vector<std::vector<int32_t>> tbin(count);
   std::vector<std::vector<uint16_t>> ent(count);
   std::vector<std::vector<float2>> dvals(count), diag(count);
+  std::vector<std::vector<float>> diag32(count);
   std::vector<double> norm1(count, 0.0);
   std::vector<int> ndiag(count, 0);
   std::vector<std::array<int, kBMaxDiag>> doffs(count);
@@ -1468,6 +1479,14 @@ extern "C" int rks_create_batched_dev(rks_dbatch** out, int count, const int64_t
         if (!(norm1[i] > 0.0)) okv[i] = 0;
         doffs[i].fill(0);
         ndiag[i] = build_dia(ni, ldu, rowptr[i], colind[i], dvals[i], doffs[i].data(), diag[i]);
+        // FP32 values (zero low words): the diagonal storage in FP32
+        bool f32 = ndiag[i] > 0;
+        for (int64_t q = 0; q < nnz && f32; ++q) f32 = dvals[i][q].y == 0.f;
+        if (f32) {
+          diag32[i].resize(diag[i].size());
+          for (size_t q = 0; q < diag[i].size(); ++q) diag32[i][q] = diag[i][q].x;
+          diag[i].clear();
+        }
       }
     };
     const int nt = std::max(1, std::min<int>(count, (int)std::thread::hardware_concurrency()));
@@ -1489,7 +1508,7 @@ extern "C" int rks_create_batched_dev(rks_dbatch** out, int count, const int64_t
     const size_t sz[kParts] = {(size_t)(ni + 1) * 4, (size_t)nnz * 4, (size_t)nnz * 8, tbin[i].size() * 4,
                                ent[i].size() * 2, (size_t)ntile * kBR * (m + 1) * 8, (size_t)2 * ntile * d * 8,
                                (size_t)ntile * (k + 1) * 4 * 8, (size_t)ldu * (k + 1) * 8,
-                               ndiag[i] ? diag[i].size() * 8 : 0};
+                               ndiag[i] ? (diag32[i].empty() ? diag[i].size() * 8 : diag32[i].size() * 4) : 0};
     for (int q = 0; q < kParts; ++q) {
       off[(size_t)i * kParts + q] = total;
       total += align_up(sz[q]);
@@ -1537,6 +1556,7 @@ extern "C" int rks_create_batched_dev(rks_dbatch** out, int count, const int64_t
     P.D = ndiag[i];
     for (int e = 0; e < kBMaxDiag; ++e) P.doff[e] = doffs[i][e];
     P.dvals = ndiag[i] ? (const float2*)(base + of[9]) : nullptr;
+    P.dv32 = ndiag[i] && !diag32[i].empty() ? 1 : 0;
     P.out = b->d_out + (size_t)i * out_stride(b);
     P.info = b->d_info + (size_t)i * kBInfo;
     P.norm1 = norm1[i];
@@ -1545,7 +1565,10 @@ extern "C" int rks_create_batched_dev(rks_dbatch** out, int count, const int64_t
         (nnz && cudaMemcpy((void*)P.vals, dvals[i].data(), nnz * 8, cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemcpy((void*)P.tbin, tbin[i].data(), tbin[i].size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy((void*)P.ent, ent[i].data(), ent[i].size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
-        (P.D && cudaMemcpy((void*)P.dvals, diag[i].data(), diag[i].size() * 8, cudaMemcpyHostToDevice) != cudaSuccess))
+        (P.D && !P.dv32 &&
+         cudaMemcpy((void*)P.dvals, diag[i].data(), diag[i].size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (P.D && P.dv32 &&
+         cudaMemcpy((void*)P.dvals, diag32[i].data(), diag32[i].size() * 4, cudaMemcpyHostToDevice) != cudaSuccess))
       return fail(RKS_ECUDA);
   }
   // largest first (cost ~ nnz + n m), ties by index
