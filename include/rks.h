@@ -102,7 +102,7 @@ typedef struct {
                           The sketch sums, the small dense work and the final
                           residuals are FP64 in all three. */
   double mixed_tol;    /* RKS_PREC_MIXED: tolerance of the FP32 phase on the
-                          opts.conv scale; 0: 64 * 2^-24 */
+                          opts.conv scale; 0: 32 * 2^-24 with keep > 0, 64 * 2^-24 with keep = 0 */
   double verify;       /* > 0: after convergence, check the FP64 residuals
                           ||A x - l x|| / (||A||_1 ||x||) <= verify; if one
                           fails, divide tol and eta_lock by 4 and continue the

@@ -233,8 +233,10 @@ int flag_status(int f) {
 void expand_df_launches(rks_ctx* c, int c0) {
   const double n = (double)c->n, P = 8.0, PV = c->f32 ? 4.0 : 8.0;
   // algorithmic bytes of the storage the SpMV reads: CSR/ELLPACK values and
-  // columns (and row pointers), or the D diagonals; x read once, w written
-  const double spmv_bytes = c->A2.dvals ? (double)c->A2.D * PV * n + 2 * PV * n
+  // columns (and row pointers), or the D diagonals (FP32 copies when A's
+  // values are FP32 numbers); x read once, w written
+  const double PA = (c->A2.dvals && c->A2.dvals_f32 && c->A2.D <= 8) ? 4.0 : PV;
+  const double spmv_bytes = c->A2.dvals ? (double)c->A2.D * PA * n + 2 * PV * n
                                         : (double)c->nnz * (PV + 4) + 4.0 * (n + 1) + 2 * PV * n;
   for (int j = c0; j < c->m; ++j) {
     const int col = j + 1;
@@ -266,7 +268,8 @@ void expand_df_launches(rks_ctx* c, int c0) {
 // two passes of (dot products with every basis column, update), and the norm.
 void expand_ks_launches(rks_ctx* c, int c0) {
   const double n = (double)c->n, P = 8.0;
-  const double spmv_bytes = c->A2.dvals ? (double)c->A2.D * P * n + 2 * P * n
+  const double PA = (c->A2.dvals && c->A2.dvals_f32 && c->A2.D <= 8) ? 4.0 : P;
+  const double spmv_bytes = c->A2.dvals ? (double)c->A2.D * PA * n + 2 * P * n
                                         : (double)c->nnz * (P + 4) + 4.0 * (n + 1) + 2 * P * n;
   const int G = c->tiles.G;
   for (int j = c0; j < c->m; ++j) {
@@ -1480,11 +1483,14 @@ static int solve_impl(rks_ctx* c) {
     c->A2.evals = c->ell_valf;
     if (c->dia_d) c->A2.dvals = c->dia_valf;
     c->A2.f32 = true;
-    const double floor32 = c->opts.mixed_tol > 0 ? c->opts.mixed_tol : 64.0 * 5.9604644775390625e-08;
-    c->tol = std::max(tol0, floor32);
-    c->eta_lock = std::max(eta0, 0.5 * floor32);
     const int lock0 = c->opts.lock, aggr0 = c->opts.aggressive;
     const bool carry = c->opts.keep > 0 && c->opts.ortho == RKS_ORTHO_SKETCH;
+    // target of this phase: 32 u_32 when phase 2 continues from it (every
+    // FP32 restart counts), 64 u_32 (just above the FP32 floor) otherwise
+    const double floor32 = c->opts.mixed_tol > 0 ? c->opts.mixed_tol
+                                                 : (carry ? 32.0 : 64.0) * 5.9604644775390625e-08;
+    c->tol = std::max(tol0, floor32);
+    c->eta_lock = std::max(eta0, 0.5 * floor32);
     if (carry) {
       c->opts.lock = 0;
       c->opts.aggressive = 0;
