@@ -383,6 +383,15 @@ def run_ours(args) -> None:
     path = ("spmv_sketch", "ls", "update_sketch", "finish")
     path_bytes = sum(breakdown[c]["bytes"] for c in path)
     path_ms = sum(breakdown[c]["ms"] for c in path)
+    # the same aggregate split by the basis the launches worked on (the mixed
+    # path's FP32 phase and its double-float phase)
+    spmv_rgs_by_basis = {}
+    b32 = sum(breakdown[c]["bytes_f32"] for c in path)
+    m32 = sum(breakdown[c]["ms_f32"] for c in path)
+    for name, b_, m_ in (("fp32", b32, m32), ("df", path_bytes - b32, path_ms - m32)):
+        if m_ > 0 and b_ > 0:
+            g = b_ / (m_ * 1e-3) / 1e9
+            spmv_rgs_by_basis[name] = {"gbs": g, "frac": g / peaks["hbm_gbs"], "ms": m_}
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "peak_source": peaks["source"],
@@ -431,6 +440,7 @@ def run_ours(args) -> None:
             "roofline": roofline,
             "spmv_rgs_gbs": path_bytes / (path_ms * 1e-3) / 1e9 if path_ms else None,
             "spmv_rgs_frac": (path_bytes / (path_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]) if path_ms else None,
+            "spmv_rgs_by_basis": spmv_rgs_by_basis,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(agg["launches_total"]),

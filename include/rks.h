@@ -212,6 +212,9 @@ typedef struct {
                           scale, verify - tol with the FP64 check, tol times
                           the smallest wanted |lambda| / ||A||_1 on the
                           |lambda| scale; otherwise mixed_phase2 = 2) */
+  int64_t launches_f32[RKS_NK];   /* the part of launches, ms and bytes above */
+  double ms_f32[RKS_NK];          /* made with the FP32 basis (RKS_PREC_MIXED's */
+  double bytes_f32[RKS_NK];       /* first phase) */
 } rks_stats;
 
 /* Counters of the last rks_solve (see rks_stats). */

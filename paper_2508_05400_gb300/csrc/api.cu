@@ -179,7 +179,7 @@ int prof_begin(rks_ctx* c, int cls) {
     c->evclass.resize(c->evpool.size() / 2);
   }
   int slot = c->evused++;
-  c->evclass[slot] = cls;
+  c->evclass[slot] = cls + (c->f32 ? RKS_NK : 0);   // FP32-basis launches counted apart as well
   cudaEventRecord(c->evpool[2 * slot], c->stream);
   return slot;
 }
@@ -188,6 +188,10 @@ void prof_end(rks_ctx* c, int slot, int cls, int nlaunch, double bytes, double f
   c->stats.launches[cls] += nlaunch;
   c->stats.bytes[cls] += bytes;
   c->stats.flops[cls] += flops;
+  if (c->f32) {
+    c->stats.launches_f32[cls] += nlaunch;
+    c->stats.bytes_f32[cls] += bytes;
+  }
   if (slot >= 0) cudaEventRecord(c->evpool[2 * slot + 1], c->stream);
 }
 
@@ -195,8 +199,11 @@ void prof_end(rks_ctx* c, int slot, int cls, int nlaunch, double bytes, double f
 void prof_flush(rks_ctx* c) {
   for (int s = 0; s < c->evused; ++s) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->evpool[2 * s], c->evpool[2 * s + 1]) == cudaSuccess)
-      c->stats.ms[c->evclass[s]] += ms;
+    if (cudaEventElapsedTime(&ms, c->evpool[2 * s], c->evpool[2 * s + 1]) == cudaSuccess) {
+      const int cls = c->evclass[s] % RKS_NK;
+      c->stats.ms[cls] += ms;
+      if (c->evclass[s] >= RKS_NK) c->stats.ms_f32[cls] += ms;
+    }
   }
   c->evused = 0;
 }

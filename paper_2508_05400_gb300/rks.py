@@ -57,11 +57,13 @@ class Stats(C.Structure):
     _fields_ = [("launches", C.c_int64 * 6), ("ms", C.c_double * 6), ("bytes", C.c_double * 6),
                 ("flops", C.c_double * 6), ("host_ms", C.c_double), ("whitenings", C.c_int64),
                 ("reorders", C.c_int64), ("fp32_restarts", C.c_int), ("mixed_phase2", C.c_int),
-                ("handover_rel", C.c_double)]
+                ("handover_rel", C.c_double), ("launches_f32", C.c_int64 * 6), ("ms_f32", C.c_double * 6),
+                ("bytes_f32", C.c_double * 6)]
 
     def as_dict(self) -> dict:
         out = {name: {"launches": self.launches[i], "ms": self.ms[i], "bytes": self.bytes[i],
-                      "flops": self.flops[i]} for i, name in enumerate(KCLASSES)}
+                      "flops": self.flops[i], "launches_f32": self.launches_f32[i], "ms_f32": self.ms_f32[i],
+                      "bytes_f32": self.bytes_f32[i]} for i, name in enumerate(KCLASSES)}
         out["host_ms"] = self.host_ms
         out["whitenings"] = self.whitenings
         out["reorders"] = self.reorders
