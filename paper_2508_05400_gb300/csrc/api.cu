@@ -1197,7 +1197,11 @@ static int handover_df(rks_ctx* c, double thr, double* rel) {
   if (!rc) rc = dalloc(&part, (size_t)gj * ka);
   if (!rc) rc = dalloc(&dfw, (size_t)(2 * ka + 1) * ldu);
   auto release = [&]() { cudaFree(work); cudaFree(dinv); cudaFree(part); cudaFree(dfw); };
-  if (rc) { release(); return rc; }
+  if (rc) {
+    release();
+    cudaGetLastError();   // a failed allocation leaves its error for the next launch check
+    return rc;
+  }
   const int ps = prof_begin(c, RKS_K_OTHER);
   rks::launch_f32_to_df_cols(n, c->Uf, ldu, ka + 1, c->U2, c->stream);
   // double-float scratch: U in columns 0 .. ka-1, V = U T in ka .. 2ka-1,
@@ -1551,8 +1555,8 @@ static int solve_impl(rks_ctx* c) {
       if (cont) {
         c->stats.mixed_phase2 = 1;
         rc = run_alg1(c, nullptr, std::max(1, limit - c->restarts), c->opts.verify, 60, &converged, true);
-      } else if (h != RKS_EINVAL && h != RKS_EDENSE) {
-        rc = h;
+      } else if (h != RKS_EINVAL && h != RKS_EDENSE && h != RKS_ENOMEM) {
+        rc = h;                          // a CUDA error; the others fall back below
       }
       // a fresh double-float phase: without the hand-over (at least one
       // restart, as a partial result must be a double-float decomposition),
