@@ -54,11 +54,12 @@ NCU_TRAFFIC = {
     # third restart of the 1000^2 workload: 541.6 / 547.1 MB against 528 /
     # 536 MB; the bin lists of Omega are the rest)
     ("update_sketch", "df", "convdiff2d_1000"): {"kernels_sha": "fdc1ba79cef500a9", "ratio": 1.023},
-    # k_df_update_sketch<float> of the 160^3 operator at 100^3 (FP32 phase, c ~ 41, first expansion;
-    # profiles/update_spmv_ls_convdiff3d_100_mixed.md): DRAM 189.1 MB against 172 MB of algorithmic
-    # bytes.  Applied to the mean launch of the 160^3 solve (c ~ 100, FP32 and double-float launches),
-    # where the bin lists' share of the traffic is smaller: an upper estimate by a few percent.
-    ("update_sketch", "mixed", "convdiff3d_160"): {"kernels_sha": "fdc1ba79cef500a9", "ratio": 1.10},
+    # k_df_update_sketch<float, 20> of the 160^3 operator at 100^3 (FP32 phase, c = 61, first
+    # expansion; profiles/update_spmv_ls_convdiff3d_100_mixed.md): DRAM 275.9 MB (4.01 TB/s over
+    # 68.9 us) against 252 MB of algorithmic bytes.  Applied to the mean launch of the 160^3 solve
+    # (c ~ 100, FP32 and double-float launches), where the bin lists' share of the traffic is
+    # smaller: an upper estimate by a few percent.
+    ("update_sketch", "mixed", "convdiff3d_160"): {"kernels_sha": "03fc6acf03ac0121", "ratio": 1.095},
 }
 
 
