@@ -74,6 +74,26 @@ __device__ __forceinline__ void df_add(float bh, float bl, float& s, float& t) {
   t += e2 + bl;
 }
 
+// (s, t) += a * b for values stored as TA and TB: an FP32 value has no low
+// word, so its terms are left out (df_mac's operations otherwise, in its
+// order; the sums differ from df_mac's at most in the sign of a zero)
+template <class TA, class TB>
+__device__ __forceinline__ void mac_st(float2 a, float2 b, float& s, float& t) {
+  constexpr bool A1 = sizeof(TA) == 4, B1 = sizeof(TB) == 4;
+  if constexpr (!A1 && !B1) {
+    df_mac(a.x, a.y, b.x, b.y, s, t);
+  } else {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    if constexpr (!B1) e = fmaf(a.x, b.y, e);
+    if constexpr (!A1) e = fmaf(a.y, b.x, e);
+    float s2, e2;
+    two_sum(s, p, s2, e2);
+    s = s2;
+    t += e2 + e;
+  }
+}
+
 __device__ __forceinline__ float2 df_norm(float s, float t) {
   float h, l;
   fast_two_sum(s, t, h, l);
@@ -262,11 +282,20 @@ __global__ void __launch_bounds__(256) k_tiles_build(const int64_t* __restrict__
   }
 }
 
-// (s, e) += sign * vals[row] for one bin-list entry
+// (s, e) += sign * vals[row] for one bin-list entry; LO = false: the tile
+// holds FP32 values (zero low words), whose low words are left out
+template <bool LO>
 __device__ __forceinline__ void tile_add(uint32_t x, const float2* vals, float& s, float& e) {
   const float2 v = vals[x & 0x7FFFu];
   const uint32_t sg = (x & 0x8000u) << 16;
-  df_add(__uint_as_float(__float_as_uint(v.x) ^ sg), __uint_as_float(__float_as_uint(v.y) ^ sg), s, e);
+  if (LO) {
+    df_add(__uint_as_float(__float_as_uint(v.x) ^ sg), __uint_as_float(__float_as_uint(v.y) ^ sg), s, e);
+  } else {
+    float s2, e2;
+    two_sum(s, __uint_as_float(__float_as_uint(v.x) ^ sg), s2, e2);
+    s = s2;
+    e += e2;
+  }
 }
 
 // Sketch of one staged tile: acc[row] += sum over the row's bin list of
@@ -275,6 +304,7 @@ __device__ __forceinline__ void tile_add(uint32_t x, const float2* vals, float& 
 // H adjacent lanes share a position (each takes every H-th entry) when d is
 // small; their sums are combined by a fixed xor tree.  A sketch row has one
 // position per tile, so acc[row] has one writer per tile.
+template <bool LO>
 __device__ __forceinline__ void tile_gather(int d, int H, const float2* vals, const int* offs, const uint32_t* ms,
                                             const uint16_t* es, float2* acc) {
   const int total = d * H;
@@ -292,12 +322,12 @@ __device__ __forceinline__ void tile_gather(int d, int H, const float2* vals, co
       for (; q + 3 * H < cnt; q += 4 * H) {
         const uint32_t x0 = es[offs[q] + p], x1 = es[offs[q + H] + p];
         const uint32_t x2 = es[offs[q + 2 * H] + p], x3 = es[offs[q + 3 * H] + p];
-        tile_add(x0, vals, s, e);
-        tile_add(x1, vals, s, e);
-        tile_add(x2, vals, s, e);
-        tile_add(x3, vals, s, e);
+        tile_add<LO>(x0, vals, s, e);
+        tile_add<LO>(x1, vals, s, e);
+        tile_add<LO>(x2, vals, s, e);
+        tile_add<LO>(x3, vals, s, e);
       }
-      for (; q < cnt; q += H) tile_add(es[offs[q] + p], vals, s, e);
+      for (; q < cnt; q += H) tile_add<LO>(es[offs[q] + p], vals, s, e);
     }
     for (int o = 1; o < H; o <<= 1) {
       const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
@@ -470,15 +500,15 @@ __global__ void __launch_bounds__(512) k_df_spmv_sketch(
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (ca[u] >= 0) df_mac(va[u].x, va[u].y, xa[u].x, xa[u].y, sa, ta);
-        if (cb[u] >= 0) df_mac(vbv[u].x, vbv[u].y, xb[u].x, xb[u].y, sb, tb);
+        if (ca[u] >= 0) mac_st<TA, TU>(va[u], xa[u], sa, ta);
+        if (cb[u] >= 0) mac_st<TA, TU>(vbv[u], xb[u], sb, tb);
       }
     }
     if (la < rows) v[la] = stv(w + r0 + la, df_norm(sa, ta));
     if (lb < rows) v[lb] = stv(w + r0 + lb, df_norm(sb, tb));
     if (SK) {
       __syncthreads();
-      tile_gather(d, tv.H, v, of, ms, es, acc);
+      tile_gather<sizeof(TU) == 8>(d, tv.H, v, of, ms, es, acc);
     }
   }
   if (SK) tile_write_part(acc, d, part);
@@ -533,8 +563,8 @@ __global__ void __launch_bounds__(512) k_df_spmv_ell(
       for (int e = 0; e < R1; ++e) {
         const float2 xa = ca[e] >= 0 ? ldv(x + ca[e]) : make_float2(0.f, 0.f);
         const float2 xb = cb[e] >= 0 ? ldv(x + cb[e]) : make_float2(0.f, 0.f);
-        if (ca[e] >= 0) df_mac(va[e].x, va[e].y, xa.x, xa.y, sa, ta);
-        if (cb[e] >= 0) df_mac(vbv[e].x, vbv[e].y, xb.x, xb.y, sb, tb);
+        if (ca[e] >= 0) mac_st<TA, TU>(va[e], xa, sa, ta);
+        if (cb[e] >= 0) mac_st<TA, TU>(vbv[e], xb, sb, tb);
       }
     }
     constexpr int RU = 4;                         // rounds of four entries
@@ -557,15 +587,15 @@ __global__ void __launch_bounds__(512) k_df_spmv_ell(
       }
 #pragma unroll
       for (int u = 0; u < RU; ++u) {
-        if (ca[u] >= 0) df_mac(va[u].x, va[u].y, xa[u].x, xa[u].y, sa, ta);
-        if (cb[u] >= 0) df_mac(vbv[u].x, vbv[u].y, xb[u].x, xb[u].y, sb, tb);
+        if (ca[u] >= 0) mac_st<TA, TU>(va[u], xa[u], sa, ta);
+        if (cb[u] >= 0) mac_st<TA, TU>(vbv[u], xb[u], sb, tb);
       }
     }
     if (oka) v[la] = stv(w + ia, df_norm(sa, ta));
     if (okb) v[lb] = stv(w + ib, df_norm(sb, tb));
     if (SK) {
       __syncthreads();
-      tile_gather(d, tv.H, v, of, ms, es, acc);
+      tile_gather<sizeof(TU) == 8>(d, tv.H, v, of, ms, es, acc);
     }
   }
   if (SK) tile_write_part(acc, d, part);
@@ -605,7 +635,7 @@ __global__ void __launch_bounds__(512) k_df_spmv_warp(const int32_t* __restrict_
         const int p0 = rowptr[r0 + l], p1 = rowptr[r0 + l + 1];
         for (int p = p0 + lane; p < p1; p += LPR) {
           const float2 a = ldv(vals + p), xv = ldv(x + colind[p]);
-          df_mac(a.x, a.y, xv.x, xv.y, sh, sl);
+          mac_st<TA, TU>(a, xv, sh, sl);
         }
       }
 #pragma unroll
@@ -621,7 +651,7 @@ __global__ void __launch_bounds__(512) k_df_spmv_warp(const int32_t* __restrict_
     }
     if (SK) {
       __syncthreads();
-      tile_gather(d, tv.H, v, of, ms, es, acc);
+      tile_gather<sizeof(TU) == 8>(d, tv.H, v, of, ms, es, acc);
     }
   }
   if (SK) tile_write_part(acc, d, part);
@@ -913,8 +943,8 @@ __global__ void __launch_bounds__(512, 2) k_df_spmv_dia(const DiaOffs offs, int 
 #pragma unroll
         for (int u = 0; u < RU; ++u) {
           if (e0 + u < D) {
-            df_mac(va[u].x, va[u].y, xa[u].x, xa[u].y, sa, ta);
-            df_mac(vb[u].x, vb[u].y, xb[u].x, xb[u].y, sb, tb);
+            mac_st<TA, TU>(va[u], xa[u], sa, ta);
+            mac_st<TA, TU>(vb[u], xb[u], sb, tb);
           }
         }
       }
@@ -935,8 +965,8 @@ __global__ void __launch_bounds__(512, 2) k_df_spmv_dia(const DiaOffs offs, int 
 #pragma unroll
         for (int u = 0; u < RU; ++u) {
           if (e0 + u < D) {
-            df_mac(va[u].x, va[u].y, xa[u].x, xa[u].y, sa, ta);
-            df_mac(vb[u].x, vb[u].y, xb[u].x, xb[u].y, sb, tb);
+            mac_st<TA, TU>(va[u], xa[u], sa, ta);
+            mac_st<TA, TU>(vb[u], xb[u], sb, tb);
           }
         }
       }
@@ -945,7 +975,7 @@ __global__ void __launch_bounds__(512, 2) k_df_spmv_dia(const DiaOffs offs, int 
     if (okb) v[lb] = stv(w + ib, df_norm(sb, tb));
     if (SK) {
       __syncthreads();
-      tile_gather(d, tv.H, v, of, ms, es, acc);
+      tile_gather<sizeof(TU) == 8>(d, tv.H, v, of, ms, es, acc);
     }
   }
   if (SK) tile_write_part(acc, d, part);
@@ -1038,8 +1068,8 @@ __global__ void __launch_bounds__(512, MINB) k_df_update_sketch(
       {
         float2 w0, w1;
         ld2(U + i + (int64_t)c * ldu, w0, w1);
-        df_mac(w0.x, w0.y, sc.x, sc.y, s0, t0a);
-        df_mac(w1.x, w1.y, sc.x, sc.y, s1, t1a);
+        mac_st<TU, float2>(w0, sc, s0, t0a);
+        mac_st<TU, float2>(w1, sc, s1, t1a);
       }
       const TU* up = U + i;
       int col = 0;
@@ -1050,16 +1080,16 @@ __global__ void __launch_bounds__(512, MINB) k_df_update_sketch(
 #pragma unroll
         for (int q = 0; q < UNR; ++q) {
           const float2 r = rsh[col + q];
-          df_mac(a[q].x, a[q].y, r.x, r.y, s0, t0a);
-          df_mac(bb[q].x, bb[q].y, r.x, r.y, s1, t1a);
+          mac_st<TU, float2>(a[q], r, s0, t0a);
+          mac_st<TU, float2>(bb[q], r, s1, t1a);
         }
       }
       for (; col < c; ++col) {
         float2 a, bb;
         ld2(up + (int64_t)col * ldu, a, bb);
         const float2 r = rsh[col];
-        df_mac(a.x, a.y, r.x, r.y, s0, t0a);
-        df_mac(bb.x, bb.y, r.x, r.y, s1, t1a);
+        mac_st<TU, float2>(a, r, s0, t0a);
+        mac_st<TU, float2>(bb, r, s1, t1a);
       }
       const float2 v0 = stv(U + i + (int64_t)c * ldu, df_norm(s0, t0a));
       v[l] = v0;
@@ -1072,7 +1102,7 @@ __global__ void __launch_bounds__(512, MINB) k_df_update_sketch(
     }
     if (SK) {
       __syncthreads();
-      tile_gather(d, tv.H, v, of, ms, es, acc);
+      tile_gather<sizeof(TU) == 8>(d, tv.H, v, of, ms, es, acc);
     }
   }
   if (SK) tile_write_part(acc, d, part);
@@ -1601,7 +1631,7 @@ __global__ void __launch_bounds__(512) k_df_sketch_vec(const TU* __restrict__ x,
     tile_stage(tv, t, r0, rows, of, ms, es);
     for (int l = threadIdx.x; l < rows; l += blockDim.x) v[l] = ldv(x + r0 + l);
     __syncthreads();
-    tile_gather(d, tv.H, v, of, ms, es, acc);
+    tile_gather<sizeof(TU) == 8>(d, tv.H, v, of, ms, es, acc);
   }
   tile_write_part(acc, d, part);
 }
