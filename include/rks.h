@@ -643,6 +643,17 @@ int rks_host_reorder_select(int n, double* T, const int* select, double* Z);
  * arrays (column j = eigenvector j).  Host only. */
 int rks_host_quasi_eig(int n, const double* T, double* lam_re, double* lam_im, double* Y_re, double* Y_im);
 
+/* Re-orthonormalisation of a drifted Krylov-Schur decomposition in the
+ * sketch (the mixed path's hand-over to double-float; the whitening of
+ * Sec. 3.3 with the last vector): A U = U T + u b^T with U of ka columns,
+ * S = [Omega U, Omega u] (d x (ka+1), column-major, host, overwritten by Q of
+ * S = Q R).  Returns Rinv = R^-1 ((ka+1) x (ka+1)) and the decomposition of
+ * [V v] = [U u] R^-1: A V = V Tn + v bn^T, Tn = (R11 T + r12 b^T) R11^-1
+ * (ka x ka), bn^T = r22 b^T R11^-1 (ka).  T: ka x ka, b: ka; all host.
+ * Returns RKS_OK, RKS_EINVAL, or RKS_EDENSE if R is singular.  Host only. */
+int rks_host_sketch_reorthonormalize(int d, int ka, double* S, const double* T, const double* b, double* Rinv,
+                                     double* Tn, double* bn);
+
 /* The device dense step of the persistent batched solver on one matrix
  * (test entry point): B (m x m, host, m <= 64) -> real Schur form T = Q^T B Q
  * whose leading blocks are the best blocks for `which` covering nsort

@@ -1289,35 +1289,10 @@ static int handover_df(rks_ctx* c, double thr, double* rel) {
     if (!(du <= 1e-6 * nu)) return RKS_EINVAL;   // not the decomposition the FP32 phase left
   }
   const int kb = ka + 1;
-  std::vector<double> R((size_t)kb * kb), Rinv((size_t)kb * kb, 0.0);
-  rks_dense::house_qr(d, kb, Sall.data(), R.data());
-  for (int j = 0; j < kb; ++j) {
-    if (R[j + (size_t)j * kb] == 0.0) return RKS_EINVAL;
-    Rinv[j + (size_t)j * kb] = 1.0 / R[j + (size_t)j * kb];
-    for (int i = j - 1; i >= 0; --i) {
-      double acc = 0.0;
-      for (int l = i + 1; l <= j; ++l) acc += R[i + (size_t)l * kb] * Rinv[l + (size_t)j * kb];
-      Rinv[i + (size_t)j * kb] = -acc / R[i + (size_t)i * kb];
-    }
-  }
-  // T' = (R11 T + r12 b^T) R11^-1, b'^T = r22 b^T R11^-1
-  std::vector<double> P((size_t)ka * ka, 0.0), Tn((size_t)ka * ka, 0.0), bn(ka, 0.0);
-  for (int j = 0; j < ka; ++j)
-    for (int i = 0; i < ka; ++i) {
-      double acc = R[i + (size_t)ka * kb] * b[j];
-      for (int l = i; l < ka; ++l) acc += R[i + (size_t)l * kb] * T[l + (size_t)j * ka];
-      P[i + (size_t)j * ka] = acc;
-    }
-  for (int j = 0; j < ka; ++j) {
-    for (int i = 0; i < ka; ++i) {
-      double acc = 0.0;
-      for (int l = 0; l <= j; ++l) acc += P[i + (size_t)l * ka] * Rinv[l + (size_t)j * kb];
-      Tn[i + (size_t)j * ka] = acc;
-    }
-    double acc = 0.0;
-    for (int l = 0; l <= j; ++l) acc += b[l] * Rinv[l + (size_t)j * kb];
-    bn[j] = R[ka + (size_t)ka * kb] * acc;
-  }
+  std::vector<double> Rinv((size_t)kb * kb), Tn((size_t)ka * ka), bn(ka);
+  if (rks_dense::sketch_reorthonormalize(d, ka, Sall.data(), T.data(), b.data(), Rinv.data(), Tn.data(),
+                                         bn.data()) != 0)
+    return RKS_EINVAL;
   // [V v] = [U u] diag(cs) R^-1 in place
   rc = restart_launch(c, 0, kb, Rinv, c->cs_h.data(), kb, -1);
   if (rc) return rc;
@@ -1756,6 +1731,12 @@ int rks_host_reorder_select(int n, double* T, const int* select, double* Z) {
   std::vector<char> sel(bl.size());
   for (size_t t = 0; t < bl.size(); ++t) sel[t] = select[bl[t].start] != 0;
   return rks_dense::reorder_select(n, T, n, Z, n, n, sel) == 0 ? RKS_OK : RKS_EDENSE;
+}
+
+int rks_host_sketch_reorthonormalize(int d, int ka, double* S, const double* T, const double* b, double* Rinv,
+                                     double* Tn, double* bn) {
+  if (d < 1 || ka < 1 || ka + 1 > d || !S || !T || !b || !Rinv || !Tn || !bn) return RKS_EINVAL;
+  return rks_dense::sketch_reorthonormalize(d, ka, S, T, b, Rinv, Tn, bn) == 0 ? RKS_OK : RKS_EDENSE;
 }
 
 int rks_host_quasi_eig(int n, const double* T, double* lam_re, double* lam_im, double* Y_re, double* Y_im) {

@@ -554,6 +554,43 @@ int reorder_select(int n, double* T, int ldt, double* Z, int ldz, int nz, const 
   return 0;
 }
 
+int sketch_reorthonormalize(int d, int ka, double* S, const double* T, const double* b, double* Rinv, double* Tn,
+                            double* bn) {
+  const int kb = ka + 1;
+  std::vector<double> R((size_t)kb * kb);
+  house_qr(d, kb, S, R.data());
+  for (int j = 0; j < kb; ++j)
+    for (int i = 0; i < kb; ++i) Rinv[i + (size_t)j * kb] = 0.0;
+  for (int j = 0; j < kb; ++j) {          // R^-1 by back substitution
+    if (R[j + (size_t)j * kb] == 0.0) return -1;
+    Rinv[j + (size_t)j * kb] = 1.0 / R[j + (size_t)j * kb];
+    for (int i = j - 1; i >= 0; --i) {
+      double acc = 0.0;
+      for (int l = i + 1; l <= j; ++l) acc += R[i + (size_t)l * kb] * Rinv[l + (size_t)j * kb];
+      Rinv[i + (size_t)j * kb] = -acc / R[i + (size_t)i * kb];
+    }
+  }
+  // P = R11 T + r12 b^T, Tn = P R11^-1 (R11^-1 is the leading block of R^-1)
+  std::vector<double> P((size_t)ka * ka);
+  for (int j = 0; j < ka; ++j)
+    for (int i = 0; i < ka; ++i) {
+      double acc = R[i + (size_t)ka * kb] * b[j];
+      for (int l = i; l < ka; ++l) acc += R[i + (size_t)l * kb] * T[l + (size_t)j * ka];
+      P[i + (size_t)j * ka] = acc;
+    }
+  for (int j = 0; j < ka; ++j) {
+    for (int i = 0; i < ka; ++i) {
+      double acc = 0.0;
+      for (int l = 0; l <= j; ++l) acc += P[i + (size_t)l * ka] * Rinv[l + (size_t)j * kb];
+      Tn[i + (size_t)j * ka] = acc;
+    }
+    double acc = 0.0;
+    for (int l = 0; l <= j; ++l) acc += b[l] * Rinv[l + (size_t)j * kb];
+    bn[j] = R[ka + (size_t)ka * kb] * acc;
+  }
+  return 0;
+}
+
 void house_qr(int d, int ka, double* S, double* R) {
   std::vector<double> V((size_t)d * ka, 0.0), beta(ka, 0.0);
   std::vector<double> A(S, S + (size_t)d * ka);

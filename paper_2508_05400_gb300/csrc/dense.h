@@ -38,6 +38,14 @@ int reorder_select(int n, double* T, int ldt, double* Z, int ldz, int nz, const 
 // Householder QR of the d x ka matrix S (column-major, ld d): R (ka x ka,
 // upper triangular, positive diagonal); S is overwritten by the explicit Q.
 void house_qr(int d, int ka, double* S, double* R);
+// A Krylov-Schur decomposition A U = U T + u b^T (U: ka columns) whose basis
+// [U u] has drifted from sketch-orthonormality: S (d x (ka+1), column-major,
+// in: [Omega U, Omega u], out: Q) -> R from S = Q R, Rinv = R^-1 ((ka+1)^2),
+// and the decomposition of [V v] = [U u] R^-1, A V = V Tn + v bn^T with
+// Tn = (R11 T + r12 b^T) R11^-1 and bn^T = r22 b^T R11^-1 (Tn: ka x ka, bn:
+// ka).  Returns 0, or -1 if R is singular (outputs undefined).
+int sketch_reorthonormalize(int d, int ka, double* S, const double* T, const double* b, double* Rinv, double* Tn,
+                            double* bn);
 // Eigenvalues and unit 2-norm eigenvectors of a quasi-triangular T; a 2x2
 // block at (i, i+1) gives columns i (Im > 0) and i+1 (its conjugate).
 int quasi_eig(int n, const double* T, int ldt, double* lam_re, double* lam_im,

@@ -200,6 +200,8 @@ def lib() -> C.CDLL:
         L.rks_host_reorder_select.restype = C.c_int
         L.rks_host_quasi_eig.argtypes = [C.c_int, _P, _P, _P, _P, _P]
         L.rks_host_quasi_eig.restype = C.c_int
+        L.rks_host_sketch_reorthonormalize.argtypes = [C.c_int, C.c_int, _P, _P, _P, _P, _P, _P]
+        L.rks_host_sketch_reorthonormalize.restype = C.c_int
         _lib = L
     return _lib
 
@@ -523,6 +525,20 @@ def host_reorder_select(T: np.ndarray, select):
     _check(lib().rks_host_reorder_select(n, Tf.ctypes.data, sel.ctypes.data, Z.ctypes.data),
            "rks_host_reorder_select")
     return Tf, Z
+
+
+def host_sketch_reorthonormalize(S: np.ndarray, T: np.ndarray, b: np.ndarray):
+    """(Q, Rinv, Tn, bn) of rks_host_sketch_reorthonormalize for S = [Omega U, Omega u]."""
+    d, kb = S.shape
+    ka = kb - 1
+    Sf = np.asfortranarray(S, dtype=np.float64).copy(order="F")
+    Tf = np.asfortranarray(T, dtype=np.float64)
+    bf = np.ascontiguousarray(b, dtype=np.float64)
+    Rinv, Tn, bn = _fortran((kb, kb)), _fortran((ka, ka)), np.zeros(ka)
+    _check(lib().rks_host_sketch_reorthonormalize(d, ka, Sf.ctypes.data, Tf.ctypes.data, bf.ctypes.data,
+                                                  Rinv.ctypes.data, Tn.ctypes.data, bn.ctypes.data),
+           "rks_host_sketch_reorthonormalize")
+    return Sf, Rinv, Tn, bn
 
 
 def host_quasi_eig(T: np.ndarray):

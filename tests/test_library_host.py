@@ -101,6 +101,41 @@ def test_host_quasi_eig_matches_scipy(lib):
             assert np.isclose(lam[j + 1], lam[j].conj())
 
 
+@pytest.mark.parametrize("ka,drift", [(8, 1e-7), (20, 1e-3), (1, 0.3)])
+def test_host_sketch_reorthonormalize_keeps_the_decomposition(lib, ka, drift):
+    # A built so that A U = U T + u b^T holds exactly for a basis [U u] that
+    # is only nearly orthonormal under a sketch Omega (as after the mixed
+    # path's correction): [V v] = [U u] R^-1 must satisfy A V = V Tn + v bn^T
+    # and have orthonormal sketches Q = Omega [V v]
+    rng = np.random.default_rng(40 + ka)
+    n, d = 300, 4 * ka + 20
+    Om = rng.standard_normal((d, n)) / np.sqrt(d)
+    W = np.linalg.qr(rng.standard_normal((n, ka + 1)))[0]
+    # sketch-orthonormal start, then a drift of relative size `drift`
+    Qs, Rs = np.linalg.qr(Om @ W)
+    W = W @ np.linalg.inv(Rs)
+    W = W + drift * rng.standard_normal(W.shape) * np.linalg.norm(W, axis=0) / np.sqrt(n)
+    U, u = W[:, :ka], W[:, ka]
+    T = np.triu(rng.standard_normal((ka, ka))) + np.diag(rng.uniform(1, 2, ka))
+    b = rng.standard_normal(ka)
+    Up = np.linalg.pinv(U)
+    A = (U @ T + np.outer(u, b)) @ Up + rng.standard_normal((n, n)) @ (np.eye(n) - U @ Up)
+    assert np.linalg.norm(A @ U - U @ T - np.outer(u, b)) <= 1e-9 * np.linalg.norm(A @ U)
+    S = Om @ W
+    Q, Rinv, Tn, bn = K.host_sketch_reorthonormalize(S, T, b)
+    Vv = W @ Rinv
+    V, v = Vv[:, :ka], Vv[:, ka]
+    assert np.allclose(Rinv, np.triu(Rinv))
+    assert np.linalg.norm(Q.T @ Q - np.eye(ka + 1)) <= 1e-12 * (ka + 1)
+    assert np.linalg.norm(Om @ Vv - Q) <= 1e-10 * np.linalg.norm(Q)
+    rel = A @ V - V @ Tn - np.outer(v, bn)
+    assert np.linalg.norm(rel) <= 1e-9 * np.linalg.norm(A @ V)
+    # the eigenvalues of T are those of Tn (a similarity of the projected part)
+    assert np.allclose(np.sort_complex(np.linalg.eigvals(Tn + np.outer(
+        np.linalg.lstsq(V, v, rcond=None)[0], bn))), np.sort_complex(np.linalg.eigvals(
+        T + np.outer(np.linalg.lstsq(U, u, rcond=None)[0], b))), atol=1e-7 * np.linalg.norm(T))
+
+
 def test_host_reorder_select_matches_lapack_dtrsen(lib):
     # The aggressive-deflation reorder (Sec. 4.3): flagged blocks first, both
     # groups in their original order, as LAPACK dtrsen orders them.  Same
